@@ -1,0 +1,176 @@
+/*
+ * coffee.h — C ABI of the GB300 finite-element local-assembly library (libcoffee.so).
+ *
+ * The operation is local assembly as structured in Luporini et al., "COFFEE: an
+ * Optimizing Compiler for Finite Element Local Assembly" (arXiv:1407.0904),
+ * section 2 ("Structure of a local assembly kernel"; Listings 1 and 2): for every
+ * mesh cell, (1) the affine Jacobian J, its determinant and inverse K are computed
+ * from the cell's vertex coordinates, (2) basis functions are tabulated at
+ * quadrature points on the reference cell, and (3) the element matrix is
+ * evaluated by a quadrature loop nest A[j][k] += integrand * det * W[i].
+ * Section 3.3 (the outer-product equation) observes that the j-k nest is a sum of
+ * outer products; this library pre-sums the quadrature loop into fixed reference
+ * tensors T[k][i*n+j] and evaluates A_e = sum_k G_e[k] T[k] as a batched dense
+ * contraction over cells (section 5.9 reduces Helmholtz to a few matrix products in
+ * the same spirit, one cell at a time).
+ *
+ * Conventions (the paper leaves them open):
+ *  - reference cells: triangle (0,0),(1,0),(0,1); tetrahedron (0,0,0),(1,0,0),
+ *    (0,1,0),(0,0,1);
+ *  - geometry (pinned by Listing 1): J[r][c] = x_{c+1}[r] - x_0[r], x = x_0 + J xi,
+ *    K = J^{-1}, dphi/dx_c = sum_a K[a][c] dphi/dxi_a; the measure is |det J|;
+ *  - degree-k Lagrange nodes: lattice points (a,b,c)/k with a+b+c <= k, ordered with
+ *    c slowest, then b, then a fastest (degree 1: the vertex order);
+ *  - element matrices are [ncells][ndof][ndof] row-major; row = test function,
+ *    column = trial function;
+ *  - vector-valued (Burgers) dofs are blocked by component: I = c*ns + i.
+ *
+ * Forms (section 5.2 names Helmholtz, advection-diffusion and Burgers):
+ *  MASS        A[i][j] = int phi_i phi_j
+ *  HELMHOLTZ   A[i][j] = int grad phi_i . grad phi_j + phi_i phi_j          (Listing 1)
+ *  ADVDIFF     A[i][j] = int eps grad phi_i . grad phi_j + phi_i (b . grad phi_j),
+ *              eps (scalar) and b (vector) are P1 fields given per coefficient node
+ *  BURGERS_JAC A[(ci,i),(cj,j)] = int phi_i phi_j d_cj u_ci
+ *                               + [ci==cj] (phi_i (u . grad phi_j) + nu grad phi_i . grad phi_j),
+ *              the Jacobian of int (u.grad u).v + nu grad u : grad v for the vector
+ *              degree-k field u (Listing 2 is its degree-1 instance)
+ *
+ * Ownership: the caller owns every buffer it passes. The library owns only its
+ * device cache of reference tensors (created on first use per device, guarded by a
+ * mutex, kept until process exit) and batch plans (freed by coffee_batch_free).
+ *
+ * Errors: every entry point returns a coffee_status. Argument errors are detected
+ * on the host before any launch; the message of the last error on the calling
+ * thread is returned by coffee_last_error(). Launches are asynchronous on the given
+ * stream (NULL = legacy default stream); errors raised while a kernel runs are
+ * reported by coffee_check_errors(). No entry point traps on the device.
+ */
+#ifndef COFFEE_H
+#define COFFEE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t (struct CUstream_st*), declared without CUDA headers. */
+typedef struct CUstream_st* coffee_stream_t;
+
+typedef enum { COFFEE_TRIANGLE = 0, COFFEE_TETRAHEDRON = 1 } coffee_cell;
+
+typedef enum {
+  COFFEE_MASS = 0,
+  COFFEE_HELMHOLTZ = 1,
+  COFFEE_ADVDIFF = 2,
+  COFFEE_BURGERS_JAC = 3
+} coffee_form;
+
+/* Arithmetic of the contraction.  FP64: CUDA-core FP64, double output.
+ * TF32 / BF16: one tensor-core pass (FP32 accumulate, float output).
+ * TF32X3 / BF16X3: operands split x = hi + lo, products hi*hi + hi*lo + lo*hi
+ * accumulated in FP32 on the tensor cores, float output. */
+typedef enum {
+  COFFEE_FP64 = 0,
+  COFFEE_TF32 = 1,
+  COFFEE_TF32X3 = 2,
+  COFFEE_BF16 = 3,
+  COFFEE_BF16X3 = 4
+} coffee_precision;
+
+typedef enum {
+  COFFEE_OK = 0,
+  COFFEE_ERR_INVALID_ARG = -1,
+  COFFEE_ERR_UNSUPPORTED = -2,
+  COFFEE_ERR_CUDA = -3,
+  COFFEE_ERR_DEVICE_INDEX = -4,
+  COFFEE_ERR_NOMEM = -5,
+  COFFEE_ERR_TIMEOUT = -6
+} coffee_status;
+
+/* Flags of coffee_assemble_args.flags */
+#define COFFEE_FLAG_VALIDATE 1u /* range-check cell2vert/cell2dof on the device */
+
+/* Number of rows of the element matrix: (k+1)(k+2)/2 (triangle) or
+ * (k+1)(k+2)(k+3)/6 (tetrahedron), times d for BURGERS_JAC. Negative on error. */
+int coffee_ndof(int form, int degree, int cell);
+
+/* Reference-element tabulation (section 2, step 2: the static basis tables W, X_D10,
+ * X_D01, Y of Listing 1). Host-only, FP64, no CUDA call.
+ * Fills a quadrature rule on the reference cell exact for polynomials of degree
+ * `quad_degree` (collapsed Gauss-Jacobi product rule) and the degree-`degree`
+ * Lagrange basis at its points:
+ *   points  [nq][d], weights [nq], basis [nq][ndof], grads [nq][ndof][d]
+ *   (grads are derivatives with respect to the reference coordinates).
+ * Any output pointer may be NULL; call first with all NULL to query *nq and *ndof.
+ * degree 1..6, quad_degree 0..30. */
+int coffee_tabulate(int cell, int degree, int quad_degree, int* nq, int* ndof,
+                    double* points, double* weights, double* basis, double* grads);
+
+/* Reference tensors of a form (host-only, FP64): T [K][N] with N = ns*ns, where the
+ * element matrix (or, for BURGERS_JAC, each of its d*d component blocks) is
+ * sum_k G_e[k] T[k] for per-cell geometry/coefficient factors G_e.
+ * Pass T = NULL to query *K and *N. */
+int coffee_reference_tensor(int form, int degree, int cell, int* K, int* N, double* T);
+
+/* FP64 local assembly (plain one-thread-per-cell kernel), all pointers on the device:
+ *   coords    [nverts][d] double
+ *   cell2vert [ncells][d+1] int32
+ *   coef      ADVDIFF: [eps (ncoefnodes) | b (ncoefnodes*d, node-major)] double
+ *             BURGERS_JAC: u [ncoefnodes][d] double (viscosity nu = 0.01)
+ *             MASS/HELMHOLTZ: NULL
+ *   cell2dof  ADVDIFF: [ncells][d+1]; BURGERS_JAC: [ncells][ns]; else NULL
+ *   out       [ncells][ndof][ndof] double
+ * ncoefnodes is not passed here and is taken as unbounded (no validation);
+ * coffee_assemble_ex takes the full argument set. ncells == 0 is a no-op.
+ * Asynchronous on `stream`; allocates nothing but the first-use table cache. */
+int coffee_assemble(int form, int degree, int cell, const double* coords,
+                    const int32_t* cell2vert, const double* coef, const int32_t* cell2dof,
+                    void* out, int64_t ncells, coffee_stream_t stream);
+
+typedef struct {
+  int form;            /* coffee_form */
+  int degree;          /* 1..4 */
+  int cell;            /* coffee_cell */
+  int precision;       /* coffee_precision; FP64 -> double out, else float out */
+  double nu;           /* BURGERS_JAC viscosity (0.01 in the benchmarks) */
+  const double* coords;      /* device [nverts][d] */
+  int64_t nverts;
+  const int32_t* cell2vert;  /* device [ncells][d+1] */
+  const double* coef;        /* device, layout as in coffee_assemble, or NULL */
+  int64_t ncoefnodes;
+  const int32_t* cell2dof;   /* device, or NULL */
+  void* out;                 /* device [ncells][ndof][ndof], double or float */
+  int64_t ncells;
+  unsigned flags;            /* COFFEE_FLAG_* */
+} coffee_assemble_args;
+
+/* Local assembly with a chosen precision. FP64 runs the plain FP64 kernel; the
+ * other precisions run the tcgen05 tensor-core contraction with geometry fused into
+ * its producer warps (FP32 geometry, FP64 for ill-conditioned cells).
+ * Returns COFFEE_ERR_UNSUPPORTED for combinations without a kernel. */
+int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream);
+
+/* Adjoint of local assembly (new; the paper has no backward pass).
+ * Given dout = dL/dA ([ncells][ndof][ndof], double for FP64, float otherwise),
+ * ACCUMULATES (+=) dL/dcoords into d_coords [nverts][d] and dL/dcoef into d_coef
+ * (coefficient layout; may be NULL when the form has no coefficient). Geometry is
+ * recomputed, not stored. deterministic != 0 sums cell contributions in a fixed
+ * order (no floating-point atomics). Device pointers, asynchronous on stream. */
+int coffee_assemble_backward(const coffee_assemble_args* a, const void* dout,
+                             double* d_coords, double* d_coef, int deterministic,
+                             coffee_stream_t stream);
+
+/* Device error word: synchronises `stream`, returns COFFEE_ERR_DEVICE_INDEX if a
+ * validated launch met an out-of-range index, COFFEE_ERR_TIMEOUT if a kernel wait
+ * gave up, COFFEE_OK otherwise, and clears the word. */
+int coffee_check_errors(coffee_stream_t stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* coffee_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COFFEE_H */

@@ -470,7 +470,7 @@ bool valid(int form, int k, int cell) {
 
 void set_threads(int nthreads) {
 #ifdef _OPENMP
-  if (nthreads > 0) omp_set_num_threads(nthreads);
+  omp_set_num_threads(nthreads > 0 ? nthreads : omp_get_num_procs());
 #else
   (void)nthreads;
 #endif
@@ -488,7 +488,7 @@ int oracle_ndof(int form, int degree, int cell) {
 
 int oracle_threads_available(void) {
 #ifdef _OPENMP
-  return omp_get_max_threads();
+  return omp_get_num_procs();
 #else
   return 1;
 #endif

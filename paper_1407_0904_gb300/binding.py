@@ -1,0 +1,242 @@
+"""Python binding of libcoffee.so (ctypes): argument marshalling only.
+
+Every step of local assembly runs inside the library's CUDA kernels; this module
+checks tensor dtypes/devices, passes raw device pointers and the current CUDA stream
+through the C ABI declared in include/coffee.h, and turns status codes into
+exceptions. There is no CPU fallback: if the library is missing the calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC = 0, 1, 2, 3
+TRIANGLE, TETRAHEDRON = 0, 1
+FP64, TF32, TF32X3, BF16, BF16X3 = 0, 1, 2, 3, 4
+FLAG_VALIDATE = 1
+
+FORM_NAMES = {MASS: "mass", HELMHOLTZ: "helmholtz", ADVDIFF: "advdiff", BURGERS_JAC: "burgers_jac"}
+PRECISION_NAMES = {FP64: "fp64", TF32: "tf32", TF32X3: "tf32x3", BF16: "bf16", BF16X3: "bf16x3"}
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcoffee.so")
+_lib = None
+
+
+class CoffeeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("coffee status %d: %s" % (status, msg))
+        self.status = status
+
+
+class AssembleArgs(ctypes.Structure):
+    _fields_ = [
+        ("form", ctypes.c_int), ("degree", ctypes.c_int), ("cell", ctypes.c_int),
+        ("precision", ctypes.c_int), ("nu", ctypes.c_double),
+        ("coords", ctypes.c_void_p), ("nverts", ctypes.c_int64),
+        ("cell2vert", ctypes.c_void_p),
+        ("coef", ctypes.c_void_p), ("ncoefnodes", ctypes.c_int64),
+        ("cell2dof", ctypes.c_void_p),
+        ("out", ctypes.c_void_p), ("ncells", ctypes.c_int64),
+        ("flags", ctypes.c_uint),
+    ]
+
+
+def lib():
+    """Load libcoffee.so (built by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libcoffee.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, L64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        L.coffee_ndof.argtypes = [I, I, I]
+        L.coffee_tabulate.argtypes = [I, I, I, P, P, P, P, P, P]
+        L.coffee_reference_tensor.argtypes = [I, I, I, P, P, P]
+        L.coffee_assemble.argtypes = [I, I, I, P, P, P, P, P, L64, P]
+        L.coffee_assemble_ex.argtypes = [ctypes.POINTER(AssembleArgs), P]
+        L.coffee_assemble_backward.argtypes = [ctypes.POINTER(AssembleArgs), P, P, P, I, P]
+        L.coffee_check_errors.argtypes = [P]
+        L.coffee_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise CoffeeError(rc, lib().coffee_last_error().decode())
+    return rc
+
+
+def dim(cell):
+    return 2 if cell == TRIANGLE else 3
+
+
+def ndof(form, degree, cell):
+    n = lib().coffee_ndof(form, degree, cell)
+    if n < 0:
+        _check(n)
+    return n
+
+
+def nnodes(cell, degree):
+    return ndof(MASS, degree, cell)
+
+
+def tabulate(cell, degree, quad_degree):
+    """Quadrature rule and Lagrange basis on the reference cell (host, FP64).
+
+    Returns (points [nq,d], weights [nq], basis [nq,ndof], grads [nq,ndof,d])."""
+    L = lib()
+    nq, nd = ctypes.c_int(), ctypes.c_int()
+    _check(L.coffee_tabulate(cell, degree, quad_degree, ctypes.byref(nq), ctypes.byref(nd),
+                             None, None, None, None))
+    d = dim(cell)
+    pts = np.zeros((nq.value, d))
+    wts = np.zeros(nq.value)
+    phi = np.zeros((nq.value, nd.value))
+    grd = np.zeros((nq.value, nd.value, d))
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(L.coffee_tabulate(cell, degree, quad_degree, None, None, p(pts), p(wts), p(phi), p(grd)))
+    return pts, wts, phi, grd
+
+
+def reference_tensor(form, degree, cell):
+    """Reference tensors T [K, ns*ns] (host, FP64)."""
+    L = lib()
+    K, N = ctypes.c_int(), ctypes.c_int()
+    _check(L.coffee_reference_tensor(form, degree, cell, ctypes.byref(K), ctypes.byref(N), None))
+    T = np.zeros((K.value, N.value))
+    _check(L.coffee_reference_tensor(form, degree, cell, None, None, T.ctypes.data_as(ctypes.c_void_p)))
+    return T
+
+
+def _dev(t, dtype, name):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
+              out=None, nu=0.01, validate=False, ncoefnodes=None):
+    coords = _dev(coords, torch.float64, "coords")
+    cell2vert = _dev(cell2vert, torch.int32, "cell2vert")
+    coef = _dev(coef, torch.float64, "coef")
+    cell2dof = _dev(cell2dof, torch.int32, "cell2dof")
+    d = dim(cell)
+    ncells = cell2vert.shape[0]
+    if cell2vert.dim() != 2 or cell2vert.shape[1] != d + 1:
+        raise ValueError("cell2vert must be [ncells, %d]" % (d + 1))
+    n = ndof(form, degree, cell)
+    odt = torch.float64 if precision == FP64 else torch.float32
+    if out is None:
+        out = torch.empty((ncells, n, n), dtype=odt, device=coords.device)
+    else:
+        _dev(out, odt, "out")
+        if out.numel() != ncells * n * n:
+            raise ValueError("out must hold ncells*ndof*ndof elements")
+    if ncoefnodes is None and coef is not None:
+        ncoefnodes = coef.numel() // (1 + d) if form == ADVDIFF else coef.numel() // d
+    a = AssembleArgs()
+    a.form, a.degree, a.cell, a.precision, a.nu = form, degree, cell, precision, nu
+    a.coords, a.nverts = _ptr(coords), coords.shape[0]
+    a.cell2vert = _ptr(cell2vert)
+    a.coef, a.ncoefnodes = _ptr(coef), int(ncoefnodes or 0)
+    a.cell2dof = _ptr(cell2dof)
+    a.out, a.ncells = _ptr(out), ncells
+    a.flags = FLAG_VALIDATE if validate else 0
+    return a, out
+
+
+def assemble(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
+             out=None, nu=0.01, validate=False, stream=None):
+    """Element matrices [ncells, ndof, ndof] (float64 for FP64, float32 otherwise) on the device."""
+    a, out = make_args(form, degree, cell, coords, cell2vert, coef, cell2dof, precision, out, nu,
+                       validate)
+    _check(lib().coffee_assemble_ex(ctypes.byref(a), _stream_handle(stream)))
+    return out
+
+
+def assemble_plain(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, out=None,
+                   stream=None):
+    """coffee_assemble, the plain-argument FP64 entry point (nu = 0.01)."""
+    coords = _dev(coords, torch.float64, "coords")
+    cell2vert = _dev(cell2vert, torch.int32, "cell2vert")
+    coef = _dev(coef, torch.float64, "coef")
+    cell2dof = _dev(cell2dof, torch.int32, "cell2dof")
+    n = ndof(form, degree, cell)
+    ncells = cell2vert.shape[0]
+    if out is None:
+        out = torch.empty((ncells, n, n), dtype=torch.float64, device=coords.device)
+    _check(lib().coffee_assemble(form, degree, cell, _ptr(coords), _ptr(cell2vert), _ptr(coef),
+                                 _ptr(cell2dof), _ptr(out), ncells, _stream_handle(stream)))
+    return out
+
+
+def check_errors(stream=None):
+    """Synchronise the stream and raise if a kernel flagged an error."""
+    _check(lib().coffee_check_errors(_stream_handle(stream)))
+
+
+_copy_streams = {}
+
+
+def assemble_host(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
+                  out=None, nu=0.01, chunks=4, device=None):
+    """Local assembly from HOST (ideally pinned) tensors into a host tensor.
+
+    Inputs are copied to the device, the cell range is processed in `chunks` launches
+    and each chunk's element matrices are copied back on a second stream while the
+    next chunk computes. Returns the host tensor `out` (allocated pinned if None); it
+    is complete once the current CUDA stream has reached this point."""
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    main = torch.cuda.current_stream(dev)
+    if dev not in _copy_streams:
+        _copy_streams[dev] = torch.cuda.Stream(dev)
+    side = _copy_streams[dev]
+    d_coords = coords.to(dev, non_blocking=True)
+    d_c2v = cell2vert.to(dev, non_blocking=True)
+    d_coef = None if coef is None else coef.to(dev, non_blocking=True)
+    d_c2d = None if cell2dof is None else cell2dof.to(dev, non_blocking=True)
+    ncells = cell2vert.shape[0]
+    n = ndof(form, degree, cell)
+    odt = torch.float64 if precision == FP64 else torch.float32
+    if out is None:
+        out = torch.empty((ncells, n, n), dtype=odt, pin_memory=True)
+    d_out = torch.empty((ncells, n, n), dtype=odt, device=dev)
+    d_out.record_stream(side)
+    ncoef = None
+    if coef is not None:
+        ncoef = coef.numel() // (1 + dim(cell)) if form == ADVDIFF else coef.numel() // dim(cell)
+    bounds = np.linspace(0, ncells, max(1, chunks) + 1).astype(np.int64)
+    for i in range(len(bounds) - 1):
+        lo, hi = int(bounds[i]), int(bounds[i + 1])
+        if hi <= lo:
+            continue
+        a, _ = make_args(form, degree, cell, d_coords, d_c2v[lo:hi],
+                         d_coef, None if d_c2d is None else d_c2d[lo:hi], precision, d_out[lo:hi],
+                         nu, False, ncoef)
+        _check(lib().coffee_assemble_ex(ctypes.byref(a), ctypes.c_void_p(main.cuda_stream)))
+        ev = torch.cuda.Event()
+        ev.record(main)
+        side.wait_event(ev)
+        with torch.cuda.stream(side):
+            out[lo:hi].copy_(d_out[lo:hi], non_blocking=True)
+    main.wait_stream(side)
+    return out

@@ -1,0 +1,279 @@
+// C-ABI entry points of libcoffee.so (declared in include/coffee.h): argument
+// validation, the per-device cache of reference tensors, and kernel dispatch.
+#include <cuda_runtime.h>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+#include "../../include/coffee.h"
+#include "coffee_internal.h"
+
+namespace coffee {
+
+static thread_local std::string g_last_error;
+
+int fail(int status, const std::string& msg) {
+  g_last_error = msg;
+  return status;
+}
+
+static int cuda_fail(cudaError_t e, const char* where) {
+  return fail(COFFEE_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+namespace {
+
+struct TcEntry {
+  uint8_t* image = nullptr;
+  TcTable meta{};
+};
+
+struct DeviceCache {
+  unsigned* err = nullptr;
+  int num_sms = 0;
+  std::map<std::tuple<int, int, int>, double*> fp64;    // (form, degree, cell)
+  std::map<std::tuple<int, int, int, int>, TcEntry> tc;  // + precision
+};
+
+std::mutex g_mu;
+std::map<int, DeviceCache> g_cache;
+
+int device_cache(DeviceCache** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  DeviceCache& c = g_cache[dev];
+  if (!c.err) {
+    e = cudaMalloc(&c.err, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(error word)");
+    e = cudaMemset(c.err, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(error word)");
+    e = cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  *out = &c;
+  return COFFEE_OK;
+}
+
+int fp64_table(DeviceCache& c, int form, int degree, int cell, const double** T) {
+  auto key = std::make_tuple(form, degree, cell);
+  auto it = c.fp64.find(key);
+  if (it != c.fp64.end()) {
+    *T = it->second;
+    return COFFEE_OK;
+  }
+  std::vector<double> h;
+  reference_tensor(form, degree, cell, h);
+  double* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, h.size() * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(reference tensor)");
+  e = cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(reference tensor)");
+  c.fp64[key] = d;
+  *T = d;
+  return COFFEE_OK;
+}
+
+int tc_table(DeviceCache& c, int form, int degree, int cell, int prec, TcTable* meta) {
+  auto key = std::make_tuple(form, degree, cell, prec);
+  auto it = c.tc.find(key);
+  if (it == c.tc.end()) {
+    std::vector<uint8_t> img;
+    TcEntry ent;
+    build_tc_image(form, degree, cell, prec, img, ent.meta);
+    cudaError_t e = cudaMalloc(&ent.image, img.size());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(tensor-core table)");
+    e = cudaMemcpy(ent.image, img.data(), img.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(tensor-core table)");
+    ent.meta.image = ent.image;
+    it = c.tc.emplace(key, ent).first;
+  }
+  *meta = it->second.meta;
+  return COFFEE_OK;
+}
+
+bool valid_fdc(int form, int degree, int cell) {
+  return form >= FORM_MASS && form <= FORM_BURGERS && degree >= 1 && degree <= 4 &&
+         (cell == CELL_TRI || cell == CELL_TET);
+}
+
+int check_args(const coffee_assemble_args* a) {
+  if (!a) return fail(COFFEE_ERR_INVALID_ARG, "args is NULL");
+  if (!valid_fdc(a->form, a->degree, a->cell))
+    return fail(COFFEE_ERR_INVALID_ARG, "form/degree/cell out of range (degree 1..4, tri/tet)");
+  if (a->precision < PREC_FP64 || a->precision > PREC_BF16X3)
+    return fail(COFFEE_ERR_INVALID_ARG, "precision out of range");
+  if (a->ncells < 0) return fail(COFFEE_ERR_INVALID_ARG, "ncells < 0");
+  if (a->ncells == 0) return COFFEE_OK;
+  if (!a->coords || !a->cell2vert || !a->out)
+    return fail(COFFEE_ERR_INVALID_ARG, "coords, cell2vert and out must be non-NULL");
+  if ((a->flags & COFFEE_FLAG_VALIDATE) && a->nverts <= 0)
+    return fail(COFFEE_ERR_INVALID_ARG, "validation needs nverts > 0");
+  if (a->form == FORM_ADVDIFF || a->form == FORM_BURGERS) {
+    if (!a->coef || !a->cell2dof)
+      return fail(COFFEE_ERR_INVALID_ARG, "this form needs coef and cell2dof");
+    if (a->ncoefnodes <= 0) return fail(COFFEE_ERR_INVALID_ARG, "ncoefnodes must be > 0");
+  }
+  if (a->ncells > (int64_t)INT32_MAX * 128)
+    return fail(COFFEE_ERR_INVALID_ARG, "ncells too large");
+  return COFFEE_OK;
+}
+
+}  // namespace
+}  // namespace coffee
+
+using namespace coffee;
+
+extern "C" {
+
+int coffee_ndof(int form, int degree, int cell) {
+  if (!(form >= 0 && form <= 3 && degree >= 1 && degree <= 6 && (cell == 0 || cell == 1)))
+    return fail(COFFEE_ERR_INVALID_ARG, "form/degree/cell out of range");
+  int ns = nnodes(cell, degree);
+  return form == FORM_BURGERS ? (cell == CELL_TRI ? 2 : 3) * ns : ns;
+}
+
+int coffee_tabulate(int cell, int degree, int quad_degree, int* nq, int* ndof, double* points,
+                    double* weights, double* basis, double* grads) {
+  if (!(cell == 0 || cell == 1) || degree < 1 || degree > 6 || quad_degree < 0 || quad_degree > 30)
+    return fail(COFFEE_ERR_INVALID_ARG, "cell/degree/quad_degree out of range");
+  std::vector<double> pts, wts;
+  quadrature_rule(cell, quad_degree, pts, wts);
+  const int n = (int)wts.size(), nd = nnodes(cell, degree), d = cell == 0 ? 2 : 3;
+  if (nq) *nq = n;
+  if (ndof) *ndof = nd;
+  if (points) std::memcpy(points, pts.data(), pts.size() * sizeof(double));
+  if (weights) std::memcpy(weights, wts.data(), wts.size() * sizeof(double));
+  if (basis || grads) lagrange_basis(cell, degree, n, pts.data(), basis, grads);
+  (void)d;
+  return COFFEE_OK;
+}
+
+int coffee_reference_tensor(int form, int degree, int cell, int* K, int* N, double* T) {
+  if (!valid_fdc(form, degree, cell)) return fail(COFFEE_ERR_INVALID_ARG, "form/degree/cell out of range");
+  const int ns = nnodes(cell, degree);
+  if (K) *K = form_K(form, degree, cell);
+  if (N) *N = ns * ns;
+  if (T) {
+    std::vector<double> h;
+    reference_tensor(form, degree, cell, h);
+    std::memcpy(T, h.data(), h.size() * sizeof(double));
+  }
+  return COFFEE_OK;
+}
+
+int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream) {
+  int rc = check_args(a);
+  if (rc != COFFEE_OK || a->ncells == 0) return rc;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceCache* c = nullptr;
+  if ((rc = device_cache(&c)) != COFFEE_OK) return rc;
+  const int d = a->cell == CELL_TRI ? 2 : 3;
+  const int ns = nnodes(a->cell, a->degree);
+  const int ndof = a->form == FORM_BURGERS ? d * ns : ns;
+  const bool validate = (a->flags & COFFEE_FLAG_VALIDATE) != 0;
+  if (a->precision == PREC_FP64) {
+    const double* T = nullptr;
+    if ((rc = fp64_table(*c, a->form, a->degree, a->cell, &T)) != COFFEE_OK) return rc;
+    Fp64Params p{};
+    p.coords = a->coords;
+    p.c2v = a->cell2vert;
+    p.coef = a->coef;
+    p.c2d = a->cell2dof;
+    p.T = T;
+    p.out = a->out;
+    p.err = c->err;
+    p.ncells = a->ncells;
+    p.nverts = a->nverts;
+    p.ncoefnodes = a->ncoefnodes;
+    p.ns = ns;
+    p.N = ns * ns;
+    p.ndof = ndof;
+    p.nu = a->nu;
+    p.validate = validate ? 1 : 0;
+    cudaError_t e = (cudaError_t)launch_fp64(a->form, a->cell, p, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch(assemble_fp64)");
+    return COFFEE_OK;
+  }
+  if (!tc_supported(a->form, a->degree, a->cell, a->precision))
+    return fail(COFFEE_ERR_UNSUPPORTED, "no tensor-core kernel for this form/degree/cell/precision");
+  TcTable meta{};
+  if ((rc = tc_table(*c, a->form, a->degree, a->cell, a->precision, &meta)) != COFFEE_OK) return rc;
+  TcParams p{};
+  p.coords = a->coords;
+  p.c2v = a->cell2vert;
+  p.coef = a->coef;
+  p.c2d = a->cell2dof;
+  p.image = meta.image;
+  p.out = static_cast<float*>(a->out);
+  p.err = c->err;
+  p.ncells = a->ncells;
+  p.nverts = a->nverts;
+  p.ncoefnodes = a->ncoefnodes;
+  p.ns = ns;
+  p.N = ndof * ndof;
+  p.mtiles = meta.mtiles;
+  p.kbytes = meta.kbytes;
+  p.parts = meta.parts;
+  p.precision = a->precision;
+  p.validate = validate ? 1 : 0;
+  p.nu = a->nu;
+  std::string why;
+  cudaError_t e = (cudaError_t)launch_tc(a->form, a->cell, p, c->num_sms, stream, why);
+  if (e != cudaSuccess) return cuda_fail(e, ("launch(assemble_tc) " + why).c_str());
+  return COFFEE_OK;
+}
+
+int coffee_assemble(int form, int degree, int cell, const double* coords, const int32_t* cell2vert,
+                    const double* coef, const int32_t* cell2dof, void* out, int64_t ncells,
+                    coffee_stream_t stream) {
+  coffee_assemble_args a{};
+  a.form = form;
+  a.degree = degree;
+  a.cell = cell;
+  a.precision = COFFEE_FP64;
+  a.nu = 0.01;
+  a.coords = coords;
+  a.nverts = 0;
+  a.cell2vert = cell2vert;
+  a.coef = coef;
+  a.ncoefnodes = INT64_MAX;
+  a.cell2dof = cell2dof;
+  a.out = out;
+  a.ncells = ncells;
+  a.flags = 0;
+  return coffee_assemble_ex(&a, stream);
+}
+
+int coffee_assemble_backward(const coffee_assemble_args* a, const void* dout, double* d_coords,
+                             double* d_coef, int deterministic, coffee_stream_t stream) {
+  (void)a; (void)dout; (void)d_coords; (void)d_coef; (void)deterministic; (void)stream;
+  return fail(COFFEE_ERR_UNSUPPORTED, "backward pass not built yet");
+}
+
+int coffee_check_errors(coffee_stream_t stream) {
+  DeviceCache* c = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    int rc = device_cache(&c);
+    if (rc != COFFEE_OK) return rc;
+  }
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  unsigned w = 0;
+  e = cudaMemcpy(&w, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(error word)");
+  if (w) {
+    e = cudaMemset(c->err, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(error word)");
+  }
+  if (w & ERR_TIMEOUT) return fail(COFFEE_ERR_TIMEOUT, "a device wait gave up (bounded spin)");
+  if (w & ERR_INDEX) return fail(COFFEE_ERR_DEVICE_INDEX, "out-of-range index in cell2vert/cell2dof");
+  return COFFEE_OK;
+}
+
+const char* coffee_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <vector>
+#include <string>
+
+namespace coffee {
+
+enum { CELL_TRI = 0, CELL_TET = 1 };
+enum { FORM_MASS = 0, FORM_HELMHOLTZ = 1, FORM_ADVDIFF = 2, FORM_BURGERS = 3 };
+enum { PREC_FP64 = 0, PREC_TF32 = 1, PREC_TF32X3 = 2, PREC_BF16 = 3, PREC_BF16X3 = 4 };
+
+// Device error word bits
+enum : unsigned { ERR_INDEX = 1u, ERR_TIMEOUT = 2u };
+
+// ---- host tabulation (tabulate.cpp) ----
+int nnodes(int cell, int k);
+int npairs(int d);
+void pair_index(int d, int p, int& a, int& b);
+int quad_degree_for(int form, int k);
+int form_K(int form, int k, int cell);
+void quadrature_rule(int cell, int degree, std::vector<double>& pts, std::vector<double>& wts);
+void lagrange_basis(int cell, int k, int npts, const double* x, double* phi, double* grads);
+void reference_tensor(int form, int k, int cell, std::vector<double>& T);
+
+// ---- error reporting (api.cu) ----
+int fail(int status, const std::string& msg);
+
+// ---- FP64 plain kernel (k_fp64.cu) ----
+struct Fp64Params {
+  const double* coords;
+  const int32_t* c2v;
+  const double* coef;
+  const int32_t* c2d;
+  const double* T;  // [K][N] with N = ns*ns
+  void* out;        // double [ncells][ndof][ndof]
+  unsigned* err;
+  int64_t ncells, nverts, ncoefnodes;
+  int ns, N, ndof;
+  double nu;
+  int validate;
+};
+// returns cudaError_t as int
+int launch_fp64(int form, int cell, const Fp64Params& p, void* stream);
+
+// ---- tcgen05 tensor-core contraction (k_tc.cu) ----
+// Operand image of the reference tensor for the tensor cores: for each M-tile of
+// 128 output rows, the hi part then (split precisions) the lo part, each
+// 128 rows x kbytes bytes in the canonical no-swizzle K-major core-matrix layout.
+struct TcTable {
+  const uint8_t* image;  // device
+  int mtiles;            // ceil(N / 128) (per block for Burgers)
+  int kbytes;            // bytes per operand row (multiple of 32)
+  int kelems;            // padded K (elements)
+  int K;                 // true K
+  int parts;             // 1 (single pass) or 2 (hi, lo)
+  int64_t tile_bytes;    // bytes of one part of one M-tile = 128 * kbytes
+};
+
+struct TcParams {
+  const double* coords;
+  const int32_t* c2v;
+  const double* coef;
+  const int32_t* c2d;
+  const uint8_t* image;  // TcTable image
+  float* out;
+  unsigned* err;
+  int64_t ncells, nverts, ncoefnodes;
+  int ns, N;             // outputs per cell
+  int mtiles, kbytes, parts;
+  int precision;
+  int validate;
+  double nu;
+};
+int tc_supported(int form, int degree, int cell, int precision);
+int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
+// Build the operand image on the host
+void build_tc_image(int form, int degree, int cell, int precision, std::vector<uint8_t>& img,
+                    TcTable& meta);
+
+}  // namespace coffee

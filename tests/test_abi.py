@@ -1,0 +1,150 @@
+"""CPU checks of the C-ABI library: it loads, exports every declared symbol, rejects bad
+arguments on the host, and its host-side tabulation agrees with the oracle's own."""
+import ctypes
+import itertools
+import os
+import re
+import subprocess
+from math import factorial
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1407_0904_gb300 as coffee
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if fn.endswith(".h"):
+            src = open(os.path.join(inc, fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"^[A-Za-z_][\w \*]*?\b(coffee_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = coffee.lib()
+    names = declared_symbols()
+    assert {"coffee_tabulate", "coffee_assemble", "coffee_assemble_ex",
+            "coffee_assemble_backward", "coffee_check_errors"} <= names
+    out = subprocess.run(["nm", "-D", "--defined-only", coffee.binding.LIB_PATH],
+                         capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (coffee_\w+)", out))
+    missing = names - exported
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_host_argument_errors_before_any_launch():
+    lib = coffee.lib()
+    a = coffee.binding.AssembleArgs()
+    a.form, a.degree, a.cell, a.precision, a.ncells = 9, 1, 0, 0, 10
+    assert lib.coffee_assemble_ex(ctypes.byref(a), None) == -1
+    a.form, a.degree = 1, 7
+    assert lib.coffee_assemble_ex(ctypes.byref(a), None) == -1
+    a.degree, a.precision = 2, 11
+    assert lib.coffee_assemble_ex(ctypes.byref(a), None) == -1
+    a.precision, a.ncells = 0, -1
+    assert lib.coffee_assemble_ex(ctypes.byref(a), None) == -1
+    assert b"ncells" in lib.coffee_last_error()
+    a.ncells = 5  # NULL pointers
+    assert lib.coffee_assemble_ex(ctypes.byref(a), None) == -1
+    a.ncells = 0  # empty input is a no-op that never touches the GPU
+    assert lib.coffee_assemble_ex(ctypes.byref(a), None) == 0
+    a.form, a.ncells = coffee.ADVDIFF, 3
+    a.coords = a.cell2vert = a.out = 16  # non-NULL, never dereferenced on the host
+    assert lib.coffee_assemble_ex(ctypes.byref(a), None) == -1  # advdiff without coefficients
+    assert lib.coffee_tabulate(5, 1, 2, None, None, None, None, None, None) == -1
+    assert lib.coffee_ndof(0, 9, 0) == -1
+
+
+@pytest.mark.parametrize("cell", [0, 1])
+def test_ndof(cell):
+    for k in range(1, 5):
+        ns = (k + 1) * (k + 2) // 2 if cell == 0 else (k + 1) * (k + 2) * (k + 3) // 6
+        assert coffee.ndof(coffee.HELMHOLTZ, k, cell) == ns == oracle.ndof(oracle.HELMHOLTZ, k, cell)
+        assert coffee.ndof(coffee.BURGERS_JAC, k, cell) == (2 + cell) * ns
+
+
+@pytest.mark.parametrize("cell", [0, 1])
+@pytest.mark.parametrize("p", range(0, 15))
+def test_tabulate_rule_exact_on_monomials(cell, p):
+    d = 2 + cell
+    pts, w, _, _ = coffee.tabulate(cell, 1, p)
+    assert np.all(w > 0)
+    for e in itertools.product(range(p + 1), repeat=d):
+        if sum(e) > p:
+            continue
+        val = np.sum(w * np.prod(pts ** np.array(e), axis=1))
+        ex = np.prod([factorial(x) for x in e]) / factorial(sum(e) + d)
+        assert abs(val - ex) <= 2e-14 * ex
+
+
+@pytest.mark.parametrize("cell", [0, 1])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_tabulate_basis_matches_oracle(cell, k):
+    pts, w, phi, grd = coffee.tabulate(cell, k, 2 * k)
+    ophi, ogrd = oracle.basis(cell, k, pts)
+    assert np.abs(phi - ophi).max() < 1e-13
+    assert np.abs(grd - ogrd).max() < 1e-12
+
+
+@pytest.mark.parametrize("form", [coffee.MASS, coffee.HELMHOLTZ, coffee.ADVDIFF])
+@pytest.mark.parametrize("cell", [0, 1])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_reference_tensor_on_reference_cell_matches_oracle(form, cell, k):
+    """On the reference cell J = I, |det| = 1, so G is known without geometry code:
+    MASS G=[1]; HELMHOLTZ G=[1, delta_ab]; ADVDIFF G=[eps_v delta_ab | b_v,a]."""
+    d = 2 + cell
+    T = coffee.reference_tensor(form, k, cell)
+    ns = oracle.ndof(form, k, cell)
+    X = np.vstack([np.zeros(d), np.eye(d)])
+    c2v = np.arange(d + 1, dtype=np.int32)[None]
+    pairs = [(a, b) for a in range(d) for b in range(a, d)]
+    coef = c2d = None
+    if form == coffee.MASS:
+        G = np.array([1.0])
+    elif form == coffee.HELMHOLTZ:
+        G = np.array([1.0] + [1.0 if a == b else 0.0 for a, b in pairs])
+    else:
+        rng = np.random.default_rng(k)
+        eps = rng.uniform(0.5, 1.5, d + 1)
+        b = rng.uniform(-1, 1, (d + 1, d))
+        coef = np.concatenate([eps, b.ravel()])
+        c2d = c2v.copy()
+        G = np.concatenate([[eps[v] * (1.0 if a == bb else 0.0) for v in range(d + 1) for a, bb in pairs],
+                            b.ravel()])
+    A = (G @ T).reshape(ns, ns)
+    R = oracle.assemble(form, k, cell, X, c2v, coef, c2d)[0]
+    assert np.abs(A - R).max() < 1e-13 * np.abs(R).max()
+
+
+@pytest.mark.parametrize("cell,k", [(0, 1), (0, 2), (1, 1), (1, 2)])
+def test_burgers_reference_tensor_on_reference_cell_matches_oracle(cell, k):
+    """Reference cell, u given: block (ci,cj) = sum_{r,a} u[r,ci] delta_{a,cj} T1 +
+    [ci==cj] (sum_{r,a} u[r,a] T2 + nu sum_p delta_p T3)."""
+    d = 2 + cell
+    T = coffee.reference_tensor(coffee.BURGERS_JAC, k, cell)
+    ns = oracle.ndof(oracle.MASS, k, cell)
+    X = np.vstack([np.zeros(d), np.eye(d)])
+    c2v = np.arange(d + 1, dtype=np.int32)[None]
+    u = np.random.default_rng(3).standard_normal((ns, d))
+    c2d = np.arange(ns, dtype=np.int32)[None]
+    T1, T2, T3 = T[:ns * d], T[ns * d:2 * ns * d], T[2 * ns * d:]
+    pairs = [(a, b) for a in range(d) for b in range(a, d)]
+    A = np.zeros((d * ns, d * ns))
+    for ci in range(d):
+        for cj in range(d):
+            G1 = np.array([u[r, ci] * (1.0 if a == cj else 0.0) for r in range(ns) for a in range(d)])
+            blk = G1 @ T1
+            if ci == cj:
+                blk = blk + u.ravel() @ T2 + 0.01 * np.array([1.0 if a == b else 0.0 for a, b in pairs]) @ T3
+            A[ci * ns:(ci + 1) * ns, cj * ns:(cj + 1) * ns] = blk.reshape(ns, ns)
+    R = oracle.assemble(oracle.BURGERS_JAC, k, cell, X, c2v, u, c2d)[0]
+    assert np.abs(A - R).max() < 1e-13 * np.abs(R).max()
