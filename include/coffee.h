@@ -116,7 +116,7 @@ int coffee_reference_tensor(int form, int degree, int cell, int* K, int* N, doub
 /* FP64 local assembly (plain one-thread-per-cell kernel), all pointers on the device:
  *   coords    [nverts][d] double
  *   cell2vert [ncells][d+1] int32
- *   coef      ADVDIFF: [eps (ncoefnodes) | b (ncoefnodes*d, node-major)] double
+ *   coef      ADVDIFF: [ncoefnodes][1+d] double, row = (eps, b_0, .., b_{d-1})
  *             BURGERS_JAC: u [ncoefnodes][d] double (viscosity nu = 0.01)
  *             MASS/HELMHOLTZ: NULL
  *   cell2dof  ADVDIFF: [ncells][d+1]; BURGERS_JAC: [ncells][ns]; else NULL
@@ -144,6 +144,11 @@ typedef struct {
   int64_t ncells;
   unsigned flags;            /* COFFEE_FLAG_* */
 } coffee_assemble_args;
+
+/* 1 if coffee_assemble_ex has a kernel for (form, degree, cell, precision), else 0.
+ * FP64 covers every form, degree 1..4, both cells; the tensor-core precisions cover
+ * the combinations whose operands fit in shared memory. Host-only. */
+int coffee_supported(int form, int degree, int cell, int precision);
 
 /* Local assembly with a chosen precision. FP64 runs the plain FP64 kernel; the
  * other precisions run the tcgen05 tensor-core contraction with geometry fused into

@@ -447,8 +447,8 @@ void gather(const Ctx& c, const double* coords, const int32_t* c2v, const double
   if (c.form == FORM_ADVDIFF) {
     for (int v = 0; v <= d; ++v) {
       int64_t id = c2d[e * (d + 1) + v];
-      cf[v] = coef[id];
-      for (int r = 0; r < d; ++r) cf[(d + 1) + v * d + r] = coef[ncoefnodes + id * d + r];
+      cf[v] = coef[id * (d + 1)];
+      for (int r = 0; r < d; ++r) cf[(d + 1) + v * d + r] = coef[id * (d + 1) + 1 + r];
     }
   } else if (c.form == FORM_BURGERS) {
     for (int rr = 0; rr < c.ns; ++rr) {
@@ -526,7 +526,7 @@ int oracle_basis(int cell, int k, int npts, const double* x, double* phi, double
 }
 
 // Element matrices out [ncells][ndof][ndof] (float64) for cells [0, ncells).
-// coef/c2d: ADVDIFF: coef = [eps (ncoefnodes) | b (ncoefnodes*d)], c2d [ncells][d+1];
+// coef/c2d: ADVDIFF: coef = [ncoefnodes][1+d] rows (eps, b_0..b_{d-1}), c2d [ncells][d+1];
 //           BURGERS: coef = u [ncoefnodes][d], c2d [ncells][ns]; otherwise unused.
 int oracle_assemble(int form, int degree, int cell, double nu, const double* coords,
                     const int32_t* c2v, const double* coef, const int32_t* c2d,
@@ -616,8 +616,8 @@ int oracle_assemble_backward(int form, int degree, int cell, double nu, const do
     if (form == FORM_ADVDIFF) {
       for (int v = 0; v <= d; ++v) {
         int64_t id = c2d[e * (d + 1) + v];
-        d_coef[id] += L[nx + v];
-        for (int r = 0; r < d; ++r) d_coef[ncoefnodes + id * d + r] += L[nx + (d + 1) + v * d + r];
+        d_coef[id * (d + 1)] += L[nx + v];
+        for (int r = 0; r < d; ++r) d_coef[id * (d + 1) + 1 + r] += L[nx + (d + 1) + v * d + r];
       }
     } else if (form == FORM_BURGERS) {
       for (int rr = 0; rr < c.ns; ++rr) {

@@ -58,6 +58,7 @@ def lib():
         L.coffee_assemble_ex.argtypes = [ctypes.POINTER(AssembleArgs), P]
         L.coffee_assemble_backward.argtypes = [ctypes.POINTER(AssembleArgs), P, P, P, I, P]
         L.coffee_check_errors.argtypes = [P]
+        L.coffee_supported.argtypes = [I, I, I, I]
         L.coffee_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
@@ -78,6 +79,15 @@ def ndof(form, degree, cell):
     if n < 0:
         _check(n)
     return n
+
+
+def supported(form, degree, cell, precision):
+    """True if the library has a kernel for this (form, degree, cell, precision)."""
+    return bool(lib().coffee_supported(form, degree, cell, precision))
+
+
+def tc_available(form, degree, cell, precision):
+    return precision != FP64 and supported(form, degree, cell, precision)
 
 
 def nnodes(cell, degree):

@@ -164,6 +164,12 @@ int coffee_reference_tensor(int form, int degree, int cell, int* K, int* N, doub
   return COFFEE_OK;
 }
 
+int coffee_supported(int form, int degree, int cell, int precision) {
+  if (!valid_fdc(form, degree, cell) || precision < PREC_FP64 || precision > PREC_BF16X3) return 0;
+  if (precision == PREC_FP64) return 1;
+  return tc_supported(form, degree, cell, precision);
+}
+
 int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream) {
   int rc = check_args(a);
   if (rc != COFFEE_OK || a->ncells == 0) return rc;

@@ -145,10 +145,11 @@ __global__ void __launch_bounds__(128) k_assemble_fp64(const Fp64Params p) {
     } else {  // ADVDIFF
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const double eps = __ldg(p.coef + cid[v]);
+        const double* cv = p.coef + (int64_t)cid[v] * (D + 1);  // (eps, b) row of the node
+        const double eps = __ldg(cv);
         double bv[D];
 #pragma unroll
-        for (int r = 0; r < D; ++r) bv[r] = __ldg(p.coef + p.ncoefnodes + (int64_t)cid[v] * D + r);
+        for (int r = 0; r < D; ++r) bv[r] = __ldg(cv + 1 + r);
 #pragma unroll
         for (int q = 0; q < P; ++q) G[v * P + q] = eps * H[q];
 #pragma unroll

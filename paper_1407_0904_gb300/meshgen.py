@@ -139,12 +139,13 @@ def cell2dof(mesh, k, permute_seed=None):
 
 
 def advdiff_coefficients(mesh, seed, permute_seed=None):
-    """eps ~ U[0.5,1.5] and b ~ U[-1,1]^d per P1 node: (coef flat [eps | b], cell2dof, nnodes)."""
+    """eps ~ U[0.5,1.5] and b ~ U[-1,1]^d per P1 node: (coef [nnodes*(1+d)] with rows
+    (eps, b_0, .., b_{d-1}), cell2dof, nnodes)."""
     c2d, nn = cell2dof(mesh, 1, permute_seed)
     rng = np.random.default_rng(seed)
     eps = rng.uniform(0.5, 1.5, size=nn)
     b = rng.uniform(-1.0, 1.0, size=(nn, mesh.dim))
-    return np.concatenate([eps, b.ravel()]), c2d, nn
+    return np.concatenate([eps[:, None], b], axis=1).ravel(), c2d, nn
 
 
 def burgers_coefficients(mesh, k, seed, permute_seed=None):

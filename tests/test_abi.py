@@ -116,7 +116,7 @@ def test_reference_tensor_on_reference_cell_matches_oracle(form, cell, k):
         rng = np.random.default_rng(k)
         eps = rng.uniform(0.5, 1.5, d + 1)
         b = rng.uniform(-1, 1, (d + 1, d))
-        coef = np.concatenate([eps, b.ravel()])
+        coef = np.concatenate([eps[:, None], b], axis=1).ravel()
         c2d = c2v.copy()
         G = np.concatenate([[eps[v] * (1.0 if a == bb else 0.0) for v in range(d + 1) for a, bb in pairs],
                             b.ravel()])

@@ -249,7 +249,7 @@ def test_advdiff_bilinear_identity_exact(cell, k):
     verts = [[sp.Rational(v) for v in row] for row in X]
     eps_v = np.array([float(v) for v in exact.evaluate(eps, xs, verts)])
     b_v = np.array([[float(bb.subs(dict(zip(xs, v)))) for bb in b] for v in verts])
-    coef = np.concatenate([eps_v, b_v.ravel()])
+    coef = np.concatenate([eps_v[:, None], b_v], axis=1).ravel()
     c2d = np.arange(d + 1, dtype=np.int32)[None]
     nodes = exact.physical_nodes(X, k)
     P = np.array([float(v) for v in exact.evaluate(p, xs, nodes)])
@@ -327,7 +327,7 @@ def test_advdiff_constant_trial_and_linearity(cell, k):
     A3 = oracle.assemble(oracle.ADVDIFF, k, cell, m.coords, m.cell2vert, 2 * coef - 3 * c2, c2d)
     assert scaled_err(A3, 2 * A - 3 * A2) < 1e-13
     # eps = 1, b = 0 reduces to the stiffness part of Helmholtz
-    ones = np.concatenate([np.ones(nn), np.zeros(nn * m.dim)])
+    ones = np.concatenate([np.ones((nn, 1)), np.zeros((nn, m.dim))], axis=1).ravel()
     S = oracle.assemble(oracle.ADVDIFF, k, cell, m.coords, m.cell2vert, ones, c2d)
     H = oracle.assemble(oracle.HELMHOLTZ, k, cell, m.coords, m.cell2vert)
     M = oracle.assemble(oracle.MASS, k, cell, m.coords, m.cell2vert)

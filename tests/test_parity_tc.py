@@ -1,0 +1,127 @@
+"""Parity of the tcgen05 tensor-core kernel with the FP64 oracle.
+
+Error metric: per cell, max_ij |A - A_oracle| / max_ij |A_oracle|, maximised over cells.
+Tolerances: TF32X3 1e-5; BF16X3 1e-4 (its split leaves ~2^-16 per product, so it is
+held to a looser bound and its measured error is printed); single-pass TF32/BF16 1e-2.
+Sizes span several 128-cell tiles with a ragged last tile.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1407_0904_gb300 as coffee
+from paper_1407_0904_gb300 import meshgen
+from tests.helpers import (TRI, TET, MASS, HELMHOLTZ, ADVDIFF, coefficients, rel_err_per_cell,
+                           to_device, oracle_ref)
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+TOL = {coffee.TF32X3: 1e-5, coffee.BF16X3: 1e-4, coffee.TF32: 1e-2, coffee.BF16: 1e-2}
+
+
+def ragged_mesh(cell, seed):
+    if cell == TRI:
+        return meshgen.tri_mesh(23, perturb=0.2, seed=seed)        # 1058 cells = 8 tiles + 34
+    return meshgen.tet_mesh(6, perturb=0.15, seed=seed, ncells=1000)  # 7 tiles + 104
+
+
+CASES = [(f, c, k, p) for f in (MASS, HELMHOLTZ, ADVDIFF) for c in (TRI, TET) for k in (1, 2, 3, 4)
+         for p in (coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16)]
+
+
+@pytest.mark.parametrize("form,cell,k,prec", CASES)
+def test_tc_matches_oracle(form, cell, k, prec):
+    if not coffee.supported(form, k, cell, prec):
+        pytest.skip("combination not built (operands exceed shared memory)")
+    mesh = ragged_mesh(cell, seed=20 + k)
+    coef, c2d = coefficients(form, mesh, k, seed=7)
+    ref = oracle_ref(form, k, cell, mesh, coef, c2d)
+    x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    out = coffee.assemble(form, k, cell, x, c2v, cf, cd, precision=prec, validate=True)
+    coffee.check_errors()
+    assert out.dtype == torch.float32
+    err = rel_err_per_cell(out.cpu().numpy(), ref)
+    print("%s %s P%d %s: %.3e" % (coffee.FORM_NAMES[form], "tri" if cell == TRI else "tet", k,
+                                  coffee.PRECISION_NAMES[prec], err))
+    assert err < TOL[prec]
+
+
+@pytest.mark.parametrize("ncells", [1, 127, 128, 129, 255, 257])
+def test_tile_edges(ncells):
+    mesh = meshgen.tet_mesh(4, perturb=0.15, seed=3, ncells=ncells)
+    ref = oracle_ref(HELMHOLTZ, 3, TET, mesh, None, None)
+    x, c2v, _, _ = to_device(mesh, None, None, DEV)
+    out = torch.full((ncells + 3, 20, 20), 7.0, dtype=torch.float32, device=DEV)
+    coffee.assemble(HELMHOLTZ, 3, TET, x, c2v, precision=coffee.TF32X3, out=out[:ncells])
+    torch.cuda.synchronize()
+    assert rel_err_per_cell(out[:ncells].cpu().numpy(), ref) < 1e-5
+    assert torch.all(out[ncells:] == 7.0)  # nothing written past the last cell
+
+
+def test_empty_input_is_noop():
+    mesh = meshgen.tet_mesh(2, seed=3)
+    x, c2v, _, _ = to_device(mesh, None, None, DEV)
+    out = coffee.assemble(HELMHOLTZ, 2, TET, x, c2v[:0], precision=coffee.TF32X3)
+    assert out.shape == (0, 10, 10)
+
+
+def test_sliver_cells_take_fp64_geometry():
+    rng = np.random.default_rng(5)
+    X = np.concatenate([meshgen.sliver_tet(rng, flat) for flat in (1e-1, 1e-2, 1e-3, 1e-4)])
+    c2v = np.arange(16, dtype=np.int32).reshape(4, 4)
+    mesh = meshgen.Mesh(TET, X, c2v, None, (1, 1, 1))
+    ref = oracle_ref(HELMHOLTZ, 2, TET, mesh, None, None)
+    x, cv, _, _ = to_device(mesh, None, None, DEV)
+    out = coffee.assemble(HELMHOLTZ, 2, TET, x, cv, precision=coffee.TF32X3)
+    assert rel_err_per_cell(out.cpu().numpy(), ref) < 1e-5
+
+
+def test_validation_flags_bad_index_tc():
+    mesh = meshgen.tet_mesh(3, seed=4)
+    x, c2v, _, _ = to_device(mesh, None, None, DEV)
+    bad = c2v.clone()
+    bad[17, 1] = -3
+    coffee.assemble(MASS, 2, TET, x, bad, precision=coffee.TF32X3, validate=True)
+    with pytest.raises(coffee.CoffeeError) as ei:
+        coffee.check_errors()
+    assert ei.value.status == -4
+
+
+def test_permuted_coefficient_numbering_tc():
+    mesh = ragged_mesh(TET, seed=8)
+    coef, c2d = coefficients(ADVDIFF, mesh, 2, seed=8, permute_seed=77)
+    ref = oracle_ref(ADVDIFF, 2, TET, mesh, coef, c2d)
+    x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    out = coffee.assemble(ADVDIFF, 2, TET, x, c2v, cf, cd, precision=coffee.TF32X3)
+    assert rel_err_per_cell(out.cpu().numpy(), ref) < 1e-5
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_full_size_config2_tc_sampled(k):
+    """1,572,864 Kuhn tets, Helmholtz Pk in TF32X3, in the launch configuration the
+    benchmark times: sampled cells vs the oracle, plus the mesh's total mass."""
+    mesh = meshgen.tet_mesh(64, perturb=0.15, seed=2)
+    x, c2v, _, _ = to_device(mesh, None, None, DEV)
+    out = coffee.assemble(HELMHOLTZ, k, TET, x, c2v, precision=coffee.TF32X3)
+    sel = np.random.default_rng(k).choice(mesh.ncells, size=2000, replace=False)
+    sel = np.concatenate([sel, [0, mesh.ncells - 1]])
+    ref = oracle_ref(HELMHOLTZ, k, TET, mesh, None, None, sel=sel)
+    got = out[torch.from_numpy(sel).to(DEV)].cpu().numpy()
+    assert rel_err_per_cell(got, ref) < 1e-5
+    del out
+    m = coffee.assemble(MASS, k, TET, x, c2v, precision=coffee.TF32X3)
+    assert abs(m.double().sum().item() - 1.0) < 1e-5
+
+
+def test_config3_advdiff_p2_2pow20_sampled():
+    mesh = meshgen.tet_mesh(64, 64, 43, perturb=0.15, seed=3, ncells=2 ** 20)
+    coef, c2d = coefficients(ADVDIFF, mesh, 2, seed=3)
+    x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    out = coffee.assemble(ADVDIFF, 2, TET, x, c2v, cf, cd, precision=coffee.TF32X3)
+    sel = np.random.default_rng(3).choice(mesh.ncells, size=3000, replace=False)
+    ref = oracle_ref(ADVDIFF, 2, TET, mesh, coef, c2d, sel=sel)
+    got = out[torch.from_numpy(sel).to(DEV)].cpu().numpy()
+    assert rel_err_per_cell(got, ref) < 1e-5
+    # A 1 = 0 on every cell (both terms vanish on constants)
+    rows = out.double().sum(dim=2).abs().amax(dim=1) / out.double().abs().amax(dim=(1, 2))
+    assert rows.max().item() < 1e-5
