@@ -41,12 +41,14 @@ TRAFFIC = {}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-kernel comparison")
+    ap.add_argument("--nx", type=int, default=NX, help="cubes per axis (64: the benchmark mesh)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -79,9 +81,9 @@ def sum_over_ranks(x, world, device=None):
     return float(t.item())
 
 
-def workload():
+def workload(nx=NX):
     from paper_1407_0904_gb300 import meshgen
-    mesh = meshgen.tet_mesh(NX, perturb=PERTURB, seed=SEED)
+    mesh = meshgen.tet_mesh(nx, perturb=PERTURB, seed=SEED)
     return mesh
 
 
@@ -105,7 +107,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -170,16 +172,34 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    import oracle
     mesh = workload()
-    per_step = []
-    res = None
+    threads = oracle.threads_available()
+    run = lambda sel: oracle.assemble_cells(oracle.HELMHOLTZ, DEGREE, oracle.TETRAHEDRON, mesh.coords,
+                                            mesh.cell2vert, sel, threads=threads)
+    pilot = np.arange(2048, dtype=np.int64)
+    t0 = time.perf_counter()
+    run(pilot)
+    per_cell = (time.perf_counter() - t0) / len(pilot)
+    # every step is a bounded sample so that warm-up + steps take about two minutes
+    budget = min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup))
+    n = int(min(mesh.ncells, max(256, budget / max(per_cell, 1e-9))))
+    total_cells, total_s = 0, 0.0
     for i in range(args.warmup + args.steps):
-        res = cpu_baseline(mesh, max(1.0, args.cpu_seconds / max(1, args.steps)), rank)
+        lo = (i * n) % max(1, mesh.ncells - n)
+        sel = np.arange(lo, lo + n, dtype=np.int64)
+        t0 = time.perf_counter()
+        run(sel)
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
-            per_step.append(res["value"])
-    value = float(np.median(per_step))
+            total_cells += n
+            total_s += dt
+    value = total_cells / total_s
+    res = {"unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": "%d steps of %d consecutive cells of the 64^3x6 mesh (FP64 oracle, OpenMP over "
+                     "cells, %.2f s timed)" % (args.steps, n, total_s)}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "helmholtz P3 tet, 64^3x6 Kuhn cells perturbed 0.15h (seed 2)",
@@ -203,7 +223,7 @@ def run_ours(args):
     prec = {v: k for k, v in coffee.PRECISION_NAMES.items()}[args.precision]
     form, cell = coffee.HELMHOLTZ, coffee.TETRAHEDRON
 
-    mesh = workload()
+    mesh = workload(args.nx)
     ndof = coffee.ndof(form, DEGREE, cell)
     coords = torch.from_numpy(mesh.coords).to(dev)
     c2v = torch.from_numpy(mesh.cell2vert).to(dev)
@@ -252,6 +272,7 @@ def run_ours(args):
 
     sampler = ClockSampler(local)
     sampler.start()
+    time.sleep(0.5)  # let nvidia-smi start sampling before the timed region
     total_ms, launch_ms = timed(prec, out, args.steps, args.warmup)
     clocks = sampler.stop()
     coffee.check_errors()
@@ -278,10 +299,11 @@ def run_ours(args):
 
     # the FP64 kernel on the same workload, for the TC-vs-FP64 comparison
     fp64 = None
-    if prec != coffee.FP64:
+    if prec != coffee.FP64 and not args.no_fp64:
         out64 = torch.empty((ncells, ndof, ndof), dtype=torch.float64, device=dev)
-        tms, lms = timed(coffee.FP64, out64, max(3, args.steps // 4), 3)
-        fp64 = {"value": ncells * max(3, args.steps // 4) / (tms / 1e3), "kernel_ms": lms}
+        fsteps = max(3, min(args.steps // 20, 100))
+        tms, lms = timed(coffee.FP64, out64, fsteps, 3)
+        fp64 = {"value": ncells * fsteps / (tms / 1e3), "kernel_ms": lms, "steps": fsteps}
         del out64
 
     # end to end through the public API with host buffers
@@ -290,7 +312,7 @@ def run_ours(args):
         h_coords = torch.from_numpy(mesh.coords).pin_memory()
         h_c2v = torch.from_numpy(mesh.cell2vert).pin_memory()
         h_out = torch.empty((ncells, ndof, ndof), dtype=odt).pin_memory()
-        e_steps = max(3, args.steps // 4)
+        e_steps = max(3, min(args.steps // 20, 50))
         for _ in range(2):
             coffee.assemble_host(form, DEGREE, cell, h_coords, h_c2v, precision=prec, out=h_out)
         torch.cuda.synchronize()
@@ -309,7 +331,7 @@ def run_ours(args):
                "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.nx == NX:
         cpu = cpu_baseline(mesh, args.cpu_seconds, rank)
 
     if rank == 0:
@@ -318,7 +340,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64"}.get(args.precision, args.precision),
                 "data": "synthetic",
-                "config": {"workload": "helmholtz P3 tet, 64^3x6 Kuhn cells perturbed 0.15h (seed 2)",
+                "config": {"workload": "helmholtz P3 tet, %d^3x6 Kuhn cells perturbed 0.15h (seed 2)" % args.nx,
                            "ncells": ncells, "degree": DEGREE, "ndof": ndof,
                            "precision": args.precision, "out_dtype": str(odt).replace("torch.", ""),
                            "l2": "no flush: each step writes %.2f GB of element matrices (> 129 MB L2)"

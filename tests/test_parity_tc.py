@@ -2,7 +2,10 @@
 
 Error metric: per cell, max_ij |A - A_oracle| / max_ij |A_oracle|, maximised over cells.
 Tolerances: TF32X3 1e-5; BF16X3 1e-4 (its split leaves ~2^-16 per product, so it is
-held to a looser bound and its measured error is printed); single-pass TF32/BF16 1e-2.
+held to a looser bound and its measured error is printed); single-pass TF32 1e-2;
+single-pass BF16 2e-2: each product carries up to 2 * 2^-9 rounding error and the
+stiffness entries cancel (zero row sums), so sum_k |G_k T_k| / max|A_e| reaches 4-5 on
+P1 tetrahedra, giving about 1e-2 in the worst cell.
 Sizes span several 128-cell tiles with a ragged last tile.
 """
 import numpy as np
@@ -16,7 +19,7 @@ from tests.helpers import (TRI, TET, MASS, HELMHOLTZ, ADVDIFF, coefficients, rel
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
-TOL = {coffee.TF32X3: 1e-5, coffee.BF16X3: 1e-4, coffee.TF32: 1e-2, coffee.BF16: 1e-2}
+TOL = {coffee.TF32X3: 1e-5, coffee.BF16X3: 1e-4, coffee.TF32: 1e-2, coffee.BF16: 2e-2}
 
 
 def ragged_mesh(cell, seed):
