@@ -35,7 +35,7 @@ L2_BYTES = 129 * 2 ** 20
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # tensor-core kernel on this workload, keyed by the sha256 of the kernel source it
 # was measured on; reported as null when the source has changed since.
-TRAFFIC = {}
+TRAFFIC = {"6c29018be2a5f373": 2.487e9}  # 31.97 MB read + 2.455 GB written (two launches)
 
 
 def parse():
