@@ -223,6 +223,7 @@ int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream) {
   p.mtiles = meta.mtiles;
   p.kbytes = meta.kbytes;
   p.parts = meta.parts;
+  p.ksteps_off = meta.ksteps_off;
   p.precision = a->precision;
   p.validate = validate ? 1 : 0;
   p.nu = a->nu;

@@ -54,6 +54,7 @@ struct TcTable {
   int kelems;            // padded K (elements)
   int K;                 // true K
   int parts;             // 1 (single pass) or 2 (hi, lo)
+  int ksteps_off;        // Burgers: K-steps of the off-diagonal component blocks
   int64_t tile_bytes;    // bytes of one part of one M-tile = 128 * kbytes
 };
 
@@ -68,12 +69,17 @@ struct TcParams {
   int64_t ncells, nverts, ncoefnodes;
   int ns, N;             // outputs per cell
   int mtiles, kbytes, parts;
+  int ksteps_off;        // Burgers: K-steps of the off-diagonal component blocks
   int precision;
   int validate;
   double nu;
 };
 int tc_supported(int form, int degree, int cell, int precision);
 int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
+// Burgers-Jacobian tensor-core kernel (k_tc_burgers.cu)
+int burgers_tc_supported(int degree, int cell, int precision);
+void build_burgers_image(int degree, int cell, int prec, std::vector<uint8_t>& img, TcTable& meta);
+int launch_burgers_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
 // Build the operand image on the host
 void build_tc_image(int form, int degree, int cell, int precision, std::vector<uint8_t>& img,
                     TcTable& meta);

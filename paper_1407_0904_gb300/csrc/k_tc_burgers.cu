@@ -1,0 +1,420 @@
+// tcgen05 local assembly of the Burgers Jacobian (vector degree-k Lagrange, Listing 2's
+// problem generalised to degree k).
+//
+// The element matrix has d x d component blocks (ci, cj) of ns x ns entries. With
+// P = |det J| K = sign(det) adj and Q[r][a] = sum_c u[r][c] P[a][c], every block is a
+// contraction against fixed reference tensors:
+//   block(ci,cj) = sum_{r,a} u[r][ci] P[a][cj] T1[r,a]
+//                + [ci==cj] ( sum_{r,a} Q[r][a] T2[r,a] + nu sum_p H_p T3[p] )
+// where T1 = int d_a phi_r phi_i phi_j, T2 = int phi_r phi_i d_a phi_j and T3 the
+// stiffness pair tensors. One shared-memory A operand [T1 | T2 | T3]^T (rows = block
+// entries) serves every block: off-diagonal blocks contract over its T1 columns only,
+// diagonal blocks over all of them. Producers build one block's factors per operand
+// stage (the per-block B operand), so the operand stages stay the size of one block.
+// Pipeline roles, TMEM ring and bounded waits are those of k_tc.cu.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstring>
+#include <cmath>
+#include "coffee_internal.h"
+#include "tc_common.cuh"
+
+namespace coffee {
+namespace {
+using namespace tc;
+
+template <int D, int NS, int PREC>
+struct BurgersShape {
+  using PT = PrecTraits<PREC>;
+  static constexpr int KSTEP = PT::tf32 ? 8 : 16;
+  static constexpr int ELEM = PT::tf32 ? 4 : 2;
+  static constexpr int P = D * (D + 1) / 2;
+  static constexpr int K1 = NS * D;                          // columns of T1 (and of T2)
+  static constexpr int KA1 = round_up(K1, KSTEP);            // T1 padded: off-diagonal K
+  static constexpr int KD = round_up(KA1 + K1 + P, KSTEP);   // diagonal K
+  static constexpr int NBLK = NS * NS;
+  static constexpr int MT = (NBLK + BM - 1) / BM;
+  static constexpr int PARTS = PT::split ? 2 : 1;
+};
+
+template <int D, int NS, int PREC>
+__global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, int nstages) {
+  using S = BurgersShape<D, NS, PREC>;
+  using PT = PrecTraits<PREC>;
+  constexpr int NV = D + 1, P = S::P, KA1 = S::KA1, KD = S::KD, PARTS = S::PARTS;
+  constexpr int NB = D * D;
+  constexpr uint32_t IDESC = make_idesc(PT::tf32 ? 2 : 1, BM, BN);
+
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int kbytes = p.kbytes;  // = KD * ELEM
+  const int tile_bytes = BM * kbytes;
+  const int a_bytes = S::MT * PARTS * tile_bytes;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + a_bytes;
+  Barriers* bars = reinterpret_cast<Barriers*>(sB + nstages * PARTS * tile_bytes);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (p.ncells + BN - 1) / BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      mbar_init(smem_u32(&bars->full[s]), 128);
+      mbar_init(smem_u32(&bars->empty[s]), 1);
+    }
+    for (int r = 0; r < RING; ++r) {
+      mbar_init(smem_u32(&bars->tfull[r]), 1);
+      mbar_init(smem_u32(&bars->tempty[r]), 8);
+    }
+    mbar_init(smem_u32(&bars->done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&bars->tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(p.image);
+    uint4* dst = reinterpret_cast<uint4*>(sA);
+    for (int i = threadIdx.x; i < a_bytes / 16; i += NTHREADS) dst[i] = __ldg(src + i);
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+
+  if (warp >= PROD_WARP0 && warp < MMA_WARP) {
+    // ---------------- producers: one cell per thread, one block per stage ----------------
+    const int row = threadIdx.x - PROD_WARP0 * 32;
+    int it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int64_t e = t * BN + row;
+      float u[NS][D], Pm[D][D], Q[NS][D], H[P];
+      bool live = e < p.ncells, bad = false;
+      if (live) {
+        int vid[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          vid[v] = __ldg(p.c2v + e * NV + v);
+          if (p.validate && (vid[v] < 0 || vid[v] >= p.nverts)) bad = true;
+        }
+        int did[NS];
+#pragma unroll
+        for (int r = 0; r < NS; ++r) {
+          did[r] = __ldg(p.c2d + e * NS + r);
+          if (p.validate && (did[r] < 0 || did[r] >= p.ncoefnodes)) bad = true;
+        }
+        if (bad) {
+          atomicOr(p.err, ERR_INDEX);
+          live = false;
+        } else {
+          double X[NV][D];
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int r = 0; r < D; ++r) X[v][r] = __ldg(p.coords + (int64_t)vid[v] * D + r);
+          float adj[D][D], Dm, sg;
+          cell_geometry<D>(X, adj, Dm, sg);
+          const float inv = 1.0f / Dm;
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int c = 0; c < D; ++c) Pm[a][c] = sg * adj[a][c];
+          int q = 0;
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = a; b < D; ++b) {
+              float s = 0.f;
+#pragma unroll
+              for (int r = 0; r < D; ++r) s = fmaf(adj[a][r], adj[b][r], s);
+              H[q++] = (float)p.nu * s * inv;
+            }
+#pragma unroll
+          for (int r = 0; r < NS; ++r) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) u[r][c] = (float)__ldg(p.coef + (int64_t)did[r] * D + c);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+              float s = 0.f;
+#pragma unroll
+              for (int c = 0; c < D; ++c) s = fmaf(u[r][c], Pm[a][c], s);
+              Q[r][a] = s;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int blk = 0; blk < NB; ++blk, ++it) {
+        const int ci = blk / D, cj = blk % D;
+        const int s = it % nstages;
+        const uint32_t use = (uint32_t)(it / nstages);
+        if (!mbar_wait(smem_u32(&bars->empty[s]), (use & 1u) ^ 1u, p.err)) { ok = false; break; }
+        float G[KD];
+#pragma unroll
+        for (int k = 0; k < KD; ++k) G[k] = 0.f;
+        if (live) {
+#pragma unroll
+          for (int r = 0; r < NS; ++r)
+#pragma unroll
+            for (int a = 0; a < D; ++a) G[r * D + a] = u[r][ci] * Pm[a][cj];
+          if (ci == cj) {
+#pragma unroll
+            for (int r = 0; r < NS; ++r)
+#pragma unroll
+              for (int a = 0; a < D; ++a) G[KA1 + r * D + a] = Q[r][a];
+#pragma unroll
+            for (int q = 0; q < P; ++q) G[KA1 + S::K1 + q] = H[q];
+          }
+        }
+        uint8_t* hi = sB + (size_t)s * PARTS * tile_bytes;
+        if (ci == cj)
+          store_operand_row<PREC, KD, KD>(hi, hi + tile_bytes, row, G, kbytes);
+        else
+          store_operand_row<PREC, KD, KA1>(hi, hi + tile_bytes, row, G, kbytes);
+        fence_proxy_async();
+        mbar_arrive(smem_u32(&bars->full[s]));
+      }
+    }
+  } else if (warp == MMA_WARP) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t sbo = 8u * (uint32_t)kbytes;
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      uint32_t rc = 0;
+      int it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int blk = 0; blk < NB && ok; ++blk, ++it) {
+          const bool diag = (blk / D) == (blk % D);
+          const int ksteps = diag ? KD / S::KSTEP : KA1 / S::KSTEP;
+          const int s = it % nstages;
+          const uint32_t use = (uint32_t)(it / nstages);
+          if (!mbar_wait(smem_u32(&bars->full[s]), use & 1u, p.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t bstage = b0 + (uint32_t)(s * PARTS * tile_bytes);
+          for (int m = 0; m < S::MT; ++m, ++rc) {
+            const uint32_t slot = rc % RING, round = rc / RING;
+            if (!mbar_wait(smem_u32(&bars->tempty[slot]), (round & 1u) ^ 1u, p.err)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t d = tmem + slot * BN;
+            const uint32_t atile = a0 + (uint32_t)(m * PARTS * tile_bytes);
+            uint32_t acc = 0;
+            for (int ks = 0; ks < ksteps; ++ks) {
+              const uint32_t ko = (uint32_t)ks * 256u;
+              if constexpr (PT::split) {
+                mma<PT::tf32>(d, make_desc(atile + ko, sbo), make_desc(bstage + tile_bytes + ko, sbo), IDESC, acc);
+                acc = 1;
+                mma<PT::tf32>(d, make_desc(atile + tile_bytes + ko, sbo), make_desc(bstage + ko, sbo), IDESC, 1);
+              }
+              mma<PT::tf32>(d, make_desc(atile + ko, sbo), make_desc(bstage + ko, sbo), IDESC, acc);
+              acc = 1;
+            }
+            tc_commit(smem_u32(&bars->tfull[slot]));
+          }
+          tc_commit(smem_u32(&bars->empty[s]));
+        }
+      }
+      tc_commit(smem_u32(&bars->done));
+      mbar_wait(smem_u32(&bars->done), 0, p.err);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3, half = warp >> 2;
+    const int ndof = D * NS;
+    uint32_t rc = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int64_t cbase = t * BN + half * 64;
+      const int64_t rem = p.ncells - cbase;
+      const int ncol = rem < 64 ? (int)rem : 64;
+      for (int blk = 0; blk < NB && ok; ++blk) {
+        const int ci = blk / D, cj = blk % D;
+        for (int m = 0; m < S::MT; ++m, ++rc) {
+          const uint32_t slot = rc % RING, round = rc / RING;
+          if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) { ok = false; break; }
+          tc_fence_after();
+          const int o = m * BM + q * 32 + lane;  // entry (i, j) of the block
+          if (m * BM + q * 32 < S::NBLK && ncol > 0) {
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + slot * BN + half * 64;
+            uint32_t v0[32], v1[32];
+            tmem_ld32(taddr, v0);
+            tmem_ld32(taddr + 32, v1);
+            tmem_wait_ld();
+            if (o < S::NBLK) {
+              const int i = o / NS, j = o - (o / NS) * NS;
+              float* dst = p.out + cbase * p.N + (int64_t)(ci * NS + i) * ndof + cj * NS + j;
+              const int64_t stride = p.N;
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj)
+                if (jj < ncol) __stcs(dst + jj * stride, __uint_as_float(v0[jj]));
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj)
+                if (32 + jj < ncol) __stcs(dst + (32 + jj) * stride, __uint_as_float(v1[jj]));
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+constexpr int SMEM_LIMIT = 227 * 1024;
+constexpr int SMEM_ONE_CTA = 120 * 1024;
+
+struct BGeom {
+  int ns, K1, KA1, KD, kstep, elem, parts, mtiles, kbytes;
+};
+
+bool bgeom(int degree, int cell, int prec, BGeom& g) {
+  if (prec == PREC_FP64 || prec < 0 || prec > PREC_BF16X3) return false;
+  // compiled instances: triangles P1-P4, tetrahedra P1-P2
+  if (cell == CELL_TRI ? (degree < 1 || degree > 4) : (degree < 1 || degree > 2)) return false;
+  const int d = cell == CELL_TRI ? 2 : 3, P = d * (d + 1) / 2;
+  const bool tf32 = prec == PREC_TF32 || prec == PREC_TF32X3;
+  g.ns = nnodes(cell, degree);
+  g.kstep = tf32 ? 8 : 16;
+  g.elem = tf32 ? 4 : 2;
+  g.K1 = g.ns * d;
+  g.KA1 = (g.K1 + g.kstep - 1) / g.kstep * g.kstep;
+  g.KD = (g.KA1 + g.K1 + P + g.kstep - 1) / g.kstep * g.kstep;
+  g.parts = (prec == PREC_TF32X3 || prec == PREC_BF16X3) ? 2 : 1;
+  g.mtiles = (g.ns * g.ns + BM - 1) / BM;
+  g.kbytes = g.KD * g.elem;
+  return true;
+}
+
+int bstages(const BGeom& g) {
+  const int a = g.mtiles * g.parts * BM * g.kbytes;
+  const int b = g.parts * BN * g.kbytes;
+  const int fixed = a + (int)sizeof(Barriers) + 1024 + 64;
+  int s = MAX_STAGES;
+  while (s >= 2 && fixed + s * b > SMEM_LIMIT) --s;
+  return s >= 2 ? s : 0;
+}
+
+template <int D, int NS, int PREC>
+cudaError_t launch_b(const TcParams& p, int num_sms, cudaStream_t s, int nst, int smem) {
+  auto kern = k_burgers_tc<D, NS, PREC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (p.ncells + BN - 1) / BN;
+  const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
+  kern<<<grid, NTHREADS, smem, s>>>(p, nst);
+  return cudaGetLastError();
+}
+
+template <int D, int NS>
+cudaError_t launch_bp(const TcParams& p, int num_sms, cudaStream_t s, int nst, int smem) {
+  switch (p.precision) {
+    case PREC_TF32: return launch_b<D, NS, PREC_TF32>(p, num_sms, s, nst, smem);
+    case PREC_TF32X3: return launch_b<D, NS, PREC_TF32X3>(p, num_sms, s, nst, smem);
+    case PREC_BF16: return launch_b<D, NS, PREC_BF16>(p, num_sms, s, nst, smem);
+    case PREC_BF16X3: return launch_b<D, NS, PREC_BF16X3>(p, num_sms, s, nst, smem);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+int burgers_tc_supported(int degree, int cell, int precision) {
+  BGeom g;
+  if (!bgeom(degree, cell, precision, g)) return 0;
+  return bstages(g) > 0 ? 1 : 0;
+}
+
+void build_burgers_image(int degree, int cell, int prec, std::vector<uint8_t>& img, TcTable& meta) {
+  BGeom g;
+  bgeom(degree, cell, prec, g);
+  std::vector<double> T;
+  reference_tensor(FORM_BURGERS, degree, cell, T);
+  const int d = cell == CELL_TRI ? 2 : 3, P = d * (d + 1) / 2;
+  const int nb = g.ns * g.ns;
+  const bool tf32 = g.elem == 4;
+  const int64_t tile = (int64_t)BM * g.kbytes;
+  img.assign((size_t)(g.mtiles * g.parts * tile), 0);
+  for (int m = 0; m < g.mtiles; ++m)
+    for (int r = 0; r < BM; ++r) {
+      const int o = m * BM + r;
+      for (int k = 0; k < g.KD; ++k) {
+        int trow = -1;  // row of the reference tensor feeding A column k
+        if (k < g.K1) trow = k;
+        else if (k >= g.KA1 && k < g.KA1 + g.K1) trow = g.ns * d + (k - g.KA1);
+        else if (k >= g.KA1 + g.K1 && k < g.KA1 + g.K1 + P) trow = 2 * g.ns * d + (k - g.KA1 - g.K1);
+        const double x = (o < nb && trow >= 0) ? T[(size_t)trow * nb + o] : 0.0;
+        const uint32_t off = canon_off(r, k * g.elem, g.kbytes);
+        uint8_t* hi = img.data() + (size_t)(m * g.parts) * tile;
+        uint8_t* lo = hi + tile;
+        if (tf32) {
+          const uint32_t h = host_tf32_rna((float)x);
+          const uint32_t l = host_tf32_rna((float)(x - (double)host_f(h)));
+          std::memcpy(hi + off, &h, 4);
+          if (g.parts == 2) std::memcpy(lo + off, &l, 4);
+        } else {
+          const uint16_t h = host_bf16_rn((float)x);
+          const uint16_t l = host_bf16_rn((float)(x - (double)host_bf16_f(h)));
+          std::memcpy(hi + off, &h, 2);
+          if (g.parts == 2) std::memcpy(lo + off, &l, 2);
+        }
+      }
+    }
+  meta = TcTable{};
+  meta.mtiles = g.mtiles;
+  meta.kbytes = g.kbytes;
+  meta.kelems = g.KD;
+  meta.K = g.KA1 + g.K1 + P;
+  meta.parts = g.parts;
+  meta.ksteps_off = g.KA1 / g.kstep;
+  meta.tile_bytes = tile;
+}
+
+int launch_burgers_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why) {
+  if (p.ncells == 0) return (int)cudaSuccess;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  BGeom g{};
+  g.mtiles = p.mtiles;
+  g.parts = p.parts;
+  g.kbytes = p.kbytes;
+  const int nst = bstages(g);
+  if (nst == 0) {
+    why = "operands do not fit in shared memory";
+    return (int)cudaErrorInvalidValue;
+  }
+  int smem = g.mtiles * g.parts * BM * g.kbytes + nst * g.parts * BN * g.kbytes + (int)sizeof(Barriers) + 1024 + 64;
+  if (smem < SMEM_ONE_CTA) smem = SMEM_ONE_CTA;
+  if (cell == CELL_TRI) {
+    switch (p.ns) {
+      case 3: return (int)launch_bp<2, 3>(p, num_sms, s, nst, smem);
+      case 6: return (int)launch_bp<2, 6>(p, num_sms, s, nst, smem);
+      case 10: return (int)launch_bp<2, 10>(p, num_sms, s, nst, smem);
+      case 15: return (int)launch_bp<2, 15>(p, num_sms, s, nst, smem);
+    }
+  } else {
+    switch (p.ns) {
+      case 4: return (int)launch_bp<3, 4>(p, num_sms, s, nst, smem);
+      case 10: return (int)launch_bp<3, 10>(p, num_sms, s, nst, smem);
+    }
+  }
+  why = "no compiled Burgers instance for this degree";
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace coffee

@@ -1,0 +1,297 @@
+// Shared building blocks of the tcgen05 kernels: PTX wrappers (mbarrier, tcgen05,
+// descriptors), operand splitting into tf32/bf16 hi/lo parts, the canonical no-swizzle
+// K-major shared-memory layout, and the FP32 cell geometry with its FP64 fallback.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstring>
+#include "coffee_internal.h"
+
+namespace coffee {
+namespace tc {
+
+constexpr int BN = 128;             // cells per tile = MMA N
+constexpr int BM = 128;             // output rows per MMA = MMA M
+constexpr int NTHREADS = 13 * 32;   // 8 epilogue, 4 producer, 1 MMA warp
+constexpr int PROD_WARP0 = 8;
+constexpr int MMA_WARP = 12;
+constexpr int RING = 4;             // TMEM accumulator slots of BN columns
+constexpr int TMEM_COLS = RING * BN;
+constexpr int MAX_STAGES = 4;
+constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr float KAPPA_FP64 = 32.0f;  // Frobenius condition number above which geometry is FP64
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: true when the phase completed, false (and the error word set) on expiry.
+static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned* err) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try(bar, parity)) return true;
+    if (global_ns() - t0 > WAIT_NS) {
+      atomicOr(err, ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+// Shared-memory matrix descriptor, no swizzle, K-major canonical layout:
+// core matrices of 8 rows x 16 bytes (128 contiguous bytes); LBO = distance between
+// core matrices adjacent in K (128 B here), SBO = distance between 8-row groups.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;  // descriptor version of tcgen05
+  return d;
+}
+// Instruction descriptor: D = f32, A/B = tf32 (2) or bf16 (1), both K-major, N, M.
+__host__ __device__ constexpr uint32_t make_idesc(int ab_fmt, int M, int N) {
+  return (1u << 4) | ((uint32_t)ab_fmt << 7) | ((uint32_t)ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+template <bool TF32>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  if constexpr (TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+// 32 lanes x 32 consecutive columns of 32-bit data -> 32 registers per thread
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+        "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+        "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+        "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------- operand splitting
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+template <int PREC>
+struct PrecTraits;
+template <>
+struct PrecTraits<PREC_TF32> { static constexpr bool tf32 = true, split = false; };
+template <>
+struct PrecTraits<PREC_TF32X3> { static constexpr bool tf32 = true, split = true; };
+template <>
+struct PrecTraits<PREC_BF16> { static constexpr bool tf32 = false, split = false; };
+template <>
+struct PrecTraits<PREC_BF16X3> { static constexpr bool tf32 = false, split = true; };
+
+// Byte offset of (row r, byte kb) in a canonical K-major operand with kbytes per row.
+__host__ __device__ __forceinline__ uint32_t canon_off(int r, int kb, int kbytes) {
+  return (uint32_t)((r >> 3) * (8 * kbytes) + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15));
+}
+
+// Store the row of factors G[0..KP) for cell row r into the hi (and lo) B operand parts.
+// Only the first NCOLS columns (a multiple of the 16-byte chunk) are written.
+template <int PREC, int KP, int NCOLS = KP>
+__device__ __forceinline__ void store_operand_row(uint8_t* hi, uint8_t* lo, int r, const float (&G)[KP],
+                                                  int kbytes) {
+  using PT = PrecTraits<PREC>;
+  if constexpr (PT::tf32) {
+#pragma unroll
+    for (int c = 0; c < NCOLS / 4; ++c) {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float x = G[c * 4 + q];
+        h[q] = tf32_rna(x);
+        l[q] = tf32_rna(x - __uint_as_float(h[q]));
+      }
+      const uint32_t off = canon_off(r, c * 16, kbytes);
+      *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+      if constexpr (PT::split) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NCOLS / 8; ++c) {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float x0 = G[c * 8 + 2 * q], x1 = G[c * 8 + 2 * q + 1];
+        __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+        __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+        __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+        h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      }
+      const uint32_t off = canon_off(r, c * 16, kbytes);
+      *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+      if constexpr (PT::split) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
+__host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// 2x2 minor a*d - b*c with one rounding error on the larger product term
+__device__ __forceinline__ float minor2(float a, float d, float b, float c) {
+  const float w = b * c;
+  const float e = fmaf(-b, c, w);  // exact error of w
+  const float f = fmaf(a, d, -w);
+  return f + e;
+}
+
+// Geometry in FP32 from FP64 vertex differences; falls back to FP64 for badly
+// conditioned cells. Produces adj (K = adj/det), |det| and sign(det).
+template <int D>
+__device__ __forceinline__ void cell_geometry(const double (&X)[D + 1][D], float (&adj)[D][D], float& Dm,
+                                              float& sg) {
+  float J[D][D];
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) J[r][c] = (float)(X[c + 1][r] - X[0][r]);
+  float det;
+  if constexpr (D == 2) {
+    det = minor2(J[0][0], J[1][1], J[0][1], J[1][0]);
+    adj[0][0] = J[1][1]; adj[0][1] = -J[0][1];
+    adj[1][0] = -J[1][0]; adj[1][1] = J[0][0];
+  } else {
+    // adj[a][r] = cofactor[r][a]
+    adj[0][0] = minor2(J[1][1], J[2][2], J[1][2], J[2][1]);
+    adj[1][0] = minor2(J[1][2], J[2][0], J[1][0], J[2][2]);
+    adj[2][0] = minor2(J[1][0], J[2][1], J[1][1], J[2][0]);
+    adj[0][1] = minor2(J[0][2], J[2][1], J[0][1], J[2][2]);
+    adj[1][1] = minor2(J[0][0], J[2][2], J[0][2], J[2][0]);
+    adj[2][1] = minor2(J[0][1], J[2][0], J[0][0], J[2][1]);
+    adj[0][2] = minor2(J[0][1], J[1][2], J[0][2], J[1][1]);
+    adj[1][2] = minor2(J[0][2], J[1][0], J[0][0], J[1][2]);
+    adj[2][2] = minor2(J[0][0], J[1][1], J[0][1], J[1][0]);
+    det = fmaf(J[0][0], adj[0][0], fmaf(J[0][1], adj[1][0], J[0][2] * adj[2][0]));
+  }
+  float nj = 0.f, na = 0.f;
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      nj = fmaf(J[r][c], J[r][c], nj);
+      na = fmaf(adj[r][c], adj[r][c], na);
+    }
+  // kappa_F^2 = |J|_F^2 |adj|_F^2 / det^2
+  const bool bad = !(nj * na <= KAPPA_FP64 * KAPPA_FP64 * det * det);
+  if (bad) {
+    double Jd[D][D], A[D][D], dd;
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) Jd[r][c] = X[c + 1][r] - X[0][r];
+    if constexpr (D == 2) {
+      dd = Jd[0][0] * Jd[1][1] - Jd[0][1] * Jd[1][0];
+      A[0][0] = Jd[1][1]; A[0][1] = -Jd[0][1]; A[1][0] = -Jd[1][0]; A[1][1] = Jd[0][0];
+    } else {
+      A[0][0] = Jd[1][1] * Jd[2][2] - Jd[1][2] * Jd[2][1];
+      A[1][0] = Jd[1][2] * Jd[2][0] - Jd[1][0] * Jd[2][2];
+      A[2][0] = Jd[1][0] * Jd[2][1] - Jd[1][1] * Jd[2][0];
+      A[0][1] = Jd[0][2] * Jd[2][1] - Jd[0][1] * Jd[2][2];
+      A[1][1] = Jd[0][0] * Jd[2][2] - Jd[0][2] * Jd[2][0];
+      A[2][1] = Jd[0][1] * Jd[2][0] - Jd[0][0] * Jd[2][1];
+      A[0][2] = Jd[0][1] * Jd[1][2] - Jd[0][2] * Jd[1][1];
+      A[1][2] = Jd[0][2] * Jd[1][0] - Jd[0][0] * Jd[1][2];
+      A[2][2] = Jd[0][0] * Jd[1][1] - Jd[0][1] * Jd[1][0];
+      dd = Jd[0][0] * A[0][0] + Jd[0][1] * A[1][0] + Jd[0][2] * A[2][0];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int r = 0; r < D; ++r) adj[a][r] = (float)A[a][r];
+    det = (float)dd;
+  }
+  Dm = fabsf(det);
+  sg = det < 0.f ? -1.f : 1.f;
+}
+
+
+struct alignas(8) Barriers {
+  uint64_t full[MAX_STAGES];
+  uint64_t empty[MAX_STAGES];
+  uint64_t tfull[RING];
+  uint64_t tempty[RING];
+  uint64_t done;
+  uint32_t tmem_base;
+};
+
+// host-side operand rounding (same rounding as the device conversions)
+inline uint32_t host_tf32_rna(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0x1000u) & 0xFFFFE000u;
+  return u;
+}
+inline float host_f(uint32_t u) {
+  float x;
+  std::memcpy(&x, &u, 4);
+  return x;
+}
+inline uint16_t host_bf16_rn(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+inline float host_bf16_f(uint16_t h) { return host_f((uint32_t)h << 16); }
+
+
+}  // namespace tc
+}  // namespace coffee

@@ -14,8 +14,8 @@ import torch
 
 import paper_1407_0904_gb300 as coffee
 from paper_1407_0904_gb300 import meshgen
-from tests.helpers import (TRI, TET, MASS, HELMHOLTZ, ADVDIFF, coefficients, rel_err_per_cell,
-                           to_device, oracle_ref)
+from tests.helpers import (TRI, TET, MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC, coefficients,
+                           rel_err_per_cell, to_device, oracle_ref)
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -28,8 +28,8 @@ def ragged_mesh(cell, seed):
     return meshgen.tet_mesh(6, perturb=0.15, seed=seed, ncells=1000)  # 7 tiles + 104
 
 
-CASES = [(f, c, k, p) for f in (MASS, HELMHOLTZ, ADVDIFF) for c in (TRI, TET) for k in (1, 2, 3, 4)
-         for p in (coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16)]
+CASES = [(f, c, k, p) for f in (MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC) for c in (TRI, TET)
+         for k in (1, 2, 3, 4) for p in (coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16)]
 
 
 @pytest.mark.parametrize("form,cell,k,prec", CASES)
@@ -128,3 +128,28 @@ def test_config3_advdiff_p2_2pow20_sampled():
     # A 1 = 0 on every cell (both terms vanish on constants)
     rows = out.double().sum(dim=2).abs().amax(dim=1) / out.double().abs().amax(dim=(1, 2))
     assert rows.max().item() < 1e-5
+
+
+def test_config3_burgers_p2_2pow20_sampled():
+    """2^20 Kuhn tets, vector P2 Burgers Jacobian (nu = 0.01, u ~ N(0,1)) in TF32X3:
+    sampled cells vs the oracle."""
+    mesh = meshgen.tet_mesh(64, 64, 43, perturb=0.15, seed=3, ncells=2 ** 20)
+    coef, c2d = coefficients(BURGERS_JAC, mesh, 2, seed=3)
+    x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    out = coffee.assemble(BURGERS_JAC, 2, TET, x, c2v, cf, cd, precision=coffee.TF32X3)
+    assert out.shape == (2 ** 20, 30, 30)
+    sel = np.random.default_rng(4).choice(mesh.ncells, size=2000, replace=False)
+    sel = np.concatenate([sel, [mesh.ncells - 1]])
+    ref = oracle_ref(BURGERS_JAC, 2, TET, mesh, coef, c2d, sel=sel)
+    got = out[torch.from_numpy(sel).to(DEV)].cpu().numpy()
+    assert rel_err_per_cell(got, ref) < 1e-5
+
+
+def test_burgers_permuted_numbering_tc():
+    mesh = ragged_mesh(TET, seed=9)
+    coef, c2d = coefficients(BURGERS_JAC, mesh, 2, seed=9, permute_seed=5)
+    ref = oracle_ref(BURGERS_JAC, 2, TET, mesh, coef, c2d)
+    x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    out = coffee.assemble(BURGERS_JAC, 2, TET, x, c2v, cf, cd, precision=coffee.TF32X3, validate=True)
+    coffee.check_errors()
+    assert rel_err_per_cell(out.cpu().numpy(), ref) < 1e-5
