@@ -1,15 +1,17 @@
 #!/usr/bin/env python3
-"""Benchmark: Helmholtz P3 element matrices on 1,572,864 perturbed Kuhn tetrahedra.
+"""Benchmark of GB300 local assembly. Default workload: Helmholtz P3 element matrices on
+the 64^3 x 6 = 1,572,864-cell perturbed Kuhn mesh, tensor-core form (TF32X3).
 
 One step = one pass of the whole local-assembly path (gather -> geometry ->
-contraction -> store) over the whole mesh, i.e. one launch of the library's
-assembly kernel through the C ABI. Prints one JSON line (rank 0).
+contraction -> store) over the whole mesh: one launch of the library's assembly kernel
+through the C ABI. Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32x3|fp64|...]
-  python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+                  [--workload helmholtz-p3-tet|advdiff-p2-tet|burgers-p2-tet|...]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on bounded samples
 
 Multi-GPU (torchrun): the forward path has no exchange step, so every rank runs an
-independent replica of the workload (weak scaling); timing is max over ranks.
+independent replica of the workload (weak scaling); the time is the max over ranks.
 """
 import argparse
 import hashlib
@@ -24,18 +26,66 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+HEADLINE = "helmholtz-p3-tet"
 METRIC = "Helmholtz P3-tet element matrices/s: TC form vs FP64 kernel, % roofline"
 UNIT = "element matrices/s"
-NX = 64            # 64^3 cubes x 6 Kuhn tets = 1,572,864 cells
-DEGREE = 3
-PERTURB = 0.15
-SEED = 2
 L2_BYTES = 129 * 2 ** 20
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# tensor-core kernel on this workload, keyed by the sha256 of the kernel source it
-# was measured on; reported as null when the source has changed since.
+# tensor-core kernel on the headline workload, keyed by the sha256 prefix of the kernel
+# source it was measured on; reported as null once the source has changed.
 TRAFFIC = {"6c29018be2a5f373": 2.487e9}  # 31.97 MB read + 2.455 GB written (two launches)
+
+MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC = 0, 1, 2, 3
+TRIANGLE, TETRAHEDRON = 0, 1
+
+
+class Workload:
+    """A named benchmark case: form, degree, cell and the seeded synthetic mesh."""
+
+    def __init__(self, name, form, degree, cell, mesh_desc, make):
+        self.name, self.form, self.degree, self.cell = name, form, degree, cell
+        self.mesh_desc, self._make = mesh_desc, make
+
+    def build(self, nx=None):
+        from paper_1407_0904_gb300 import meshgen
+        mesh = self._make(meshgen, nx)
+        coef = c2d = None
+        if self.form == ADVDIFF:
+            coef, c2d, _ = meshgen.advdiff_coefficients(mesh, seed=3)
+        elif self.form == BURGERS_JAC:
+            u, c2d, _ = meshgen.burgers_coefficients(mesh, self.degree, seed=3)
+            coef = u.ravel()
+        return mesh, coef, c2d
+
+
+def _kuhn64(mg, nx):
+    return mg.tet_mesh(nx or 64, perturb=0.15, seed=2)
+
+
+def _kuhn2pow20(mg, nx):
+    if nx:
+        return mg.tet_mesh(nx, perturb=0.15, seed=3)
+    return mg.tet_mesh(64, 64, 43, perturb=0.15, seed=3, ncells=2 ** 20)
+
+
+def _tri64(mg, nx):
+    return mg.tri_mesh(nx or 64, perturb=0.2, seed=1)
+
+
+WORKLOADS = {}
+for _k in (1, 2, 3, 4):
+    WORKLOADS["helmholtz-p%d-tet" % _k] = Workload(
+        "helmholtz-p%d-tet" % _k, HELMHOLTZ, _k, TETRAHEDRON,
+        "64^3x6 Kuhn tets perturbed 0.15h (seed 2)", _kuhn64)
+WORKLOADS["advdiff-p2-tet"] = Workload("advdiff-p2-tet", ADVDIFF, 2, TETRAHEDRON,
+                                       "Kuhn 64x64x43 truncated to 2^20 tets, perturbed 0.15h (seed 3), "
+                                       "eps~U[0.5,1.5], b~U[-1,1]^3 per vertex", _kuhn2pow20)
+WORKLOADS["burgers-p2-tet"] = Workload("burgers-p2-tet", BURGERS_JAC, 2, TETRAHEDRON,
+                                       "Kuhn 64x64x43 truncated to 2^20 tets, perturbed 0.15h (seed 3), "
+                                       "vector P2 u~N(0,1), nu=0.01", _kuhn2pow20)
+WORKLOADS["helmholtz-p1-tri"] = Workload("helmholtz-p1-tri", HELMHOLTZ, 1, TRIANGLE,
+                                         "unit square 64x64x2 triangles perturbed 0.2h (seed 1)", _tri64)
 
 
 def parse():
@@ -44,56 +94,43 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="tf32x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-kernel comparison")
-    ap.add_argument("--nx", type=int, default=NX, help="cubes per axis (64: the benchmark mesh)")
+    ap.add_argument("--nx", type=int, default=None, help="smaller mesh (cells per axis) for profiling")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def max_over_ranks(x, world, device=None):
-    """Max of a float over ranks (identity for one rank)."""
+def reduce_over_ranks(x, world, op, device=None):
+    """Max or sum of a float over ranks (identity for one rank)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
     t = torch.tensor([x], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
 
 
-def sum_over_ranks(x, world, device=None):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
-
-
-def workload(nx=NX):
-    from paper_1407_0904_gb300 import meshgen
-    mesh = meshgen.tet_mesh(nx, perturb=PERTURB, seed=SEED)
-    return mesh
-
-
-def alg_bytes_per_cell(mesh, ndof, out_bytes):
-    """Algorithmic HBM bytes per cell: cell2vert + coords (each once) + the element matrix."""
-    return 4 * 4 + 8 * 3 * mesh.nverts / mesh.ncells + out_bytes * ndof * ndof
+def alg_bytes_per_cell(wl, mesh, c2d, coef, ndof, out_bytes):
+    """Algorithmic HBM bytes per cell: every input once, plus the element matrix."""
+    d = 2 if wl.cell == TRIANGLE else 3
+    b = 4 * (d + 1) + 8 * d * mesh.nverts / mesh.ncells + out_bytes * ndof * ndof
+    if c2d is not None:
+        b += 4 * c2d.shape[1] + 8 * coef.size / mesh.ncells
+    return b
 
 
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -121,7 +158,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
@@ -130,6 +167,7 @@ class ClockSampler:
             try:
                 sm.append(float(f[1]))
                 mx.append(float(f[2]))
+                pw.append(float(f[3]))
             except ValueError:
                 continue
             for n, v in zip(names, f[5:9]):
@@ -138,7 +176,8 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "power_w_max": float(max(pw)) if pw else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
 
 
 def kernel_source_sha():
@@ -148,24 +187,41 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def cpu_baseline(mesh, target_seconds, rank):
+def oracle_cells(wl, mesh, coef, c2d, sel, threads=0):
+    import oracle
+    return oracle.assemble_cells(wl.form, wl.degree, wl.cell, mesh.coords, mesh.cell2vert, sel,
+                                 coef, c2d, threads=threads)
+
+
+def cpu_baseline(wl, mesh, coef, c2d, target_seconds):
     """The FP64 oracle, as it stands, on a bounded prefix of the same workload."""
     import oracle
     threads = oracle.threads_available()
     pilot = np.arange(min(2048, mesh.ncells), dtype=np.int64)
     t0 = time.perf_counter()
-    oracle.assemble_cells(oracle.HELMHOLTZ, DEGREE, oracle.TETRAHEDRON, mesh.coords,
-                          mesh.cell2vert, pilot, threads=threads)
+    oracle_cells(wl, mesh, coef, c2d, pilot, threads)
     per = (time.perf_counter() - t0) / len(pilot)
     n = int(min(mesh.ncells, max(len(pilot), target_seconds / max(per, 1e-9))))
     sel = np.arange(n, dtype=np.int64)
     t0 = time.perf_counter()
-    oracle.assemble_cells(oracle.HELMHOLTZ, DEGREE, oracle.TETRAHEDRON, mesh.coords,
-                          mesh.cell2vert, sel, threads=threads)
+    oracle_cells(wl, mesh, coef, c2d, sel, threads)
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "first %d of %d cells of the same mesh (FP64 oracle, OpenMP over cells, %.1f s)"
                       % (n, mesh.ncells, dt)}
+
+
+def metric_of(wl):
+    if wl.name == HEADLINE:
+        return METRIC
+    return "%s P%d-%s element matrices/s" % (["Mass", "Helmholtz", "Advection-diffusion", "Burgers Jacobian"][wl.form],
+                                             wl.degree, "tri" if wl.cell == TRIANGLE else "tet")
+
+
+def mesh_desc_of(wl, nx, mesh):
+    if nx is None:
+        return wl.mesh_desc
+    return "%d cells (reduced mesh, %d per axis)" % (mesh.ncells, nx)
 
 
 def run_reference(args):
@@ -173,13 +229,12 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    mesh = workload()
+    wl = WORKLOADS[args.workload]
+    mesh, coef, c2d = wl.build(args.nx)
     threads = oracle.threads_available()
-    run = lambda sel: oracle.assemble_cells(oracle.HELMHOLTZ, DEGREE, oracle.TETRAHEDRON, mesh.coords,
-                                            mesh.cell2vert, sel, threads=threads)
-    pilot = np.arange(2048, dtype=np.int64)
+    pilot = np.arange(min(2048, mesh.ncells), dtype=np.int64)
     t0 = time.perf_counter()
-    run(pilot)
+    oracle_cells(wl, mesh, coef, c2d, pilot, threads)
     per_cell = (time.perf_counter() - t0) / len(pilot)
     # every step is a bounded sample so that warm-up + steps take about two minutes
     budget = min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup))
@@ -189,22 +244,22 @@ def run_reference(args):
         lo = (i * n) % max(1, mesh.ncells - n)
         sel = np.arange(lo, lo + n, dtype=np.int64)
         t0 = time.perf_counter()
-        run(sel)
+        oracle_cells(wl, mesh, coef, c2d, sel, threads)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             total_cells += n
             total_s += dt
     value = total_cells / total_s
-    res = {"unit": UNIT, "cores": threads, "kind": "oracle",
-           "sample": "%d steps of %d consecutive cells of the 64^3x6 mesh (FP64 oracle, OpenMP over "
+    cpu = {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": "%d steps of %d consecutive cells of the benchmark mesh (FP64 oracle, OpenMP over "
                      "cells, %.2f s timed)" % (args.steps, n, total_s)}
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "helmholtz P3 tet, 64^3x6 Kuhn cells perturbed 0.15h (seed 2)",
-                       "ncells": mesh.ncells, "degree": DEGREE},
-            "cpu_baseline": dict(res, value=value),
+    line = {"impl": "reference", "metric": metric_of(wl), "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "%s, %s" % (wl.name, mesh_desc_of(wl, args.nx, mesh)),
+                       "ncells": mesh.ncells, "degree": wl.degree},
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -221,12 +276,17 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = {v: k for k, v in coffee.PRECISION_NAMES.items()}[args.precision]
-    form, cell = coffee.HELMHOLTZ, coffee.TETRAHEDRON
+    wl = WORKLOADS[args.workload]
+    form, cell, degree = wl.form, wl.cell, wl.degree
+    if not coffee.supported(form, degree, cell, prec):
+        raise SystemExit("no kernel for %s in %s" % (wl.name, args.precision))
 
-    mesh = workload(args.nx)
-    ndof = coffee.ndof(form, DEGREE, cell)
+    mesh, coef_np, c2d_np = wl.build(args.nx)
+    ndof = coffee.ndof(form, degree, cell)
     coords = torch.from_numpy(mesh.coords).to(dev)
     c2v = torch.from_numpy(mesh.cell2vert).to(dev)
+    coef = None if coef_np is None else torch.from_numpy(coef_np).to(dev)
+    c2d = None if c2d_np is None else torch.from_numpy(c2d_np).to(dev)
     ncells = mesh.ncells
     out_bytes = 8 if prec == coffee.FP64 else 4
     odt = torch.float64 if prec == coffee.FP64 else torch.float32
@@ -234,17 +294,15 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step(precision, o):
-        coffee.assemble(form, DEGREE, cell, coords, c2v, precision=precision, out=o)
+        coffee.assemble(form, degree, cell, coords, c2v, coef, c2d, precision=precision, out=o)
 
     # parity spot check of the benchmarked configuration against the oracle
     step(prec, out)
     coffee.check_errors()
     max_err = None
     if rank == 0:
-        import oracle
-        sel = np.random.default_rng(0).choice(ncells, size=512, replace=False)
-        ref = oracle.assemble_cells(oracle.HELMHOLTZ, DEGREE, oracle.TETRAHEDRON, mesh.coords,
-                                    mesh.cell2vert, sel)
+        sel = np.random.default_rng(0).choice(ncells, size=min(512, ncells), replace=False)
+        ref = oracle_cells(wl, mesh, coef_np, c2d_np, sel)
         got = out[torch.from_numpy(sel).to(dev)].double().cpu().numpy()
         max_err = float(np.max(np.abs(got - ref).reshape(len(sel), -1).max(1)
                                / np.abs(ref).reshape(len(sel), -1).max(1)))
@@ -266,9 +324,7 @@ def run_ours(args):
             b.record(stream)
         t1.record(stream)
         torch.cuda.synchronize()
-        total_ms = t0.elapsed_time(t1)
-        per_launch = [a.elapsed_time(b) for a, b in evs]
-        return total_ms, float(np.mean(per_launch))
+        return t0.elapsed_time(t1), float(np.mean([a.elapsed_time(b) for a, b in evs]))
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -276,12 +332,12 @@ def run_ours(args):
     total_ms, launch_ms = timed(prec, out, args.steps, args.warmup)
     clocks = sampler.stop()
     coffee.check_errors()
-    total_ms = max_over_ranks(total_ms, world, dev)
+    total_ms = reduce_over_ranks(total_ms, world, "max", dev)
     ms_per_step = total_ms / args.steps
-    value = sum_over_ranks(ncells * args.steps, world, dev) / (total_ms / 1e3)
+    value = reduce_over_ranks(ncells * args.steps, world, "sum", dev) / (total_ms / 1e3)
 
     # roofline of the dominant (only) kernel: algorithmic bytes per launch / launch time
-    per_cell = alg_bytes_per_cell(mesh, ndof, out_bytes)
+    per_cell = alg_bytes_per_cell(wl, mesh, c2d_np, coef_np, ndof, out_bytes)
     achieved = per_cell * ncells / (launch_ms / 1e3) / 1e9
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -289,15 +345,13 @@ def run_ours(args):
         peaks = json.load(open(pk))
     peak = float(peaks.get("hbm_gbs", 6800.0))
     sha = kernel_source_sha()
-    traffic = TRAFFIC.get(sha) if prec != coffee.FP64 else None
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+    traffic = TRAFFIC.get(sha) if (prec != coffee.FP64 and wl.name == HEADLINE and args.nx is None) else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "alg_bytes_per_cell": per_cell, "kernel_ms": launch_ms}
     if prec == coffee.FP64:
-        roof["note"] = "FP64 kernel: bound by FP64 ALU, HBM fraction reported for context"
+        roof["note"] = "FP64 kernel: bound by the FP64 ALU (1.25 TFLOP/s measured); HBM fraction for context"
 
-    # the FP64 kernel on the same workload, for the TC-vs-FP64 comparison
     fp64 = None
     if prec != coffee.FP64 and not args.no_fp64:
         out64 = torch.empty((ncells, ndof, ndof), dtype=torch.float64, device=dev)
@@ -311,10 +365,14 @@ def run_ours(args):
     if not args.no_e2e:
         h_coords = torch.from_numpy(mesh.coords).pin_memory()
         h_c2v = torch.from_numpy(mesh.cell2vert).pin_memory()
+        h_coef = None if coef_np is None else torch.from_numpy(coef_np).pin_memory()
+        h_c2d = None if c2d_np is None else torch.from_numpy(c2d_np).pin_memory()
         h_out = torch.empty((ncells, ndof, ndof), dtype=odt).pin_memory()
         e_steps = max(3, min(args.steps // 20, 50))
+        call = lambda: coffee.assemble_host(form, degree, cell, h_coords, h_c2v, h_coef, h_c2d,
+                                            precision=prec, out=h_out)
         for _ in range(2):
-            coffee.assemble_host(form, DEGREE, cell, h_coords, h_c2v, precision=prec, out=h_out)
+            call()
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -322,32 +380,31 @@ def run_ours(args):
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(e_steps):
-            coffee.assemble_host(form, DEGREE, cell, h_coords, h_c2v, precision=prec, out=h_out)
+            call()
         b.record(stream)
         torch.cuda.synchronize()
-        ems = max_over_ranks(a.elapsed_time(b), world, dev)
-        e2e = {"value": sum_over_ranks(ncells * e_steps, world, dev) / (ems / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(h_coords.numel() * 8 + h_c2v.numel() * 4),
-               "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())}
+        ems = reduce_over_ranks(a.elapsed_time(b), world, "max", dev)
+        h2d = h_coords.numel() * 8 + h_c2v.numel() * 4
+        if h_coef is not None:
+            h2d += h_coef.numel() * 8 + h_c2d.numel() * 4
+        e2e = {"value": reduce_over_ranks(ncells * e_steps, world, "sum", dev) / (ems / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.nx == NX:
-        cpu = cpu_baseline(mesh, args.cpu_seconds, rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.nx is None:
+        cpu = cpu_baseline(wl, mesh, coef_np, c2d_np, args.cpu_seconds)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        line = {"metric": metric_of(wl), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp64": "f64"}.get(args.precision, args.precision),
-                "data": "synthetic",
-                "config": {"workload": "helmholtz P3 tet, %d^3x6 Kuhn cells perturbed 0.15h (seed 2)" % args.nx,
-                           "ncells": ncells, "degree": DEGREE, "ndof": ndof,
+                "dtype": {"fp64": "f64"}.get(args.precision, args.precision), "data": "synthetic",
+                "config": {"workload": "%s, %s" % (wl.name, mesh_desc_of(wl, args.nx, mesh)),
+                           "ncells": ncells, "degree": degree, "ndof": ndof,
                            "precision": args.precision, "out_dtype": str(odt).replace("torch.", ""),
-                           "l2": "no flush: each step writes %.2f GB of element matrices (> 129 MB L2)"
-                                 % (ncells * ndof * ndof * out_bytes / 1e9),
+                           "l2": l2_note(ncells * ndof * ndof * out_bytes),
                            "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roof, "max_rel_err_vs_oracle": max_err,
-                "fp64_kernel": fp64,
+                "roofline": roof, "max_rel_err_vs_oracle": max_err, "fp64_kernel": fp64,
                 "tc_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
                 "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": args.steps,
                 "clocks": clocks, "kernel_sha": sha}
@@ -355,6 +412,12 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def l2_note(out_bytes):
+    if out_bytes > L2_BYTES:
+        return "no flush: each step writes %.2f GB of element matrices (> 129 MB L2)" % (out_bytes / 1e9)
+    return "output %.2f MB fits in L2: no flush, a latency-bound small case" % (out_bytes / 1e6)
 
 
 def main():
