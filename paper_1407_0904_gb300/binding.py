@@ -250,3 +250,51 @@ def assemble_host(form, degree, cell, coords, cell2vert, coef=None, cell2dof=Non
             out[lo:hi].copy_(d_out[lo:hi], non_blocking=True)
     main.wait_stream(side)
     return out
+
+
+def assemble_backward(form, degree, cell, coords, cell2vert, dout, coef=None, cell2dof=None,
+                      precision=FP64, d_coords=None, d_coef=None, deterministic=False,
+                      validate=False, nu=0.01, stream=None):
+    """Adjoint of assemble: accumulates dL/dcoords (and dL/dcoef) for dout = dL/dA.
+
+    dout is float64 for precision FP64 and float32 otherwise. Returns (d_coords, d_coef);
+    tensors passed in are accumulated into (+=), missing ones start at zero."""
+    odt = torch.float64 if precision == FP64 else torch.float32
+    a, _ = make_args(form, degree, cell, coords, cell2vert, coef, cell2dof, precision,
+                     _dev(dout, odt, "dout"), nu, validate)
+    if d_coords is None:
+        d_coords = torch.zeros_like(coords)
+    _dev(d_coords, torch.float64, "d_coords")
+    if coef is not None and form == ADVDIFF:
+        if d_coef is None:
+            d_coef = torch.zeros_like(coef)
+        _dev(d_coef, torch.float64, "d_coef")
+    else:
+        d_coef = None
+    _check(lib().coffee_assemble_backward(ctypes.byref(a), _ptr(dout), _ptr(d_coords), _ptr(d_coef),
+                                          1 if deterministic else 0, _stream_handle(stream)))
+    return d_coords, d_coef
+
+
+class AssembleFn(torch.autograd.Function):
+    """Element matrices as a differentiable function of vertex coordinates and coefficients.
+
+    AssembleFn.apply(coords, coef, cell2vert, cell2dof, form, degree, cell, precision,
+    deterministic) -> [ncells, ndof, ndof]; backward gives dL/dcoords and dL/dcoef through
+    the library's adjoint kernel (geometry recomputed, not stored)."""
+
+    @staticmethod
+    def forward(ctx, coords, coef, cell2vert, cell2dof, form, degree, cell, precision=FP64,
+                deterministic=False):
+        out = assemble(form, degree, cell, coords, cell2vert, coef, cell2dof, precision=precision)
+        ctx.save_for_backward(coords, coef, cell2vert, cell2dof)
+        ctx.meta = (form, degree, cell, precision, deterministic)
+        return out
+
+    @staticmethod
+    def backward(ctx, dout):
+        coords, coef, c2v, c2d = ctx.saved_tensors
+        form, degree, cell, precision, deterministic = ctx.meta
+        dc, dk = assemble_backward(form, degree, cell, coords, c2v, dout.contiguous(), coef, c2d,
+                                   precision=precision, deterministic=deterministic)
+        return dc, dk, None, None, None, None, None, None, None

@@ -1,6 +1,7 @@
 // C-ABI entry points of libcoffee.so (declared in include/coffee.h): argument
 // validation, the per-device cache of reference tensors, and kernel dispatch.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -256,8 +257,78 @@ int coffee_assemble(int form, int degree, int cell, const double* coords, const 
 
 int coffee_assemble_backward(const coffee_assemble_args* a, const void* dout, double* d_coords,
                              double* d_coef, int deterministic, coffee_stream_t stream) {
-  (void)a; (void)dout; (void)d_coords; (void)d_coef; (void)deterministic; (void)stream;
-  return fail(COFFEE_ERR_UNSUPPORTED, "backward pass not built yet");
+  int rc = check_args(a);
+  if (rc != COFFEE_OK || a->ncells == 0) return rc;
+  if (a->form == FORM_BURGERS)
+    return fail(COFFEE_ERR_UNSUPPORTED, "no GPU adjoint for the Burgers Jacobian");
+  if (!dout || !d_coords) return fail(COFFEE_ERR_INVALID_ARG, "dout and d_coords must be non-NULL");
+  if (deterministic && (a->nverts <= 0 || (a->form == FORM_ADVDIFF && d_coef && a->ncoefnodes <= 0)))
+    return fail(COFFEE_ERR_INVALID_ARG, "deterministic mode needs nverts (and ncoefnodes)");
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceCache* c = nullptr;
+  if ((rc = device_cache(&c)) != COFFEE_OK) return rc;
+  const double* T = nullptr;
+  if ((rc = fp64_table(*c, a->form, a->degree, a->cell, &T)) != COFFEE_OK) return rc;
+  const int d = a->cell == CELL_TRI ? 2 : 3;
+  const int ns = nnodes(a->cell, a->degree);
+  BwdParams p{};
+  p.coords = a->coords;
+  p.c2v = a->cell2vert;
+  p.coef = a->coef;
+  p.c2d = a->cell2dof;
+  p.T = T;
+  p.dout = dout;
+  p.dout_fp32 = a->precision != PREC_FP64;
+  p.d_coords = d_coords;
+  p.d_coef = a->form == FORM_ADVDIFF ? d_coef : nullptr;
+  p.err = c->err;
+  p.ncells = a->ncells;
+  p.nverts = a->nverts;
+  p.ncoefnodes = a->ncoefnodes;
+  p.N = ns * ns;
+  p.validate = (a->flags & COFFEE_FLAG_VALIDATE) ? 1 : 0;
+  cudaStream_t s = stream;
+  if (!deterministic) {
+    cudaError_t e = (cudaError_t)launch_backward(a->form, a->cell, p, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launch(assemble_backward)");
+    return COFFEE_OK;
+  }
+  // deterministic: per-cell contributions, then per-node sums in increasing cell order.
+  // Scratch is stream-ordered (cudaMallocAsync / cudaFreeAsync on `stream`).
+  const int nl = bwd_local_len(a->form, a->cell);
+  const int64_t nn = std::max<int64_t>(a->nverts, p.d_coef ? a->ncoefnodes : 0);
+  const int64_t width = d + 1;
+  const size_t b_local = sizeof(double) * (size_t)a->ncells * nl;
+  const size_t b_cnt = sizeof(int32_t) * (size_t)nn;
+  const size_t b_off = sizeof(int64_t) * (size_t)(nn + 1);
+  const size_t b_slots = sizeof(int64_t) * (size_t)(a->ncells * width);
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t total = al(b_local) + 2 * al(b_cnt) + al(b_off) + al(b_slots);
+  uint8_t* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), total, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(backward scratch)");
+  double* local = reinterpret_cast<double*>(ws);
+  int32_t* cnt = reinterpret_cast<int32_t*>(ws + al(b_local));
+  int32_t* cur = reinterpret_cast<int32_t*>(ws + al(b_local) + al(b_cnt));
+  int64_t* off = reinterpret_cast<int64_t*>(ws + al(b_local) + 2 * al(b_cnt));
+  int64_t* slots = reinterpret_cast<int64_t*>(ws + al(b_local) + 2 * al(b_cnt) + al(b_off));
+  p.local = local;
+  e = (cudaError_t)launch_backward(a->form, a->cell, p, s);
+  if (e == cudaSuccess)
+    e = (cudaError_t)launch_ordered_sum(a->cell2vert, a->ncells, (int)width, a->nverts, local, nl, 0, d,
+                                        d_coords, d, 0, cnt, cur, off, slots, c->err, s);
+  if (e == cudaSuccess && p.d_coef) {
+    e = (cudaError_t)launch_ordered_sum(a->cell2dof, a->ncells, (int)width, a->ncoefnodes, local, nl,
+                                        (d + 1) * d, 1, d_coef, d + 1, 0, cnt, cur, off, slots, c->err, s);
+    if (e == cudaSuccess)
+      e = (cudaError_t)launch_ordered_sum(a->cell2dof, a->ncells, (int)width, a->ncoefnodes, local, nl,
+                                          (d + 1) * d + (d + 1), d, d_coef, d + 1, 1, cnt, cur, off, slots,
+                                          c->err, s);
+  }
+  cudaError_t e2 = cudaFreeAsync(ws, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launch(deterministic backward)");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(backward scratch)");
+  return COFFEE_OK;
 }
 
 int coffee_check_errors(coffee_stream_t stream) {

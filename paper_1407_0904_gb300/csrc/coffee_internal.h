@@ -43,6 +43,30 @@ struct Fp64Params {
 // returns cudaError_t as int
 int launch_fp64(int form, int cell, const Fp64Params& p, void* stream);
 
+// ---- adjoint (k_bwd.cu) ----
+struct BwdParams {
+  const double* coords;
+  const int32_t* c2v;
+  const double* coef;
+  const int32_t* c2d;
+  const double* T;       // FP64 reference tensors [K][N]
+  const void* dout;      // [ncells][N], double or float
+  int dout_fp32;
+  double* d_coords;      // accumulated (atomic mode)
+  double* d_coef;        // accumulated (atomic mode), may be NULL
+  double* local;         // deterministic mode: per-cell contributions [ncells][nl], else NULL
+  unsigned* err;
+  int64_t ncells, nverts, ncoefnodes;
+  int N;
+  int validate;
+};
+int bwd_local_len(int form, int cell);
+int launch_backward(int form, int cell, const BwdParams& p, void* stream);
+int launch_ordered_sum(const int32_t* idx, int64_t ncells, int width, int64_t nnodes, const double* local,
+                       int nl, int base, int comps, double* grad, int grad_stride, int grad_off,
+                       int32_t* cnt, int32_t* cursor, int64_t* off, int64_t* slots, unsigned* err,
+                       void* stream);
+
 // ---- tcgen05 tensor-core contraction (k_tc.cu) ----
 // Operand image of the reference tensor for the tensor cores: for each M-tile of
 // 128 output rows, the hi part then (split precisions) the lo part, each
