@@ -166,6 +166,29 @@ int coffee_assemble_backward(const coffee_assemble_args* a, const void* dout,
                              double* d_coords, double* d_coef, int deterministic,
                              coffee_stream_t stream);
 
+/* Allocation-free deterministic adjoint. The paper has no counterpart: this exists for
+ * callers that cannot allocate device memory while they run -- latency-critical loops
+ * that must avoid cudaMalloc/cudaFree (they can synchronise the device), applications
+ * whose device memory belongs to their own pool or caching allocator, and fixed-budget
+ * deployments. It computes exactly what coffee_assemble_backward(a, dout, d_coords,
+ * d_coef, deterministic = 1, stream) computes (same kernels, same summation order) but
+ * allocates nothing: its scratch is one fixed device array inside the library (about
+ * 4.4 MB, reserved on every GPU that loads the library until the process exits).
+ *   limits: ncells <= 16384; 1 <= nverts <= 16384; for ADVDIFF with d_coef,
+ *           1 <= ncoefnodes <= 16384; forms MASS, HELMHOLTZ, ADVDIFF (BURGERS_JAC returns
+ *           COFFEE_ERR_UNSUPPORTED); larger inputs return COFFEE_ERR_INVALID_ARG with a
+ *           message naming the limit. COFFEE_FLAG_VALIDATE is rejected: indices must be
+ *           in range (check them first with coffee_assemble_backward and the flag).
+ *   arguments: as coffee_assemble_backward; d_coords/d_coef are accumulated (+=).
+ *   set-up: the first call on a device looks up the array's device address
+ *           (cudaGetSymbolAddress) with that device current; make that first call
+ *           before any stream capture.
+ *   sharing: every call on a device uses the same array and leaves its contents behind;
+ *           each call clears what must start at zero. Calls that overlap on the GPU
+ *           (other streams, other host threads) race on the array: serialise them. */
+int coffee_assemble_backward_noalloc(const coffee_assemble_args* a, const void* dout,
+                                     double* d_coords, double* d_coef, coffee_stream_t stream);
+
 /* Device error word: synchronises `stream`, returns COFFEE_ERR_DEVICE_INDEX if a
  * validated launch met an out-of-range index, COFFEE_ERR_TIMEOUT if a kernel wait
  * gave up, COFFEE_OK otherwise, and clears the word. */

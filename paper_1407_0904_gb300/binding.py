@@ -298,3 +298,24 @@ class AssembleFn(torch.autograd.Function):
         dc, dk = assemble_backward(form, degree, cell, coords, c2v, dout.contiguous(), coef, c2d,
                                    precision=precision, deterministic=deterministic)
         return dc, dk, None, None, None, None, None, None, None
+
+
+def assemble_backward_noalloc(form, degree, cell, coords, cell2vert, dout, coef=None, cell2dof=None,
+                              precision=FP64, d_coords=None, d_coef=None, stream=None):
+    """The allocation-free adjoint (coffee_assemble_backward_noalloc): the same result as
+    assemble_backward(..., deterministic=True) without any device allocation inside the
+    library; at most 16384 cells and 16384 vertices / coefficient nodes."""
+    L = lib()
+    L.coffee_assemble_backward_noalloc.argtypes = [ctypes.POINTER(AssembleArgs), ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    odt = torch.float64 if precision == FP64 else torch.float32
+    a, _ = make_args(form, degree, cell, coords, cell2vert, coef, cell2dof, precision,
+                     _dev(dout, odt, "dout"), 0.01, False)
+    if d_coords is None:
+        d_coords = torch.zeros_like(coords)
+    if coef is not None and form == ADVDIFF and d_coef is None:
+        d_coef = torch.zeros_like(coef)
+    _check(L.coffee_assemble_backward_noalloc(ctypes.byref(a), _ptr(dout), _ptr(d_coords),
+                                              _ptr(d_coef if form == ADVDIFF else None),
+                                              _stream_handle(stream)))
+    return d_coords, (d_coef if form == ADVDIFF else None)
