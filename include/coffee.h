@@ -189,6 +189,21 @@ int coffee_assemble_backward(const coffee_assemble_args* a, const void* dout,
 int coffee_assemble_backward_noalloc(const coffee_assemble_args* a, const void* dout,
                                      double* d_coords, double* d_coef, coffee_stream_t stream);
 
+/* Mixed batch: several (form, degree, cell) groups assembled by ONE persistent launch
+ * (the paper runs one specialised kernel per form, degree and cell shape, sections 4-5).
+ * Each group is a coffee_assemble_args (its own inputs, output and cell count); all groups
+ * share one tensor-core precision and are MASS, HELMHOLTZ or ADVDIFF. The plan (host)
+ * uploads the groups' tables, cuts every group into 128-cell tiles and gives each CTA a
+ * contiguous range of tiles of about equal cost (bytes written + item_overhead per
+ * 128-output slice). Planning allocates device memory and synchronises; launching only
+ * enqueues one kernel, so it can be captured in a CUDA graph. The plan refers to the
+ * groups' device buffers, which must stay valid while it is launched.
+ *   grid <= 0 selects one CTA per SM; item_overhead < 0 selects the default (16384). */
+int coffee_batch_plan(const coffee_assemble_args* groups, int ngroups, int grid, double item_overhead,
+                      void** plan);
+int coffee_batch_launch(void* plan, coffee_stream_t stream);
+void coffee_batch_free(void* plan);
+
 /* Device error word: synchronises `stream`, returns COFFEE_ERR_DEVICE_INDEX if a
  * validated launch met an out-of-range index, COFFEE_ERR_TIMEOUT if a kernel wait
  * gave up, COFFEE_OK otherwise, and clears the word. */

@@ -319,3 +319,45 @@ def assemble_backward_noalloc(form, degree, cell, coords, cell2vert, dout, coef=
                                               _ptr(d_coef if form == ADVDIFF else None),
                                               _stream_handle(stream)))
     return d_coords, (d_coef if form == ADVDIFF else None)
+
+
+class BatchPlan:
+    """Several (form, degree, cell) groups assembled by one persistent launch.
+
+    groups: list of dicts with keys form, degree, cell, coords, cell2vert and optionally
+    coef, cell2dof, out. All groups use `precision` (a tensor-core precision).
+    launch() only enqueues one kernel on the current stream (CUDA-graph capturable)."""
+
+    def __init__(self, groups, precision=TF32X3, grid=0, item_overhead=-1.0, validate=False):
+        L = lib()
+        L.coffee_batch_plan.argtypes = [ctypes.POINTER(AssembleArgs), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]
+        L.coffee_batch_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.coffee_batch_free.argtypes = [ctypes.c_void_p]
+        self._keep = []
+        self.outputs = []
+        arr = (AssembleArgs * len(groups))()
+        for i, g in enumerate(groups):
+            a, out = make_args(g["form"], g["degree"], g["cell"], g["coords"], g["cell2vert"],
+                               g.get("coef"), g.get("cell2dof"), precision, g.get("out"),
+                               g.get("nu", 0.01), validate)
+            arr[i] = a
+            self.outputs.append(out)
+            self._keep.append((g["coords"], g["cell2vert"], g.get("coef"), g.get("cell2dof"), out))
+        self._plan = ctypes.c_void_p()
+        _check(L.coffee_batch_plan(arr, len(groups), grid, item_overhead, ctypes.byref(self._plan)))
+
+    def launch(self, stream=None):
+        _check(lib().coffee_batch_launch(self._plan, _stream_handle(stream)))
+        return self.outputs
+
+    def free(self):
+        if self._plan:
+            lib().coffee_batch_free(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

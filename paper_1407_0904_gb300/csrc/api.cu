@@ -354,4 +354,136 @@ int coffee_check_errors(coffee_stream_t stream) {
 
 const char* coffee_last_error(void) { return g_last_error.c_str(); }
 
+namespace {
+struct BatchPlanImpl {
+  BatchLaunch L{};
+  BatchGroup* d_groups = nullptr;
+  int64_t* d_ranges = nullptr;
+  int device = 0;
+};
+}  // namespace
+
+int coffee_batch_plan(const coffee_assemble_args* groups, int ngroups, int grid, double item_overhead,
+                      void** plan) {
+  if (!plan) return fail(COFFEE_ERR_INVALID_ARG, "plan is NULL");
+  *plan = nullptr;
+  if (!groups || ngroups <= 0) return fail(COFFEE_ERR_INVALID_ARG, "no groups");
+  const int prec = groups[0].precision;
+  if (prec == PREC_FP64) return fail(COFFEE_ERR_UNSUPPORTED, "batches run on the tensor cores (not FP64)");
+  for (int i = 0; i < ngroups; ++i) {
+    int rc = check_args(&groups[i]);
+    if (rc != COFFEE_OK) return rc;
+    if (groups[i].precision != prec) return fail(COFFEE_ERR_INVALID_ARG, "all groups must share one precision");
+    if (groups[i].form == FORM_BURGERS)
+      return fail(COFFEE_ERR_UNSUPPORTED, "the mixed batch covers MASS, HELMHOLTZ and ADVDIFF");
+  }
+  if (item_overhead < 0) item_overhead = 16384.0;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceCache* c = nullptr;
+  int rc = device_cache(&c);
+  if (rc != COFFEE_OK) return rc;
+  std::vector<BatchGroup> hg(ngroups);
+  std::vector<double> cost;  // per work item
+  int kbytes_max = 32, parts = 1;
+  int64_t items = 0;
+  for (int i = 0; i < ngroups; ++i) {
+    const coffee_assemble_args* a = &groups[i];
+    TcTable meta{};
+    if ((rc = tc_table(*c, a->form, a->degree, a->cell, prec, &meta)) != COFFEE_OK) return rc;
+    const int ns = nnodes(a->cell, a->degree);
+    BatchGroup& g = hg[i];
+    std::memset(&g, 0, sizeof(g));
+    g.p.coords = a->coords;
+    g.p.c2v = a->cell2vert;
+    g.p.coef = a->coef;
+    g.p.c2d = a->cell2dof;
+    g.p.image = meta.image;
+    g.p.out = static_cast<float*>(a->out);
+    g.p.err = c->err;
+    g.p.ncells = a->ncells;
+    g.p.nverts = a->nverts;
+    g.p.ncoefnodes = a->ncoefnodes;
+    g.p.ns = ns;
+    g.p.N = ns * ns;
+    g.p.mtiles = meta.mtiles;
+    g.p.kbytes = meta.kbytes;
+    g.p.parts = meta.parts;
+    g.p.precision = prec;
+    g.p.validate = (a->flags & COFFEE_FLAG_VALIDATE) ? 1 : 0;
+    g.p.nu = a->nu;
+    g.item0 = items;
+    g.form = a->form;
+    g.cell = a->cell;
+    g.degree = a->degree;
+    kbytes_max = std::max(kbytes_max, meta.kbytes);
+    parts = meta.parts;
+    const int64_t nt = (a->ncells + 127) / 128;
+    for (int64_t t = 0; t < nt; ++t) {
+      const int64_t cells = std::min<int64_t>(128, a->ncells - t * 128);
+      cost.push_back(4.0 * (double)cells * g.p.N + item_overhead * meta.mtiles);
+    }
+    items += nt;
+  }
+  if (items == 0) return fail(COFFEE_ERR_INVALID_ARG, "all groups are empty");
+  int nstages = 0;
+  const int smem = batch_smem(kbytes_max, parts, &nstages);
+  if (smem == 0) return fail(COFFEE_ERR_UNSUPPORTED, "batch operands do not fit in shared memory");
+  if (grid <= 0) grid = c->num_sms;
+  grid = (int)std::min<int64_t>(grid, items);
+  // contiguous ranges of about equal cost
+  double total = 0.0;
+  for (double x : cost) total += x;
+  std::vector<int64_t> ranges(grid + 1, items);
+  ranges[0] = 0;
+  double acc = 0.0;
+  int b = 1;
+  for (int64_t i = 0; i < items && b < grid; ++i) {
+    acc += cost[i];
+    if (acc >= total * b / grid) ranges[b++] = i + 1;
+  }
+  for (; b < grid; ++b) ranges[b] = items;
+  auto* P = new BatchPlanImpl();
+  cudaGetDevice(&P->device);
+  cudaError_t e = cudaMalloc(&P->d_groups, sizeof(BatchGroup) * ngroups);
+  if (e == cudaSuccess) e = cudaMalloc(&P->d_ranges, sizeof(int64_t) * (grid + 1));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(P->d_groups, hg.data(), sizeof(BatchGroup) * ngroups, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(P->d_ranges, ranges.data(), sizeof(int64_t) * (grid + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = (cudaError_t)batch_prepare(prec, smem);
+  if (e != cudaSuccess) {
+    cudaFree(P->d_groups);
+    cudaFree(P->d_ranges);
+    delete P;
+    return cuda_fail(e, "coffee_batch_plan");
+  }
+  P->L.groups = P->d_groups;
+  P->L.ngroups = ngroups;
+  P->L.ranges = P->d_ranges;
+  P->L.grid = grid;
+  P->L.smem = smem;
+  P->L.nstages = nstages;
+  P->L.kbytes_max = kbytes_max;
+  P->L.precision = prec;
+  P->L.err = c->err;
+  *plan = P;
+  return COFFEE_OK;
+}
+
+int coffee_batch_launch(void* plan, coffee_stream_t stream) {
+  if (!plan) return fail(COFFEE_ERR_INVALID_ARG, "plan is NULL");
+  auto* P = static_cast<BatchPlanImpl*>(plan);
+  cudaError_t e = (cudaError_t)batch_launch(P->L, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "launch(batch)");
+  return COFFEE_OK;
+}
+
+void coffee_batch_free(void* plan) {
+  if (!plan) return;
+  auto* P = static_cast<BatchPlanImpl*>(plan);
+  cudaFree(P->d_groups);
+  cudaFree(P->d_ranges);
+  delete P;
+}
+
 }  // extern "C"

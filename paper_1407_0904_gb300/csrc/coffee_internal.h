@@ -104,6 +104,23 @@ int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, 
 int burgers_tc_supported(int degree, int cell, int precision);
 void build_burgers_image(int degree, int cell, int prec, std::vector<uint8_t>& img, TcTable& meta);
 int launch_burgers_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
+// ---- mixed-batch persistent kernel (k_batch.cu) ----
+struct BatchGroup {
+  TcParams p;      // the group's inputs, output, table image, N, mtiles, kbytes
+  int64_t item0;   // first work item (128-cell tile) of the group in the work list
+  int form, cell, degree, pad;
+};
+struct BatchLaunch {
+  const BatchGroup* groups;  // device
+  int ngroups;
+  const int64_t* ranges;     // device [grid+1]: work items of CTA b are [ranges[b], ranges[b+1])
+  int grid, smem, nstages, kbytes_max, precision;
+  unsigned* err;
+};
+int batch_smem(int kbytes_max, int parts, int* nstages);
+int batch_prepare(int precision, int smem);
+int batch_launch(const BatchLaunch& L, void* stream);
+
 // Build the operand image on the host
 void build_tc_image(int form, int degree, int cell, int precision, std::vector<uint8_t>& img,
                     TcTable& meta);

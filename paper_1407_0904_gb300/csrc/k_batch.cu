@@ -1,0 +1,317 @@
+// Mixed-batch local assembly: many (form, degree, cell) groups in ONE persistent
+// tcgen05 launch.
+//
+// The paper's code generator specialises one kernel per (form, degree, cell shape) and
+// PyOP2 runs them one after another (sections 4-5); its cost model picks per-kernel
+// parameters (section 4's cost-model figure). Here every group's cells are cut into
+// 128-cell tiles, the tiles of all groups form one work list, and each CTA takes a
+// contiguous, cost-balanced range of it (host plan). Per work item:
+//   producer warps 8..11  compute the group's factors G_e (runtime switch over form and
+//                         cell shape) into a B-operand stage laid out with that group's K;
+//   loader warp 13        streams the group's T^T operand, one 128-output M-tile at a
+//                         time, from global memory (L2-resident) into a two-slot ring with
+//                         cp.async.bulk, completion tracked by transaction-count mbarriers;
+//   MMA warp 12           issues tcgen05.mma per M-tile into the TMEM ring;
+//   epilogue warps 0..7   store the element matrices into the group's output.
+// Groups therefore need not share K, N or tables, and no group's table has to fit in
+// shared memory beside the others. All waits are bounded as in k_tc.cu.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include "coffee_internal.h"
+#include "tc_common.cuh"
+
+namespace coffee {
+namespace {
+using namespace tc;
+
+constexpr int BATCH_THREADS = 14 * 32;  // + one loader warp
+constexpr int LOADER_WARP = 13;
+constexpr int ASLOTS = 2;
+
+struct alignas(8) BatchBars {
+  uint64_t full[MAX_STAGES];
+  uint64_t empty[MAX_STAGES];
+  uint64_t tfull[RING];
+  uint64_t tempty[RING];
+  uint64_t afull[ASLOTS];
+  uint64_t aempty[ASLOTS];
+  uint64_t done;
+  uint32_t tmem_base;
+};
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// group of the work item `it` (groups are few; linear scan over their first items)
+__device__ __forceinline__ int group_of(const BatchGroup* gs, int ngroups, int64_t it) {
+  int g = 0;
+  while (g + 1 < ngroups && gs[g + 1].item0 <= it) ++g;
+  return g;
+}
+
+template <int PREC, int FORM, int D>
+__device__ __forceinline__ void produce_row(const BatchGroup& g, int64_t e, bool live, uint8_t* hi, uint8_t* lo,
+                                            int row) {
+  using PT = PrecTraits<PREC>;
+  constexpr int KSTEP = PT::tf32 ? 8 : 16;
+  constexpr int KP = round_up(Form<FORM, D>::K, KSTEP);
+  float G[KP];
+  bool bad = false;
+  if (live) {
+    cell_factors<FORM, D, KP>(g.p, e, G, bad);
+    if (bad) atomicOr(g.p.err, ERR_INDEX);
+  }
+  if (!live || bad) {
+#pragma unroll
+    for (int k = 0; k < KP; ++k) G[k] = 0.f;
+  }
+  store_operand_row<PREC, KP>(hi, lo, row, G, g.p.kbytes);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(BATCH_THREADS, 1)
+    k_batch_tc(const BatchGroup* __restrict__ groups, int ngroups, const int64_t* __restrict__ ranges,
+               int nstages, int kbytes_max, unsigned* err) {
+  using PT = PrecTraits<PREC>;
+  constexpr int PARTS = PT::split ? 2 : 1;
+  constexpr uint32_t IDESC = make_idesc(PT::tf32 ? 2 : 1, BM, BN);
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int slot_bytes = PARTS * BM * kbytes_max;  // one A slot or one B stage
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + ASLOTS * slot_bytes;
+  BatchBars* bars = reinterpret_cast<BatchBars*>(sB + nstages * slot_bytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t it0 = ranges[blockIdx.x], it1 = ranges[blockIdx.x + 1];
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      mbar_init(smem_u32(&bars->full[s]), 128);
+      mbar_init(smem_u32(&bars->empty[s]), 1);
+    }
+    for (int r = 0; r < RING; ++r) {
+      mbar_init(smem_u32(&bars->tfull[r]), 1);
+      mbar_init(smem_u32(&bars->tempty[r]), 8);
+    }
+    for (int j = 0; j < ASLOTS; ++j) {
+      mbar_init(smem_u32(&bars->afull[j]), 1);
+      mbar_init(smem_u32(&bars->aempty[j]), 1);
+    }
+    mbar_init(smem_u32(&bars->done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&bars->tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+
+  if (warp >= PROD_WARP0 && warp < MMA_WARP) {
+    // ---------------- producers ----------------
+    const int row = threadIdx.x - PROD_WARP0 * 32;
+    int k = 0;
+    for (int64_t it = it0; it < it1; ++it, ++k) {
+      const int gi = group_of(groups, ngroups, it);
+      const BatchGroup& g = groups[gi];
+      const int s = k % nstages;
+      const uint32_t use = (uint32_t)(k / nstages);
+      if (!mbar_wait(smem_u32(&bars->empty[s]), (use & 1u) ^ 1u, err)) break;
+      const int64_t e = (it - g.item0) * BN + row;
+      const bool live = e < g.p.ncells;
+      uint8_t* hi = sB + (size_t)s * slot_bytes;
+      uint8_t* lo = hi + BM * g.p.kbytes;
+      switch (g.form * 2 + g.cell) {
+        case FORM_MASS * 2 + CELL_TRI: produce_row<PREC, FORM_MASS, 2>(g, e, live, hi, lo, row); break;
+        case FORM_MASS * 2 + CELL_TET: produce_row<PREC, FORM_MASS, 3>(g, e, live, hi, lo, row); break;
+        case FORM_HELMHOLTZ * 2 + CELL_TRI: produce_row<PREC, FORM_HELMHOLTZ, 2>(g, e, live, hi, lo, row); break;
+        case FORM_HELMHOLTZ * 2 + CELL_TET: produce_row<PREC, FORM_HELMHOLTZ, 3>(g, e, live, hi, lo, row); break;
+        case FORM_ADVDIFF * 2 + CELL_TRI: produce_row<PREC, FORM_ADVDIFF, 2>(g, e, live, hi, lo, row); break;
+        default: produce_row<PREC, FORM_ADVDIFF, 3>(g, e, live, hi, lo, row); break;
+      }
+      fence_proxy_async();
+      mbar_arrive(smem_u32(&bars->full[s]));
+    }
+  } else if (warp == LOADER_WARP) {
+    // ---------------- T^T operand loader ----------------
+    if (lane == 0) {
+      uint32_t la = 0, last_round[ASLOTS] = {0, 0};
+      bool used[ASLOTS] = {false, false};
+      bool ok = true;
+      for (int64_t it = it0; it < it1 && ok; ++it) {
+        const BatchGroup& g = groups[group_of(groups, ngroups, it)];
+        const uint32_t part_bytes = (uint32_t)(BM * g.p.kbytes);
+        for (int m = 0; m < g.p.mtiles; ++m, ++la) {
+          const uint32_t j = la % ASLOTS, round = la / ASLOTS;
+          if (!mbar_wait(smem_u32(&bars->aempty[j]), (round & 1u) ^ 1u, err)) { ok = false; break; }
+          const uint32_t bar = smem_u32(&bars->afull[j]);
+          mbar_arrive_expect_tx(bar, part_bytes * PARTS);
+          used[j] = true;
+          last_round[j] = round;
+          const uint8_t* src = g.p.image + (size_t)m * PARTS * part_bytes;
+          const uint32_t dst = smem_u32(sA + (size_t)j * slot_bytes);
+#pragma unroll
+          for (int q = 0; q < PARTS; ++q) bulk_g2s(dst + q * part_bytes, src + (size_t)q * part_bytes, part_bytes, bar);
+        }
+      }
+      // every copy this thread started has landed before shared memory is released
+      for (int j = 0; j < ASLOTS; ++j)
+        if (used[j]) mbar_wait(smem_u32(&bars->afull[j]), last_round[j] & 1u, err);
+    }
+    __syncwarp();
+  } else if (warp == MMA_WARP) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      uint32_t rc = 0, ma = 0;
+      int k = 0;
+      bool ok = true;
+      for (int64_t it = it0; it < it1 && ok; ++it, ++k) {
+        const BatchGroup& g = groups[group_of(groups, ngroups, it)];
+        const int kb = g.p.kbytes, ksteps = kb / 32;
+        const uint32_t sbo = 8u * (uint32_t)kb, part = (uint32_t)(BM * kb);
+        const int s = k % nstages;
+        const uint32_t use = (uint32_t)(k / nstages);
+        if (!mbar_wait(smem_u32(&bars->full[s]), use & 1u, err)) break;
+        tc_fence_after();
+        const uint32_t bstage = b0 + (uint32_t)(s * slot_bytes);
+        for (int m = 0; m < g.p.mtiles; ++m, ++rc, ++ma) {
+          const uint32_t j = ma % ASLOTS, around = ma / ASLOTS;
+          if (!mbar_wait(smem_u32(&bars->afull[j]), around & 1u, err)) { ok = false; break; }
+          const uint32_t slot = rc % RING, round = rc / RING;
+          if (!mbar_wait(smem_u32(&bars->tempty[slot]), (round & 1u) ^ 1u, err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d = tmem + slot * BN;
+          const uint32_t atile = a0 + j * (uint32_t)slot_bytes;
+          uint32_t acc = 0;
+          for (int ks = 0; ks < ksteps; ++ks) {
+            const uint32_t ko = (uint32_t)ks * 256u;
+            if constexpr (PT::split) {
+              mma<PT::tf32>(d, make_desc(atile + ko, sbo), make_desc(bstage + part + ko, sbo), IDESC, acc);
+              acc = 1;
+              mma<PT::tf32>(d, make_desc(atile + part + ko, sbo), make_desc(bstage + ko, sbo), IDESC, 1);
+            }
+            mma<PT::tf32>(d, make_desc(atile + ko, sbo), make_desc(bstage + ko, sbo), IDESC, acc);
+            acc = 1;
+          }
+          tc_commit(smem_u32(&bars->tfull[slot]));
+          tc_commit(smem_u32(&bars->aempty[j]));
+        }
+        tc_commit(smem_u32(&bars->empty[s]));
+      }
+      tc_commit(smem_u32(&bars->done));
+      mbar_wait(smem_u32(&bars->done), 0, err);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3, half = warp >> 2;
+    uint32_t rc = 0;
+    bool ok = true;
+    for (int64_t it = it0; it < it1 && ok; ++it) {
+      const BatchGroup& g = groups[group_of(groups, ngroups, it)];
+      const int64_t cbase = (it - g.item0) * BN + half * 64;
+      const int64_t rem = g.p.ncells - cbase;
+      const int ncol = rem <= 0 ? 0 : (rem < 64 ? (int)rem : 64);
+      const int N = g.p.N;
+      for (int m = 0; m < g.p.mtiles; ++m, ++rc) {
+        const uint32_t slot = rc % RING, round = rc / RING;
+        if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, err)) { ok = false; break; }
+        tc_fence_after();
+        const int o = m * BM + q * 32 + lane;
+        if (m * BM + q * 32 < N && ncol > 0) {
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + slot * BN + half * 64;
+          uint32_t v0[32], v1[32];
+          tmem_ld32(taddr, v0);
+          tmem_ld32(taddr + 32, v1);
+          tmem_wait_ld();
+          if (o < N) {
+            float* dst = g.p.out + cbase * N + o;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < ncol) __stcs(dst + (int64_t)j * N, __uint_as_float(v0[j]));
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (32 + j < ncol) __stcs(dst + (int64_t)(32 + j) * N, __uint_as_float(v1[j]));
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+constexpr int SMEM_LIMIT = 227 * 1024;
+constexpr int SMEM_ONE_CTA = 120 * 1024;
+
+template <int PREC>
+cudaError_t prepare_t(int smem) {
+  return cudaFuncSetAttribute(k_batch_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+template <int PREC>
+cudaError_t launch_t(const BatchLaunch& L, cudaStream_t s) {
+  k_batch_tc<PREC><<<L.grid, BATCH_THREADS, L.smem, s>>>(L.groups, L.ngroups, L.ranges, L.nstages, L.kbytes_max,
+                                                         L.err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int batch_smem(int kbytes_max, int parts, int* nstages) {
+  const int slot = parts * BM * kbytes_max;
+  const int fixed = ASLOTS * slot + (int)sizeof(BatchBars) + 1024 + 64;
+  int s = MAX_STAGES;
+  while (s >= 2 && fixed + s * slot > SMEM_LIMIT) --s;
+  if (s < 2) return 0;
+  *nstages = s;
+  const int smem = fixed + s * slot;
+  return smem < SMEM_ONE_CTA ? SMEM_ONE_CTA : smem;
+}
+
+int batch_prepare(int precision, int smem) {
+  switch (precision) {
+    case PREC_TF32: return (int)prepare_t<PREC_TF32>(smem);
+    case PREC_TF32X3: return (int)prepare_t<PREC_TF32X3>(smem);
+    case PREC_BF16: return (int)prepare_t<PREC_BF16>(smem);
+    case PREC_BF16X3: return (int)prepare_t<PREC_BF16X3>(smem);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+int batch_launch(const BatchLaunch& L, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (L.precision) {
+    case PREC_TF32: return (int)launch_t<PREC_TF32>(L, s);
+    case PREC_TF32X3: return (int)launch_t<PREC_TF32X3>(L, s);
+    case PREC_BF16: return (int)launch_t<PREC_BF16>(L, s);
+    case PREC_BF16X3: return (int)launch_t<PREC_BF16X3>(L, s);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace coffee

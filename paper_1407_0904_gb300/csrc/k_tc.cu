@@ -38,81 +38,6 @@ namespace {
 using namespace tc;
 
 // ----------------------------------------------------------- per-cell factors
-template <int FORM, int D>
-struct Form {
-  static constexpr int P = D * (D + 1) / 2;
-  static constexpr int K = FORM == FORM_MASS ? 1 : FORM == FORM_HELMHOLTZ ? 1 + P : (D + 1) * P + (D + 1) * D;
-};
-
-// Per-cell factors G[0..KP) (zero padded) for MASS / HELMHOLTZ / ADVDIFF.
-template <int FORM, int D, int KP>
-__device__ __forceinline__ void cell_factors(const TcParams& p, int64_t e, float (&G)[KP], bool& bad) {
-  constexpr int NV = D + 1, P = D * (D + 1) / 2;
-#pragma unroll
-  for (int k = 0; k < KP; ++k) G[k] = 0.f;
-  int vid[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    vid[v] = __ldg(p.c2v + e * NV + v);
-    if (p.validate && (vid[v] < 0 || vid[v] >= p.nverts)) bad = true;
-  }
-  int cid[NV];
-  if constexpr (FORM == FORM_ADVDIFF) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      cid[v] = __ldg(p.c2d + e * NV + v);
-      if (p.validate && (cid[v] < 0 || cid[v] >= p.ncoefnodes)) bad = true;
-    }
-  }
-  if (bad) return;
-  double X[NV][D];
-#pragma unroll
-  for (int v = 0; v < NV; ++v)
-#pragma unroll
-    for (int r = 0; r < D; ++r) X[v][r] = __ldg(p.coords + (int64_t)vid[v] * D + r);
-  float adj[D][D], Dm, sg;
-  cell_geometry<D>(X, adj, Dm, sg);
-  const float inv = 1.0f / Dm;
-  float H[P];
-  {
-    int q = 0;
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-      for (int b = a; b < D; ++b) {
-        float s = 0.f;
-#pragma unroll
-        for (int r = 0; r < D; ++r) s = fmaf(adj[a][r], adj[b][r], s);
-        H[q++] = s * inv;
-      }
-  }
-  if constexpr (FORM == FORM_MASS) {
-    G[0] = Dm;
-  } else if constexpr (FORM == FORM_HELMHOLTZ) {
-    G[0] = Dm;
-#pragma unroll
-    for (int q = 0; q < P; ++q) G[1 + q] = H[q];
-  } else {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const double* cv = p.coef + (int64_t)cid[v] * (D + 1);  // (eps, b) row of the node
-      const float eps = (float)__ldg(cv);
-      float bv[D];
-#pragma unroll
-      for (int r = 0; r < D; ++r) bv[r] = (float)__ldg(cv + 1 + r);
-#pragma unroll
-      for (int q = 0; q < P; ++q) G[v * P + q] = eps * H[q];
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        float s = 0.f;
-#pragma unroll
-        for (int r = 0; r < D; ++r) s = fmaf(adj[a][r], bv[r], s);
-        G[NV * P + v * D + a] = sg * s;
-      }
-    }
-  }
-}
-
 // ------------------------------------------------------------------- kernel
 template <int FORM, int D, int PREC>
 __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, int nstages) {

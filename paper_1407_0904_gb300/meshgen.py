@@ -172,3 +172,22 @@ def sliver_tet(rng=None, flat=1e-3):
     if rng is not None:
         X = X + rng.uniform(-1e-3, 1e-3, size=X.shape) * flat
     return X
+
+
+BATCH_FORMS = (0, 1, 2)  # mass, Helmholtz, advection-diffusion
+
+
+def batch_groups(tri_mesh_, tet_mesh_, tri_degrees=(1, 2, 3, 4), tet_degrees=(1, 2, 3), seed=4):
+    """Mixed-batch groups: every (form, degree) on both meshes, each group a contiguous
+    range of cells whose size follows a seeded Zipf(s=1) split of the mesh's cells.
+
+    Returns a list of dicts {form, degree, cell, start, count}."""
+    out = []
+    for mesh, degrees, sd in ((tri_mesh_, tri_degrees, seed), (tet_mesh_, tet_degrees, seed + 1)):
+        kinds = [(f, k) for k in degrees for f in BATCH_FORMS]
+        counts = zipf_counts(len(kinds), mesh.ncells, s=1.0, seed=sd)
+        start = 0
+        for (f, k), n in zip(kinds, counts):
+            out.append({"form": f, "degree": k, "cell": mesh.cell, "start": int(start), "count": int(n)})
+            start += n
+    return out
