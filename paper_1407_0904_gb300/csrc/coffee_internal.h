@@ -120,6 +120,8 @@ struct BatchLaunch {
 int batch_smem(int kbytes_max, int parts, int* nstages);
 int batch_prepare(int precision, int smem);
 int batch_launch(const BatchLaunch& L, void* stream);
+int stream_one_supported(int form, int kbytes, int parts);
+int launch_stream_one(const BatchGroup& g, int num_sms, void* stream);
 
 // Build the operand image on the host
 void build_tc_image(int form, int degree, int cell, int precision, std::vector<uint8_t>& img,

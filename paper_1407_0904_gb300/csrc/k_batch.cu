@@ -78,9 +78,8 @@ __device__ __forceinline__ void produce_row(const BatchGroup& g, int64_t e, bool
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(BATCH_THREADS, 1)
-    k_batch_tc(const BatchGroup* __restrict__ groups, int ngroups, const int64_t* __restrict__ ranges,
-               int nstages, int kbytes_max, unsigned* err) {
+__device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups, int ngroups, int64_t it0,
+                                           int64_t it1, int nstages, int kbytes_max, unsigned* err) {
   using PT = PrecTraits<PREC>;
   constexpr int PARTS = PT::split ? 2 : 1;
   constexpr uint32_t IDESC = make_idesc(PT::tf32 ? 2 : 1, BM, BN);
@@ -91,7 +90,6 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
   uint8_t* sB = smem + ASLOTS * slot_bytes;
   BatchBars* bars = reinterpret_cast<BatchBars*>(sB + nstages * slot_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t it0 = ranges[blockIdx.x], it1 = ranges[blockIdx.x + 1];
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nstages; ++s) {
@@ -266,12 +264,36 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1)
   }
 }
 
+// Several groups: work items of CTA b are [ranges[b], ranges[b+1]) (cost-balanced on the host).
+template <int PREC>
+__global__ void __launch_bounds__(BATCH_THREADS, 1)
+    k_batch_tc(const BatchGroup* __restrict__ groups, int ngroups, const int64_t* __restrict__ ranges,
+               int nstages, int kbytes_max, unsigned* err) {
+  batch_body<PREC>(groups, ngroups, ranges[blockIdx.x], ranges[blockIdx.x + 1], nstages, kbytes_max, err);
+}
+
+// One group passed by value (no device allocation): equal split of its tiles over the grid.
+template <int PREC>
+__global__ void __launch_bounds__(BATCH_THREADS, 1)
+    k_stream_one_tc(const __grid_constant__ BatchGroup g, int64_t items, int nstages, int kbytes_max) {
+  const int64_t it0 = items * blockIdx.x / gridDim.x, it1 = items * (blockIdx.x + 1) / gridDim.x;
+  batch_body<PREC>(&g, 1, it0, it1, nstages, kbytes_max, g.p.err);
+}
+
 constexpr int SMEM_LIMIT = 227 * 1024;
 constexpr int SMEM_ONE_CTA = 120 * 1024;
 
 template <int PREC>
 cudaError_t prepare_t(int smem) {
-  return cudaFuncSetAttribute(k_batch_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_batch_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_stream_one_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+template <int PREC>
+cudaError_t launch_one_t(const BatchGroup& g, int64_t items, int grid, int smem, int nstages, int kbytes_max,
+                         cudaStream_t s) {
+  k_stream_one_tc<PREC><<<grid, BATCH_THREADS, smem, s>>>(g, items, nstages, kbytes_max);
+  return cudaGetLastError();
 }
 template <int PREC>
 cudaError_t launch_t(const BatchLaunch& L, cudaStream_t s) {
@@ -299,6 +321,31 @@ int batch_prepare(int precision, int smem) {
     case PREC_TF32X3: return (int)prepare_t<PREC_TF32X3>(smem);
     case PREC_BF16: return (int)prepare_t<PREC_BF16>(smem);
     case PREC_BF16X3: return (int)prepare_t<PREC_BF16X3>(smem);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+// Single group with its T^T operand streamed per M-tile (used when it does not fit in
+// shared memory for the resident-operand kernel).
+int stream_one_supported(int form, int kbytes, int parts) {
+  int nst = 0;
+  return form != FORM_BURGERS && batch_smem(kbytes, parts, &nst) > 0;
+}
+
+int launch_stream_one(const BatchGroup& g, int num_sms, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int nstages = 0;
+  const int smem = batch_smem(g.p.kbytes, g.p.parts, &nstages);
+  if (smem == 0) return (int)cudaErrorInvalidValue;
+  cudaError_t e = (cudaError_t)batch_prepare(g.p.precision, smem);
+  if (e != cudaSuccess) return (int)e;
+  const int64_t items = (g.p.ncells + BN - 1) / BN;
+  const int grid = (int)(items < num_sms ? items : num_sms);
+  switch (g.p.precision) {
+    case PREC_TF32: return (int)launch_one_t<PREC_TF32>(g, items, grid, smem, nstages, g.p.kbytes, s);
+    case PREC_TF32X3: return (int)launch_one_t<PREC_TF32X3>(g, items, grid, smem, nstages, g.p.kbytes, s);
+    case PREC_BF16: return (int)launch_one_t<PREC_BF16>(g, items, grid, smem, nstages, g.p.kbytes, s);
+    case PREC_BF16X3: return (int)launch_one_t<PREC_BF16X3>(g, items, grid, smem, nstages, g.p.kbytes, s);
   }
   return (int)cudaErrorInvalidValue;
 }

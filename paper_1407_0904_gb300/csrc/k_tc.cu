@@ -270,7 +270,8 @@ int tc_supported(int form, int degree, int cell, int precision) {
   if (form == FORM_BURGERS) return burgers_tc_supported(degree, cell, precision);
   Geom g;
   if (degree < 1 || degree > 4 || !geom_of(form, degree, cell, precision, g)) return 0;
-  return stages_for(g) > 0 ? 1 : 0;
+  if (stages_for(g) > 0) return 1;
+  return stream_one_supported(form, g.kbytes, g.parts);
 }
 
 void build_tc_image(int form, int degree, int cell, int prec, std::vector<uint8_t>& img, TcTable& meta) {
@@ -327,8 +328,17 @@ int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, 
   g.mtiles = p.mtiles;
   const int nst = stages_for(g);
   if (nst == 0) {
-    why = "operands do not fit in shared memory";
-    return (int)cudaErrorInvalidValue;
+    // T^T does not fit beside the operand stages: stream it per M-tile instead
+    BatchGroup bg;
+    std::memset(&bg, 0, sizeof(bg));
+    bg.p = p;
+    bg.form = form;
+    bg.cell = cell;
+    if (!stream_one_supported(form, p.kbytes, p.parts)) {
+      why = "operands do not fit in shared memory";
+      return (int)cudaErrorInvalidValue;
+    }
+    return launch_stream_one(bg, num_sms, stream);
   }
   int smem = g.mtiles * g.parts * BM * g.kbytes + nst * g.parts * BN * g.kbytes + (int)sizeof(Barriers) + 1024 + 64;
   if (smem < SMEM_ONE_CTA) smem = SMEM_ONE_CTA;
