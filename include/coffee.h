@@ -90,6 +90,12 @@ typedef enum {
 
 /* Flags of coffee_assemble_args.flags */
 #define COFFEE_FLAG_VALIDATE 1u /* range-check cell2vert/cell2dof on the device */
+/* Tuning knobs of the tensor-core kernels (results are identical; only speed changes):
+ * OUTPUT_LANES: keep element-matrix entries on the TMEM lanes (one 128-output slice per
+ *   accumulator) even when the matrix is small enough to put cells on the lanes;
+ * TWO_STAGES: at most two operand stages (leaves shared memory to other kernels). */
+#define COFFEE_FLAG_OUTPUT_LANES 2u
+#define COFFEE_FLAG_TWO_STAGES 4u
 
 /* Number of rows of the element matrix: (k+1)(k+2)/2 (triangle) or
  * (k+1)(k+2)(k+3)/6 (tetrahedron), times d for BURGERS_JAC. Negative on error. */

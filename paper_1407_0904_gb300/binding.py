@@ -15,6 +15,8 @@ MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC = 0, 1, 2, 3
 TRIANGLE, TETRAHEDRON = 0, 1
 FP64, TF32, TF32X3, BF16, BF16X3 = 0, 1, 2, 3, 4
 FLAG_VALIDATE = 1
+FLAG_OUTPUT_LANES = 2   # tuning knob: element-matrix entries on the TMEM lanes
+FLAG_TWO_STAGES = 4     # tuning knob: at most two operand stages
 
 FORM_NAMES = {MASS: "mass", HELMHOLTZ: "helmholtz", ADVDIFF: "advdiff", BURGERS_JAC: "burgers_jac"}
 PRECISION_NAMES = {FP64: "fp64", TF32: "tf32", TF32X3: "tf32x3", BF16: "bf16", BF16X3: "bf16x3"}
@@ -144,7 +146,7 @@ def _stream_handle(stream):
 
 
 def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
-              out=None, nu=0.01, validate=False, ncoefnodes=None):
+              out=None, nu=0.01, validate=False, ncoefnodes=None, tune=0):
     coords = _dev(coords, torch.float64, "coords")
     cell2vert = _dev(cell2vert, torch.int32, "cell2vert")
     coef = _dev(coef, torch.float64, "coef")
@@ -170,17 +172,39 @@ def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, p
     a.coef, a.ncoefnodes = _ptr(coef), int(ncoefnodes or 0)
     a.cell2dof = _ptr(cell2dof)
     a.out, a.ncells = _ptr(out), ncells
-    a.flags = FLAG_VALIDATE if validate else 0
+    a.flags = (FLAG_VALIDATE if validate else 0) | int(tune)
     return a, out
 
 
 def assemble(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
-             out=None, nu=0.01, validate=False, stream=None):
-    """Element matrices [ncells, ndof, ndof] (float64 for FP64, float32 otherwise) on the device."""
+             out=None, nu=0.01, validate=False, stream=None, tune=None):
+    """Element matrices [ncells, ndof, ndof] (float64 for FP64, float32 otherwise) on the device.
+
+    tune: FLAG_OUTPUT_LANES / FLAG_TWO_STAGES knobs; None uses the autotuner's choice for
+    this (form, degree, cell, precision) when one is cached, else the library default."""
+    if tune is None:
+        tune = _tuned_flags(form, degree, cell, precision)
     a, out = make_args(form, degree, cell, coords, cell2vert, coef, cell2dof, precision, out, nu,
-                       validate)
+                       validate, tune=tune)
     _check(lib().coffee_assemble_ex(ctypes.byref(a), _stream_handle(stream)))
     return out
+
+
+_tune_cache = None
+
+
+def _tuned_flags(form, degree, cell, precision):
+    """Knobs chosen by the autotuner (paper_1407_0904_gb300.tune) for this GPU, if any."""
+    global _tune_cache
+    if precision == FP64:
+        return 0
+    if _tune_cache is None:
+        try:
+            from . import tune as _tune
+            _tune_cache = _tune.load_cache()
+        except Exception:
+            _tune_cache = {}
+    return int(_tune_cache.get("%d/%d/%d/%d" % (form, degree, cell, precision), {}).get("flags", 0))
 
 
 def assemble_plain(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, out=None,

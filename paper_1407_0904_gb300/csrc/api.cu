@@ -225,6 +225,8 @@ int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream) {
   p.kbytes = meta.kbytes;
   p.parts = meta.parts;
   p.ksteps_off = meta.ksteps_off;
+  p.tune = ((a->flags & COFFEE_FLAG_OUTPUT_LANES) ? TUNE_OUTPUT_LANES : 0u) |
+           ((a->flags & COFFEE_FLAG_TWO_STAGES) ? TUNE_TWO_STAGES : 0u);
   p.precision = a->precision;
   p.validate = validate ? 1 : 0;
   p.nu = a->nu;

@@ -98,7 +98,7 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
     }
     for (int r = 0; r < RING; ++r) {
       mbar_init(smem_u32(&bars->tfull[r]), 1);
-      mbar_init(smem_u32(&bars->tempty[r]), 8);
+      mbar_init(smem_u32(&bars->tempty[r]), EPI_WARPS);
     }
     for (int j = 0; j < ASLOTS; ++j) {
       mbar_init(smem_u32(&bars->afull[j]), 1);
@@ -122,13 +122,16 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
 
   if (warp >= PROD_WARP0 && warp < MMA_WARP) {
     // ---------------- producers ----------------
-    const int row = threadIdx.x - PROD_WARP0 * 32;
-    int k = 0;
-    for (int64_t it = it0; it < it1; ++it, ++k) {
+    const int pw = warp - PROD_WARP0;
+    const int grp = pw >> 2, row = ((pw & 3) << 5) + lane;
+    const int spg = nstages / PROD_GROUPS;
+    for (int64_t it = it0 + grp; it < it1; it += PROD_GROUPS) {
+      const int64_t k = it - it0;
       const int gi = group_of(groups, ngroups, it);
       const BatchGroup& g = groups[gi];
-      const int s = k % nstages;
-      const uint32_t use = (uint32_t)(k / nstages);
+      int s;
+      uint32_t use;
+      stage_of(k / PROD_GROUPS, grp, spg, s, use);
       if (!mbar_wait(smem_u32(&bars->empty[s]), (use & 1u) ^ 1u, err)) break;
       const int64_t e = (it - g.item0) * BN + row;
       const bool live = e < g.p.ncells;
@@ -183,8 +186,9 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
         const BatchGroup& g = groups[group_of(groups, ngroups, it)];
         const int kb = g.p.kbytes, ksteps = kb / 32;
         const uint32_t sbo = 8u * (uint32_t)kb, part = (uint32_t)(BM * kb);
-        const int s = k % nstages;
-        const uint32_t use = (uint32_t)(k / nstages);
+        int s;
+        uint32_t use;
+        stage_of(k / PROD_GROUPS, k % PROD_GROUPS, nstages / PROD_GROUPS, s, use);
         if (!mbar_wait(smem_u32(&bars->full[s]), use & 1u, err)) break;
         tc_fence_after();
         const uint32_t bstage = b0 + (uint32_t)(s * slot_bytes);
@@ -218,20 +222,21 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
     __syncwarp();
   } else {
     // ---------------- epilogue ----------------
-    const int q = warp & 3, half = warp >> 2;
+    const int q = warp;  // TMEM lane quadrant
     uint32_t rc = 0;
     bool ok = true;
     for (int64_t it = it0; it < it1 && ok; ++it) {
       const BatchGroup& g = groups[group_of(groups, ngroups, it)];
-      const int64_t cbase = (it - g.item0) * BN + half * 64;
-      const int64_t rem = g.p.ncells - cbase;
-      const int ncol = rem <= 0 ? 0 : (rem < 64 ? (int)rem : 64);
       const int N = g.p.N;
       for (int m = 0; m < g.p.mtiles; ++m, ++rc) {
         const uint32_t slot = rc % RING, round = rc / RING;
         if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, err)) { ok = false; break; }
         tc_fence_after();
         const int o = m * BM + q * 32 + lane;
+        for (int half = 0; half < 2; ++half) {
+        const int64_t cbase = (it - g.item0) * BN + half * 64;
+        const int64_t rem = g.p.ncells - cbase;
+        const int ncol = rem <= 0 ? 0 : (rem < 64 ? (int)rem : 64);
         if (m * BM + q * 32 < N && ncol > 0) {
           const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + slot * BN + half * 64;
           uint32_t v0[32], v1[32];
@@ -247,6 +252,7 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
             for (int j = 0; j < 32; ++j)
               if (32 + j < ncol) __stcs(dst + (int64_t)(32 + j) * N, __uint_as_float(v1[j]));
           }
+        }
         }
         tc_fence_before();
         __syncwarp();
@@ -307,8 +313,8 @@ cudaError_t launch_t(const BatchLaunch& L, cudaStream_t s) {
 int batch_smem(int kbytes_max, int parts, int* nstages) {
   const int slot = parts * BM * kbytes_max;
   const int fixed = ASLOTS * slot + (int)sizeof(BatchBars) + 1024 + 64;
-  int s = MAX_STAGES;
-  while (s >= 2 && fixed + s * slot > SMEM_LIMIT) --s;
+  int s = MAX_STAGES;  // even: the stages are split between the two producer groups
+  while (s >= 2 && fixed + s * slot > SMEM_LIMIT) s -= 2;
   if (s < 2) return 0;
   *nstages = s;
   const int smem = fixed + s * slot;

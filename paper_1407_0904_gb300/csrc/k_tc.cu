@@ -9,18 +9,18 @@
 // tensor cores.
 //
 // Work decomposition (one persistent CTA per SM, cells tiled by 128):
-//   producer warps 8..11  gather each cell's vertices (and coefficient dofs),
+//   producer warps 4..11  (two groups on alternate tiles) gather each cell's vertices (and coefficient dofs),
 //                         compute J, det, adj in FP32 (FP64 when the cell is badly
 //                         conditioned) and the factors G_e, split them into
 //                         tensor-core operands (tf32 or bf16, hi/lo for the split
 //                         precisions) and store them as the B operand (cells x K,
 //                         K-major) of a shared-memory stage;
 //   MMA warp 12           one thread issues tcgen05.mma: D[o][cell] += T^T[o][k] G[cell][k]
-//                         for every 128-row slice of the outputs, into a ring of
-//                         four 128-column TMEM accumulators;
-//   epilogue warps 0..7   tcgen05.ld a slice (lanes = outputs, columns = cells) and
-//                         store it: a warp writes 32 consecutive outputs of one cell
-//                         per instruction (128 contiguous bytes).
+//                         for every 128-row slice of the outputs into TMEM accumulators;
+//   epilogue warps 0..3   tcgen05.ld the accumulator and store it: 128-byte warp stores
+//                         of 32 outputs of one cell (outputs on the TMEM lanes), or
+//                         16-byte stores of a thread's own row (cells on the lanes, for
+//                         element matrices of at most 128 entries).
 // T^T (the A operand) stays resident in shared memory for the whole launch.
 // Every mbarrier wait is bounded (about 2 s of %globaltimer); on expiry the
 // kernel sets the error word and unwinds, freeing its TMEM.
@@ -37,27 +37,35 @@ namespace {
 
 using namespace tc;
 
-// ----------------------------------------------------------- per-cell factors
 // ------------------------------------------------------------------- kernel
-template <int FORM, int D, int PREC>
+// Two orientations of the per-tile contraction.
+//  outputs on lanes (any N): D[o][cell] = T^T G^T, one 128-column TMEM accumulator per
+//         128-output slice (ring of four); each epilogue warp store writes 32 consecutive
+//         outputs of one cell (128 bytes).
+//  cells on lanes (N <= 128, LANES): D[cell][o] = G T, M = 128 cells, N = outputs rounded
+//         up to 16; an epilogue thread holds consecutive outputs of its own cell and writes
+//         its row with 16-byte stores, so every output row is written by one thread in
+//         order. The operands are the same shared-memory images with their roles swapped.
+template <int FORM, int D, int PREC, bool LANES>
 __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, int nstages) {
   using PT = PrecTraits<PREC>;
   constexpr int KSTEP = PT::tf32 ? 8 : 16;  // K elements per MMA (32 bytes)
   constexpr int KP = round_up(Form<FORM, D>::K, KSTEP);
   constexpr int PARTS = PT::split ? 2 : 1;
-  constexpr uint32_t IDESC = make_idesc(PT::tf32 ? 2 : 1, BM, BN);
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int kbytes = p.kbytes;
   const int tile_bytes = BM * kbytes;  // one part of one operand tile (A: 128 outputs, B: 128 cells)
   const int a_bytes = p.mtiles * PARTS * tile_bytes;
+  const int N = p.N;
   uint8_t* sA = smem;
   uint8_t* sB = smem + a_bytes;
   Barriers* bars = reinterpret_cast<Barriers*>(sB + nstages * PARTS * tile_bytes);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (p.ncells + BN - 1) / BN;
+  const int NP = (N + 15) & ~15;  // LANES: MMA N (outputs, multiple of 16)
 
   // ---- set-up: barriers, TMEM, resident A operand ----
   if (threadIdx.x == 0) {
@@ -67,7 +75,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
     }
     for (int r = 0; r < RING; ++r) {
       mbar_init(smem_u32(&bars->tfull[r]), 1);
-      mbar_init(smem_u32(&bars->tempty[r]), 8);
+      mbar_init(smem_u32(&bars->tempty[r]), EPI_WARPS);
     }
     mbar_init(smem_u32(&bars->done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -91,12 +99,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
   const uint32_t tmem = bars->tmem_base;
 
   if (warp >= PROD_WARP0 && warp < MMA_WARP) {
-    // ---------------- producers: one cell per thread ----------------
-    const int row = threadIdx.x - PROD_WARP0 * 32;
-    int it = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-      const int s = it % nstages;
-      const uint32_t use = (uint32_t)(it / nstages);
+    // ---------------- producers: one cell per thread, two groups on alternate tiles ----------------
+    const int pw = warp - PROD_WARP0;
+    const int grp = pw >> 2, row = ((pw & 3) << 5) + lane;
+    const int spg = nstages / PROD_GROUPS;
+    int64_t li = 0;
+    for (int64_t t = blockIdx.x + (int64_t)grp * gridDim.x; t < ntiles;
+         t += (int64_t)PROD_GROUPS * gridDim.x, ++li) {
+      int s;
+      uint32_t use;
+      stage_of(li, grp, spg, s, use);
       if (!mbar_wait(smem_u32(&bars->empty[s]), (use & 1u) ^ 1u, p.err)) break;
       const int64_t e = t * BN + row;
       float G[KP];
@@ -120,12 +132,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
       const int ksteps = kbytes / 32;
       const uint32_t sbo = 8u * (uint32_t)kbytes;
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-      uint32_t rc = 0;  // TMEM ring counter
-      int it = 0;
+      const uint32_t idesc = make_idesc(PT::tf32 ? 2 : 1, BM, LANES ? NP : BN);
+      uint32_t rc = 0;  // accumulator ring counter
+      const int spg = nstages / PROD_GROUPS;
+      int64_t tl = 0;  // local tile number
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
-        const int s = it % nstages;
-        const uint32_t use = (uint32_t)(it / nstages);
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+        int s;
+        uint32_t use;
+        stage_of(tl / PROD_GROUPS, (int)(tl % PROD_GROUPS), spg, s, use);
         if (!mbar_wait(smem_u32(&bars->full[s]), use & 1u, p.err)) break;
         tc_fence_after();
         const uint32_t bstage = b0 + (uint32_t)(s * PARTS * tile_bytes);
@@ -135,16 +150,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
           tc_fence_after();
           const uint32_t d = tmem + slot * BN;
           const uint32_t atile = a0 + (uint32_t)(m * PARTS * tile_bytes);
+          // outputs on lanes: A = T^T slice, B = G stage; cells on lanes: A = G, B = T^T
+          const uint32_t xo = LANES ? bstage : atile, xc = LANES ? atile : bstage;
           uint32_t acc = 0;
           for (int ks = 0; ks < ksteps; ++ks) {
             const uint32_t ko = (uint32_t)ks * 256u;
             if constexpr (PT::split) {
               // small terms first: T_hi G_lo, T_lo G_hi, then T_hi G_hi
-              mma<PT::tf32>(d, make_desc(atile + ko, sbo), make_desc(bstage + tile_bytes + ko, sbo), IDESC, acc);
+              const uint32_t ahl = LANES ? xo + tile_bytes : xo, bhl = LANES ? xc : xc + tile_bytes;
+              mma<PT::tf32>(d, make_desc(ahl + ko, sbo), make_desc(bhl + ko, sbo), idesc, acc);
               acc = 1;
-              mma<PT::tf32>(d, make_desc(atile + tile_bytes + ko, sbo), make_desc(bstage + ko, sbo), IDESC, 1);
+              const uint32_t alh = LANES ? xo : xo + tile_bytes, blh = LANES ? xc + tile_bytes : xc;
+              mma<PT::tf32>(d, make_desc(alh + ko, sbo), make_desc(blh + ko, sbo), idesc, 1);
             }
-            mma<PT::tf32>(d, make_desc(atile + ko, sbo), make_desc(bstage + ko, sbo), IDESC, acc);
+            mma<PT::tf32>(d, make_desc(xo + ko, sbo), make_desc(xc + ko, sbo), idesc, acc);
             acc = 1;
           }
           tc_commit(smem_u32(&bars->tfull[slot]));
@@ -156,41 +175,86 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
       mbar_wait(smem_u32(&bars->done), 0, p.err);
     }
     __syncwarp();
+  } else if constexpr (LANES) {
+    // ---------------- epilogue, cells on lanes: each thread writes its cell's row ----------------
+    const int q = warp;  // lanes 32q..32q+31 = cells of the tile
+    const bool vec = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(p.out) & 15) == 0;
+    uint32_t rc = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++rc) {
+      const uint32_t slot = rc % RING, round = rc / RING;
+      if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) { ok = false; break; }
+      tc_fence_after();
+      const int64_t cell = t * BN + q * 32 + lane;
+      float* row = p.out + cell * N;
+      if (t * BN + q * 32 < p.ncells) {  // warp-uniform
+        for (int c0 = 0; c0 < NP; c0 += 32) {
+          uint32_t v[32];
+          if (NP - c0 >= 32) {
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + slot * BN + c0, v);
+          } else {
+            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + slot * BN + c0,
+                      *reinterpret_cast<uint32_t(*)[16]>(v));
+          }
+          tmem_wait_ld();
+          if (cell < p.ncells) {
+            const int w = (N - c0) < 32 ? N - c0 : 32;
+            if (vec) {
+#pragma unroll
+              for (int k = 0; k < 8; ++k)
+                if (4 * k < w)
+                  __stcs(reinterpret_cast<float4*>(row + c0 + 4 * k),
+                         make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
+                                     __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3])));
+            } else {
+#pragma unroll
+              for (int k = 0; k < 32; ++k)
+                if (k < w) __stcs(row + c0 + k, __uint_as_float(v[k]));
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
+    }
   } else {
-    // ---------------- epilogue: TMEM -> registers -> global ----------------
-    const int q = warp & 3, half = warp >> 2;
+    // ---------------- epilogue, direct 128-byte stores ----------------
+    const int q = warp;  // TMEM lane quadrant
     uint32_t rc = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const int64_t cbase = t * BN + half * 64;
-      const int64_t rem = p.ncells - cbase;
-      const int ncol = rem < 64 ? (int)rem : 64;
       for (int m = 0; m < p.mtiles; ++m, ++rc) {
         const uint32_t slot = rc % RING, round = rc / RING;
         if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) { ok = false; break; }
         tc_fence_after();
         const int o = m * BM + q * 32 + lane;
-        if (m * BM + q * 32 < p.N && ncol > 0) {
-          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + slot * BN + half * 64;
-          uint32_t v0[32], v1[32];
-          tmem_ld32(taddr, v0);
-          tmem_ld32(taddr + 32, v1);
-          tmem_wait_ld();
-          if (o < p.N) {
-            float* dst = p.out + cbase * p.N + o;
-            const int64_t stride = p.N;
-            if (ncol == 64) {
+        for (int half = 0; half < 2; ++half) {
+          const int64_t cbase = t * BN + half * 64;
+          const int64_t rem = p.ncells - cbase;
+          const int ncol = rem <= 0 ? 0 : (rem < 64 ? (int)rem : 64);
+          if (m * BM + q * 32 < N && ncol > 0) {
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + slot * BN + half * 64;
+            uint32_t v0[32], v1[32];
+            tmem_ld32(taddr, v0);
+            tmem_ld32(taddr + 32, v1);
+            tmem_wait_ld();
+            if (o < N) {
+              float* dst = p.out + cbase * N + o;
+              const int64_t stride = N;
+              if (ncol == 64) {
 #pragma unroll
-              for (int j = 0; j < 32; ++j) __stcs(dst + j * stride, __uint_as_float(v0[j]));
+                for (int jj = 0; jj < 32; ++jj) __stcs(dst + jj * stride, __uint_as_float(v0[jj]));
 #pragma unroll
-              for (int j = 0; j < 32; ++j) __stcs(dst + (32 + j) * stride, __uint_as_float(v1[j]));
-            } else {
+                for (int jj = 0; jj < 32; ++jj) __stcs(dst + (32 + jj) * stride, __uint_as_float(v1[jj]));
+              } else {
 #pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (j < ncol) __stcs(dst + j * stride, __uint_as_float(v0[j]));
+                for (int jj = 0; jj < 32; ++jj)
+                  if (jj < ncol) __stcs(dst + jj * stride, __uint_as_float(v0[jj]));
 #pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (32 + j < ncol) __stcs(dst + (32 + j) * stride, __uint_as_float(v1[j]));
+                for (int jj = 0; jj < 32; ++jj)
+                  if (32 + jj < ncol) __stcs(dst + (32 + jj) * stride, __uint_as_float(v1[jj]));
+              }
             }
           }
         }
@@ -218,6 +282,9 @@ struct Geom {
   int K, kelems, kbytes, parts, mtiles, N;
 };
 
+// Cells-on-lanes orientation: the element matrix fits one 128-output slice
+bool lanes_ok(int mtiles) { return mtiles == 1; }
+
 bool geom_of(int form, int degree, int cell, int prec, Geom& g) {
   if (form == FORM_BURGERS) return false;
   if (prec == PREC_FP64) return false;
@@ -237,29 +304,36 @@ int stages_for(const Geom& g) {
   const int a = g.mtiles * g.parts * BM * g.kbytes;
   const int b = g.parts * BN * g.kbytes;
   const int fixed = a + (int)sizeof(Barriers) + 1024 + 64;
-  int s = MAX_STAGES;
-  while (s >= 2 && fixed + s * b > SMEM_LIMIT) --s;
+  int s = MAX_STAGES;  // even: the stages are split between the two producer groups
+  while (s >= 2 && fixed + s * b > SMEM_LIMIT) s -= 2;
   return s >= 2 ? s : 0;
 }
 
 template <int FORM, int D, int PREC>
-cudaError_t launch_typed(const TcParams& p, int num_sms, cudaStream_t s, int nstages, int smem) {
-  auto kern = k_assemble_tc<FORM, D, PREC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+cudaError_t launch_typed(const TcParams& p, int num_sms, cudaStream_t s, int nstages, int smem, bool lanes) {
   const int64_t ntiles = (p.ncells + BN - 1) / BN;
   const int grid = (int)std::min<int64_t>(ntiles, num_sms);
-  kern<<<grid, NTHREADS, smem, s>>>(p, nstages);
+  if (lanes) {
+    auto kern = k_assemble_tc<FORM, D, PREC, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NTHREADS, smem, s>>>(p, nstages);
+  } else {
+    auto kern = k_assemble_tc<FORM, D, PREC, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NTHREADS, smem, s>>>(p, nstages);
+  }
   return cudaGetLastError();
 }
 
 template <int FORM, int D>
-cudaError_t launch_prec(int prec, const TcParams& p, int num_sms, cudaStream_t s, int nst, int smem) {
+cudaError_t launch_prec(int prec, const TcParams& p, int num_sms, cudaStream_t s, int nst, int smem, bool lanes) {
   switch (prec) {
-    case PREC_TF32: return launch_typed<FORM, D, PREC_TF32>(p, num_sms, s, nst, smem);
-    case PREC_TF32X3: return launch_typed<FORM, D, PREC_TF32X3>(p, num_sms, s, nst, smem);
-    case PREC_BF16: return launch_typed<FORM, D, PREC_BF16>(p, num_sms, s, nst, smem);
-    case PREC_BF16X3: return launch_typed<FORM, D, PREC_BF16X3>(p, num_sms, s, nst, smem);
+    case PREC_TF32: return launch_typed<FORM, D, PREC_TF32>(p, num_sms, s, nst, smem, lanes);
+    case PREC_TF32X3: return launch_typed<FORM, D, PREC_TF32X3>(p, num_sms, s, nst, smem, lanes);
+    case PREC_BF16: return launch_typed<FORM, D, PREC_BF16>(p, num_sms, s, nst, smem, lanes);
+    case PREC_BF16X3: return launch_typed<FORM, D, PREC_BF16X3>(p, num_sms, s, nst, smem, lanes);
   }
   return cudaErrorInvalidValue;
 }
@@ -326,7 +400,11 @@ int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, 
   g.kbytes = p.kbytes;
   g.parts = p.parts;
   g.mtiles = p.mtiles;
-  const int nst = stages_for(g);
+  g.N = p.N;
+  // cells on the lanes only pays for tiny element matrices (measured: P1 tets gain, P2 loses)
+  const bool lanes = !(p.tune & TUNE_OUTPUT_LANES) && lanes_ok(p.mtiles) && p.N <= 32;
+  int nst = stages_for(g);
+  if (nst > 2 && (p.tune & TUNE_TWO_STAGES)) nst = 2;
   if (nst == 0) {
     // T^T does not fit beside the operand stages: stream it per M-tile instead
     BatchGroup bg;
@@ -340,22 +418,23 @@ int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, 
     }
     return launch_stream_one(bg, num_sms, stream);
   }
-  int smem = g.mtiles * g.parts * BM * g.kbytes + nst * g.parts * BN * g.kbytes + (int)sizeof(Barriers) + 1024 + 64;
+  int smem = g.mtiles * g.parts * BM * g.kbytes + nst * g.parts * BN * g.kbytes +
+             (int)sizeof(Barriers) + 1024 + 64;
   if (smem < SMEM_ONE_CTA) smem = SMEM_ONE_CTA;
   const bool tri = cell == CELL_TRI;
   cudaError_t e = cudaErrorInvalidValue;
   switch (form) {
     case FORM_MASS:
-      e = tri ? launch_prec<FORM_MASS, 2>(p.precision, p, num_sms, s, nst, smem)
-              : launch_prec<FORM_MASS, 3>(p.precision, p, num_sms, s, nst, smem);
+      e = tri ? launch_prec<FORM_MASS, 2>(p.precision, p, num_sms, s, nst, smem, lanes)
+              : launch_prec<FORM_MASS, 3>(p.precision, p, num_sms, s, nst, smem, lanes);
       break;
     case FORM_HELMHOLTZ:
-      e = tri ? launch_prec<FORM_HELMHOLTZ, 2>(p.precision, p, num_sms, s, nst, smem)
-              : launch_prec<FORM_HELMHOLTZ, 3>(p.precision, p, num_sms, s, nst, smem);
+      e = tri ? launch_prec<FORM_HELMHOLTZ, 2>(p.precision, p, num_sms, s, nst, smem, lanes)
+              : launch_prec<FORM_HELMHOLTZ, 3>(p.precision, p, num_sms, s, nst, smem, lanes);
       break;
     case FORM_ADVDIFF:
-      e = tri ? launch_prec<FORM_ADVDIFF, 2>(p.precision, p, num_sms, s, nst, smem)
-              : launch_prec<FORM_ADVDIFF, 3>(p.precision, p, num_sms, s, nst, smem);
+      e = tri ? launch_prec<FORM_ADVDIFF, 2>(p.precision, p, num_sms, s, nst, smem, lanes)
+              : launch_prec<FORM_ADVDIFF, 3>(p.precision, p, num_sms, s, nst, smem, lanes);
       break;
   }
   return (int)e;

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
     }
     for (int r = 0; r < RING; ++r) {
       mbar_init(smem_u32(&bars->tfull[r]), 1);
-      mbar_init(smem_u32(&bars->tempty[r]), 8);
+      mbar_init(smem_u32(&bars->tempty[r]), EPI_WARPS);
     }
     mbar_init(smem_u32(&bars->done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -90,10 +90,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
 
   if (warp >= PROD_WARP0 && warp < MMA_WARP) {
     // ---------------- producers: one cell per thread, one block per stage ----------------
-    const int row = threadIdx.x - PROD_WARP0 * 32;
-    int it = 0;
+    const int pw = warp - PROD_WARP0;
+    const int grp = pw >> 2, row = ((pw & 3) << 5) + lane;
+    const int spg = nstages / PROD_GROUPS;
     bool ok = true;
-    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    for (int64_t tl = grp; ok; tl += PROD_GROUPS) {  // local tile number; groups alternate
+      const int64_t t = blockIdx.x + tl * gridDim.x;
+      if (t >= ntiles) break;
+      int64_t li = (tl / PROD_GROUPS) * NB;  // index among this group's blocks
       const int64_t e = t * BN + row;
       float u[NS][D], Pm[D][D], Q[NS][D], H[P];
       bool live = e < p.ncells, bad = false;
@@ -151,10 +155,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
         }
       }
 #pragma unroll
-      for (int blk = 0; blk < NB; ++blk, ++it) {
+      for (int blk = 0; blk < NB; ++blk, ++li) {
         const int ci = blk / D, cj = blk % D;
-        const int s = it % nstages;
-        const uint32_t use = (uint32_t)(it / nstages);
+        int s;
+        uint32_t use;
+        stage_of(li, grp, spg, s, use);
         if (!mbar_wait(smem_u32(&bars->empty[s]), (use & 1u) ^ 1u, p.err)) { ok = false; break; }
         float G[KD];
 #pragma unroll
@@ -188,14 +193,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
       const uint32_t sbo = 8u * (uint32_t)kbytes;
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
       uint32_t rc = 0;
-      int it = 0;
+      const int spg = nstages / PROD_GROUPS;
+      int64_t tl = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        for (int blk = 0; blk < NB && ok; ++blk, ++it) {
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+        const int grp = (int)(tl % PROD_GROUPS);
+        for (int blk = 0; blk < NB && ok; ++blk) {
           const bool diag = (blk / D) == (blk % D);
           const int ksteps = diag ? KD / S::KSTEP : KA1 / S::KSTEP;
-          const int s = it % nstages;
-          const uint32_t use = (uint32_t)(it / nstages);
+          int s;
+          uint32_t use;
+          stage_of((tl / PROD_GROUPS) * NB + blk, grp, spg, s, use);
           if (!mbar_wait(smem_u32(&bars->full[s]), use & 1u, p.err)) { ok = false; break; }
           tc_fence_after();
           const uint32_t bstage = b0 + (uint32_t)(s * PARTS * tile_bytes);
@@ -227,14 +235,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
     __syncwarp();
   } else {
     // ---------------- epilogue ----------------
-    const int q = warp & 3, half = warp >> 2;
+    const int q = warp;  // TMEM lane quadrant
     const int ndof = D * NS;
     uint32_t rc = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const int64_t cbase = t * BN + half * 64;
-      const int64_t rem = p.ncells - cbase;
-      const int ncol = rem < 64 ? (int)rem : 64;
       for (int blk = 0; blk < NB && ok; ++blk) {
         const int ci = blk / D, cj = blk % D;
         for (int m = 0; m < S::MT; ++m, ++rc) {
@@ -242,6 +247,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
           if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) { ok = false; break; }
           tc_fence_after();
           const int o = m * BM + q * 32 + lane;  // entry (i, j) of the block
+          for (int half = 0; half < 2; ++half) {
+          const int64_t cbase = t * BN + half * 64;
+          const int64_t rem = p.ncells - cbase;
+          const int ncol = rem <= 0 ? 0 : (rem < 64 ? (int)rem : 64);
           if (m * BM + q * 32 < S::NBLK && ncol > 0) {
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + slot * BN + half * 64;
             uint32_t v0[32], v1[32];
@@ -259,6 +268,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
               for (int jj = 0; jj < 32; ++jj)
                 if (32 + jj < ncol) __stcs(dst + (32 + jj) * stride, __uint_as_float(v1[jj]));
             }
+          }
           }
           tc_fence_before();
           __syncwarp();
@@ -306,8 +316,8 @@ int bstages(const BGeom& g) {
   const int a = g.mtiles * g.parts * BM * g.kbytes;
   const int b = g.parts * BN * g.kbytes;
   const int fixed = a + (int)sizeof(Barriers) + 1024 + 64;
-  int s = MAX_STAGES;
-  while (s >= 2 && fixed + s * b > SMEM_LIMIT) --s;
+  int s = MAX_STAGES;  // even: the stages are split between the two producer groups
+  while (s >= 2 && fixed + s * b > SMEM_LIMIT) s -= 2;
   return s >= 2 ? s : 0;
 }
 

@@ -13,9 +13,20 @@ namespace tc {
 
 constexpr int BN = 128;             // cells per tile = MMA N
 constexpr int BM = 128;             // output rows per MMA = MMA M
-constexpr int NTHREADS = 13 * 32;   // 8 epilogue, 4 producer, 1 MMA warp
-constexpr int PROD_WARP0 = 8;
+constexpr int NTHREADS = 13 * 32;   // 4 epilogue, 8 producer (two groups), 1 MMA warp
+constexpr int EPI_WARPS = 4;        // warps 0..3, one per TMEM lane quadrant
+constexpr int PROD_WARP0 = 4;       // warps 4..11: producer groups 0 and 1 take alternate tiles
+constexpr int PROD_GROUPS = 2;
 constexpr int MMA_WARP = 12;
+
+// Operand stages are split between the producer groups (stages g, g+2, ..): a group only
+// ever waits for the release of its own previous use of a stage, one phase back, which
+// is what parity-based mbarrier waits can tell apart. li is the item's index among its
+// group's items; spg = stages per group.
+__host__ __device__ __forceinline__ void stage_of(int64_t li, int grp, int spg, int& s, uint32_t& use) {
+  s = grp + PROD_GROUPS * (int)(li % spg);
+  use = (uint32_t)(li / spg);
+}
 constexpr int RING = 4;             // TMEM accumulator slots of BN columns
 constexpr int TMEM_COLS = RING * BN;
 constexpr int MAX_STAGES = 4;
@@ -119,6 +130,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 1-D bulk store of `bytes` (multiple of 16) from shared to global memory (bulk group).
+__device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until at most one bulk group of this thread still reads its shared-memory source
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// 32 lanes x 16 consecutive columns of 32-bit data -> 16 registers per thread
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
 
 // ------------------------------------------------------- operand splitting
 __device__ __forceinline__ uint32_t tf32_rna(float x) {

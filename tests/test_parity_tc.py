@@ -153,3 +153,19 @@ def test_burgers_permuted_numbering_tc():
     out = coffee.assemble(BURGERS_JAC, 2, TET, x, c2v, cf, cd, precision=coffee.TF32X3, validate=True)
     coffee.check_errors()
     assert rel_err_per_cell(out.cpu().numpy(), ref) < 1e-5
+
+
+@pytest.mark.parametrize("form,cell,k", [(HELMHOLTZ, TET, 3), (HELMHOLTZ, TET, 1), (ADVDIFF, TET, 2),
+                                         (MASS, TRI, 2), (HELMHOLTZ, TET, 4), (BURGERS_JAC, TET, 2)])
+def test_tuning_knobs_give_identical_results(form, cell, k):
+    """The autotuner's knobs (cells or outputs on the TMEM lanes, operand stages) change
+    only speed: every setting writes bit-identical element matrices."""
+    mesh = ragged_mesh(cell, seed=60 + k)
+    coef, c2d = coefficients(form, mesh, k, seed=61)
+    x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    outs = [coffee.assemble(form, k, cell, x, c2v, cf, cd, precision=coffee.TF32X3, tune=t)
+            for t in (0, coffee.FLAG_OUTPUT_LANES, coffee.FLAG_TWO_STAGES,
+                      coffee.FLAG_OUTPUT_LANES | coffee.FLAG_TWO_STAGES)]
+    torch.cuda.synchronize()
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
