@@ -96,6 +96,14 @@ typedef enum {
  * TWO_STAGES: at most two operand stages (leaves shared memory to other kernels). */
 #define COFFEE_FLAG_OUTPUT_LANES 2u
 #define COFFEE_FLAG_TWO_STAGES 4u
+/* cells per TMEM accumulator when the outputs are on the lanes (tile shape of the MMA:
+ * M = 128 outputs x N = 128, 64 or 32 cells); default 128, or 64 above 512 outputs */
+#define COFFEE_FLAG_SUBTILE_64 8u
+#define COFFEE_FLAG_SUBTILE_32 16u
+#define COFFEE_FLAG_SUBTILE_128 32u
+/* cells on the TMEM lanes (M = 128 cells, N = entries) for element matrices of up to 128
+ * entries; by default only up to 32 entries */
+#define COFFEE_FLAG_CELL_LANES 64u
 
 /* Number of rows of the element matrix: (k+1)(k+2)/2 (triangle) or
  * (k+1)(k+2)(k+3)/6 (tetrahedron), times d for BURGERS_JAC. Negative on error. */

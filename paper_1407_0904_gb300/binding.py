@@ -17,6 +17,10 @@ FP64, TF32, TF32X3, BF16, BF16X3 = 0, 1, 2, 3, 4
 FLAG_VALIDATE = 1
 FLAG_OUTPUT_LANES = 2   # tuning knob: element-matrix entries on the TMEM lanes
 FLAG_TWO_STAGES = 4     # tuning knob: at most two operand stages
+FLAG_SUBTILE_64 = 8     # tuning knob: 64 cells per TMEM accumulator
+FLAG_SUBTILE_32 = 16    # tuning knob: 32 cells per TMEM accumulator
+FLAG_SUBTILE_128 = 32   # tuning knob: 128 cells per TMEM accumulator
+FLAG_CELL_LANES = 64    # tuning knob: cells on the TMEM lanes (element matrices <= 128 entries)
 
 FORM_NAMES = {MASS: "mass", HELMHOLTZ: "helmholtz", ADVDIFF: "advdiff", BURGERS_JAC: "burgers_jac"}
 PRECISION_NAMES = {FP64: "fp64", TF32: "tf32", TF32X3: "tf32x3", BF16: "bf16", BF16X3: "bf16x3"}
@@ -368,6 +372,12 @@ class BatchPlan:
             arr[i] = a
             self.outputs.append(out)
             self._keep.append((g["coords"], g["cell2vert"], g.get("coef"), g.get("cell2dof"), out))
+        if item_overhead is None or item_overhead < 0:
+            try:
+                from . import tune as _tune
+                item_overhead = float(_tune.load_batch().get("item_overhead", -1.0))
+            except Exception:
+                item_overhead = -1.0
         self._plan = ctypes.c_void_p()
         _check(L.coffee_batch_plan(arr, len(groups), grid, item_overhead, ctypes.byref(self._plan)))
 

@@ -226,7 +226,11 @@ int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream) {
   p.parts = meta.parts;
   p.ksteps_off = meta.ksteps_off;
   p.tune = ((a->flags & COFFEE_FLAG_OUTPUT_LANES) ? TUNE_OUTPUT_LANES : 0u) |
-           ((a->flags & COFFEE_FLAG_TWO_STAGES) ? TUNE_TWO_STAGES : 0u);
+           ((a->flags & COFFEE_FLAG_TWO_STAGES) ? TUNE_TWO_STAGES : 0u) |
+           ((a->flags & COFFEE_FLAG_SUBTILE_64) ? TUNE_SUB64 : 0u) |
+           ((a->flags & COFFEE_FLAG_SUBTILE_32) ? TUNE_SUB32 : 0u) |
+           ((a->flags & COFFEE_FLAG_SUBTILE_128) ? TUNE_SUB128 : 0u) |
+           ((a->flags & COFFEE_FLAG_CELL_LANES) ? TUNE_CELL_LANES : 0u);
   p.precision = a->precision;
   p.validate = validate ? 1 : 0;
   p.nu = a->nu;

@@ -13,7 +13,8 @@ enum { PREC_FP64 = 0, PREC_TF32 = 1, PREC_TF32X3 = 2, PREC_BF16 = 3, PREC_BF16X3
 // Device error word bits
 enum : unsigned { ERR_INDEX = 1u, ERR_TIMEOUT = 2u };
 // Tuning knobs of the tensor-core kernels (from coffee_assemble_args.flags)
-enum : unsigned { TUNE_OUTPUT_LANES = 1u, TUNE_TWO_STAGES = 2u };
+enum : unsigned { TUNE_OUTPUT_LANES = 1u, TUNE_TWO_STAGES = 2u, TUNE_SUB64 = 4u, TUNE_SUB32 = 8u, TUNE_SUB128 = 16u,
+                  TUNE_CELL_LANES = 32u };
 
 // ---- host tabulation (tabulate.cpp) ----
 int nnodes(int cell, int k);
@@ -97,6 +98,7 @@ struct TcParams {
   int mtiles, kbytes, parts;
   int ksteps_off;        // Burgers: K-steps of the off-diagonal component blocks
   unsigned tune;         // TUNE_* knobs
+  int subw;              // cells per TMEM accumulator (outputs-on-lanes orientation)
   int precision;
   int validate;
   double nu;

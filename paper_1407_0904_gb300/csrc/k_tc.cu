@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
       mbar_init(smem_u32(&bars->full[s]), 128);
       mbar_init(smem_u32(&bars->empty[s]), 1);
     }
-    for (int r = 0; r < RING; ++r) {
+    for (int r = 0; r < MAX_SLOTS; ++r) {
       mbar_init(smem_u32(&bars->tfull[r]), 1);
       mbar_init(smem_u32(&bars->tempty[r]), EPI_WARPS);
     }
@@ -103,18 +103,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
     const int pw = warp - PROD_WARP0;
     const int grp = pw >> 2, row = ((pw & 3) << 5) + lane;
     const int spg = nstages / PROD_GROUPS;
+    const int64_t tstep = (int64_t)PROD_GROUPS * gridDim.x;
     int64_t li = 0;
-    for (int64_t t = blockIdx.x + (int64_t)grp * gridDim.x; t < ntiles;
-         t += (int64_t)PROD_GROUPS * gridDim.x, ++li) {
+    CellIds<FORM, D> ids{}, nids{};  // this tile's and (prefetched) the next tile's index rows
+    {
+      const int64_t e0 = (blockIdx.x + (int64_t)grp * gridDim.x) * BN + row;
+      if (e0 < p.ncells) load_ids<FORM, D>(p, e0, nids);
+    }
+    for (int64_t t = blockIdx.x + (int64_t)grp * gridDim.x; t < ntiles; t += tstep, ++li) {
+      const int64_t e = t * BN + row;
+      ids = nids;
+      if (e + tstep * BN < p.ncells) load_ids<FORM, D>(p, e + tstep * BN, nids);
       int s;
       uint32_t use;
       stage_of(li, grp, spg, s, use);
       if (!mbar_wait(smem_u32(&bars->empty[s]), (use & 1u) ^ 1u, p.err)) break;
-      const int64_t e = t * BN + row;
       float G[KP];
       bool bad = false;
       if (e < p.ncells) {
-        cell_factors<FORM, D, KP>(p, e, G, bad);
+        cell_factors_ids<FORM, D, KP>(p, ids, G, bad);
         if (bad) atomicOr(p.err, ERR_INDEX);
       }
       if (e >= p.ncells || bad) {
@@ -132,7 +139,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
       const int ksteps = kbytes / 32;
       const uint32_t sbo = 8u * (uint32_t)kbytes;
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-      const uint32_t idesc = make_idesc(PT::tf32 ? 2 : 1, BM, LANES ? NP : BN);
+      const int W = LANES ? BN : p.subw;       // cells per accumulator
+      const int nslot = LANES ? RING : 512 / W;
+      const uint32_t idesc = make_idesc(PT::tf32 ? 2 : 1, BM, LANES ? NP : W);
       uint32_t rc = 0;  // accumulator ring counter
       const int spg = nstages / PROD_GROUPS;
       int64_t tl = 0;  // local tile number
@@ -144,14 +153,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
         if (!mbar_wait(smem_u32(&bars->full[s]), use & 1u, p.err)) break;
         tc_fence_after();
         const uint32_t bstage = b0 + (uint32_t)(s * PARTS * tile_bytes);
+        for (int j = 0; j < BN / W && ok; ++j)
         for (int m = 0; m < p.mtiles; ++m, ++rc) {
-          const uint32_t slot = rc % RING, round = rc / RING;
+          const uint32_t slot = rc % nslot, round = rc / nslot;
           if (!mbar_wait(smem_u32(&bars->tempty[slot]), (round & 1u) ^ 1u, p.err)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t d = tmem + slot * BN;
+          const uint32_t d = tmem + slot * W;
           const uint32_t atile = a0 + (uint32_t)(m * PARTS * tile_bytes);
+          const uint32_t bsub = bstage + (uint32_t)(j * W * kbytes);  // cells j*W.. of the stage
           // outputs on lanes: A = T^T slice, B = G stage; cells on lanes: A = G, B = T^T
-          const uint32_t xo = LANES ? bstage : atile, xc = LANES ? atile : bstage;
+          const uint32_t xo = LANES ? bstage : atile, xc = LANES ? atile : bsub;
           uint32_t acc = 0;
           for (int ks = 0; ks < ksteps; ++ks) {
             const uint32_t ko = (uint32_t)ks * 256u;
@@ -221,23 +232,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
   } else {
     // ---------------- epilogue, direct 128-byte stores ----------------
     const int q = warp;  // TMEM lane quadrant
+    const int W = p.subw, nslot = 512 / W;
     uint32_t rc = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int j = 0; j < BN / W && ok; ++j)
       for (int m = 0; m < p.mtiles; ++m, ++rc) {
-        const uint32_t slot = rc % RING, round = rc / RING;
+        const uint32_t slot = rc % nslot, round = rc / nslot;
         if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) { ok = false; break; }
         tc_fence_after();
         const int o = m * BM + q * 32 + lane;
-        for (int half = 0; half < 2; ++half) {
-          const int64_t cbase = t * BN + half * 64;
+        for (int cc = 0; cc < W; cc += 64) {
+          const int cw = W - cc < 64 ? W - cc : 64;  // 64 or 32 columns
+          const int64_t cbase = t * BN + j * W + cc;
           const int64_t rem = p.ncells - cbase;
-          const int ncol = rem <= 0 ? 0 : (rem < 64 ? (int)rem : 64);
+          const int ncol = rem <= 0 ? 0 : (rem < cw ? (int)rem : cw);
           if (m * BM + q * 32 < N && ncol > 0) {
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + slot * BN + half * 64;
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + slot * W + cc;
             uint32_t v0[32], v1[32];
             tmem_ld32(taddr, v0);
-            tmem_ld32(taddr + 32, v1);
+            if (cw == 64) tmem_ld32(taddr + 32, v1);
             tmem_wait_ld();
             if (o < N) {
               float* dst = p.out + cbase * N + o;
@@ -402,7 +416,13 @@ int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, 
   g.mtiles = p.mtiles;
   g.N = p.N;
   // cells on the lanes only pays for tiny element matrices (measured: P1 tets gain, P2 loses)
-  const bool lanes = !(p.tune & TUNE_OUTPUT_LANES) && lanes_ok(p.mtiles) && p.N <= 32;
+  const bool lanes = !(p.tune & TUNE_OUTPUT_LANES) && lanes_ok(p.mtiles) &&
+                     (p.N <= 32 || (p.tune & TUNE_CELL_LANES));
+  // cells per accumulator (outputs on lanes): narrower sub-tiles finish whole rows sooner,
+  // which keeps the open rows of large element matrices within L2
+  TcParams q = p;
+  q.subw = (p.tune & TUNE_SUB32) ? 32 : (p.tune & TUNE_SUB64) ? 64 : (p.tune & TUNE_SUB128) ? 128
+                                                                                             : (p.mtiles > 4 ? 64 : 128);
   int nst = stages_for(g);
   if (nst > 2 && (p.tune & TUNE_TWO_STAGES)) nst = 2;
   if (nst == 0) {
@@ -425,16 +445,16 @@ int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, 
   cudaError_t e = cudaErrorInvalidValue;
   switch (form) {
     case FORM_MASS:
-      e = tri ? launch_prec<FORM_MASS, 2>(p.precision, p, num_sms, s, nst, smem, lanes)
-              : launch_prec<FORM_MASS, 3>(p.precision, p, num_sms, s, nst, smem, lanes);
+      e = tri ? launch_prec<FORM_MASS, 2>(q.precision, q, num_sms, s, nst, smem, lanes)
+              : launch_prec<FORM_MASS, 3>(q.precision, q, num_sms, s, nst, smem, lanes);
       break;
     case FORM_HELMHOLTZ:
-      e = tri ? launch_prec<FORM_HELMHOLTZ, 2>(p.precision, p, num_sms, s, nst, smem, lanes)
-              : launch_prec<FORM_HELMHOLTZ, 3>(p.precision, p, num_sms, s, nst, smem, lanes);
+      e = tri ? launch_prec<FORM_HELMHOLTZ, 2>(q.precision, q, num_sms, s, nst, smem, lanes)
+              : launch_prec<FORM_HELMHOLTZ, 3>(q.precision, q, num_sms, s, nst, smem, lanes);
       break;
     case FORM_ADVDIFF:
-      e = tri ? launch_prec<FORM_ADVDIFF, 2>(p.precision, p, num_sms, s, nst, smem, lanes)
-              : launch_prec<FORM_ADVDIFF, 3>(p.precision, p, num_sms, s, nst, smem, lanes);
+      e = tri ? launch_prec<FORM_ADVDIFF, 2>(q.precision, q, num_sms, s, nst, smem, lanes)
+              : launch_prec<FORM_ADVDIFF, 3>(q.precision, q, num_sms, s, nst, smem, lanes);
       break;
   }
   return (int)e;

@@ -29,6 +29,7 @@ __host__ __device__ __forceinline__ void stage_of(int64_t li, int grp, int spg, 
 }
 constexpr int RING = 4;             // TMEM accumulator slots of BN columns
 constexpr int TMEM_COLS = RING * BN;
+constexpr int MAX_SLOTS = 16;       // accumulator slots of 32 columns (narrowest sub-tile)
 constexpr int MAX_STAGES = 4;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr float KAPPA_FP64 = 32.0f;  // Frobenius condition number above which geometry is FP64
@@ -300,22 +301,42 @@ struct Form {
 };
 
 // Per-cell factors G[0..KP) (zero padded) for MASS / HELMHOLTZ / ADVDIFF.
+// The cell's index rows (cell2vert, and cell2dof for ADVDIFF); loaded one tile ahead by
+// the producers so that their DRAM latency overlaps the previous cell's work.
+template <int FORM, int D>
+struct CellIds {
+  int vid[D + 1];
+  int cid[FORM == FORM_ADVDIFF ? D + 1 : 1];
+};
+
+template <int FORM, int D>
+__device__ __forceinline__ void load_ids(const TcParams& p, int64_t e, CellIds<FORM, D>& ids) {
+  constexpr int NV = D + 1;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) ids.vid[v] = __ldg(p.c2v + e * NV + v);
+  if constexpr (FORM == FORM_ADVDIFF) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ids.cid[v] = __ldg(p.c2d + e * NV + v);
+  }
+}
+
 template <int FORM, int D, int KP>
-__device__ __forceinline__ void cell_factors(const TcParams& p, int64_t e, float (&G)[KP], bool& bad) {
+__device__ __forceinline__ void cell_factors_ids(const TcParams& p, const CellIds<FORM, D>& ids, float (&G)[KP],
+                                                 bool& bad) {
   constexpr int NV = D + 1, P = D * (D + 1) / 2;
 #pragma unroll
   for (int k = 0; k < KP; ++k) G[k] = 0.f;
   int vid[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    vid[v] = __ldg(p.c2v + e * NV + v);
+    vid[v] = ids.vid[v];
     if (p.validate && (vid[v] < 0 || vid[v] >= p.nverts)) bad = true;
   }
   int cid[NV];
   if constexpr (FORM == FORM_ADVDIFF) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      cid[v] = __ldg(p.c2d + e * NV + v);
+      cid[v] = ids.cid[v];
       if (p.validate && (cid[v] < 0 || cid[v] >= p.ncoefnodes)) bad = true;
     }
   }
@@ -368,11 +389,18 @@ __device__ __forceinline__ void cell_factors(const TcParams& p, int64_t e, float
   }
 }
 
+template <int FORM, int D, int KP>
+__device__ __forceinline__ void cell_factors(const TcParams& p, int64_t e, float (&G)[KP], bool& bad) {
+  CellIds<FORM, D> ids;
+  load_ids<FORM, D>(p, e, ids);
+  cell_factors_ids<FORM, D, KP>(p, ids, G, bad);
+}
+
 struct alignas(8) Barriers {
   uint64_t full[MAX_STAGES];
   uint64_t empty[MAX_STAGES];
-  uint64_t tfull[RING];
-  uint64_t tempty[RING];
+  uint64_t tfull[MAX_SLOTS];
+  uint64_t tempty[MAX_SLOTS];
   uint64_t done;
   uint32_t tmem_base;
 };

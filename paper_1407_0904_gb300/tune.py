@@ -1,16 +1,199 @@
-"""Autotuner placeholder: cache location and loader (the tuner itself lands next)."""
+"""Autotuner of the tensor-core kernels.
+
+The paper chooses its transformation parameters (split factor, unroll-and-jam factor, loop
+permutation) with a cost model rather than by autotuning, because autotuning every
+generated kernel at JIT time is too slow (section 4). Here the kernels are fixed and few,
+so they are tuned once per GPU: for every (form, degree, cell, precision) the tuner times
+each combination of the kernels' knobs on a seeded synthetic mesh and records the fastest
+in a JSON cache that `assemble` consults. For the mixed batch it tunes the plan's per-item
+cost overhead (how work is balanced over the CTAs).
+
+Knobs (all give bit-identical results; only speed changes):
+  FLAG_OUTPUT_LANES   element-matrix entries on the TMEM lanes even for tiny matrices
+  FLAG_CELL_LANES     cells on the TMEM lanes for matrices of up to 128 entries
+  FLAG_SUBTILE_128/64/32  cells per TMEM accumulator with outputs on the lanes (MMA N)
+  FLAG_TWO_STAGES     at most two operand stages
+
+  python -m paper_1407_0904_gb300.tune [--ncells N] [--out PATH]
+"""
+import argparse
 import json
 import os
+import sys
+
+CACHE_VERSION = 1
 
 
 def cache_path():
-    return os.environ.get("COFFEE_TUNE_CACHE", os.path.join(os.path.dirname(os.path.abspath(__file__)),
-                                                            "tune_cache.json"))
+    return os.environ.get("COFFEE_TUNE_CACHE",
+                          os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json"))
 
 
-def load_cache():
-    p = cache_path()
+def _gpu_name():
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device()) if torch.cuda.is_available() else ""
+
+
+def load_cache(path=None, gpu=None):
+    """Entries tuned on this GPU model ({} when there is no cache for it)."""
+    p = path or cache_path()
     if not os.path.exists(p):
         return {}
     with open(p) as f:
-        return json.load(f).get("entries", {})
+        data = json.load(f)
+    if data.get("version") != CACHE_VERSION:
+        return {}
+    name = gpu if gpu is not None else _gpu_name()
+    if data.get("gpu") and name and data["gpu"] != name:
+        return {}
+    return data.get("entries", {})
+
+
+def load_batch(path=None, gpu=None):
+    """Tuned mixed-batch settings for this GPU model ({} when none)."""
+    p = path or cache_path()
+    if not os.path.exists(p) or not load_cache(p, gpu):
+        return {}
+    with open(p) as f:
+        return json.load(f).get("batch", {})
+
+
+def candidates(coffee, n_outputs):
+    F = coffee
+    c = [0, F.FLAG_TWO_STAGES, F.FLAG_SUBTILE_128, F.FLAG_SUBTILE_64, F.FLAG_SUBTILE_32,
+         F.FLAG_SUBTILE_64 | F.FLAG_TWO_STAGES]
+    if n_outputs <= 128:
+        c += [F.FLAG_OUTPUT_LANES, F.FLAG_CELL_LANES, F.FLAG_CELL_LANES | F.FLAG_TWO_STAGES]
+    return sorted(set(c))
+
+
+def _mesh(cell, ncells, seed=7):
+    from . import meshgen
+    if cell == 0:
+        n = 1
+        while 2 * n * n < ncells:
+            n += 1
+        return meshgen.tri_mesh(n, perturb=0.2, seed=seed)
+    n = 1
+    while 6 * n ** 3 < ncells:
+        n += 1
+    return meshgen.tet_mesh(n, perturb=0.15, seed=seed, ncells=ncells)
+
+
+def time_case(coffee, form, degree, cell, precision, mesh, tune, reps=20, warmup=3):
+    import torch
+    from . import meshgen
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x = torch.from_numpy(mesh.coords).to(dev)
+    c2v = torch.from_numpy(mesh.cell2vert).to(dev)
+    cf = cd = None
+    if form == coffee.ADVDIFF:
+        coef, c2d, _ = meshgen.advdiff_coefficients(mesh, seed=3)
+        cf, cd = torch.from_numpy(coef).to(dev), torch.from_numpy(c2d).to(dev)
+    elif form == coffee.BURGERS_JAC:
+        u, c2d, _ = meshgen.burgers_coefficients(mesh, degree, seed=3)
+        cf, cd = torch.from_numpy(u.ravel()).to(dev), torch.from_numpy(c2d).to(dev)
+    n = coffee.ndof(form, degree, cell)
+    out = torch.empty((mesh.ncells, n, n), dtype=torch.float32, device=dev)
+    run = lambda: coffee.assemble(form, degree, cell, x, c2v, cf, cd, precision=precision, out=out, tune=tune)
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        run()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def tune_all(forms=None, cells=(0, 1), degrees=(1, 2, 3, 4), precisions=None, ncells=2 ** 19, reps=20,
+             log=print):
+    from . import binding as coffee
+    forms = forms or (coffee.MASS, coffee.HELMHOLTZ, coffee.ADVDIFF)
+    precisions = precisions or (coffee.TF32X3,)
+    entries = {}
+    meshes = {c: _mesh(c, ncells) for c in cells}
+    for form in forms:
+        for cell in cells:
+            for k in degrees:
+                for prec in precisions:
+                    if not coffee.supported(form, k, cell, prec):
+                        continue
+                    n = coffee.ndof(form, k, cell) ** 2
+                    times = {}
+                    for t in candidates(coffee, n):
+                        times[t] = time_case(coffee, form, k, cell, prec, meshes[cell], t, reps=reps)
+                    best = min(times, key=times.get)
+                    key = "%d/%d/%d/%d" % (form, k, cell, prec)
+                    entries[key] = {"flags": int(best), "ms": times[best], "ncells": meshes[cell].ncells,
+                                    "candidates": {str(t): round(v, 5) for t, v in times.items()}}
+                    log("%s %s P%d %s: best flags %d (%.4f ms; default %.4f ms)" % (
+                        coffee.FORM_NAMES[form], "tri" if cell == 0 else "tet", k,
+                        coffee.PRECISION_NAMES[prec], best, times[best], times[0]))
+    return entries
+
+
+def tune_batch(ncells_per_mesh=2 ** 17, log=print):
+    """Per-item overhead of the batch plan's cost model, timed on a mixed batch."""
+    import torch
+    from . import binding as coffee
+    from . import meshgen
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = 1
+    while 2 * n * n < ncells_per_mesh:
+        n += 1
+    tri = meshgen.tri_mesh(n, perturb=0.2, seed=4)
+    tet = meshgen.tet_mesh(48, perturb=0.15, seed=4, ncells=ncells_per_mesh)
+    groups = []
+    for m in (tri, tet):
+        coef, c2d, _ = meshgen.advdiff_coefficients(m, seed=4)
+        x, c2v = torch.from_numpy(m.coords).to(dev), torch.from_numpy(m.cell2vert).to(dev)
+        cf, cd = torch.from_numpy(coef).to(dev), torch.from_numpy(c2d).to(dev)
+        for spec in meshgen.batch_groups(tri, tet, seed=4):
+            if spec["cell"] != m.cell:
+                continue
+            sl = slice(spec["start"], spec["start"] + spec["count"])
+            g = dict(form=spec["form"], degree=spec["degree"], cell=spec["cell"], coords=x,
+                     cell2vert=c2v[sl].contiguous())
+            if spec["form"] == coffee.ADVDIFF:
+                g["coef"], g["cell2dof"] = cf, cd[sl].contiguous()
+            groups.append(g)
+    times = {}
+    for ovh in (0.0, 4096.0, 16384.0, 65536.0, 262144.0):
+        plan = coffee.BatchPlan(groups, item_overhead=ovh)
+        for _ in range(3):
+            plan.launch()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(20):
+            plan.launch()
+        b.record()
+        torch.cuda.synchronize()
+        times[ovh] = a.elapsed_time(b) / 20
+        plan.free()
+    best = min(times, key=times.get)
+    log("batch: best item overhead %g (%.4f ms)" % (best, times[best]))
+    return {"item_overhead": best, "ms": times[best], "candidates": {str(k): round(v, 5) for k, v in times.items()}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--ncells", type=int, default=2 ** 19)
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args(argv)
+    entries = tune_all(ncells=args.ncells, reps=args.reps)
+    batch = tune_batch()
+    data = {"version": CACHE_VERSION, "gpu": _gpu_name(), "entries": entries, "batch": batch}
+    out = args.out or cache_path()
+    with open(out, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    print("wrote", out)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -165,7 +165,10 @@ def test_tuning_knobs_give_identical_results(form, cell, k):
     x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
     outs = [coffee.assemble(form, k, cell, x, c2v, cf, cd, precision=coffee.TF32X3, tune=t)
             for t in (0, coffee.FLAG_OUTPUT_LANES, coffee.FLAG_TWO_STAGES,
-                      coffee.FLAG_OUTPUT_LANES | coffee.FLAG_TWO_STAGES)]
+                      coffee.FLAG_OUTPUT_LANES | coffee.FLAG_TWO_STAGES,
+                      coffee.FLAG_OUTPUT_LANES | coffee.FLAG_SUBTILE_64,
+                      coffee.FLAG_OUTPUT_LANES | coffee.FLAG_SUBTILE_32,
+                      coffee.FLAG_SUBTILE_128, coffee.FLAG_CELL_LANES)]
     torch.cuda.synchronize()
     for o in outs[1:]:
         assert torch.equal(o, outs[0])
