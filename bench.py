@@ -34,7 +34,7 @@ L2_BYTES = 129 * 2 ** 20
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # tensor-core kernel on the headline workload, keyed by the sha256 prefix of the kernel
 # source it was measured on; reported as null once the source has changed.
-TRAFFIC = {"6c29018be2a5f373": 2.487e9}  # 31.97 MB read + 2.455 GB written (two launches)
+TRAFFIC = {"2997aae8e32b210a": 2.492e9}  # 31.87 MB read + 2.46 GB written per launch (two launches)
 
 MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC = 0, 1, 2, 3
 TRIANGLE, TETRAHEDRON = 0, 1
@@ -88,13 +88,25 @@ WORKLOADS["helmholtz-p1-tri"] = Workload("helmholtz-p1-tri", HELMHOLTZ, 1, TRIAN
                                          "unit square 64x64x2 triangles perturbed 0.2h (seed 1)", _tri64)
 
 
+# workloads with their own step (not a single-group forward launch)
+SPECIAL = {
+    "batch-mixed": "21 (form, degree) groups, Zipf(s=1) counts (seed 4): 2^19 triangles "
+                   "(512^2 x 2, P1-P4) + 2^19 Kuhn tets (64x64x22 truncated, P1-P3); mass, "
+                   "Helmholtz, advection-diffusion; one persistent launch per step",
+    "adjoint-helmholtz-p2-tet": "backward of Helmholtz P2 on 2^19 Kuhn tets (64x64x22 truncated, "
+                                "seed 5), dL/dA ~ N(0,1), atomic accumulation",
+    "adjoint-advdiff-p2-tet": "backward of advection-diffusion P2 on 2^19 Kuhn tets (64x64x22 "
+                              "truncated, seed 5), dL/dA ~ N(0,1), atomic accumulation",
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS) + sorted(SPECIAL))
     ap.add_argument("--precision", default="tf32x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -182,8 +194,9 @@ class ClockSampler:
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1407_0904_gb300", "csrc", "k_tc.cu"), "rb") as f:
-        h.update(f.read())
+    for name in ("k_tc.cu", "tc_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1407_0904_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -420,8 +433,168 @@ def l2_note(out_bytes):
     return "output %.2f MB fits in L2: no flush, a latency-bound small case" % (out_bytes / 1e6)
 
 
+def timed_steps(step, steps, warmup, world, stream):
+    """CUDA-event time of `steps` calls of step() after `warmup` untimed ones (ms total, ms per call)."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for a, b in evs:
+        a.record(stream)
+        step()
+        b.record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1), float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+
+def run_special(args):
+    """Config-4 mixed batch and config-5 adjoint workloads."""
+    import torch
+    import paper_1407_0904_gb300 as coffee
+    from paper_1407_0904_gb300 import meshgen
+    import oracle
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    prec = {v: k for k, v in coffee.PRECISION_NAMES.items()}[args.precision]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    max_err = None
+    if args.workload == "batch-mixed":
+        tri = meshgen.tri_mesh(512, perturb=0.2, seed=4)
+        tet = meshgen.tet_mesh(64, 64, 22, perturb=0.15, seed=4, ncells=2 ** 19)
+        if args.nx:
+            tri = meshgen.tri_mesh(args.nx * 4, perturb=0.2, seed=4)
+            tet = meshgen.tet_mesh(args.nx, perturb=0.15, seed=4)
+        meshes = {}
+        for m in (tri, tet):
+            coef, c2d, _ = meshgen.advdiff_coefficients(m, seed=4)
+            meshes[m.cell] = (m, torch.from_numpy(m.coords).to(dev), torch.from_numpy(m.cell2vert).to(dev),
+                              coef, c2d, torch.from_numpy(coef).to(dev), torch.from_numpy(c2d).to(dev))
+        groups, specs, per_bytes = [], [], 0.0
+        for spec in meshgen.batch_groups(tri, tet, seed=4):
+            m, x, c2v, coef, c2d, cf, cd = meshes[spec["cell"]]
+            sl = slice(spec["start"], spec["start"] + spec["count"])
+            g = dict(form=spec["form"], degree=spec["degree"], cell=spec["cell"], coords=x,
+                     cell2vert=c2v[sl].contiguous())
+            d = m.dim
+            nd = coffee.ndof(spec["form"], spec["degree"], spec["cell"])
+            per_bytes += spec["count"] * (4 * (d + 1) + 4 * nd * nd)
+            if spec["form"] == ADVDIFF:
+                g["coef"], g["cell2dof"] = cf, cd[sl].contiguous()
+                per_bytes += spec["count"] * 4 * (d + 1)
+            groups.append(g)
+            specs.append(spec)
+        per_bytes += sum(8 * meshes[c][0].coords.size for c in meshes)
+        plan = coffee.BatchPlan(groups, precision=prec)
+        ncells = sum(s["count"] for s in specs)
+        plan.launch()
+        coffee.check_errors()
+        if rank == 0:  # sampled parity of every group
+            errs = []
+            for g, out, spec in zip(groups, plan.outputs, specs):
+                if spec["count"] == 0:
+                    continue
+                m, _, _, coef, c2d, _, _ = meshes[spec["cell"]]
+                idx = np.random.default_rng(spec["start"]).choice(spec["count"], size=min(64, spec["count"]),
+                                                                  replace=False)
+                sel = spec["start"] + idx
+                adv = spec["form"] == ADVDIFF
+                ref = oracle.assemble_cells(spec["form"], spec["degree"], spec["cell"], m.coords, m.cell2vert, sel,
+                                            coef if adv else None, c2d if adv else None)
+                got = out[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+                errs.append(float(np.max(np.abs(got - ref).reshape(len(sel), -1).max(1)
+                                         / np.abs(ref).reshape(len(sel), -1).max(1))))
+            max_err = max(errs)
+        step = plan.launch
+        kernel = "k_batch_tc"
+        launches_per_step = 1
+        note = None
+    else:
+        form = HELMHOLTZ if "helmholtz" in args.workload else ADVDIFF
+        mesh = meshgen.tet_mesh(64, 64, 22, perturb=0.15, seed=5, ncells=2 ** 19) if not args.nx else \
+            meshgen.tet_mesh(args.nx, perturb=0.15, seed=5)
+        coef = c2d = None
+        if form == ADVDIFF:
+            coef, c2d, _ = meshgen.advdiff_coefficients(mesh, seed=5)
+        x = torch.from_numpy(mesh.coords).to(dev)
+        c2v = torch.from_numpy(mesh.cell2vert).to(dev)
+        cf = None if coef is None else torch.from_numpy(coef).to(dev)
+        cd = None if c2d is None else torch.from_numpy(c2d).to(dev)
+        ncells = mesh.ncells
+        odt = torch.float64 if prec == coffee.FP64 else torch.float32
+        g = torch.Generator(device=dev).manual_seed(5)
+        dout = torch.randn((ncells, 10, 10), dtype=odt, device=dev, generator=g)
+        dx = torch.zeros_like(x)
+        dc = None if cf is None else torch.zeros_like(cf)
+        step = lambda: coffee.assemble_backward(form, 2, TETRAHEDRON, x, c2v, dout, cf, cd, precision=prec,
+                                                d_coords=dx, d_coef=dc)
+        per_bytes = ncells * (16 + dout.element_size() * 100) + 8 * mesh.coords.size * 2
+        if cf is not None:
+            per_bytes += ncells * 16 + 8 * coef.size * 2
+        if rank == 0:  # gradient at sampled vertices vs the oracle over their incident cells
+            dx.zero_()
+            if dc is not None:
+                dc.zero_()
+            step()
+            torch.cuda.synchronize()
+            verts = np.random.default_rng(5).choice(np.unique(mesh.cell2vert), size=20, replace=False)
+            cells = np.nonzero(np.isin(mesh.cell2vert, verts).any(axis=1))[0]
+            gx, _ = oracle.assemble_backward(form, 2, TETRAHEDRON, mesh.coords, mesh.cell2vert[cells],
+                                             dout[torch.from_numpy(cells).to(dev)].double().cpu().numpy(),
+                                             coef, None if c2d is None else c2d[cells])
+            got = dx.cpu().numpy()[verts]
+            max_err = float(np.abs(got - gx[verts]).max() / np.abs(gx[verts]).max())
+        kernel = "k_backward"
+        launches_per_step = 1
+        note = "adjoint: bound by the FP64 ALU (per cell K*N FP64 FMAs); HBM fraction for context"
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.5)
+    total_ms, launch_ms = timed_steps(step, args.steps, args.warmup, world, stream)
+    clocks = sampler.stop()
+    coffee.check_errors()
+    total_ms = reduce_over_ranks(total_ms, world, "max", dev)
+    value = reduce_over_ranks(ncells * args.steps, world, "sum", dev) / (total_ms / 1e3)
+    achieved = per_bytes / (launch_ms / 1e3) / 1e9
+    if rank == 0:
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": "measured" if peaks else "fallback",
+                "alg_bytes_per_step": per_bytes, "kernel_ms": launch_ms, "kernel": kernel}
+        if note:
+            roof["note"] = note
+        line = {"metric": SPECIAL[args.workload].split(",")[0] + " cells/s", "value": value, "unit": "cells/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64"}.get(args.precision, args.precision), "data": "synthetic",
+                "config": {"workload": "%s: %s" % (args.workload, SPECIAL[args.workload]), "ncells": ncells,
+                           "precision": args.precision, "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roof, "max_rel_err_vs_oracle": max_err, "e2e": None, "cpu_baseline": None,
+                "gpu_launches": args.steps * launches_per_step, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload in SPECIAL:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU reference arm covers the "
+                              "single-group workloads"}))
+            return 0
+        return run_special(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
