@@ -174,7 +174,8 @@ int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream);
  * Given dout = dL/dA ([ncells][ndof][ndof], double for FP64, float otherwise),
  * ACCUMULATES (+=) dL/dcoords into d_coords [nverts][d] and dL/dcoef into d_coef
  * (coefficient layout; may be NULL when the form has no coefficient). Geometry is
- * recomputed, not stored. deterministic != 0 sums cell contributions in a fixed
+ * recomputed, not stored. The arithmetic runs in the type of dout: FP64, or FP32 for the
+ * tensor-core precisions (gradients are always accumulated in FP64). deterministic != 0 sums cell contributions in a fixed
  * order (no floating-point atomics). Device pointers, asynchronous on stream. */
 int coffee_assemble_backward(const coffee_assemble_args* a, const void* dout,
                              double* d_coords, double* d_coef, int deterministic,

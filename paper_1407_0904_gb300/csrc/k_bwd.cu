@@ -32,8 +32,8 @@ struct BForm {
   static constexpr int NL = NV * D + NCF;                              // local gradient length
 };
 
-template <int D>
-__device__ __forceinline__ void adjugate64(const double (&J)[D][D], double (&adj)[D][D], double& det) {
+template <typename T, int D>
+__device__ __forceinline__ void adjugate(const T (&J)[D][D], T (&adj)[D][D], T& det) {
   if constexpr (D == 2) {
     det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
     adj[0][0] = J[1][1]; adj[0][1] = -J[0][1];
@@ -54,12 +54,16 @@ __device__ __forceinline__ void adjugate64(const double (&J)[D][D], double (&adj
 
 // Local gradient L[0 .. NL): vertex coordinates (v*D + r), then coefficient values in the
 // oracle's cell-local order (eps_v, then b_{v,r}).
+// The arithmetic runs in the type of dL/dA (CT = TA): FP64 for FP64 dL/dA, FP32 for FP32
+// dL/dA (vertex differences are still taken in FP64 and rounded). Gradients are accumulated
+// into FP64 arrays.
 template <int FORM, int D, typename TA>
 __global__ void __launch_bounds__(BT) k_backward(const BwdParams p) {
   using F = BForm<FORM, D>;
+  using CT = TA;
   constexpr int NV = F::NV, P = F::P, K = F::K;
   __shared__ TA sA[BT][CH + 1];
-  __shared__ double sT[K][CH];
+  __shared__ CT sT[K][CH];
 
   const int t = threadIdx.x;
   const int64_t c0 = (int64_t)blockIdx.x * BT;
@@ -70,9 +74,9 @@ __global__ void __launch_bounds__(BT) k_backward(const BwdParams p) {
   const int N = p.N;
 
   // ---- Gbar = T . vec(dA_e) ----
-  double Gb[K];
+  CT Gb[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) Gb[k] = 0.0;
+  for (int k = 0; k < K; ++k) Gb[k] = CT(0);
   for (int o0 = 0; o0 < N; o0 += CH) {
     const int w = (N - o0) < CH ? (N - o0) : CH;
     __syncthreads();
@@ -82,12 +86,12 @@ __global__ void __launch_bounds__(BT) k_backward(const BwdParams p) {
     }
     for (int i = t; i < K * CH; i += BT) {
       const int k = i / CH, o = i - k * CH;
-      sT[k][o] = o < w ? p.T[(int64_t)k * N + o0 + o] : 0.0;
+      sT[k][o] = o < w ? (CT)p.T[(int64_t)k * N + o0 + o] : CT(0);
     }
     __syncthreads();
     if (live) {
       for (int o = 0; o < w; ++o) {
-        const double a = (double)sA[t][o];
+        const CT a = sA[t][o];
 #pragma unroll
         for (int k = 0; k < K; ++k) Gb[k] = fma(sT[k][o], a, Gb[k]);
       }
@@ -117,7 +121,8 @@ __global__ void __launch_bounds__(BT) k_backward(const BwdParams p) {
       for (int i = 0; i < F::NL; ++i) p.local[e * F::NL + i] = 0.0;
     return;
   }
-  double X[NV][D], J[D][D], adj[D][D], det;
+  double X[NV][D];
+  CT J[D][D], adj[D][D], det;
 #pragma unroll
   for (int v = 0; v < NV; ++v)
 #pragma unroll
@@ -125,10 +130,10 @@ __global__ void __launch_bounds__(BT) k_backward(const BwdParams p) {
 #pragma unroll
   for (int r = 0; r < D; ++r)
 #pragma unroll
-    for (int c = 0; c < D; ++c) J[r][c] = X[c + 1][r] - X[0][r];
-  adjugate64<D>(J, adj, det);
-  const double Dm = fabs(det), inv = 1.0 / det;
-  double Kx[D][D], KKt[D][D];
+    for (int c = 0; c < D; ++c) J[r][c] = (CT)(X[c + 1][r] - X[0][r]);
+  adjugate<CT, D>(J, adj, det);
+  const CT Dm = fabs(det), inv = CT(1) / det;
+  CT Kx[D][D], KKt[D][D];
 #pragma unroll
   for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -137,18 +142,18 @@ __global__ void __launch_bounds__(BT) k_backward(const BwdParams p) {
   for (int a = 0; a < D; ++a)
 #pragma unroll
     for (int b = 0; b < D; ++b) {
-      double s = 0.0;
+      CT s = CT(0);
 #pragma unroll
       for (int r = 0; r < D; ++r) s += Kx[a][r] * Kx[b][r];
       KKt[a][b] = s;
     }
 
-  double Jb[D][D];
+  CT Jb[D][D];
 #pragma unroll
   for (int r = 0; r < D; ++r)
 #pragma unroll
-    for (int c = 0; c < D; ++c) Jb[r][c] = 0.0;
-  double L[F::NL > 0 ? F::NL : 1];
+    for (int c = 0; c < D; ++c) Jb[r][c] = CT(0);
+  CT L[F::NL > 0 ? F::NL : 1];
 
   // mass term: G0 = |det|
   if constexpr (FORM == FORM_MASS || FORM == FORM_HELMHOLTZ) {
@@ -159,39 +164,39 @@ __global__ void __launch_bounds__(BT) k_backward(const BwdParams p) {
   }
   // stiffness term: H = |det| K K^T with pair gradients Hbar
   if constexpr (FORM == FORM_HELMHOLTZ || FORM == FORM_ADVDIFF) {
-    double Hb[D][D];
+    CT Hb[D][D];
     int q = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
       for (int b = a; b < D; ++b) {
-        double g;
+        CT g;
         if constexpr (FORM == FORM_HELMHOLTZ) {
           g = Gb[1 + q];
         } else {
-          g = 0.0;
+          g = CT(0);
 #pragma unroll
-          for (int v = 0; v < NV; ++v) g += __ldg(p.coef + (int64_t)cid[v] * (D + 1)) * Gb[v * P + q];
+          for (int v = 0; v < NV; ++v) g += (CT)__ldg(p.coef + (int64_t)cid[v] * (D + 1)) * Gb[v * P + q];
         }
         if (a == b) {
           Hb[a][a] = g;
         } else {
-          Hb[a][b] = 0.5 * g;
-          Hb[b][a] = 0.5 * g;
+          Hb[a][b] = CT(0.5) * g;
+          Hb[b][a] = CT(0.5) * g;
         }
         ++q;
       }
-    double tr = 0.0;
+    CT tr = CT(0);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
       for (int b = 0; b < D; ++b) tr += Hb[a][b] * KKt[b][a];
-    double HK[D][D];  // Hbar K
+    CT HK[D][D];  // Hbar K
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
       for (int r = 0; r < D; ++r) {
-        double s = 0.0;
+        CT s = CT(0);
 #pragma unroll
         for (int b = 0; b < D; ++b) s += Hb[a][b] * Kx[b][r];
         HK[a][r] = s;
@@ -201,17 +206,17 @@ __global__ void __launch_bounds__(BT) k_backward(const BwdParams p) {
     for (int a = 0; a < D; ++a)
 #pragma unroll
       for (int r = 0; r < D; ++r) {
-        double s = 0.0;
+        CT s = CT(0);
 #pragma unroll
         for (int b = 0; b < D; ++b) s += KKt[a][b] * HK[b][r];
-        Jb[r][a] += Dm * tr * Kx[a][r] - 2.0 * Dm * s;
+        Jb[r][a] += Dm * tr * Kx[a][r] - CT(2) * Dm * s;
       }
   }
   if constexpr (FORM == FORM_ADVDIFF) {
     // eps_v gradient: sum_p Gbar[v,p] H_p with H_p = D KKt[a][b]
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      double s = 0.0;
+      CT s = CT(0);
       int q = 0;
 #pragma unroll
       for (int a = 0; a < D; ++a)
@@ -220,18 +225,18 @@ __global__ void __launch_bounds__(BT) k_backward(const BwdParams p) {
       L[NV * D + v] = s;
     }
     // advection: G[v,a] = sum_r P[a][r] b_{v,r}, P = D K
-    double Pb[D][D];
+    CT Pb[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int r = 0; r < D; ++r) Pb[a][r] = 0.0;
+      for (int r = 0; r < D; ++r) Pb[a][r] = CT(0);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const double* cv = p.coef + (int64_t)cid[v] * (D + 1);
 #pragma unroll
       for (int r = 0; r < D; ++r) {
-        const double bvr = __ldg(cv + 1 + r);
-        double s = 0.0;
+        const CT bvr = (CT)__ldg(cv + 1 + r);
+        CT s = CT(0);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           Pb[a][r] += Gb[NV * P + v * D + a] * bvr;
@@ -240,17 +245,17 @@ __global__ void __launch_bounds__(BT) k_backward(const BwdParams p) {
         L[NV * D + NV + v * D + r] = s;
       }
     }
-    double tr2 = 0.0;
+    CT tr2 = CT(0);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
       for (int r = 0; r < D; ++r) tr2 += Pb[a][r] * Kx[a][r];
-    double PtK[D][D];  // Pbar^T K
+    CT PtK[D][D];  // Pbar^T K
 #pragma unroll
     for (int r = 0; r < D; ++r)
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        double s = 0.0;
+        CT s = CT(0);
 #pragma unroll
         for (int a = 0; a < D; ++a) s += Pb[a][r] * Kx[a][c];
         PtK[r][c] = s;
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(BT) k_backward(const BwdParams p) {
     for (int a = 0; a < D; ++a)
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        double s = 0.0;
+        CT s = CT(0);
 #pragma unroll
         for (int r = 0; r < D; ++r) s += Kx[a][r] * PtK[r][c];
         Jb[c][a] += Dm * tr2 * Kx[a][c] - Dm * s;
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(BT) k_backward(const BwdParams p) {
   // vertices: x_{c+1} += Jbar[:, c], x_0 -= sum_c Jbar[:, c]
 #pragma unroll
   for (int r = 0; r < D; ++r) {
-    double s = 0.0;
+    CT s = CT(0);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       L[(c + 1) * D + r] = Jb[r][c];
@@ -280,21 +285,21 @@ __global__ void __launch_bounds__(BT) k_backward(const BwdParams p) {
   if (p.local) {  // deterministic mode: per-cell contributions, summed later in cell order
     double* dst = p.local + e * F::NL;
 #pragma unroll
-    for (int i = 0; i < F::NL; ++i) dst[i] = L[i];
+    for (int i = 0; i < F::NL; ++i) dst[i] = (double)L[i];
     return;
   }
 #pragma unroll
   for (int v = 0; v < NV; ++v)
 #pragma unroll
-    for (int r = 0; r < D; ++r) atomicAdd(p.d_coords + (int64_t)vid[v] * D + r, L[v * D + r]);
+    for (int r = 0; r < D; ++r) atomicAdd(p.d_coords + (int64_t)vid[v] * D + r, (double)L[v * D + r]);
   if constexpr (FORM == FORM_ADVDIFF) {
     if (p.d_coef) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         double* dc = p.d_coef + (int64_t)cid[v] * (D + 1);
-        atomicAdd(dc, L[NV * D + v]);
+        atomicAdd(dc, (double)L[NV * D + v]);
 #pragma unroll
-        for (int r = 0; r < D; ++r) atomicAdd(dc + 1 + r, L[NV * D + NV + v * D + r]);
+        for (int r = 0; r < D; ++r) atomicAdd(dc + 1 + r, (double)L[NV * D + NV + v * D + r]);
       }
     }
   }

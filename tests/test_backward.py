@@ -90,18 +90,25 @@ def test_autograd_function_central_differences(form):
             assert abs(fd - gc[idx]) <= 1e-9 * np.abs(gc).max()
 
 
-def test_fp32_dout_path():
-    """TF32X3 forward + float32 dL/dA: the adjoint promotes dA to FP64 internally, so the
-    gradient matches the FP64 oracle up to the FP32 rounding of dA."""
+@pytest.mark.parametrize("form", [HELMHOLTZ, ADVDIFF])
+def test_fp32_dout_path(form):
+    """TF32X3 forward + float32 dL/dA: the adjoint runs in FP32 (vertex differences in FP64),
+    so the gradient matches the FP64 oracle (fed the same float32 dL/dA) to FP32 accuracy:
+    K x N-term contractions and the chain rule, held to 1e-5 of max|grad| (measured ~4e-7)."""
     mesh = meshgen.tet_mesh(4, seed=9)
-    coef, c2d = coefficients(ADVDIFF, mesh, 2, seed=9)
+    coef, c2d = coefficients(form, mesh, 2, seed=9)
     x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
     dout32 = torch.randn((mesh.ncells, 10, 10), dtype=torch.float32, device=DEV)
-    gx, gc = oracle.assemble_backward(ADVDIFF, 2, TET, mesh.coords, mesh.cell2vert,
+    gx, gc = oracle.assemble_backward(form, 2, TET, mesh.coords, mesh.cell2vert,
                                       dout32.double().cpu().numpy(), coef, c2d)
-    dx, dc = coffee.assemble_backward(ADVDIFF, 2, TET, x, c2v, dout32, cf, cd, precision=coffee.TF32X3)
-    assert rel(dx.cpu().numpy(), gx) < 1e-10
-    assert rel(dc.cpu().numpy(), gc) < 1e-10
+    dx, dc = coffee.assemble_backward(form, 2, TET, x, c2v, dout32, cf, cd, precision=coffee.TF32X3)
+    ex = rel(dx.cpu().numpy(), gx)
+    print("fp32 adjoint %s: coords %.2e" % (coffee.FORM_NAMES[form], ex))
+    assert ex < 1e-5
+    if form == ADVDIFF:
+        ec = rel(dc.cpu().numpy(), gc)
+        print("fp32 adjoint coef %.2e" % ec)
+        assert ec < 1e-5
 
 
 @pytest.mark.parametrize("form", [HELMHOLTZ, ADVDIFF])
