@@ -153,24 +153,33 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
     if (lane == 0) {
       uint32_t la = 0, last_round[ASLOTS] = {0, 0};
       bool used[ASLOTS] = {false, false};
+      int tag[ASLOTS] = {-1, -1};  // (group, slice) held by each slot: consecutive items of a
+                                   // group find their slices already resident
       bool ok = true;
       for (int64_t it = it0; it < it1 && ok; ++it) {
-        const BatchGroup& g = groups[group_of(groups, ngroups, it)];
+        const int gi = group_of(groups, ngroups, it);
+        const BatchGroup& g = groups[gi];
         const uint32_t part_bytes = (uint32_t)(BM * g.p.kbytes);
         for (int m = 0; m < g.p.mtiles; ++m, ++la) {
           const uint32_t j = la % ASLOTS, round = la / ASLOTS;
           if (!mbar_wait(smem_u32(&bars->aempty[j]), (round & 1u) ^ 1u, err)) { ok = false; break; }
           const uint32_t bar = smem_u32(&bars->afull[j]);
-          mbar_arrive_expect_tx(bar, part_bytes * PARTS);
           used[j] = true;
-          last_round[j] = round;
+          last_round[j] = round;  // the slot's latest phase, whether it copies or not
+          if (tag[j] == gi * 64 + m) {  // already resident: complete the phase without a copy
+            mbar_arrive(bar);
+            continue;
+          }
+          tag[j] = gi * 64 + m;
+          mbar_arrive_expect_tx(bar, part_bytes * PARTS);
           const uint8_t* src = g.p.image + (size_t)m * PARTS * part_bytes;
           const uint32_t dst = smem_u32(sA + (size_t)j * slot_bytes);
 #pragma unroll
           for (int q = 0; q < PARTS; ++q) bulk_g2s(dst + q * part_bytes, src + (size_t)q * part_bytes, part_bytes, bar);
         }
       }
-      // every copy this thread started has landed before shared memory is released
+      // every copy this thread started has landed before shared memory is released (phases
+      // of a slot complete in order, so waiting for its latest phase covers all of them)
       for (int j = 0; j < ASLOTS; ++j)
         if (used[j]) mbar_wait(smem_u32(&bars->afull[j]), last_round[j] & 1u, err);
     }
