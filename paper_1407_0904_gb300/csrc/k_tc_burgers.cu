@@ -233,6 +233,55 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
       mbar_wait(smem_u32(&bars->done), 0, p.err);
     }
     __syncwarp();
+  } else if constexpr (S::MT == 1) {
+    // ---------------- epilogue: the D blocks of a block-row together ----------------
+    // Blocks (ci, 0..D-1) occupy consecutive accumulator slots; writing them together means
+    // each output row (ci, i) -- all D*NS columns -- is completed by D back-to-back stores.
+    const int q = warp;  // TMEM lane quadrant
+    const int ndof = D * NS;
+    const int o = q * 32 + lane;  // entry (i, j) of a block
+    const int i = o / NS, j = o - (o / NS) * NS;
+    uint32_t rc = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int ci = 0; ci < D && ok; ++ci, rc += D) {
+        uint32_t slot[D];
+#pragma unroll
+        for (int cj = 0; cj < D; ++cj) {
+          slot[cj] = (rc + cj) % RING;
+          if (ok && !mbar_wait(smem_u32(&bars->tfull[slot[cj]]), ((rc + cj) / RING) & 1u, p.err)) ok = false;
+        }
+        if (!ok) break;
+        tc_fence_after();
+        if (q * 32 < S::NBLK) {  // warp-uniform
+          for (int c0 = 0; c0 < BN; c0 += 16) {
+            const int64_t cbase = t * BN + c0;
+            if (cbase >= p.ncells) break;
+            const int64_t rem = p.ncells - cbase;
+            const int ncol = rem < 16 ? (int)rem : 16;
+            uint32_t v[D][16];
+#pragma unroll
+            for (int cj = 0; cj < D; ++cj) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + slot[cj] * BN + c0, v[cj]);
+            tmem_wait_ld();
+            if (o < S::NBLK) {
+              float* row = p.out + cbase * p.N + (int64_t)(ci * NS + i) * ndof + j;
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj)
+                if (jj < ncol) {
+#pragma unroll
+                  for (int cj = 0; cj < D; ++cj) __stcs(row + (int64_t)jj * p.N + cj * NS, __uint_as_float(v[cj][jj]));
+                }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+#pragma unroll
+          for (int cj = 0; cj < D; ++cj) mbar_arrive(smem_u32(&bars->tempty[slot[cj]]));
+        }
+      }
+    }
   } else {
     // ---------------- epilogue ----------------
     const int q = warp;  // TMEM lane quadrant
