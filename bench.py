@@ -34,7 +34,7 @@ L2_BYTES = 129 * 2 ** 20
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # tensor-core kernel on the headline workload, keyed by the sha256 prefix of the kernel
 # source it was measured on; reported as null once the source has changed.
-TRAFFIC = {"2997aae8e32b210a": 2.492e9}  # 31.87 MB read + 2.46 GB written per launch (two launches)
+TRAFFIC = {"f4722a933c1e26e5": 2.492e9}  # 31.86 MB read + 2.46 GB written per launch (two launches)
 
 MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC = 0, 1, 2, 3
 TRIANGLE, TETRAHEDRON = 0, 1
@@ -93,6 +93,9 @@ SPECIAL = {
     "batch-mixed": "21 (form, degree) groups, Zipf(s=1) counts (seed 4): 2^19 triangles "
                    "(512^2 x 2, P1-P4) + 2^19 Kuhn tets (64x64x22 truncated, P1-P3); mass, "
                    "Helmholtz, advection-diffusion; one persistent launch per step",
+    "global-helmholtz-p3-tet": "fused global assembly (CSR) of Helmholtz P3 on 64^3 x 6 = 1,572,864 Kuhn "
+                               "tets (seed 2): one step zeroes the CSR values and adds every element matrix "
+                               "into them from the tensor-core accumulators; pattern and entry map are set-up",
     "adjoint-helmholtz-p2-tet": "backward of Helmholtz P2 on 2^19 Kuhn tets (64x64x22 truncated, "
                                 "seed 5), dL/dA ~ N(0,1), atomic accumulation",
     "adjoint-advdiff-p2-tet": "backward of advection-diffusion P2 on 2^19 Kuhn tets (64x64x22 "
@@ -194,7 +197,7 @@ class ClockSampler:
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for name in ("k_tc.cu", "tc_common.cuh"):
+    for name in ("k_tc.cu", "k_tc_kernel.cuh", "tc_common.cuh"):
         with open(os.path.join(ROOT, "paper_1407_0904_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -470,6 +473,7 @@ def run_special(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))
     max_err = None
+    global_kernel_ms = None
     if args.workload == "batch-mixed":
         tri = meshgen.tri_mesh(512, perturb=0.2, seed=4)
         tet = meshgen.tet_mesh(64, 64, 22, perturb=0.15, seed=4, ncells=2 ** 19)
@@ -520,6 +524,52 @@ def run_special(args):
         kernel = "k_batch_tc"
         launches_per_step = 1
         note = None
+    elif args.workload == "global-helmholtz-p3-tet":
+        k = 3
+        mesh = meshgen.tet_mesh(args.nx or 64, perturb=0.15, seed=2)
+        c2d, nn = meshgen.cell2dof(mesh, k)
+        x = torch.from_numpy(mesh.coords).to(dev)
+        c2v = torch.from_numpy(mesh.cell2vert).to(dev)
+        M = coffee.CsrMatrix(torch.from_numpy(c2d).to(dev), nn)
+        ncells = mesh.ncells
+        odt = torch.float64 if prec == coffee.FP64 else torch.float32
+        vals = torch.zeros(M.nnz, dtype=odt, device=dev)
+
+        def assemble_only():
+            M.assemble(HELMHOLTZ, k, TETRAHEDRON, x, c2v, precision=prec, vals=vals)
+
+        def step():
+            vals.zero_()
+            assemble_only()
+
+        step()
+        coffee.check_errors()
+        if rank == 0:  # 32 sampled global rows vs the oracle's sum over their incident cells
+            rp, ci, v = M.rowptr.cpu().numpy(), M.colidx.cpu().numpy(), vals.double().cpu().numpy()
+            flat = c2d.ravel()
+            order = np.argsort(flat, kind="stable")
+            errs = []
+            for r in np.random.default_rng(2).choice(nn, 32, replace=False):
+                hits = order[np.searchsorted(flat[order], r):np.searchsorted(flat[order], r, side="right")]
+                cells, loc = hits // c2d.shape[1], hits % c2d.shape[1]
+                A_e = oracle.assemble_cells(HELMHOLTZ, k, TETRAHEDRON, mesh.coords, mesh.cell2vert, cells)
+                row = {}
+                for A, e, i in zip(A_e, cells, loc):
+                    for j in range(c2d.shape[1]):
+                        row[int(c2d[e, j])] = row.get(int(c2d[e, j]), 0.0) + A[i, j]
+                ref = np.array([row[c] for c in ci[rp[r]:rp[r + 1]].tolist()])
+                errs.append(float(np.abs(v[rp[r]:rp[r + 1]] - ref).max() / np.abs(ref).max()))
+            max_err = max(errs)
+        # the fused kernel alone (accumulating), for the roofline
+        _, kernel_ms_alone = timed_steps(assemble_only, 20, 3, world, stream)
+        N = c2d.shape[1] ** 2
+        per_bytes = ncells * (4 * 4 + 4 * N) + 8 * mesh.coords.size + 2 * M.nnz * vals.element_size()
+        kernel = "k_assemble_tc<HELMHOLTZ,tet,%s,CSR>" % args.precision
+        launches_per_step = 1
+        note = ("roofline of the fused kernel alone (%.4f ms): cell2vert + coords + the uint32 entry map "
+                "read once + every CSR value read and written once (nnz = %d); the step adds the zeroing "
+                "of the values" % (kernel_ms_alone, M.nnz))
+        global_kernel_ms = kernel_ms_alone
     else:
         form = HELMHOLTZ if "helmholtz" in args.workload else ADVDIFF
         mesh = meshgen.tet_mesh(64, 64, 22, perturb=0.15, seed=5, ncells=2 ** 19) if not args.nx else \
@@ -563,6 +613,8 @@ def run_special(args):
     time.sleep(0.5)
     total_ms, launch_ms = timed_steps(step, args.steps, args.warmup, world, stream)
     clocks = sampler.stop()
+    if args.workload == "global-helmholtz-p3-tet":
+        launch_ms = global_kernel_ms
     coffee.check_errors()
     total_ms = reduce_over_ranks(total_ms, world, "max", dev)
     value = reduce_over_ranks(ncells * args.steps, world, "sum", dev) / (total_ms / 1e3)

@@ -219,6 +219,55 @@ int coffee_batch_plan(const coffee_assemble_args* groups, int ngroups, int grid,
 int coffee_batch_launch(void* plan, coffee_stream_t stream);
 void coffee_batch_free(void* plan);
 
+/* ---- Global assembly: the consumer of local assembly ----
+ * Local assembly yields each cell's contribution to the global linear system (section 2);
+ * the framework that runs the paper's kernels over all cells of the mesh (section 4) adds
+ * these element matrices into a global sparse matrix through each cell's local-to-global
+ * dof map. These entry points do that step on the GPU in CSR form. Rows and columns share
+ * the map (the forms are square):
+ *   l2g [ncells][nloc] int32, global row of each row of the element matrix, in [0, nrows).
+ *   For scalar forms nloc = ns and l2g is the cell-to-node map of the degree-k space; for
+ *   BURGERS_JAC nloc = d*ns, component-blocked like the element matrix
+ *   (l2g[e][c*ns + i] = global dof of component c at node i). */
+
+/* CSR sparsity of the global matrix: (r, c) is stored iff some cell e has r = l2g[e][i] and
+ * c = l2g[e][j]; the columns of each row ascend.
+ *   rowptr  device [nrows+1] int64;  colidx  device [nnz] int32;  nnz  host.
+ * Two calls. With colidx == NULL the call writes rowptr and *nnz; then, with colidx
+ * allocated for nnz entries and the same rowptr, it writes the columns. Both calls allocate
+ * their scratch on the stream (cudaMallocAsync) and synchronise it before returning, so
+ * errors are reported by the call itself: COFFEE_ERR_INVALID_ARG for an l2g entry outside
+ * [0, nrows) or a rowptr that does not match l2g, COFFEE_ERR_UNSUPPORTED when a row
+ * gathers more than 4096 entries before deduplication (the sum of nloc over the cells that
+ * contain its dof). Limits: 1 <= nloc <= 128; ncells, nrows <= 2^31 - 1. */
+int coffee_sparsity(const int32_t* l2g, int64_t ncells, int nloc, int64_t nrows, int64_t* rowptr,
+                    int32_t* colidx, int64_t* nnz, coffee_stream_t stream);
+
+/* Position of every element-matrix entry in the CSR arrays:
+ * map[e][i*nloc + j] = k such that colidx[k] == l2g[e][j], rowptr[l2g[e][i]] <= k < rowptr[l2g[e][i]+1].
+ *   map  device [ncells][nloc*nloc] uint32 (nnz must be below 2^32).
+ * Asynchronous; an entry that cannot be found (l2g and the pattern disagree) is set to
+ * 0xffffffff and raises COFFEE_ERR_DEVICE_INDEX in coffee_check_errors. */
+int coffee_csr_map(const int32_t* l2g, int64_t ncells, int nloc, const int64_t* rowptr, const int32_t* colidx,
+                   int64_t nrows, uint32_t* map, coffee_stream_t stream);
+
+/* Fused global assembly: vals[map[e][o]] += A_e[o] for every cell e and entry o, where A_e
+ * is the element matrix coffee_assemble_ex computes for *a (a->out is ignored). The tensor-core
+ * precisions add the entries straight from the accumulators (the element matrices are never
+ * written to memory) into float vals; FP64 adds into double vals.
+ *   vals  device [nnz], float (tensor-core precisions) or double (FP64); the call ADDS into it,
+ *         so zero it first for a new matrix.
+ * Entries are added with floating-point atomics: the order in which the contributions to one
+ * global entry are summed is not fixed. A map entry >= nnz is skipped and raises
+ * COFFEE_ERR_DEVICE_INDEX in coffee_check_errors. The tensor-core path covers MASS, HELMHOLTZ
+ * and ADVDIFF (coffee_supported combinations whose operands stay resident in shared memory);
+ * FP64 covers every form. Otherwise COFFEE_ERR_UNSUPPORTED. */
+int coffee_assemble_csr(const coffee_assemble_args* a, const uint32_t* map, void* vals, int64_t nnz,
+                        coffee_stream_t stream);
+
+/* 1 if coffee_assemble_csr has a kernel for (form, degree, cell, precision), else 0. Host-only. */
+int coffee_csr_supported(int form, int degree, int cell, int precision);
+
 /* Device error word: synchronises `stream`, returns COFFEE_ERR_DEVICE_INDEX if a
  * validated launch met an out-of-range index, COFFEE_ERR_TIMEOUT if a kernel wait
  * gave up, COFFEE_OK otherwise, and clears the word. */

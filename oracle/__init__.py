@@ -172,3 +172,48 @@ def assemble_backward(form, degree, cell, coords, c2v, dout, coef=None, c2d=None
     if rc != 0:
         raise ValueError("oracle_assemble_backward failed")
     return d_coords, d_coef
+
+
+# ---------------------------------------------------------------- global assembly
+# Local assembly yields each cell's contribution to the global system (section 2); the
+# framework that runs the kernels over the mesh adds the element matrices into a global
+# sparse matrix through the local-to-global dof map (section 4). The oracle states that
+# step by its definition, in NumPy and FP64: A[l2g[e,i], l2g[e,j]] += A_e[i,j].
+
+def csr_pattern(l2g, nrows):
+    """CSR sparsity (rowptr int64 [nrows+1], colidx int32 [nnz]): (r, c) is stored iff some
+    cell has r = l2g[e,i] and c = l2g[e,j]; columns ascend within a row."""
+    l2g = np.asarray(l2g, dtype=np.int64)
+    n = l2g.shape[1]
+    rows = np.repeat(l2g, n, axis=1).ravel()
+    cols = np.tile(l2g, (1, n)).ravel()
+    key = np.unique(rows * nrows + cols)
+    r, c = key // nrows, key % nrows
+    rowptr = np.zeros(nrows + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum(np.bincount(r, minlength=nrows))
+    return rowptr, c.astype(np.int32)
+
+
+def csr_assemble(A_e, l2g, rowptr, colidx):
+    """Global matrix values [nnz] (FP64): the sum over cells e and entries (i, j) of A_e[e,i,j]
+    at the CSR position of (l2g[e,i], l2g[e,j]), contributions summed in cell order."""
+    l2g = np.asarray(l2g, dtype=np.int64)
+    n = l2g.shape[1]
+    nrows = rowptr.shape[0] - 1
+    rows = np.repeat(l2g, n, axis=1).ravel()
+    cols = np.tile(l2g, (1, n)).ravel()
+    row_of = np.repeat(np.arange(nrows, dtype=np.int64), np.diff(rowptr))
+    keys = row_of * nrows + colidx.astype(np.int64)  # ascending, one per stored entry
+    pos = np.searchsorted(keys, rows * nrows + cols)
+    if np.any(keys[np.minimum(pos, keys.size - 1)] != rows * nrows + cols):
+        raise ValueError("an element entry is outside the pattern")
+    return np.bincount(pos, weights=np.asarray(A_e, dtype=np.float64).ravel(), minlength=keys.size)
+
+
+def csr_dense(rowptr, colidx, vals):
+    """Dense [nrows, nrows] copy of a CSR matrix (small cases only)."""
+    nrows = rowptr.shape[0] - 1
+    A = np.zeros((nrows, nrows))
+    r = np.repeat(np.arange(nrows), np.diff(rowptr))
+    A[r, colidx] = vals
+    return A

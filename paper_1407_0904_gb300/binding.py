@@ -92,6 +92,13 @@ def supported(form, degree, cell, precision):
     return bool(lib().coffee_supported(form, degree, cell, precision))
 
 
+def csr_supported(form, degree, cell, precision):
+    """True if the fused global assembly has a kernel for this combination."""
+    L = lib()
+    L.coffee_csr_supported.argtypes = [ctypes.c_int] * 4
+    return bool(L.coffee_csr_supported(form, degree, cell, precision))
+
+
 def tc_available(form, degree, cell, precision):
     return precision != FP64 and supported(form, degree, cell, precision)
 
@@ -150,7 +157,7 @@ def _stream_handle(stream):
 
 
 def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
-              out=None, nu=0.01, validate=False, ncoefnodes=None, tune=0):
+              out=None, nu=0.01, validate=False, ncoefnodes=None, tune=0, alloc_out=True):
     coords = _dev(coords, torch.float64, "coords")
     cell2vert = _dev(cell2vert, torch.int32, "cell2vert")
     coef = _dev(coef, torch.float64, "coef")
@@ -162,7 +169,8 @@ def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, p
     n = ndof(form, degree, cell)
     odt = torch.float64 if precision == FP64 else torch.float32
     if out is None:
-        out = torch.empty((ncells, n, n), dtype=odt, device=coords.device)
+        if alloc_out:
+            out = torch.empty((ncells, n, n), dtype=odt, device=coords.device)
     else:
         _dev(out, odt, "out")
         if out.numel() != ncells * n * n:
@@ -395,3 +403,94 @@ class BatchPlan:
             self.free()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- global assembly
+def vector_l2g(cell2dof, nnodes, d):
+    """Component-blocked local-to-global map of a d-vector field on the nodes of cell2dof:
+    [ncells, d*ns] with entry (e, c*ns + i) = c*nnodes + cell2dof[e, i]."""
+    return torch.cat([cell2dof + c * nnodes for c in range(d)], dim=1).contiguous()
+
+
+def sparsity(l2g, nrows, stream=None):
+    """CSR sparsity of the global matrix of the map l2g [ncells, nloc] (int32, CUDA):
+    (rowptr int64 [nrows+1], colidx int32 [nnz]), columns ascending in each row."""
+    l2g = _dev(l2g, torch.int32, "l2g")
+    if l2g.dim() != 2:
+        raise ValueError("l2g must be [ncells, nloc]")
+    L = lib()
+    L.coffee_sparsity.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    ncells, nloc = l2g.shape
+    rowptr = torch.empty(nrows + 1, dtype=torch.int64, device=l2g.device)
+    nnz = ctypes.c_int64(0)
+    st = _stream_handle(stream)
+    _check(L.coffee_sparsity(_ptr(l2g), ncells, nloc, nrows, _ptr(rowptr), None, ctypes.byref(nnz), st))
+    colidx = torch.empty(nnz.value, dtype=torch.int32, device=l2g.device)
+    if nnz.value:
+        _check(L.coffee_sparsity(_ptr(l2g), ncells, nloc, nrows, _ptr(rowptr), _ptr(colidx), None, st))
+    return rowptr, colidx
+
+
+def csr_map(l2g, rowptr, colidx, stream=None):
+    """Position of every element-matrix entry in colidx: [ncells, nloc*nloc] uint32 values
+    held in an int32 tensor (reinterpret; entries >= 2^31 read as negative)."""
+    l2g = _dev(l2g, torch.int32, "l2g")
+    rowptr = _dev(rowptr, torch.int64, "rowptr")
+    colidx = _dev(colidx, torch.int32, "colidx")
+    L = lib()
+    L.coffee_csr_map.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    ncells, nloc = l2g.shape
+    m = torch.empty((ncells, nloc * nloc), dtype=torch.int32, device=l2g.device)
+    _check(L.coffee_csr_map(_ptr(l2g), ncells, nloc, _ptr(rowptr), _ptr(colidx), rowptr.numel() - 1, _ptr(m),
+                            _stream_handle(stream)))
+    return m
+
+
+def assemble_csr(form, degree, cell, coords, cell2vert, csr_map_, vals, coef=None, cell2dof=None,
+                 precision=FP64, nu=0.01, validate=False, stream=None, tune=0):
+    """Fused global assembly: vals[map[e, o]] += A_e[o] over all cells (vals float64 for FP64,
+    float32 otherwise; zero it first for a new matrix). Returns vals."""
+    odt = torch.float64 if precision == FP64 else torch.float32
+    vals = _dev(vals, odt, "vals")
+    csr_map_ = _dev(csr_map_, torch.int32, "map")
+    n = ndof(form, degree, cell)
+    if csr_map_.numel() != cell2vert.shape[0] * n * n:
+        raise ValueError("map must be [ncells, ndof*ndof]")
+    a, _ = make_args(form, degree, cell, coords, cell2vert, coef, cell2dof, precision, None, nu, validate,
+                     tune=tune, alloc_out=False)
+    L = lib()
+    L.coffee_assemble_csr.argtypes = [ctypes.POINTER(AssembleArgs), ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.c_void_p]
+    _check(L.coffee_assemble_csr(ctypes.byref(a), _ptr(csr_map_), _ptr(vals), vals.numel(),
+                                 _stream_handle(stream)))
+    return vals
+
+
+class CsrMatrix:
+    """Global sparse matrix of one local-to-global map: pattern and entry map built once
+    (setup), then assembled any number of times by the fused kernels."""
+
+    def __init__(self, l2g, nrows, stream=None):
+        self.l2g = _dev(l2g, torch.int32, "l2g")
+        self.nrows = int(nrows)
+        self.rowptr, self.colidx = sparsity(self.l2g, self.nrows, stream)
+        self.map = csr_map(self.l2g, self.rowptr, self.colidx, stream)
+
+    @property
+    def nnz(self):
+        return self.colidx.numel()
+
+    def assemble(self, form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
+                 vals=None, nu=0.01, validate=False, stream=None, tune=0):
+        """Values [nnz] of the assembled global matrix (vals, if given, is added into)."""
+        if vals is None:
+            vals = torch.zeros(self.nnz, dtype=torch.float64 if precision == FP64 else torch.float32,
+                               device=self.l2g.device)
+        return assemble_csr(form, degree, cell, coords, cell2vert, self.map, vals, coef, cell2dof, precision,
+                            nu, validate, stream, tune)
+
+    def to_torch(self, vals):
+        """torch sparse CSR tensor of the values (shares the pattern)."""
+        return torch.sparse_csr_tensor(self.rowptr, self.colidx, vals, size=(self.nrows, self.nrows))

@@ -122,6 +122,85 @@ int check_args(const coffee_assemble_args* a) {
   return COFFEE_OK;
 }
 
+// Local assembly (map == NULL: element matrices to a->out) or fused global assembly
+// (map != NULL: entries added into the CSR values a->out at map[cell][entry]).
+int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nnz, coffee_stream_t stream) {
+  int rc = check_args(a);
+  if (rc != COFFEE_OK || a->ncells == 0) return rc;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceCache* c = nullptr;
+  if ((rc = device_cache(&c)) != COFFEE_OK) return rc;
+  const int d = a->cell == CELL_TRI ? 2 : 3;
+  const int ns = nnodes(a->cell, a->degree);
+  const int ndof = a->form == FORM_BURGERS ? d * ns : ns;
+  const bool validate = (a->flags & COFFEE_FLAG_VALIDATE) != 0;
+  if (a->precision == PREC_FP64) {
+    const double* T = nullptr;
+    if ((rc = fp64_table(*c, a->form, a->degree, a->cell, &T)) != COFFEE_OK) return rc;
+    Fp64Params p{};
+    p.coords = a->coords;
+    p.c2v = a->cell2vert;
+    p.coef = a->coef;
+    p.c2d = a->cell2dof;
+    p.T = T;
+    p.out = a->out;
+    p.err = c->err;
+    p.ncells = a->ncells;
+    p.nverts = a->nverts;
+    p.ncoefnodes = a->ncoefnodes;
+    p.ns = ns;
+    p.N = ns * ns;
+    p.ndof = ndof;
+    p.nu = a->nu;
+    p.validate = validate ? 1 : 0;
+    p.map = map;
+    p.nnz = nnz;
+    cudaError_t e = (cudaError_t)launch_fp64(a->form, a->cell, p, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch(assemble_fp64)");
+    return COFFEE_OK;
+  }
+  if (map ? !tc_csr_supported(a->form, a->degree, a->cell, a->precision)
+          : !tc_supported(a->form, a->degree, a->cell, a->precision))
+    return fail(COFFEE_ERR_UNSUPPORTED, map ? "no fused tensor-core global assembly for this form/degree/cell/precision"
+                                              : "no tensor-core kernel for this form/degree/cell/precision");
+  TcTable meta{};
+  if ((rc = tc_table(*c, a->form, a->degree, a->cell, a->precision, &meta)) != COFFEE_OK) return rc;
+  TcParams p{};
+  p.coords = a->coords;
+  p.c2v = a->cell2vert;
+  p.coef = a->coef;
+  p.c2d = a->cell2dof;
+  p.image = meta.image;
+  p.out = static_cast<float*>(a->out);
+  p.err = c->err;
+  p.ncells = a->ncells;
+  p.nverts = a->nverts;
+  p.ncoefnodes = a->ncoefnodes;
+  p.ns = ns;
+  p.N = ndof * ndof;
+  p.mtiles = meta.mtiles;
+  p.kbytes = meta.kbytes;
+  p.parts = meta.parts;
+  p.ksteps_off = meta.ksteps_off;
+  p.tune = ((a->flags & COFFEE_FLAG_OUTPUT_LANES) ? TUNE_OUTPUT_LANES : 0u) |
+           ((a->flags & COFFEE_FLAG_TWO_STAGES) ? TUNE_TWO_STAGES : 0u) |
+           ((a->flags & COFFEE_FLAG_SUBTILE_64) ? TUNE_SUB64 : 0u) |
+           ((a->flags & COFFEE_FLAG_SUBTILE_32) ? TUNE_SUB32 : 0u) |
+           ((a->flags & COFFEE_FLAG_SUBTILE_128) ? TUNE_SUB128 : 0u) |
+           ((a->flags & COFFEE_FLAG_CELL_LANES) ? TUNE_CELL_LANES : 0u);
+  p.precision = a->precision;
+  p.validate = validate ? 1 : 0;
+  p.nu = a->nu;
+  p.map = map;
+  p.nnz = nnz;
+  std::string why;
+  cudaError_t e = map ? (cudaError_t)launch_tc_csr(a->form, a->cell, p, c->num_sms, stream, why)
+                      : (cudaError_t)launch_tc(a->form, a->cell, p, c->num_sms, stream, why);
+  if (e != cudaSuccess)
+    return cuda_fail(e, ((map ? "launch(assemble_tc_csr) " : "launch(assemble_tc) ") + why).c_str());
+  return COFFEE_OK;
+}
+
 }  // namespace
 }  // namespace coffee
 
@@ -172,72 +251,83 @@ int coffee_supported(int form, int degree, int cell, int precision) {
 }
 
 int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream) {
-  int rc = check_args(a);
-  if (rc != COFFEE_OK || a->ncells == 0) return rc;
+  return assemble_impl(a, nullptr, 0, stream);
+}
+
+int coffee_sparsity(const int32_t* l2g, int64_t ncells, int nloc, int64_t nrows, int64_t* rowptr,
+                    int32_t* colidx, int64_t* nnz, coffee_stream_t stream) {
+  if (ncells < 0 || nrows < 0 || nloc < 1 || nloc > 128)
+    return fail(COFFEE_ERR_INVALID_ARG, "need ncells >= 0, nrows >= 0, 1 <= nloc <= 128");
+  if (ncells > INT32_MAX || nrows > INT32_MAX)
+    return fail(COFFEE_ERR_INVALID_ARG, "ncells and nrows must fit in int32");
+  if (!rowptr || (!colidx && !nnz) || (ncells > 0 && !l2g))
+    return fail(COFFEE_ERR_INVALID_ARG, "l2g, rowptr and (colidx or nnz) must be non-NULL");
   std::lock_guard<std::mutex> lock(g_mu);
   DeviceCache* c = nullptr;
-  if ((rc = device_cache(&c)) != COFFEE_OK) return rc;
-  const int d = a->cell == CELL_TRI ? 2 : 3;
-  const int ns = nnodes(a->cell, a->degree);
-  const int ndof = a->form == FORM_BURGERS ? d * ns : ns;
-  const bool validate = (a->flags & COFFEE_FLAG_VALIDATE) != 0;
-  if (a->precision == PREC_FP64) {
-    const double* T = nullptr;
-    if ((rc = fp64_table(*c, a->form, a->degree, a->cell, &T)) != COFFEE_OK) return rc;
-    Fp64Params p{};
-    p.coords = a->coords;
-    p.c2v = a->cell2vert;
-    p.coef = a->coef;
-    p.c2d = a->cell2dof;
-    p.T = T;
-    p.out = a->out;
-    p.err = c->err;
-    p.ncells = a->ncells;
-    p.nverts = a->nverts;
-    p.ncoefnodes = a->ncoefnodes;
-    p.ns = ns;
-    p.N = ns * ns;
-    p.ndof = ndof;
-    p.nu = a->nu;
-    p.validate = validate ? 1 : 0;
-    cudaError_t e = (cudaError_t)launch_fp64(a->form, a->cell, p, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "launch(assemble_fp64)");
+  int rc = device_cache(&c);
+  if (rc != COFFEE_OK) return rc;
+  cudaStream_t s = stream;
+  if (ncells == 0 || nrows == 0) {
+    if (!colidx) {
+      cudaError_t e = cudaMemsetAsync(rowptr, 0, sizeof(int64_t) * (size_t)(nrows + 1), s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(rowptr)");
+      *nnz = 0;
+    }
     return COFFEE_OK;
   }
-  if (!tc_supported(a->form, a->degree, a->cell, a->precision))
-    return fail(COFFEE_ERR_UNSUPPORTED, "no tensor-core kernel for this form/degree/cell/precision");
-  TcTable meta{};
-  if ((rc = tc_table(*c, a->form, a->degree, a->cell, a->precision, &meta)) != COFFEE_OK) return rc;
-  TcParams p{};
-  p.coords = a->coords;
-  p.c2v = a->cell2vert;
-  p.coef = a->coef;
-  p.c2d = a->cell2dof;
-  p.image = meta.image;
-  p.out = static_cast<float*>(a->out);
-  p.err = c->err;
-  p.ncells = a->ncells;
-  p.nverts = a->nverts;
-  p.ncoefnodes = a->ncoefnodes;
-  p.ns = ns;
-  p.N = ndof * ndof;
-  p.mtiles = meta.mtiles;
-  p.kbytes = meta.kbytes;
-  p.parts = meta.parts;
-  p.ksteps_off = meta.ksteps_off;
-  p.tune = ((a->flags & COFFEE_FLAG_OUTPUT_LANES) ? TUNE_OUTPUT_LANES : 0u) |
-           ((a->flags & COFFEE_FLAG_TWO_STAGES) ? TUNE_TWO_STAGES : 0u) |
-           ((a->flags & COFFEE_FLAG_SUBTILE_64) ? TUNE_SUB64 : 0u) |
-           ((a->flags & COFFEE_FLAG_SUBTILE_32) ? TUNE_SUB32 : 0u) |
-           ((a->flags & COFFEE_FLAG_SUBTILE_128) ? TUNE_SUB128 : 0u) |
-           ((a->flags & COFFEE_FLAG_CELL_LANES) ? TUNE_CELL_LANES : 0u);
-  p.precision = a->precision;
-  p.validate = validate ? 1 : 0;
-  p.nu = a->nu;
-  std::string why;
-  cudaError_t e = (cudaError_t)launch_tc(a->form, a->cell, p, c->num_sms, stream, why);
-  if (e != cudaSuccess) return cuda_fail(e, ("launch(assemble_tc) " + why).c_str());
+  uint8_t* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), sparsity_scratch_bytes(ncells, nloc, nrows), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(sparsity scratch)");
+  unsigned* flag = nullptr;
+  e = (cudaError_t)launch_sparsity(l2g, ncells, nloc, nrows, rowptr, colidx, ws, &flag, c->num_sms, s);
+  unsigned hflag = 0;
+  int64_t total = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && !colidx)
+    e = cudaMemcpyAsync(&total, rowptr + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  cudaError_t e2 = cudaFreeAsync(ws, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "sparsity");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(sparsity scratch)");
+  if (hflag & ERR_CAPACITY)
+    return fail(COFFEE_ERR_UNSUPPORTED, "a row gathers more than 4096 entries (sum of nloc over its incident cells)");
+  if (hflag & ERR_INDEX)
+    return fail(COFFEE_ERR_INVALID_ARG, colidx ? "rowptr does not match l2g (count with colidx = NULL first)"
+                                               : "an l2g entry is outside [0, nrows)");
+  if (!colidx) *nnz = total;
   return COFFEE_OK;
+}
+
+int coffee_csr_map(const int32_t* l2g, int64_t ncells, int nloc, const int64_t* rowptr, const int32_t* colidx,
+                   int64_t nrows, uint32_t* map, coffee_stream_t stream) {
+  if (ncells < 0 || nrows < 0 || nloc < 1 || nloc > 128)
+    return fail(COFFEE_ERR_INVALID_ARG, "need ncells >= 0, nrows >= 0, 1 <= nloc <= 128");
+  if (ncells == 0) return COFFEE_OK;
+  if (!l2g || !rowptr || !colidx || !map) return fail(COFFEE_ERR_INVALID_ARG, "pointers must be non-NULL");
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceCache* c = nullptr;
+  int rc = device_cache(&c);
+  if (rc != COFFEE_OK) return rc;
+  cudaError_t e = (cudaError_t)launch_csr_map(l2g, ncells, nloc, rowptr, colidx, nrows, map, c->err, c->num_sms,
+                                              stream);
+  if (e != cudaSuccess) return cuda_fail(e, "launch(csr_map)");
+  return COFFEE_OK;
+}
+
+int coffee_csr_supported(int form, int degree, int cell, int precision) {
+  if (!valid_fdc(form, degree, cell) || precision < PREC_FP64 || precision > PREC_BF16X3) return 0;
+  return precision == PREC_FP64 ? 1 : tc_csr_supported(form, degree, cell, precision);
+}
+
+int coffee_assemble_csr(const coffee_assemble_args* a, const uint32_t* map, void* vals, int64_t nnz,
+                        coffee_stream_t stream) {
+  if (!a) return fail(COFFEE_ERR_INVALID_ARG, "args is NULL");
+  if (a->ncells > 0 && (!map || !vals)) return fail(COFFEE_ERR_INVALID_ARG, "map and vals must be non-NULL");
+  if (nnz < 0 || nnz > (int64_t)UINT32_MAX) return fail(COFFEE_ERR_INVALID_ARG, "nnz must be in [0, 2^32)");
+  coffee_assemble_args b = *a;
+  b.out = vals;
+  return assemble_impl(&b, map, nnz, stream);
 }
 
 int coffee_assemble(int form, int degree, int cell, const double* coords, const int32_t* cell2vert,

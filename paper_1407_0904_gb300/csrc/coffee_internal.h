@@ -11,7 +11,7 @@ enum { FORM_MASS = 0, FORM_HELMHOLTZ = 1, FORM_ADVDIFF = 2, FORM_BURGERS = 3 };
 enum { PREC_FP64 = 0, PREC_TF32 = 1, PREC_TF32X3 = 2, PREC_BF16 = 3, PREC_BF16X3 = 4 };
 
 // Device error word bits
-enum : unsigned { ERR_INDEX = 1u, ERR_TIMEOUT = 2u };
+enum : unsigned { ERR_INDEX = 1u, ERR_TIMEOUT = 2u, ERR_CAPACITY = 4u };
 // Tuning knobs of the tensor-core kernels (from coffee_assemble_args.flags)
 enum : unsigned { TUNE_OUTPUT_LANES = 1u, TUNE_TWO_STAGES = 2u, TUNE_SUB64 = 4u, TUNE_SUB32 = 8u, TUNE_SUB128 = 16u,
                   TUNE_CELL_LANES = 32u };
@@ -42,6 +42,8 @@ struct Fp64Params {
   int ns, N, ndof;
   double nu;
   int validate;
+  const uint32_t* map;  // global assembly: CSR position of every entry [ncells][ndof*ndof], else NULL
+  int64_t nnz;          // length of the CSR value array (out) when map is set
 };
 // returns cudaError_t as int
 int launch_fp64(int form, int cell, const Fp64Params& p, void* stream);
@@ -102,6 +104,8 @@ struct TcParams {
   int precision;
   int validate;
   double nu;
+  const uint32_t* map;   // global assembly: CSR position of every entry [ncells][N]; out = CSR values
+  int64_t nnz;           // length of the CSR value array when map is set
 };
 int tc_supported(int form, int degree, int cell, int precision);
 int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
@@ -127,6 +131,16 @@ int batch_prepare(int precision, int smem);
 int batch_launch(const BatchLaunch& L, void* stream);
 int stream_one_supported(int form, int kbytes, int parts);
 int launch_stream_one(const BatchGroup& g, int num_sms, void* stream);
+
+// ---- global assembly (k_csr.cu, k_tc_csr.cu) ----
+constexpr int CSR_ROW_CAP = 4096;  // entries of one row before deduplication (sum of nloc over incident cells)
+size_t sparsity_scratch_bytes(int64_t ncells, int nloc, int64_t nrows);
+int launch_sparsity(const int32_t* l2g, int64_t ncells, int nloc, int64_t nrows, int64_t* rowptr, int32_t* colidx,
+                    uint8_t* ws, unsigned** flag, int num_sms, void* stream);
+int launch_csr_map(const int32_t* l2g, int64_t ncells, int nloc, const int64_t* rowptr, const int32_t* colidx,
+                   int64_t nrows, uint32_t* map, unsigned* err, int num_sms, void* stream);
+int tc_csr_supported(int form, int degree, int cell, int precision);
+int launch_tc_csr(int form, int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
 
 // Build the operand image on the host
 void build_tc_image(int form, int degree, int cell, int precision, std::vector<uint8_t>& img,

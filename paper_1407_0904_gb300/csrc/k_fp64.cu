@@ -64,7 +64,9 @@ struct FormK {
                                                       : 1;
 };
 
-template <int FORM, int D>
+// CSR: global assembly -- every entry is added into the CSR value array p.out at the
+// position p.map[cell][entry] instead of being stored.
+template <int FORM, int D, bool CSR>
 __global__ void __launch_bounds__(128) k_assemble_fp64(const Fp64Params p) {
   constexpr int NV = D + 1;
   constexpr int P = D * (D + 1) / 2;
@@ -128,7 +130,17 @@ __global__ void __launch_bounds__(128) k_assemble_fp64(const Fp64Params p) {
 #pragma unroll
     for (int r = 0; r < D; ++r) Pm[a][r] = sg * g.adj[a][r];
 
-  double* out = static_cast<double*>(p.out) + e * (int64_t)p.ndof * p.ndof;
+  double* out = static_cast<double*>(p.out) + (CSR ? 0 : e * (int64_t)p.ndof * p.ndof);
+  const uint32_t* emap = CSR ? p.map + e * (int64_t)p.ndof * p.ndof : nullptr;
+  auto put = [&](int64_t idx, double v) {
+    if constexpr (CSR) {
+      const uint32_t pos = __ldg(emap + idx);
+      if (pos < (uint64_t)p.nnz) atomicAdd(out + pos, v);
+      else atomicOr(p.err, ERR_INDEX);
+    } else {
+      out[idx] = v;
+    }
+  };
   const double* __restrict__ T = p.T;
   const int N = p.N;
 
@@ -166,7 +178,7 @@ __global__ void __launch_bounds__(128) k_assemble_fp64(const Fp64Params p) {
       double acc = 0.0;
 #pragma unroll
       for (int k = 0; k < K; ++k) acc = fma(G[k], __ldg(T + (int64_t)k * N + o), acc);
-      out[o] = acc;
+      put(o, acc);
     }
   } else {
     // Burgers Jacobian, block (ci, cj) of size ns x ns:
@@ -212,7 +224,7 @@ __global__ void __launch_bounds__(128) k_assemble_fp64(const Fp64Params p) {
 #pragma unroll
               for (int q = 0; q < P; ++q) acc = fma(p.nu * H[q], __ldg(T3 + (int64_t)q * nb + ob), acc);
             }
-            out[(int64_t)(ci * ns + i) * ndof + cj * ns + j] = acc;
+            put((int64_t)(ci * ns + i) * ndof + cj * ns + j, acc);
           }
   }
 }
@@ -221,7 +233,8 @@ template <int FORM, int D>
 cudaError_t launch_one(const Fp64Params& p, cudaStream_t s) {
   const int threads = 128;
   const int64_t blocks = (p.ncells + threads - 1) / threads;
-  k_assemble_fp64<FORM, D><<<(unsigned)blocks, threads, 0, s>>>(p);
+  if (p.map) k_assemble_fp64<FORM, D, true><<<(unsigned)blocks, threads, 0, s>>>(p);
+  else k_assemble_fp64<FORM, D, false><<<(unsigned)blocks, threads, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,46 @@ struct BurgersShape {
   static constexpr int PARTS = PT::split ? 2 : 1;
 };
 
+// One operand row (one cell) of NCOLS columns whose k-th value is f(k), converted and
+// stored 16 bytes at a time like store_operand_row; the values are formed as they are
+// stored, so no K-long array is held in registers.
+template <int PREC, int NCOLS, class F>
+__device__ __forceinline__ void store_operand_fn(uint8_t* hi, uint8_t* lo, int r, int kbytes, F f) {
+  using PT = PrecTraits<PREC>;
+  if constexpr (PT::tf32) {
+#pragma unroll
+    for (int c = 0; c < NCOLS / 4; ++c) {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float x = f(c * 4 + q);
+        h[q] = tf32_rna(x);
+        l[q] = tf32_rna(x - __uint_as_float(h[q]));
+      }
+      const uint32_t off = canon_off(r, c * 16, kbytes);
+      *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+      if constexpr (PT::split) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NCOLS / 8; ++c) {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float x0 = f(c * 8 + 2 * q), x1 = f(c * 8 + 2 * q + 1);
+        __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+        __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+        __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+        h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      }
+      const uint32_t off = canon_off(r, c * 16, kbytes);
+      *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+      if constexpr (PT::split) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
 template <int D, int NS, int PREC>
 __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, int nstages) {
   using S = BurgersShape<D, NS, PREC>;
@@ -99,7 +139,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
       if (t >= ntiles) break;
       int64_t li = (tl / PROD_GROUPS) * NB;  // index among this group's blocks
       const int64_t e = t * BN + row;
-      float u[NS][D], Pm[D][D], Q[NS][D], H[P];
+      float u[NS][D], Pm[D][D], H[P];
       bool live = e < p.ncells, bad = false;
       if (live) {
         int vid[NV];
@@ -141,17 +181,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
               H[q++] = (float)p.nu * s * inv;
             }
 #pragma unroll
-          for (int r = 0; r < NS; ++r) {
+          for (int r = 0; r < NS; ++r)
 #pragma unroll
             for (int c = 0; c < D; ++c) u[r][c] = (float)__ldg(p.coef + (int64_t)did[r] * D + c);
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-              float s = 0.f;
-#pragma unroll
-              for (int c = 0; c < D; ++c) s = fmaf(u[r][c], Pm[a][c], s);
-              Q[r][a] = s;
-            }
-          }
         }
       }
 #pragma unroll
@@ -161,28 +193,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
         uint32_t use;
         stage_of(li, grp, spg, s, use);
         if (!mbar_wait(smem_u32(&bars->empty[s]), (use & 1u) ^ 1u, p.err)) { ok = false; break; }
-        float G[KD];
+        // factors of block (ci, cj): u[r][ci] P[a][cj] (T1 columns); on the diagonal also
+        // Q[r][a] = sum_c u[r][c] P[a][c] (T2 columns) and nu H (T3 columns); zero padding
+        auto factor = [&](int k) -> float {
+          if (!live) return 0.f;
+          if (k < S::K1) return u[k / D][ci] * Pm[k % D][cj];
+          if (k < KA1) return 0.f;
+          if (k < KA1 + S::K1) {
+            const int r = (k - KA1) / D, a = (k - KA1) % D;
+            float q = 0.f;
 #pragma unroll
-        for (int k = 0; k < KD; ++k) G[k] = 0.f;
-        if (live) {
-#pragma unroll
-          for (int r = 0; r < NS; ++r)
-#pragma unroll
-            for (int a = 0; a < D; ++a) G[r * D + a] = u[r][ci] * Pm[a][cj];
-          if (ci == cj) {
-#pragma unroll
-            for (int r = 0; r < NS; ++r)
-#pragma unroll
-              for (int a = 0; a < D; ++a) G[KA1 + r * D + a] = Q[r][a];
-#pragma unroll
-            for (int q = 0; q < P; ++q) G[KA1 + S::K1 + q] = H[q];
+            for (int c = 0; c < D; ++c) q = fmaf(u[r][c], Pm[a][c], q);
+            return q;
           }
-        }
+          if (k < KA1 + S::K1 + P) return H[k - KA1 - S::K1];
+          return 0.f;
+        };
         uint8_t* hi = sB + (size_t)s * PARTS * tile_bytes;
         if (ci == cj)
-          store_operand_row<PREC, KD, KD>(hi, hi + tile_bytes, row, G, kbytes);
+          store_operand_fn<PREC, KD>(hi, hi + tile_bytes, row, kbytes, factor);
         else
-          store_operand_row<PREC, KD, KA1>(hi, hi + tile_bytes, row, G, kbytes);
+          store_operand_fn<PREC, KA1>(hi, hi + tile_bytes, row, kbytes, factor);
         fence_proxy_async();
         mbar_arrive(smem_u32(&bars->full[s]));
       }

@@ -1,0 +1,328 @@
+// The tcgen05 local-assembly kernel template, shared by the element-matrix launcher
+// (k_tc.cu) and the fused global-assembly launcher (k_tc_csr.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include "coffee_internal.h"
+#include "tc_common.cuh"
+
+namespace coffee {
+namespace {
+
+using namespace tc;
+
+// ------------------------------------------------------------------- kernel
+// Two orientations of the per-tile contraction.
+//  outputs on lanes (any N): D[o][cell] = T^T G^T, one 128-column TMEM accumulator per
+//         128-output slice (ring of four); each epilogue warp store writes 32 consecutive
+//         outputs of one cell (128 bytes).
+//  cells on lanes (N <= 128, LANES): D[cell][o] = G T, M = 128 cells, N = outputs rounded
+//         up to 16; an epilogue thread holds consecutive outputs of its own cell and writes
+//         its row with 16-byte stores, so every output row is written by one thread in
+//         order. The operands are the same shared-memory images with their roles swapped.
+// CSR (outputs on lanes only): global assembly. Instead of being stored, every entry is
+//         added into the CSR value array p.out at the position p.map[cell][o]; the element
+//         matrices never reach memory.
+template <int FORM, int D, int PREC, bool LANES, bool CSR = false>
+__global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, int nstages) {
+  using PT = PrecTraits<PREC>;
+  constexpr int KSTEP = PT::tf32 ? 8 : 16;  // K elements per MMA (32 bytes)
+  constexpr int KP = round_up(Form<FORM, D>::K, KSTEP);
+  constexpr int PARTS = PT::split ? 2 : 1;
+
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int kbytes = p.kbytes;
+  const int tile_bytes = BM * kbytes;  // one part of one operand tile (A: 128 outputs, B: 128 cells)
+  const int a_bytes = p.mtiles * PARTS * tile_bytes;
+  const int N = p.N;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + a_bytes;
+  Barriers* bars = reinterpret_cast<Barriers*>(sB + nstages * PARTS * tile_bytes);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (p.ncells + BN - 1) / BN;
+  const int NP = (N + 15) & ~15;  // LANES: MMA N (outputs, multiple of 16)
+
+  // ---- set-up: barriers, TMEM, resident A operand ----
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      mbar_init(smem_u32(&bars->full[s]), 128);
+      mbar_init(smem_u32(&bars->empty[s]), 1);
+    }
+    for (int r = 0; r < MAX_SLOTS; ++r) {
+      mbar_init(smem_u32(&bars->tfull[r]), 1);
+      mbar_init(smem_u32(&bars->tempty[r]), EPI_WARPS);
+    }
+    mbar_init(smem_u32(&bars->done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&bars->tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(p.image);
+    uint4* dst = reinterpret_cast<uint4*>(sA);
+    for (int i = threadIdx.x; i < a_bytes / 16; i += NTHREADS) dst[i] = __ldg(src + i);
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+
+  if (warp >= PROD_WARP0 && warp < MMA_WARP) {
+    // ---------------- producers: one cell per thread, two groups on alternate tiles ----------------
+    const int pw = warp - PROD_WARP0;
+    const int grp = pw >> 2, row = ((pw & 3) << 5) + lane;
+    const int spg = nstages / PROD_GROUPS;
+    const int64_t tstep = (int64_t)PROD_GROUPS * gridDim.x;
+    int64_t li = 0;
+    CellIds<FORM, D> ids{}, nids{};  // this tile's and (prefetched) the next tile's index rows
+    {
+      const int64_t e0 = (blockIdx.x + (int64_t)grp * gridDim.x) * BN + row;
+      if (e0 < p.ncells) load_ids<FORM, D>(p, e0, nids);
+    }
+    for (int64_t t = blockIdx.x + (int64_t)grp * gridDim.x; t < ntiles; t += tstep, ++li) {
+      const int64_t e = t * BN + row;
+      ids = nids;
+      if (e + tstep * BN < p.ncells) load_ids<FORM, D>(p, e + tstep * BN, nids);
+      int s;
+      uint32_t use;
+      stage_of(li, grp, spg, s, use);
+      if (!mbar_wait(smem_u32(&bars->empty[s]), (use & 1u) ^ 1u, p.err)) break;
+      float G[KP];
+      bool bad = false;
+      if (e < p.ncells) {
+        cell_factors_ids<FORM, D, KP>(p, ids, G, bad);
+        if (bad) atomicOr(p.err, ERR_INDEX);
+      }
+      if (e >= p.ncells || bad) {
+#pragma unroll
+        for (int k = 0; k < KP; ++k) G[k] = 0.f;
+      }
+      uint8_t* hi = sB + (size_t)s * PARTS * tile_bytes;
+      store_operand_row<PREC, KP>(hi, hi + tile_bytes, row, G, kbytes);
+      fence_proxy_async();
+      mbar_arrive(smem_u32(&bars->full[s]));
+    }
+  } else if (warp == MMA_WARP) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const int ksteps = kbytes / 32;
+      const uint32_t sbo = 8u * (uint32_t)kbytes;
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      const int W = LANES ? BN : p.subw;       // cells per accumulator
+      const int nslot = LANES ? RING : 512 / W;
+      const uint32_t idesc = make_idesc(PT::tf32 ? 2 : 1, BM, LANES ? NP : W);
+      uint32_t rc = 0;  // accumulator ring counter
+      const int spg = nstages / PROD_GROUPS;
+      int64_t tl = 0;  // local tile number
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+        int s;
+        uint32_t use;
+        stage_of(tl / PROD_GROUPS, (int)(tl % PROD_GROUPS), spg, s, use);
+        if (!mbar_wait(smem_u32(&bars->full[s]), use & 1u, p.err)) break;
+        tc_fence_after();
+        const uint32_t bstage = b0 + (uint32_t)(s * PARTS * tile_bytes);
+        for (int j = 0; j < BN / W && ok; ++j)
+        for (int m = 0; m < p.mtiles; ++m, ++rc) {
+          const uint32_t slot = rc % nslot, round = rc / nslot;
+          if (!mbar_wait(smem_u32(&bars->tempty[slot]), (round & 1u) ^ 1u, p.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d = tmem + slot * W;
+          const uint32_t atile = a0 + (uint32_t)(m * PARTS * tile_bytes);
+          const uint32_t bsub = bstage + (uint32_t)(j * W * kbytes);  // cells j*W.. of the stage
+          // outputs on lanes: A = T^T slice, B = G stage; cells on lanes: A = G, B = T^T
+          const uint32_t xo = LANES ? bstage : atile, xc = LANES ? atile : bsub;
+          uint32_t acc = 0;
+          for (int ks = 0; ks < ksteps; ++ks) {
+            const uint32_t ko = (uint32_t)ks * 256u;
+            if constexpr (PT::split) {
+              // small terms first: T_hi G_lo, T_lo G_hi, then T_hi G_hi
+              const uint32_t ahl = LANES ? xo + tile_bytes : xo, bhl = LANES ? xc : xc + tile_bytes;
+              mma<PT::tf32>(d, make_desc(ahl + ko, sbo), make_desc(bhl + ko, sbo), idesc, acc);
+              acc = 1;
+              const uint32_t alh = LANES ? xo : xo + tile_bytes, blh = LANES ? xc + tile_bytes : xc;
+              mma<PT::tf32>(d, make_desc(alh + ko, sbo), make_desc(blh + ko, sbo), idesc, 1);
+            }
+            mma<PT::tf32>(d, make_desc(xo + ko, sbo), make_desc(xc + ko, sbo), idesc, acc);
+            acc = 1;
+          }
+          tc_commit(smem_u32(&bars->tfull[slot]));
+        }
+        tc_commit(smem_u32(&bars->empty[s]));
+      }
+      // all issued MMAs complete before TMEM is released
+      tc_commit(smem_u32(&bars->done));
+      mbar_wait(smem_u32(&bars->done), 0, p.err);
+    }
+    __syncwarp();
+  } else if constexpr (LANES) {
+    // ---------------- epilogue, cells on lanes: each thread writes its cell's row ----------------
+    const int q = warp;  // lanes 32q..32q+31 = cells of the tile
+    const bool vec = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(p.out) & 15) == 0;
+    uint32_t rc = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++rc) {
+      const uint32_t slot = rc % RING, round = rc / RING;
+      if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) { ok = false; break; }
+      tc_fence_after();
+      const int64_t cell = t * BN + q * 32 + lane;
+      float* row = p.out + cell * N;
+      if (t * BN + q * 32 < p.ncells) {  // warp-uniform
+        for (int c0 = 0; c0 < NP; c0 += 32) {
+          uint32_t v[32];
+          if (NP - c0 >= 32) {
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + slot * BN + c0, v);
+          } else {
+            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + slot * BN + c0,
+                      *reinterpret_cast<uint32_t(*)[16]>(v));
+          }
+          tmem_wait_ld();
+          if (cell < p.ncells) {
+            const int w = (N - c0) < 32 ? N - c0 : 32;
+            if (vec) {
+#pragma unroll
+              for (int k = 0; k < 8; ++k)
+                if (4 * k < w)
+                  __stcs(reinterpret_cast<float4*>(row + c0 + 4 * k),
+                         make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
+                                     __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3])));
+            } else {
+#pragma unroll
+              for (int k = 0; k < 32; ++k)
+                if (k < w) __stcs(row + c0 + k, __uint_as_float(v[k]));
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
+    }
+  } else {
+    // ---------------- epilogue, direct 128-byte stores ----------------
+    const int q = warp;  // TMEM lane quadrant
+    const int W = p.subw, nslot = 512 / W;
+    uint32_t rc = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int j = 0; j < BN / W && ok; ++j)
+      for (int m = 0; m < p.mtiles; ++m, ++rc) {
+        const uint32_t slot = rc % nslot, round = rc / nslot;
+        if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) { ok = false; break; }
+        tc_fence_after();
+        const int o = m * BM + q * 32 + lane;
+        for (int cc = 0; cc < W; cc += 64) {
+          const int cw = W - cc < 64 ? W - cc : 64;  // 64 or 32 columns
+          const int64_t cbase = t * BN + j * W + cc;
+          const int64_t rem = p.ncells - cbase;
+          const int ncol = rem <= 0 ? 0 : (rem < cw ? (int)rem : cw);
+          if (m * BM + q * 32 < N && ncol > 0) {
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + slot * W + cc;
+            if constexpr (CSR) {
+              // 32 cells at a time: accumulator columns, their map rows (streaming reads),
+              // then 32 reductions into the CSR values (L2)
+              const uint32_t* mp = p.map + cbase * N + o;
+              for (int c0 = 0; c0 < ncol; c0 += 32) {
+                uint32_t v[32], pos[32];
+                tmem_ld32(taddr + c0, v);
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj)
+                  pos[jj] = (o < N && c0 + jj < ncol) ? __ldcs(mp + (int64_t)(c0 + jj) * N) : 0xffffffffu;
+                tmem_wait_ld();
+                if (o < N) {
+#pragma unroll
+                  for (int jj = 0; jj < 32; ++jj)
+                    if (c0 + jj < ncol) {
+                      if (pos[jj] < (uint64_t)p.nnz) atomicAdd(p.out + pos[jj], __uint_as_float(v[jj]));
+                      else atomicOr(p.err, ERR_INDEX);
+                    }
+                }
+              }
+              continue;
+            }
+            uint32_t v0[32], v1[32];
+            tmem_ld32(taddr, v0);
+            if (cw == 64) tmem_ld32(taddr + 32, v1);
+            tmem_wait_ld();
+            if (o < N) {
+              float* dst = p.out + cbase * N + o;
+              const int64_t stride = N;
+              if (ncol == 64) {
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) __stcs(dst + jj * stride, __uint_as_float(v0[jj]));
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) __stcs(dst + (32 + jj) * stride, __uint_as_float(v1[jj]));
+              } else {
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj)
+                  if (jj < ncol) __stcs(dst + jj * stride, __uint_as_float(v0[jj]));
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj)
+                  if (32 + jj < ncol) __stcs(dst + (32 + jj) * stride, __uint_as_float(v1[jj]));
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+
+// ------------------------------------------------------------ host helpers
+constexpr int SMEM_LIMIT = 227 * 1024;
+constexpr int SMEM_ONE_CTA = 120 * 1024;  // requesting more keeps one CTA (and one TMEM owner) per SM
+
+struct Geom {
+  int K, kelems, kbytes, parts, mtiles, N;
+};
+
+// Cells-on-lanes orientation: the element matrix fits one 128-output slice
+bool lanes_ok(int mtiles) { return mtiles == 1; }
+
+bool geom_of(int form, int degree, int cell, int prec, Geom& g) {
+  if (form == FORM_BURGERS) return false;
+  if (prec == PREC_FP64) return false;
+  const bool tf32 = prec == PREC_TF32 || prec == PREC_TF32X3;
+  const int elem = tf32 ? 4 : 2, kstep = tf32 ? 8 : 16;
+  g.K = form_K(form, degree, cell);
+  g.kelems = (g.K + kstep - 1) / kstep * kstep;
+  g.kbytes = g.kelems * elem;
+  g.parts = (prec == PREC_TF32X3 || prec == PREC_BF16X3) ? 2 : 1;
+  const int ns = nnodes(cell, degree);
+  g.N = ns * ns;
+  g.mtiles = (g.N + BM - 1) / BM;
+  return true;
+}
+
+int stages_for(const Geom& g) {
+  const int a = g.mtiles * g.parts * BM * g.kbytes;
+  const int b = g.parts * BN * g.kbytes;
+  const int fixed = a + (int)sizeof(Barriers) + 1024 + 64;
+  int s = MAX_STAGES;  // even: the stages are split between the two producer groups
+  while (s >= 2 && fixed + s * b > SMEM_LIMIT) s -= 2;
+  return s >= 2 ? s : 0;
+}
+
+}  // namespace
+}  // namespace coffee
