@@ -537,7 +537,7 @@ int oracle_assemble(int form, int degree, int cell, double nu, const double* coo
   set_threads(nthreads);
 #pragma omp parallel for schedule(static)
   for (int64_t e = 0; e < ncells; ++e) {
-    double X[12], cf[64];
+    double X[12], cf[128];  // up to d*ns = 105 Burgers coefficients (vector P4 tetrahedron)
     gather(c, coords, c2v, coef, c2d, ncoefnodes, e, X, cf);
     cell_matrix<double>(c, X, cf, out + e * (int64_t)n * n);
   }
@@ -556,7 +556,7 @@ int oracle_assemble_cells(int form, int degree, int cell, double nu, const doubl
   set_threads(nthreads);
 #pragma omp parallel for schedule(static)
   for (int64_t s = 0; s < nsel; ++s) {
-    double X[12], cf[64];
+    double X[12], cf[128];  // up to d*ns = 105 Burgers coefficients (vector P4 tetrahedron)
     gather(c, coords, c2v, coef, c2d, ncoefnodes, sel[s], X, cf);
     cell_matrix<double>(c, X, cf, out + s * (int64_t)n * n);
   }
@@ -570,7 +570,7 @@ int oracle_burgers_residual(int degree, int cell, double nu, const double* coord
   if (!valid(FORM_BURGERS, degree, cell) || ncells < 0) return -1;
   Ctx c = make_ctx(FORM_BURGERS, degree, cell, nu);
   for (int64_t e = 0; e < ncells; ++e) {
-    double X[12], cf[64];
+    double X[12], cf[128];  // up to d*ns = 105 Burgers coefficients (vector P4 tetrahedron)
     gather(c, coords, c2v, u, c2d, ncoefnodes, e, X, cf);
     cell_residual_burgers(c, X, cf, out + e * (int64_t)c.d * c.ns);
   }
@@ -593,7 +593,7 @@ int oracle_assemble_backward(int form, int degree, int cell, double nu, const do
   set_threads(nthreads);
 #pragma omp parallel for schedule(static)
   for (int64_t e = 0; e < ncells; ++e) {
-    double X[12], cf[64];
+    double X[12], cf[128];  // up to d*ns = 105 Burgers coefficients (vector P4 tetrahedron)
     gather(c, coords, c2v, coef, c2d, ncoefnodes, e, X, cf);
     std::vector<Dual> Xd(nx), cfd(ncf > 0 ? ncf : 1), Ad((size_t)n * n);
     const double* G = dout + e * (int64_t)n * n;

@@ -292,7 +292,7 @@ def test_burgers_residual_exact(cell, k):
     assert abs(Vb @ R - ex) < 1e-13 * scale
 
 
-@pytest.mark.parametrize("cell,k", [(0, 1), (0, 2), (0, 3), (1, 1), (1, 2), (1, 3)])
+@pytest.mark.parametrize("cell,k", [(0, 1), (0, 2), (0, 3), (0, 4), (1, 1), (1, 2), (1, 3), (1, 4)])
 def test_burgers_jacobian_equals_central_difference_of_residual(cell, k):
     """R is quadratic in u, so (R(u+h e_J) - R(u-h e_J)) / 2h is column J exactly, any h."""
     m = meshgen.tet_mesh(1, seed=5) if cell == oracle.TETRAHEDRON else meshgen.tri_mesh(1, seed=5)
