@@ -34,6 +34,10 @@
  *                               + [ci==cj] (phi_i (u . grad phi_j) + nu grad phi_i . grad phi_j),
  *              the Jacobian of int (u.grad u).v + nu grad u : grad v for the vector
  *              degree-k field u (Listing 2 is its degree-1 instance)
+ *  BURGERS_RESIDUAL  R[(c,i)] = int (u . grad u_c) phi_i + nu grad u_c . grad phi_i, the element
+ *              VECTOR of that residual (section 2: local assembly produces element matrices and
+ *              element vectors); out is [ncells][d*ns], component-blocked like the Jacobian's rows;
+ *              coef and cell2dof as for BURGERS_JAC
  *
  * Ownership: the caller owns every buffer it passes. The library owns only its
  * device cache of reference tensors (created on first use per device, guarded by a
@@ -63,7 +67,8 @@ typedef enum {
   COFFEE_MASS = 0,
   COFFEE_HELMHOLTZ = 1,
   COFFEE_ADVDIFF = 2,
-  COFFEE_BURGERS_JAC = 3
+  COFFEE_BURGERS_JAC = 3,
+  COFFEE_BURGERS_RESIDUAL = 4 /* element vectors, see below */
 } coffee_form;
 
 /* Arithmetic of the contraction.  FP64: CUDA-core FP64, double output.
@@ -105,8 +110,9 @@ typedef enum {
  * entries; by default only up to 32 entries */
 #define COFFEE_FLAG_CELL_LANES 64u
 
-/* Number of rows of the element matrix: (k+1)(k+2)/2 (triangle) or
- * (k+1)(k+2)(k+3)/6 (tetrahedron), times d for BURGERS_JAC. Negative on error. */
+/* Number of rows of the element matrix (or length of the element vector): (k+1)(k+2)/2
+ * (triangle) or (k+1)(k+2)(k+3)/6 (tetrahedron), times d for BURGERS_JAC and
+ * BURGERS_RESIDUAL. Negative on error. */
 int coffee_ndof(int form, int degree, int cell);
 
 /* Reference-element tabulation (section 2, step 2: the static basis tables W, X_D10,
@@ -245,7 +251,12 @@ int coffee_sparsity(const int32_t* l2g, int64_t ncells, int nloc, int64_t nrows,
 
 /* Position of every element-matrix entry in the CSR arrays:
  * map[e][i*nloc + j] = k such that colidx[k] == l2g[e][j], rowptr[l2g[e][i]] <= k < rowptr[l2g[e][i]+1].
- *   map  device [ncells][nloc*nloc] uint32 (nnz must be below 2^32).
+ *   map  device uint32, 16-byte aligned, nnz below 2^32, stored in the blocks the fused assembly
+ *        reads: with npad = nloc*nloc rounded up to a multiple of 4, cells are grouped by 32
+ *        (ncells padded up to a multiple of 32) and entries by 32; block (cb, ob) holds
+ *        [32 cells][w] values, w = min(32, npad - 32*ob), at offset 32*(cb*npad + 32*ob), so
+ *        entry (e, idx) is at 32*((e/32)*npad + 32*(idx/32)) + (e%32)*w + idx%32. Length
+ *        ceil(ncells/32)*32*npad; padding entries are 0xffffffff.
  * Asynchronous; an entry that cannot be found (l2g and the pattern disagree) is set to
  * 0xffffffff and raises COFFEE_ERR_DEVICE_INDEX in coffee_check_errors. */
 int coffee_csr_map(const int32_t* l2g, int64_t ncells, int nloc, const int64_t* rowptr, const int32_t* colidx,

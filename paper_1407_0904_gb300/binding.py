@@ -12,6 +12,7 @@ import numpy as np
 import torch
 
 MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC = 0, 1, 2, 3
+BURGERS_RESIDUAL = 4  # element vectors [ncells, d*ns] of the residual whose Jacobian is BURGERS_JAC
 TRIANGLE, TETRAHEDRON = 0, 1
 FP64, TF32, TF32X3, BF16, BF16X3 = 0, 1, 2, 3, 4
 FLAG_VALIDATE = 1
@@ -22,7 +23,8 @@ FLAG_SUBTILE_32 = 16    # tuning knob: 32 cells per TMEM accumulator
 FLAG_SUBTILE_128 = 32   # tuning knob: 128 cells per TMEM accumulator
 FLAG_CELL_LANES = 64    # tuning knob: cells on the TMEM lanes (element matrices <= 128 entries)
 
-FORM_NAMES = {MASS: "mass", HELMHOLTZ: "helmholtz", ADVDIFF: "advdiff", BURGERS_JAC: "burgers_jac"}
+FORM_NAMES = {MASS: "mass", HELMHOLTZ: "helmholtz", ADVDIFF: "advdiff", BURGERS_JAC: "burgers_jac",
+              BURGERS_RESIDUAL: "burgers_residual"}
 PRECISION_NAMES = {FP64: "fp64", TF32: "tf32", TF32X3: "tf32x3", BF16: "bf16", BF16X3: "bf16x3"}
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -168,13 +170,14 @@ def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, p
         raise ValueError("cell2vert must be [ncells, %d]" % (d + 1))
     n = ndof(form, degree, cell)
     odt = torch.float64 if precision == FP64 else torch.float32
+    shape = (ncells, n) if form == BURGERS_RESIDUAL else (ncells, n, n)  # element vectors or matrices
     if out is None:
         if alloc_out:
-            out = torch.empty((ncells, n, n), dtype=odt, device=coords.device)
+            out = torch.empty(shape, dtype=odt, device=coords.device)
     else:
         _dev(out, odt, "out")
-        if out.numel() != ncells * n * n:
-            raise ValueError("out must hold ncells*ndof*ndof elements")
+        if out.numel() != int(np.prod(shape)):
+            raise ValueError("out must hold %s elements" % "x".join(map(str, shape)))
     if ncoefnodes is None and coef is not None:
         ncoefnodes = coef.numel() // (1 + d) if form == ADVDIFF else coef.numel() // d
     a = AssembleArgs()
@@ -206,17 +209,21 @@ _tune_cache = None
 
 
 def _tuned_flags(form, degree, cell, precision):
-    """Knobs chosen by the autotuner (paper_1407_0904_gb300.tune) for this GPU, if any."""
+    """Knobs chosen by the autotuner (paper_1407_0904_gb300.tune) for this GPU; without a tuned
+    entry, the tuner's cost model chooses them from the element-matrix shape."""
     global _tune_cache
-    if precision == FP64:
+    if precision == FP64 or form in (BURGERS_JAC, BURGERS_RESIDUAL):
         return 0
+    from . import tune as _tune
     if _tune_cache is None:
         try:
-            from . import tune as _tune
             _tune_cache = _tune.load_cache()
-        except Exception:
+        except (OSError, ValueError):
             _tune_cache = {}
-    return int(_tune_cache.get("%d/%d/%d/%d" % (form, degree, cell, precision), {}).get("flags", 0))
+    ent = _tune_cache.get("%d/%d/%d/%d" % (form, degree, cell, precision))
+    if ent is not None:
+        return int(ent.get("flags", 0))
+    return _tune.model_flags(ndof(form, degree, cell) ** 2)
 
 
 def assemble_plain(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, out=None,
@@ -263,9 +270,10 @@ def assemble_host(form, degree, cell, coords, cell2vert, coef=None, cell2dof=Non
     ncells = cell2vert.shape[0]
     n = ndof(form, degree, cell)
     odt = torch.float64 if precision == FP64 else torch.float32
+    shape = (ncells, n) if form == BURGERS_RESIDUAL else (ncells, n, n)
     if out is None:
-        out = torch.empty((ncells, n, n), dtype=odt, pin_memory=True)
-    d_out = torch.empty((ncells, n, n), dtype=odt, device=dev)
+        out = torch.empty(shape, dtype=odt, pin_memory=True)
+    d_out = torch.empty(shape, dtype=odt, device=dev)
     d_out.record_stream(side)
     ncoef = None
     if coef is not None:
@@ -412,6 +420,24 @@ def vector_l2g(cell2dof, nnodes, d):
     return torch.cat([cell2dof + c * nnodes for c in range(d)], dim=1).contiguous()
 
 
+def csr_map_len(ncells, nloc):
+    """Length of the blocked entry map: cells padded to 32, entries padded to a multiple of 4."""
+    return (ncells + 31) // 32 * 32 * ((nloc * nloc + 3) // 4 * 4)
+
+
+def csr_map_unblock(m, ncells, nloc):
+    """[ncells, nloc*nloc] uint32 NumPy view of a blocked entry map (host copy; for inspection):
+    block (cb, ob) = [32 cells][width] at 32*(cb*npad + 32*ob), width = min(32, npad - 32*ob)."""
+    m = (m.cpu().numpy() if isinstance(m, torch.Tensor) else np.asarray(m)).view(np.uint32)
+    n2 = nloc * nloc
+    npad = (n2 + 3) // 4 * 4
+    e = np.arange(ncells)[:, None]
+    idx = np.arange(n2)[None, :]
+    ob = idx // 32
+    bw = np.minimum(32, npad - ob * 32)
+    return m[32 * ((e // 32) * npad + 32 * ob) + (e % 32) * bw + idx % 32]
+
+
 def sparsity(l2g, nrows, stream=None):
     """CSR sparsity of the global matrix of the map l2g [ncells, nloc] (int32, CUDA):
     (rowptr int64 [nrows+1], colidx int32 [nnz]), columns ascending in each row."""
@@ -433,8 +459,9 @@ def sparsity(l2g, nrows, stream=None):
 
 
 def csr_map(l2g, rowptr, colidx, stream=None):
-    """Position of every element-matrix entry in colidx: [ncells, nloc*nloc] uint32 values
-    held in an int32 tensor (reinterpret; entries >= 2^31 read as negative)."""
+    """Position in colidx of every element-matrix entry, blocked as the fused kernels read it
+    (see csr_map_len / csr_map_unblock): uint32 values held in a flat int32 tensor (reinterpret;
+    entries >= 2^31 read as negative); padding entries are 0xffffffff."""
     l2g = _dev(l2g, torch.int32, "l2g")
     rowptr = _dev(rowptr, torch.int64, "rowptr")
     colidx = _dev(colidx, torch.int32, "colidx")
@@ -442,7 +469,7 @@ def csr_map(l2g, rowptr, colidx, stream=None):
     L.coffee_csr_map.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
     ncells, nloc = l2g.shape
-    m = torch.empty((ncells, nloc * nloc), dtype=torch.int32, device=l2g.device)
+    m = torch.empty(csr_map_len(ncells, nloc), dtype=torch.int32, device=l2g.device)
     _check(L.coffee_csr_map(_ptr(l2g), ncells, nloc, _ptr(rowptr), _ptr(colidx), rowptr.numel() - 1, _ptr(m),
                             _stream_handle(stream)))
     return m
@@ -456,8 +483,8 @@ def assemble_csr(form, degree, cell, coords, cell2vert, csr_map_, vals, coef=Non
     vals = _dev(vals, odt, "vals")
     csr_map_ = _dev(csr_map_, torch.int32, "map")
     n = ndof(form, degree, cell)
-    if csr_map_.numel() != cell2vert.shape[0] * n * n:
-        raise ValueError("map must be [ncells, ndof*ndof]")
+    if csr_map_.numel() != csr_map_len(cell2vert.shape[0], n):
+        raise ValueError("map must hold csr_map_len(ncells, ndof) entries")
     a, _ = make_args(form, degree, cell, coords, cell2vert, coef, cell2dof, precision, None, nu, validate,
                      tune=tune, alloc_out=False)
     L = lib()

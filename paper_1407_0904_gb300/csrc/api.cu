@@ -59,6 +59,7 @@ int device_cache(DeviceCache** out) {
 }
 
 int fp64_table(DeviceCache& c, int form, int degree, int cell, const double** T) {
+  form = table_form(form);
   auto key = std::make_tuple(form, degree, cell);
   auto it = c.fp64.find(key);
   if (it != c.fp64.end()) {
@@ -78,6 +79,7 @@ int fp64_table(DeviceCache& c, int form, int degree, int cell, const double** T)
 }
 
 int tc_table(DeviceCache& c, int form, int degree, int cell, int prec, TcTable* meta) {
+  form = table_form(form);
   auto key = std::make_tuple(form, degree, cell, prec);
   auto it = c.tc.find(key);
   if (it == c.tc.end()) {
@@ -96,7 +98,7 @@ int tc_table(DeviceCache& c, int form, int degree, int cell, int prec, TcTable* 
 }
 
 bool valid_fdc(int form, int degree, int cell) {
-  return form >= FORM_MASS && form <= FORM_BURGERS && degree >= 1 && degree <= 4 &&
+  return form >= FORM_MASS && form <= FORM_BURGERS_RES && degree >= 1 && degree <= 4 &&
          (cell == CELL_TRI || cell == CELL_TET);
 }
 
@@ -112,7 +114,7 @@ int check_args(const coffee_assemble_args* a) {
     return fail(COFFEE_ERR_INVALID_ARG, "coords, cell2vert and out must be non-NULL");
   if ((a->flags & COFFEE_FLAG_VALIDATE) && a->nverts <= 0)
     return fail(COFFEE_ERR_INVALID_ARG, "validation needs nverts > 0");
-  if (a->form == FORM_ADVDIFF || a->form == FORM_BURGERS) {
+  if (a->form == FORM_ADVDIFF || burgers_like(a->form)) {
     if (!a->coef || !a->cell2dof)
       return fail(COFFEE_ERR_INVALID_ARG, "this form needs coef and cell2dof");
     if (a->ncoefnodes <= 0) return fail(COFFEE_ERR_INVALID_ARG, "ncoefnodes must be > 0");
@@ -132,7 +134,7 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
   if ((rc = device_cache(&c)) != COFFEE_OK) return rc;
   const int d = a->cell == CELL_TRI ? 2 : 3;
   const int ns = nnodes(a->cell, a->degree);
-  const int ndof = a->form == FORM_BURGERS ? d * ns : ns;
+  const int ndof = burgers_like(a->form) ? d * ns : ns;
   const bool validate = (a->flags & COFFEE_FLAG_VALIDATE) != 0;
   if (a->precision == PREC_FP64) {
     const double* T = nullptr;
@@ -209,10 +211,10 @@ using namespace coffee;
 extern "C" {
 
 int coffee_ndof(int form, int degree, int cell) {
-  if (!(form >= 0 && form <= 3 && degree >= 1 && degree <= 6 && (cell == 0 || cell == 1)))
+  if (!(form >= 0 && form <= 4 && degree >= 1 && degree <= 6 && (cell == 0 || cell == 1)))
     return fail(COFFEE_ERR_INVALID_ARG, "form/degree/cell out of range");
   int ns = nnodes(cell, degree);
-  return form == FORM_BURGERS ? (cell == CELL_TRI ? 2 : 3) * ns : ns;
+  return burgers_like(form) ? (cell == CELL_TRI ? 2 : 3) * ns : ns;
 }
 
 int coffee_tabulate(int cell, int degree, int quad_degree, int* nq, int* ndof, double* points,
@@ -317,6 +319,7 @@ int coffee_csr_map(const int32_t* l2g, int64_t ncells, int nloc, const int64_t* 
 
 int coffee_csr_supported(int form, int degree, int cell, int precision) {
   if (!valid_fdc(form, degree, cell) || precision < PREC_FP64 || precision > PREC_BF16X3) return 0;
+  if (form == FORM_BURGERS_RES) return 0;
   return precision == PREC_FP64 ? 1 : tc_csr_supported(form, degree, cell, precision);
 }
 
@@ -325,6 +328,9 @@ int coffee_assemble_csr(const coffee_assemble_args* a, const uint32_t* map, void
   if (!a) return fail(COFFEE_ERR_INVALID_ARG, "args is NULL");
   if (a->ncells > 0 && (!map || !vals)) return fail(COFFEE_ERR_INVALID_ARG, "map and vals must be non-NULL");
   if (nnz < 0 || nnz > (int64_t)UINT32_MAX) return fail(COFFEE_ERR_INVALID_ARG, "nnz must be in [0, 2^32)");
+  if (reinterpret_cast<uintptr_t>(map) % 16 != 0) return fail(COFFEE_ERR_INVALID_ARG, "map must be 16-byte aligned");
+  if (a->form == FORM_BURGERS_RES)
+    return fail(COFFEE_ERR_INVALID_ARG, "the Burgers residual is an element vector, not a matrix");
   coffee_assemble_args b = *a;
   b.out = vals;
   return assemble_impl(&b, map, nnz, stream);
@@ -355,8 +361,8 @@ int coffee_assemble_backward(const coffee_assemble_args* a, const void* dout, do
                              double* d_coef, int deterministic, coffee_stream_t stream) {
   int rc = check_args(a);
   if (rc != COFFEE_OK || a->ncells == 0) return rc;
-  if (a->form == FORM_BURGERS)
-    return fail(COFFEE_ERR_UNSUPPORTED, "no GPU adjoint for the Burgers Jacobian");
+  if (burgers_like(a->form))
+    return fail(COFFEE_ERR_UNSUPPORTED, "no GPU adjoint for the Burgers forms");
   if (!dout || !d_coords) return fail(COFFEE_ERR_INVALID_ARG, "dout and d_coords must be non-NULL");
   if (deterministic && (a->nverts <= 0 || (a->form == FORM_ADVDIFF && d_coef && a->ncoefnodes <= 0)))
     return fail(COFFEE_ERR_INVALID_ARG, "deterministic mode needs nverts (and ncoefnodes)");
@@ -470,7 +476,7 @@ int coffee_batch_plan(const coffee_assemble_args* groups, int ngroups, int grid,
     int rc = check_args(&groups[i]);
     if (rc != COFFEE_OK) return rc;
     if (groups[i].precision != prec) return fail(COFFEE_ERR_INVALID_ARG, "all groups must share one precision");
-    if (groups[i].form == FORM_BURGERS)
+    if (burgers_like(groups[i].form))
       return fail(COFFEE_ERR_UNSUPPORTED, "the mixed batch covers MASS, HELMHOLTZ and ADVDIFF");
   }
   if (item_overhead < 0) item_overhead = 16384.0;

@@ -4,10 +4,19 @@
 #include <vector>
 #include <string>
 
+#ifdef __CUDACC__
+#define COFFEE_HD __host__ __device__
+#else
+#define COFFEE_HD
+#endif
+
 namespace coffee {
 
 enum { CELL_TRI = 0, CELL_TET = 1 };
-enum { FORM_MASS = 0, FORM_HELMHOLTZ = 1, FORM_ADVDIFF = 2, FORM_BURGERS = 3 };
+enum { FORM_MASS = 0, FORM_HELMHOLTZ = 1, FORM_ADVDIFF = 2, FORM_BURGERS = 3, FORM_BURGERS_RES = 4 };
+// the Burgers residual (an element vector) uses the Burgers Jacobian's reference tensors
+inline int table_form(int form) { return form == FORM_BURGERS_RES ? FORM_BURGERS : form; }
+inline bool burgers_like(int form) { return form == FORM_BURGERS || form == FORM_BURGERS_RES; }
 enum { PREC_FP64 = 0, PREC_TF32 = 1, PREC_TF32X3 = 2, PREC_BF16 = 3, PREC_BF16X3 = 4 };
 
 // Device error word bits
@@ -42,7 +51,7 @@ struct Fp64Params {
   int ns, N, ndof;
   double nu;
   int validate;
-  const uint32_t* map;  // global assembly: CSR position of every entry [ncells][ndof*ndof], else NULL
+  const uint32_t* map;  // global assembly: CSR position of every entry (blocked, csr_map_index), else NULL
   int64_t nnz;          // length of the CSR value array (out) when map is set
 };
 // returns cudaError_t as int
@@ -104,7 +113,7 @@ struct TcParams {
   int precision;
   int validate;
   double nu;
-  const uint32_t* map;   // global assembly: CSR position of every entry [ncells][N]; out = CSR values
+  const uint32_t* map;   // global assembly: CSR position of every entry (blocked, csr_map_index); out = CSR values
   int64_t nnz;           // length of the CSR value array when map is set
 };
 int tc_supported(int form, int degree, int cell, int precision);
@@ -113,6 +122,9 @@ int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, 
 int burgers_tc_supported(int degree, int cell, int precision);
 void build_burgers_image(int degree, int cell, int prec, std::vector<uint8_t>& img, TcTable& meta);
 int launch_burgers_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
+// Burgers-residual (element vector) tensor-core kernel (k_tc_burgers_res.cu)
+int burgers_res_tc_supported(int degree, int cell, int precision);
+int launch_burgers_res_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
 // ---- mixed-batch persistent kernel (k_batch.cu) ----
 struct BatchGroup {
   TcParams p;      // the group's inputs, output, table image, N, mtiles, kbytes
@@ -134,6 +146,16 @@ int launch_stream_one(const BatchGroup& g, int num_sms, void* stream);
 
 // ---- global assembly (k_csr.cu, k_tc_csr.cu) ----
 constexpr int CSR_ROW_CAP = 4096;  // entries of one row before deduplication (sum of nloc over incident cells)
+// Entry map of global assembly, blocked as the fused epilogue consumes it: cells in groups of 32
+// (padded), entries (npad = n2 rounded up to 4) in groups of 32; block (cb, ob) = [32 cells][width]
+// at offset 32*(cb*npad + 32*ob).
+inline int64_t csr_map_len(int64_t ncells, int nloc) {
+  return (ncells + 31) / 32 * 32 * (int64_t)((nloc * nloc + 3) & ~3);
+}
+COFFEE_HD inline int64_t csr_map_index(int64_t e, int idx, int npad) {
+  const int ob = idx >> 5, bw = npad - ob * 32 < 32 ? npad - ob * 32 : 32;
+  return 32 * ((e >> 5) * (int64_t)npad + 32 * ob) + (e & 31) * bw + (idx & 31);
+}
 size_t sparsity_scratch_bytes(int64_t ncells, int nloc, int64_t nrows);
 int launch_sparsity(const int32_t* l2g, int64_t ncells, int nloc, int64_t nrows, int64_t* rowptr, int32_t* colidx,
                     uint8_t* ws, unsigned** flag, int num_sms, void* stream);

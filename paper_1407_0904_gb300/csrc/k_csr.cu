@@ -206,13 +206,27 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows(const int32_t* l2g, int
 }
 
 // ---------------------------------------------------------------- position map
+// The map is stored in blocks that match the fused kernel's epilogue chunks: cells in groups of
+// 32 (padded), entries in groups of 32 (the last group npad - 32*ob wide, npad = nloc^2 rounded up
+// to 4); block (cb, ob) holds [32 cells][width] entries contiguously at 32*(cb*npad + 32*ob).
+// Padding entries (cells >= ncells, entries >= nloc^2) are 0xffffffff.
 __global__ void k_map(const int32_t* l2g, int64_t ncells, int nloc, const int64_t* rowptr,
                       const int32_t* colidx, int64_t nrows, uint32_t* map, unsigned* err) {
-  const int64_t per = (int64_t)nloc * nloc, total = ncells * per;
+  const int n2 = nloc * nloc, np = (n2 + 3) & ~3, nob = (np + 31) / 32;
+  const int64_t per_cb = 32 * (int64_t)np, total = ((ncells + 31) / 32) * per_cb;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
        x += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = x / per;
-    const int r = (int)(x - e * per), i = r / nloc, j = r - (r / nloc) * nloc;
+    const int64_t cb = x / per_cb;
+    const int r = (int)(x - cb * per_cb);
+    const int ob = r / 1024 < nob - 1 ? r / 1024 : nob - 1;
+    const int within = r - ob * 1024, bw = np - ob * 32 < 32 ? np - ob * 32 : 32;
+    const int64_t e = cb * 32 + within / bw;
+    const int idx = ob * 32 + within % bw;
+    if (e >= ncells || idx >= n2) {
+      map[x] = 0xffffffffu;
+      continue;
+    }
+    const int i = idx / nloc, j = idx - (idx / nloc) * nloc;
     const int32_t gi = l2g[e * nloc + i], gj = l2g[e * nloc + j];
     uint32_t pos = 0xffffffffu;
     if (gi >= 0 && gi < nrows && gj >= 0 && gj < nrows) {
@@ -284,7 +298,7 @@ int launch_sparsity(const int32_t* l2g, int64_t ncells, int nloc, int64_t nrows,
 int launch_csr_map(const int32_t* l2g, int64_t ncells, int nloc, const int64_t* rowptr, const int32_t* colidx,
                    int64_t nrows, uint32_t* map, unsigned* err, int num_sms, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int64_t total = ncells * (int64_t)nloc * nloc;
+  const int64_t total = csr_map_len(ncells, nloc);
   if (total == 0) return (int)cudaSuccess;
   k_map<<<grid_for(total, 256, num_sms), 256, 0, s>>>(l2g, ncells, nloc, rowptr, colidx, nrows, map, err);
   return (int)cudaGetLastError();

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(128) k_assemble_fp64(const Fp64Params p) {
       if (p.validate && (cid[v] < 0 || cid[v] >= p.ncoefnodes)) bad = true;
     }
   }
-  if constexpr (FORM == FORM_BURGERS) {
+  if constexpr (FORM == FORM_BURGERS || FORM == FORM_BURGERS_RES) {
     if (p.validate)
       for (int r = 0; r < p.ns; ++r) {
         int id = __ldg(p.c2d + e * p.ns + r);
@@ -131,10 +131,10 @@ __global__ void __launch_bounds__(128) k_assemble_fp64(const Fp64Params p) {
     for (int r = 0; r < D; ++r) Pm[a][r] = sg * g.adj[a][r];
 
   double* out = static_cast<double*>(p.out) + (CSR ? 0 : e * (int64_t)p.ndof * p.ndof);
-  const uint32_t* emap = CSR ? p.map + e * (int64_t)p.ndof * p.ndof : nullptr;
+  const int npad = (p.ndof * p.ndof + 3) & ~3;
   auto put = [&](int64_t idx, double v) {
     if constexpr (CSR) {
-      const uint32_t pos = __ldg(emap + idx);
+      const uint32_t pos = __ldg(p.map + csr_map_index(e, (int)idx, npad));
       if (pos < (uint64_t)p.nnz) atomicAdd(out + pos, v);
       else atomicOr(p.err, ERR_INDEX);
     } else {
@@ -144,7 +144,46 @@ __global__ void __launch_bounds__(128) k_assemble_fp64(const Fp64Params p) {
   const double* __restrict__ T = p.T;
   const int N = p.N;
 
-  if constexpr (FORM != FORM_BURGERS) {
+  if constexpr (FORM == FORM_BURGERS_RES) {
+    // Burgers residual (element vector, component-blocked rows (c, i)). R is C(u) u with
+    //   C[i][s] = sum_{r,a} Q[r][a] T2[r,a][i,s] + nu sum_p H_p T3[p][i,s],
+    // the advective-viscous part of the Jacobian's diagonal block: for the quadratic
+    // residual, (u.grad u) = sum_s u_s (u.grad phi_s) and grad u = sum_s u_s grad phi_s.
+    const int ns = p.ns, nb = ns * ns;
+    double u[35 * D];
+    double Q[35 * D];
+    for (int r = 0; r < ns; ++r) {
+      const int id = __ldg(p.c2d + e * ns + r);
+#pragma unroll
+      for (int c = 0; c < D; ++c) u[r * D + c] = __ldg(p.coef + (int64_t)id * D + c);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) s += u[r * D + c] * Pm[a][c];
+        Q[r * D + a] = s;
+      }
+    }
+    const double* T2 = T + (int64_t)ns * D * nb;
+    const double* T3 = T + (int64_t)2 * ns * D * nb;
+    double* outv = static_cast<double*>(p.out) + e * (int64_t)p.ndof;
+    for (int i = 0; i < ns; ++i) {
+      double R[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) R[c] = 0.0;
+      for (int s = 0; s < ns; ++s) {
+        const int ob = i * ns + s;
+        double cis = 0.0;
+        for (int k = 0; k < ns * D; ++k) cis = fma(Q[k], __ldg(T2 + (int64_t)k * nb + ob), cis);
+#pragma unroll
+        for (int q = 0; q < P; ++q) cis = fma(p.nu * H[q], __ldg(T3 + (int64_t)q * nb + ob), cis);
+#pragma unroll
+        for (int c = 0; c < D; ++c) R[c] = fma(cis, u[s * D + c], R[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c) outv[c * ns + i] = R[c];
+    }
+  } else if constexpr (FORM != FORM_BURGERS) {
     // ---- 3. per-cell factors ----
     constexpr int K = FormK<FORM, D>::value;
     double G[K];
@@ -252,6 +291,9 @@ int launch_fp64(int form, int cell, const Fp64Params& p, void* stream) {
       return (int)(tri ? launch_one<FORM_ADVDIFF, 2>(p, s) : launch_one<FORM_ADVDIFF, 3>(p, s));
     case FORM_BURGERS:
       return (int)(tri ? launch_one<FORM_BURGERS, 2>(p, s) : launch_one<FORM_BURGERS, 3>(p, s));
+    case FORM_BURGERS_RES:
+      if (p.map) return (int)cudaErrorInvalidValue;  // element vectors have no matrix entry map
+      return (int)(tri ? launch_one<FORM_BURGERS_RES, 2>(p, s) : launch_one<FORM_BURGERS_RES, 3>(p, s));
   }
   return (int)cudaErrorInvalidValue;
 }

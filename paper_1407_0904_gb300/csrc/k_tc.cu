@@ -71,6 +71,7 @@ cudaError_t launch_prec(int prec, const TcParams& p, int num_sms, cudaStream_t s
 
 int tc_supported(int form, int degree, int cell, int precision) {
   if (form == FORM_BURGERS) return burgers_tc_supported(degree, cell, precision);
+  if (form == FORM_BURGERS_RES) return burgers_res_tc_supported(degree, cell, precision);
   Geom g;
   if (degree < 1 || degree > 4 || !geom_of(form, degree, cell, precision, g)) return 0;
   if (stages_for(g) > 0) return 1;
@@ -124,6 +125,7 @@ void build_tc_image(int form, int degree, int cell, int prec, std::vector<uint8_
 int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, std::string& why) {
   if (p.ncells == 0) return (int)cudaSuccess;
   if (form == FORM_BURGERS) return launch_burgers_tc(cell, p, num_sms, stream, why);
+  if (form == FORM_BURGERS_RES) return launch_burgers_res_tc(cell, p, num_sms, stream, why);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Geom g{};
   g.kbytes = p.kbytes;

@@ -19,64 +19,11 @@
 #include <cmath>
 #include "coffee_internal.h"
 #include "tc_common.cuh"
+#include "k_tc_burgers.cuh"
 
 namespace coffee {
 namespace {
 using namespace tc;
-
-template <int D, int NS, int PREC>
-struct BurgersShape {
-  using PT = PrecTraits<PREC>;
-  static constexpr int KSTEP = PT::tf32 ? 8 : 16;
-  static constexpr int ELEM = PT::tf32 ? 4 : 2;
-  static constexpr int P = D * (D + 1) / 2;
-  static constexpr int K1 = NS * D;                          // columns of T1 (and of T2)
-  static constexpr int KA1 = round_up(K1, KSTEP);            // T1 padded: off-diagonal K
-  static constexpr int KD = round_up(KA1 + K1 + P, KSTEP);   // diagonal K
-  static constexpr int NBLK = NS * NS;
-  static constexpr int MT = (NBLK + BM - 1) / BM;
-  static constexpr int PARTS = PT::split ? 2 : 1;
-};
-
-// One operand row (one cell) of NCOLS columns whose k-th value is f(k), converted and
-// stored 16 bytes at a time like store_operand_row; the values are formed as they are
-// stored, so no K-long array is held in registers.
-template <int PREC, int NCOLS, class F>
-__device__ __forceinline__ void store_operand_fn(uint8_t* hi, uint8_t* lo, int r, int kbytes, F f) {
-  using PT = PrecTraits<PREC>;
-  if constexpr (PT::tf32) {
-#pragma unroll
-    for (int c = 0; c < NCOLS / 4; ++c) {
-      uint32_t h[4], l[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float x = f(c * 4 + q);
-        h[q] = tf32_rna(x);
-        l[q] = tf32_rna(x - __uint_as_float(h[q]));
-      }
-      const uint32_t off = canon_off(r, c * 16, kbytes);
-      *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-      if constexpr (PT::split) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < NCOLS / 8; ++c) {
-      uint32_t h[4], l[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float x0 = f(c * 8 + 2 * q), x1 = f(c * 8 + 2 * q + 1);
-        __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-        __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-        __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-        h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-      }
-      const uint32_t off = canon_off(r, c * 16, kbytes);
-      *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-      if constexpr (PT::split) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-    }
-  }
-}
 
 template <int D, int NS, int PREC>
 __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, int nstages) {
@@ -365,40 +312,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
                  : "memory");
   }
-}
-
-constexpr int SMEM_LIMIT = 227 * 1024;
-constexpr int SMEM_ONE_CTA = 120 * 1024;
-
-struct BGeom {
-  int ns, K1, KA1, KD, kstep, elem, parts, mtiles, kbytes;
-};
-
-bool bgeom(int degree, int cell, int prec, BGeom& g) {
-  if (prec == PREC_FP64 || prec < 0 || prec > PREC_BF16X3) return false;
-  // compiled instances: triangles P1-P4, tetrahedra P1-P2
-  if (cell == CELL_TRI ? (degree < 1 || degree > 4) : (degree < 1 || degree > 2)) return false;
-  const int d = cell == CELL_TRI ? 2 : 3, P = d * (d + 1) / 2;
-  const bool tf32 = prec == PREC_TF32 || prec == PREC_TF32X3;
-  g.ns = nnodes(cell, degree);
-  g.kstep = tf32 ? 8 : 16;
-  g.elem = tf32 ? 4 : 2;
-  g.K1 = g.ns * d;
-  g.KA1 = (g.K1 + g.kstep - 1) / g.kstep * g.kstep;
-  g.KD = (g.KA1 + g.K1 + P + g.kstep - 1) / g.kstep * g.kstep;
-  g.parts = (prec == PREC_TF32X3 || prec == PREC_BF16X3) ? 2 : 1;
-  g.mtiles = (g.ns * g.ns + BM - 1) / BM;
-  g.kbytes = g.KD * g.elem;
-  return true;
-}
-
-int bstages(const BGeom& g) {
-  const int a = g.mtiles * g.parts * BM * g.kbytes;
-  const int b = g.parts * BN * g.kbytes;
-  const int fixed = a + (int)sizeof(Barriers) + 1024 + 64;
-  int s = MAX_STAGES;  // even: the stages are split between the two producer groups
-  while (s >= 2 && fixed + s * b > SMEM_LIMIT) s -= 2;
-  return s >= 2 ? s : 0;
 }
 
 template <int D, int NS, int PREC>

@@ -1,0 +1,331 @@
+// tcgen05 assembly of the Burgers residual, an element vector (section 2 names element
+// vectors beside element matrices; Listing 2's problem, degree k).
+//
+// The residual is quadratic in u: with (u.grad u)_c = sum_s u[s][c] (u.grad phi_s) and
+// grad u_c = sum_s u[s][c] grad phi_s, each component block of R is
+//   R[(c, i)] = sum_s C[i][s] u[s][c],
+//   C[i][s]   = sum_{r,a} Q[r][a] T2[r,a][i,s] + nu sum_p H_p T3[p][i,s],
+// where C is the advective-viscous part of the Jacobian's diagonal block
+// (Q[r][a] = sum_c u[r][c] P[a][c], P = |det J| K). C is one contraction against the T2|T3
+// columns of the Burgers operand image, computed on the tensor cores with the CELLS on the
+// TMEM lanes (M = 128 cells, N = ns*ns outputs rounded up to 16, up to 256); each epilogue
+// thread then holds its own cell's C, multiplies it by the cell's u and writes its
+// component-blocked row of d*ns values.
+// Pipeline roles, bounded waits and the operand image are those of k_tc_burgers.cu.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstring>
+#include <cmath>
+#include "coffee_internal.h"
+#include "tc_common.cuh"
+#include "k_tc_burgers.cuh"
+
+namespace coffee {
+namespace {
+using namespace tc;
+
+template <int D, int NS, int PREC>
+__global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p, int nstages) {
+  using S = BurgersShape<D, NS, PREC>;
+  using PT = PrecTraits<PREC>;
+  constexpr int NV = D + 1, P = S::P, KA1 = S::KA1, KD = S::KD, PARTS = S::PARTS, KSTEP = S::KSTEP;
+  constexpr int NPAD = round_up(S::NBLK, 16);     // MMA N (outputs), <= 256
+  static_assert(NPAD <= 256, "residual kernel: at most 256 outputs per cell");
+  constexpr int SLOTW = S::MT == 1 ? 128 : 256;   // TMEM columns per accumulator
+  constexpr int NSLOT = 512 / SLOTW;
+  constexpr int NDOF = D * NS;
+
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int kbytes = p.kbytes;  // = KD * ELEM
+  const int tile_bytes = BM * kbytes;
+  const int a_bytes = S::MT * PARTS * tile_bytes;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + a_bytes;
+  Barriers* bars = reinterpret_cast<Barriers*>(sB + nstages * PARTS * tile_bytes);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (p.ncells + BN - 1) / BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      mbar_init(smem_u32(&bars->full[s]), 128);
+      mbar_init(smem_u32(&bars->empty[s]), 1);
+    }
+    for (int r = 0; r < NSLOT; ++r) {
+      mbar_init(smem_u32(&bars->tfull[r]), 1);
+      mbar_init(smem_u32(&bars->tempty[r]), EPI_WARPS);
+    }
+    mbar_init(smem_u32(&bars->done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&bars->tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(p.image);
+    uint4* dst = reinterpret_cast<uint4*>(sA);
+    for (int i = threadIdx.x; i < a_bytes / 16; i += NTHREADS) dst[i] = __ldg(src + i);
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+
+  if (warp >= PROD_WARP0 && warp < MMA_WARP) {
+    // ---------------- producers: one cell per thread, one tile per stage ----------------
+    const int pw = warp - PROD_WARP0;
+    const int grp = pw >> 2, row = ((pw & 3) << 5) + lane;
+    const int spg = nstages / PROD_GROUPS;
+    int64_t li = 0;
+    for (int64_t t = blockIdx.x + (int64_t)grp * gridDim.x; t < ntiles; t += (int64_t)PROD_GROUPS * gridDim.x, ++li) {
+      const int64_t e = t * BN + row;
+      int s;
+      uint32_t use;
+      stage_of(li, grp, spg, s, use);
+      if (!mbar_wait(smem_u32(&bars->empty[s]), (use & 1u) ^ 1u, p.err)) break;
+      float u[NS][D], Pm[D][D], H[P];
+      bool live = e < p.ncells;
+      if (live) {
+        int vid[NV];
+        bool bad = false;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          vid[v] = __ldg(p.c2v + e * NV + v);
+          if (p.validate && (vid[v] < 0 || vid[v] >= p.nverts)) bad = true;
+        }
+        int did[NS];
+#pragma unroll
+        for (int r = 0; r < NS; ++r) {
+          did[r] = __ldg(p.c2d + e * NS + r);
+          if (p.validate && (did[r] < 0 || did[r] >= p.ncoefnodes)) bad = true;
+        }
+        if (bad) {
+          atomicOr(p.err, ERR_INDEX);
+          live = false;
+        } else {
+          double X[NV][D];
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int r = 0; r < D; ++r) X[v][r] = __ldg(p.coords + (int64_t)vid[v] * D + r);
+          float adj[D][D], Dm, sg;
+          cell_geometry<D>(X, adj, Dm, sg);
+          const float inv = 1.0f / Dm;
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int c = 0; c < D; ++c) Pm[a][c] = sg * adj[a][c];
+          int q = 0;
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = a; b < D; ++b) {
+              float acc = 0.f;
+#pragma unroll
+              for (int r = 0; r < D; ++r) acc = fmaf(adj[a][r], adj[b][r], acc);
+              H[q++] = (float)p.nu * acc * inv;
+            }
+#pragma unroll
+          for (int r = 0; r < NS; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) u[r][c] = (float)__ldg(p.coef + (int64_t)did[r] * D + c);
+        }
+      }
+      // factors of C: Q[r][a] (T2 columns), nu H (T3 columns); the T1 columns are not used
+      auto factor = [&](int k) -> float {
+        if (!live || k < KA1) return 0.f;
+        if (k < KA1 + S::K1) {
+          const int r = (k - KA1) / D, a = (k - KA1) % D;
+          float q = 0.f;
+#pragma unroll
+          for (int c = 0; c < D; ++c) q = fmaf(u[r][c], Pm[a][c], q);
+          return q;
+        }
+        if (k < KA1 + S::K1 + P) return H[k - KA1 - S::K1];
+        return 0.f;
+      };
+      uint8_t* hi = sB + (size_t)s * PARTS * tile_bytes;
+      store_operand_fn<PREC, KD, decltype(factor), KA1>(hi, hi + tile_bytes, row, kbytes, factor);
+      fence_proxy_async();
+      mbar_arrive(smem_u32(&bars->full[s]));
+    }
+  } else if (warp == MMA_WARP) {
+    // ---------------- MMA issuer: D[cell][o] = G[cell][k] T^T[o][k], k over T2|T3 ----------------
+    if (lane == 0) {
+      const uint32_t sbo = 8u * (uint32_t)kbytes;
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      const int spg = nstages / PROD_GROUPS;
+      uint32_t rc = 0;
+      int64_t tl = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl, ++rc) {
+        int s;
+        uint32_t use;
+        stage_of(tl / PROD_GROUPS, (int)(tl % PROD_GROUPS), spg, s, use);
+        if (!mbar_wait(smem_u32(&bars->full[s]), use & 1u, p.err)) break;
+        const uint32_t slot = rc % NSLOT, round = rc / NSLOT;
+        if (!mbar_wait(smem_u32(&bars->tempty[slot]), (round & 1u) ^ 1u, p.err)) break;
+        tc_fence_after();
+        const uint32_t g = b0 + (uint32_t)(s * PARTS * tile_bytes);  // A: cells x K
+#pragma unroll
+        for (int m = 0; m < S::MT; ++m) {
+          const int nm = (NPAD - m * 128) < 128 ? NPAD - m * 128 : 128;
+          const uint32_t idesc = make_idesc(PT::tf32 ? 2 : 1, BM, nm);
+          const uint32_t tt = a0 + (uint32_t)(m * PARTS * tile_bytes);  // B: outputs x K
+          const uint32_t d = tmem + slot * SLOTW + m * 128;
+          uint32_t acc = 0;
+          for (int ks = KA1 / KSTEP; ks < KD / KSTEP; ++ks) {
+            const uint32_t ko = (uint32_t)ks * 256u;
+            if constexpr (PT::split) {
+              mma<PT::tf32>(d, make_desc(g + tile_bytes + ko, sbo), make_desc(tt + ko, sbo), idesc, acc);
+              acc = 1;
+              mma<PT::tf32>(d, make_desc(g + ko, sbo), make_desc(tt + tile_bytes + ko, sbo), idesc, 1);
+            }
+            mma<PT::tf32>(d, make_desc(g + ko, sbo), make_desc(tt + ko, sbo), idesc, acc);
+            acc = 1;
+          }
+        }
+        tc_commit(smem_u32(&bars->tfull[slot]));
+        tc_commit(smem_u32(&bars->empty[s]));
+      }
+      tc_commit(smem_u32(&bars->done));
+      mbar_wait(smem_u32(&bars->done), 0, p.err);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: each thread forms and writes its cell's residual ----------------
+    const int q = warp;  // lanes 32q..32q+31 = cells of the tile
+    uint32_t rc = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++rc) {
+      const uint32_t slot = rc % NSLOT, round = rc / NSLOT;
+      if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) break;
+      tc_fence_after();
+      const int64_t cell = t * BN + q * 32 + lane;
+      const bool live = cell < p.ncells;
+      float u[NS][D];
+#pragma unroll
+      for (int r = 0; r < NS; ++r) {
+        const int id = live ? __ldg(p.c2d + cell * NS + r) : 0;
+        const bool okid = live && id >= 0 && id < p.ncoefnodes;
+#pragma unroll
+        for (int c = 0; c < D; ++c) u[r][c] = okid ? (float)__ldg(p.coef + (int64_t)id * D + c) : 0.f;
+      }
+      float R[D][NS];
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int i = 0; i < NS; ++i) R[c][i] = 0.f;
+      if (t * BN + q * 32 < p.ncells) {  // warp-uniform
+#pragma unroll
+        for (int o0 = 0; o0 < NPAD; o0 += 16) {
+          uint32_t v[16];
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + slot * SLOTW + o0, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int o = o0 + jj;
+            if (o < S::NBLK) {
+              const int i = o / NS, s = o % NS;
+#pragma unroll
+              for (int c = 0; c < D; ++c) R[c][i] = fmaf(__uint_as_float(v[jj]), u[s][c], R[c][i]);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
+      if (live) {
+        float* row = p.out + cell * NDOF;
+        if constexpr (NDOF % 2 == 0) {
+#pragma unroll
+          for (int x = 0; x < NDOF; x += 2)
+            __stcs(reinterpret_cast<float2*>(row + x), make_float2(R[x / NS][x % NS], R[(x + 1) / NS][(x + 1) % NS]));
+        } else {
+#pragma unroll
+          for (int x = 0; x < NDOF; ++x) __stcs(row + x, R[x / NS][x % NS]);
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+template <int D, int NS, int PREC>
+cudaError_t launch_r(const TcParams& p, int num_sms, cudaStream_t s, int nst, int smem) {
+  auto kern = k_burgers_res_tc<D, NS, PREC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (p.ncells + BN - 1) / BN;
+  const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
+  kern<<<grid, NTHREADS, smem, s>>>(p, nst);
+  return cudaGetLastError();
+}
+
+template <int D, int NS>
+cudaError_t launch_rp(const TcParams& p, int num_sms, cudaStream_t s, int nst, int smem) {
+  switch (p.precision) {
+    case PREC_TF32: return launch_r<D, NS, PREC_TF32>(p, num_sms, s, nst, smem);
+    case PREC_TF32X3: return launch_r<D, NS, PREC_TF32X3>(p, num_sms, s, nst, smem);
+    case PREC_BF16: return launch_r<D, NS, PREC_BF16>(p, num_sms, s, nst, smem);
+    case PREC_BF16X3: return launch_r<D, NS, PREC_BF16X3>(p, num_sms, s, nst, smem);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+int burgers_res_tc_supported(int degree, int cell, int precision) {
+  BGeom g;
+  if (!bgeom(degree, cell, precision, g)) return 0;
+  if (g.ns * g.ns > 256) return 0;
+  return bstages(g) > 0 ? 1 : 0;
+}
+
+int launch_burgers_res_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why) {
+  if (p.ncells == 0) return (int)cudaSuccess;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  BGeom g{};
+  g.mtiles = p.mtiles;
+  g.parts = p.parts;
+  g.kbytes = p.kbytes;
+  int nst = bstages(g);
+  if (nst == 0) {
+    why = "operands do not fit in shared memory";
+    return (int)cudaErrorInvalidValue;
+  }
+  if (nst > 2 && (p.tune & TUNE_TWO_STAGES)) nst = 2;
+  int smem = g.mtiles * g.parts * BM * g.kbytes + nst * g.parts * BN * g.kbytes + (int)sizeof(Barriers) + 1024 + 64;
+  if (smem < SMEM_ONE_CTA) smem = SMEM_ONE_CTA;
+  if (cell == CELL_TRI) {
+    switch (p.ns) {
+      case 3: return (int)launch_rp<2, 3>(p, num_sms, s, nst, smem);
+      case 6: return (int)launch_rp<2, 6>(p, num_sms, s, nst, smem);
+      case 10: return (int)launch_rp<2, 10>(p, num_sms, s, nst, smem);
+      case 15: return (int)launch_rp<2, 15>(p, num_sms, s, nst, smem);
+    }
+  } else {
+    switch (p.ns) {
+      case 4: return (int)launch_rp<3, 4>(p, num_sms, s, nst, smem);
+      case 10: return (int)launch_rp<3, 10>(p, num_sms, s, nst, smem);
+    }
+  }
+  why = "no compiled Burgers-residual instance for this degree";
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace coffee

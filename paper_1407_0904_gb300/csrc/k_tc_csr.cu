@@ -44,7 +44,7 @@ int tc_csr_supported(int form, int degree, int cell, int precision) {
   if (form == FORM_BURGERS || degree < 1 || degree > 4) return 0;
   Geom g;
   if (!geom_of(form, degree, cell, precision, g)) return 0;
-  return stages_for(g) > 0 ? 1 : 0;
+  return stages_for(g, CSR_SMEM) > 0 ? 1 : 0;
 }
 
 int launch_tc_csr(int form, int cell, const TcParams& p, int num_sms, void* stream, std::string& why) {
@@ -55,7 +55,7 @@ int launch_tc_csr(int form, int cell, const TcParams& p, int num_sms, void* stre
   g.parts = p.parts;
   g.mtiles = p.mtiles;
   g.N = p.N;
-  int nst = stages_for(g);
+  int nst = stages_for(g, CSR_SMEM);
   if (nst == 0) {
     why = "operands do not fit in shared memory";
     return (int)cudaErrorInvalidValue;
@@ -64,7 +64,8 @@ int launch_tc_csr(int form, int cell, const TcParams& p, int num_sms, void* stre
   TcParams q = p;
   q.subw = (p.tune & TUNE_SUB32) ? 32 : (p.tune & TUNE_SUB64) ? 64 : (p.tune & TUNE_SUB128) ? 128
                                                                                              : (p.mtiles > 4 ? 64 : 128);
-  int smem = g.mtiles * g.parts * BM * g.kbytes + nst * g.parts * BN * g.kbytes + (int)sizeof(Barriers) + 1024 + 64;
+  int smem = g.mtiles * g.parts * BM * g.kbytes + nst * g.parts * BN * g.kbytes + (int)sizeof(Barriers) + 1024 + 64 +
+             CSR_SMEM;
   if (smem < SMEM_ONE_CTA) smem = SMEM_ONE_CTA;
   const bool tri = cell == CELL_TRI;
   cudaError_t e = cudaErrorInvalidValue;

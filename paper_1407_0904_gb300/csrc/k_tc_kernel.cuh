@@ -12,6 +12,22 @@ namespace {
 
 using namespace tc;
 
+// Global-assembly (CSR) epilogue: each epilogue warp streams the entry-map rows of its 32
+// outputs for 32 cells at a time (one 4 KB stage) from global memory into shared memory with
+// bulk asynchronous copies, CSR_AHEAD chunks ahead of the chunk it adds.
+constexpr int CSR_STAGES = 4, CSR_AHEAD = CSR_STAGES - 1;
+constexpr int CSR_STAGE_BYTES = 32 * 32 * 4;
+constexpr int CSR_SMEM = 128 + EPI_WARPS * CSR_STAGES * CSR_STAGE_BYTES + 128;  // barriers, ring, slack
+
+__device__ __forceinline__ void csr_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void csr_bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
 // ------------------------------------------------------------------- kernel
 // Two orientations of the per-tile contraction.
 //  outputs on lanes (any N): D[o][cell] = T^T G^T, one 128-column TMEM accumulator per
@@ -56,6 +72,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
       mbar_init(smem_u32(&bars->tempty[r]), EPI_WARPS);
     }
     mbar_init(smem_u32(&bars->done), 1);
+    if constexpr (CSR) {
+      uint64_t* ring = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(bars) + round_up((int)sizeof(Barriers), 128));
+      for (int i = 0; i < EPI_WARPS * CSR_STAGES; ++i) mbar_init(smem_u32(ring + i), 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == MMA_WARP) {
@@ -207,7 +227,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
     }
-  } else {
+  } else if constexpr (!CSR) {
     // ---------------- epilogue, direct 128-byte stores ----------------
     const int q = warp;  // TMEM lane quadrant
     const int W = p.subw, nslot = 512 / W;
@@ -227,28 +247,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
           const int ncol = rem <= 0 ? 0 : (rem < cw ? (int)rem : cw);
           if (m * BM + q * 32 < N && ncol > 0) {
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + slot * W + cc;
-            if constexpr (CSR) {
-              // 32 cells at a time: accumulator columns, their map rows (streaming reads),
-              // then 32 reductions into the CSR values (L2)
-              const uint32_t* mp = p.map + cbase * N + o;
-              for (int c0 = 0; c0 < ncol; c0 += 32) {
-                uint32_t v[32], pos[32];
-                tmem_ld32(taddr + c0, v);
-#pragma unroll
-                for (int jj = 0; jj < 32; ++jj)
-                  pos[jj] = (o < N && c0 + jj < ncol) ? __ldcs(mp + (int64_t)(c0 + jj) * N) : 0xffffffffu;
-                tmem_wait_ld();
-                if (o < N) {
-#pragma unroll
-                  for (int jj = 0; jj < 32; ++jj)
-                    if (c0 + jj < ncol) {
-                      if (pos[jj] < (uint64_t)p.nnz) atomicAdd(p.out + pos[jj], __uint_as_float(v[jj]));
-                      else atomicOr(p.err, ERR_INDEX);
-                    }
-                }
-              }
-              continue;
-            }
             uint32_t v0[32], v1[32];
             tmem_ld32(taddr, v0);
             if (cw == 64) tmem_ld32(taddr + 32, v1);
@@ -277,6 +275,100 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
         if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
       }
     }
+  } else {
+    // ---------------- epilogue, global assembly: entries added into the CSR values ----------------
+    const int q = warp;  // TMEM lane quadrant
+    const int W = p.subw, nslot = 512 / W;
+    const int Np = (N + 3) & ~3;  // map row stride (entries of one cell, padded to 16 bytes)
+    uint8_t* ring_base = reinterpret_cast<uint8_t*>(bars) + round_up((int)sizeof(Barriers), 128);
+    uint64_t* rbar = reinterpret_cast<uint64_t*>(ring_base) + q * CSR_STAGES;
+    uint8_t* rbuf = ring_base + 128 + q * CSR_STAGES * CSR_STAGE_BYTES;
+    // chunk = (tile, sub-tile, M-tile, 32-cell column group): the consumer's order
+    struct Chunk {
+      int64_t t;
+      int j, m, c;
+    };
+    auto advance = [&](Chunk& k) {
+      k.c += 32;
+      if (k.c >= W) {
+        k.c = 0;
+        if (++k.m >= p.mtiles) {
+          k.m = 0;
+          if (++k.j >= BN / W) {
+            k.j = 0;
+            k.t += gridDim.x;
+          }
+        }
+      }
+    };
+    // the map block of the chunk's 32 cells x this warp's 32 outputs -> stage (one bulk copy;
+    // the map is stored blocked in exactly these [32 cells][width] blocks)
+    auto issue = [&](const Chunk& k, int stage) {
+      const uint32_t bar = smem_u32(rbar + stage);
+      const int64_t cb = k.t * BN + k.j * W + k.c;  // a multiple of 32
+      const int ob = k.m * 4 + q;
+      const int bw = Np - ob * 32 < 32 ? Np - ob * 32 : 32;
+      if (lane == 0) {
+        if (k.t < ntiles && cb < p.ncells && bw > 0) {
+          csr_expect_tx(bar, (uint32_t)(32 * bw * 4));
+          csr_bulk_g2s(smem_u32(rbuf + stage * CSR_STAGE_BYTES), p.map + 32 * ((cb >> 5) * (int64_t)Np + 32 * ob),
+                       (uint32_t)(32 * bw * 4), bar);
+        } else {
+          mbar_arrive(bar);
+        }
+      }
+    };
+    Chunk prod{(int64_t)blockIdx.x, 0, 0, 0};
+    for (int k = 0; k < CSR_AHEAD; ++k) {
+      issue(prod, k);
+      advance(prod);
+    }
+    uint32_t n = 0;  // chunks consumed
+    uint32_t rc = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int j = 0; j < BN / W && ok; ++j)
+      for (int m = 0; m < p.mtiles && ok; ++m, ++rc) {
+        const uint32_t slot = rc % nslot, round = rc / nslot;
+        if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) { ok = false; break; }
+        tc_fence_after();
+        const int o = m * BM + q * 32 + lane;
+        for (int c = 0; c < W; c += 32, ++n) {
+          const int stage = (int)(n % CSR_STAGES);
+          issue(prod, (int)((n + CSR_AHEAD) % CSR_STAGES));  // refills the stage consumed last
+          advance(prod);
+          if (!mbar_wait(smem_u32(rbar + stage), (n / CSR_STAGES) & 1u, p.err)) { ok = false; ++n; break; }
+          const int64_t cbase = t * BN + j * W + c;
+          const int64_t rem = p.ncells - cbase;
+          const int ncol = rem <= 0 ? 0 : (rem < 32 ? (int)rem : 32);
+          if (m * BM + q * 32 < N && ncol > 0) {  // warp-uniform
+            uint32_t v[32], pos[32];
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + slot * W + c, v);
+            const int ob = m * 4 + q, bw = Np - ob * 32 < 32 ? Np - ob * 32 : 32;
+            const uint32_t* sp = reinterpret_cast<const uint32_t*>(rbuf + stage * CSR_STAGE_BYTES) + (lane < bw ? lane : 0);
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) pos[jj] = sp[jj * bw];
+            tmem_wait_ld();
+            if (o < N) {
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj)
+                if (jj < ncol) {
+                  if (pos[jj] < (uint64_t)p.nnz) atomicAdd(p.out + pos[jj], __uint_as_float(v[jj]));
+                  else atomicOr(p.err, ERR_INDEX);
+                }
+            }
+          }
+          fence_proxy_async();  // this stage's reads precede its next asynchronous refill
+          __syncwarp();
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
+      }
+    }
+    // copies still in flight: chunks n .. n + CSR_AHEAD - 1 (bounded waits)
+    for (int k = 0; k < CSR_AHEAD; ++k, ++n)
+      mbar_wait(smem_u32(rbar + n % CSR_STAGES), (n / CSR_STAGES) & 1u, p.err);
   }
 
   tc_fence_before();
@@ -315,12 +407,12 @@ bool geom_of(int form, int degree, int cell, int prec, Geom& g) {
   return true;
 }
 
-int stages_for(const Geom& g) {
+int stages_for(const Geom& g, int extra = 0) {
   const int a = g.mtiles * g.parts * BM * g.kbytes;
   const int b = g.parts * BN * g.kbytes;
   const int fixed = a + (int)sizeof(Barriers) + 1024 + 64;
   int s = MAX_STAGES;  // even: the stages are split between the two producer groups
-  while (s >= 2 && fixed + s * b > SMEM_LIMIT) s -= 2;
+  while (s >= 2 && fixed + extra + s * b > SMEM_LIMIT) s -= 2;
   return s >= 2 ? s : 0;
 }
 

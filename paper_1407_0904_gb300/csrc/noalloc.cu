@@ -83,7 +83,7 @@ extern "C" int coffee_assemble_backward_noalloc(const coffee_assemble_args* a, c
                                                 coffee_stream_t stream) {
   if (!a) return fail(COFFEE_ERR_INVALID_ARG, "args is NULL");
   if (!(a->form == FORM_MASS || a->form == FORM_HELMHOLTZ || a->form == FORM_ADVDIFF))
-    return fail(a->form == FORM_BURGERS ? COFFEE_ERR_UNSUPPORTED : COFFEE_ERR_INVALID_ARG,
+    return fail(burgers_like(a->form) ? COFFEE_ERR_UNSUPPORTED : COFFEE_ERR_INVALID_ARG,
                 "no-alloc adjoint: form must be MASS, HELMHOLTZ or ADVDIFF");
   if (a->degree < 1 || a->degree > 4 || !(a->cell == CELL_TRI || a->cell == CELL_TET))
     return fail(COFFEE_ERR_INVALID_ARG, "no-alloc adjoint: degree 1..4, triangle or tetrahedron");

@@ -15,11 +15,19 @@ Knobs (all give bit-identical results; only speed changes):
   FLAG_TWO_STAGES     at most two operand stages
 
   python -m paper_1407_0904_gb300.tune [--ncells N] [--out PATH]
+  python -m paper_1407_0904_gb300.tune --study    # cost model vs the tuned choices (no GPU)
+
+The study mirrors the paper's trade-off between a cost model and autotuning: `model_flags`
+chooses the knobs from the element-matrix shape alone (no timing), and `study` measures, on
+the timings the tuner recorded for every candidate, how much slower the model's choice and
+the library's built-in default are than the tuned best.
 """
 import argparse
 import json
 import os
 import sys
+
+import numpy as np
 
 CACHE_VERSION = 1
 
@@ -179,12 +187,67 @@ def tune_batch(ncells_per_mesh=2 ** 17, log=print):
     return {"item_overhead": best, "ms": times[best], "candidates": {str(k): round(v, 5) for k, v in times.items()}}
 
 
+def model_flags(n_outputs):
+    """Knobs chosen without timing, from the number of entries N of the element matrix.
+
+    - Cells on the TMEM lanes when N <= 64: one thread then writes its cell's whole row
+      (<= 256 bytes, at most two 128-byte lines) with 16-byte stores, so rows are completed
+      by one thread in order; above that a thread holds too many accumulator columns.
+    - With outputs on the lanes and exactly two 128-output slices (64 < N <= 256), 64 cells
+      per accumulator: twice the accumulators in flight, so the stores of the second, partly
+      filled slice overlap the next sub-tile's MMAs.
+    - Otherwise the library default (128 cells per accumulator up to four slices).
+    """
+    from . import binding as coffee
+    mtiles = (n_outputs + 127) // 128
+    if n_outputs <= 64:
+        return coffee.FLAG_CELL_LANES
+    if mtiles == 2:
+        return coffee.FLAG_SUBTILE_64
+    return 0
+
+
+def study(entries=None, log=print):
+    """Regret (time / tuned best - 1) of the cost model and of the built-in default for every
+    tuned (form, degree, cell, precision), from the candidates' recorded times."""
+    from . import binding as coffee
+    entries = entries if entries is not None else load_cache(gpu="")
+    rows = []
+    for key, ent in sorted(entries.items()):
+        form, k, cell, prec = map(int, key.split("/"))
+        n = coffee.ndof(form, k, cell) ** 2
+        cands = {int(float(c)): t for c, t in ent["candidates"].items()}
+        best = min(cands.values())
+        mf = model_flags(n)
+        model_t = cands.get(mf)
+        rows.append({"key": key, "form": coffee.FORM_NAMES[form], "degree": k, "cell": "tri" if cell == 0 else "tet",
+                     "N": n, "best_flags": int(ent["flags"]), "best_ms": best, "model_flags": mf,
+                     "model_regret": None if model_t is None else model_t / best - 1.0,
+                     "default_regret": cands.get(0, float("nan")) / best - 1.0})
+    for r in rows:
+        log("%-10s P%d %s N=%4d  tuned %-3d %.4f ms  model %-3d regret %s  default regret %.1f%%" % (
+            r["form"], r["degree"], r["cell"], r["N"], r["best_flags"], r["best_ms"], r["model_flags"],
+            "n/a" if r["model_regret"] is None else "%.1f%%" % (100 * r["model_regret"]), 100 * r["default_regret"]))
+    mr = [r["model_regret"] for r in rows if r["model_regret"] is not None]
+    dr = [r["default_regret"] for r in rows]
+    if mr:
+        log("model:   mean regret %.2f%%, max %.2f%%, best choice in %d of %d" % (
+            100 * np.mean(mr), 100 * max(mr), sum(x <= 1e-9 for x in mr), len(mr)))
+    log("default: mean regret %.2f%%, max %.2f%%, best choice in %d of %d" % (
+        100 * np.mean(dr), 100 * max(dr), sum(x <= 1e-9 for x in dr), len(dr)))
+    return rows
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--ncells", type=int, default=2 ** 19)
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--study", action="store_true", help="cost model vs the cached tuned choices (no GPU)")
     args = ap.parse_args(argv)
+    if args.study:
+        study()
+        return 0
     entries = tune_all(ncells=args.ncells, reps=args.reps)
     batch = tune_batch()
     data = {"version": CACHE_VERSION, "gpu": _gpu_name(), "entries": entries, "batch": batch}

@@ -77,7 +77,11 @@ def test_sparsity_and_map_bit_exact(form, cell, k, perm):
     row_of = np.repeat(np.arange(nrows, dtype=np.int64), np.diff(rp_ref))
     keys = row_of * nrows + ci_ref
     pos = np.searchsorted(keys, rows * nrows + cols)
-    np.testing.assert_array_equal(m.cpu().numpy().view(np.uint32).ravel().astype(np.int64), pos)
+    mm = coffee.csr_map_unblock(m, l2g.shape[0], n)
+    np.testing.assert_array_equal(mm.ravel().astype(np.int64), pos)
+    flat = m.cpu().numpy().view(np.uint32)
+    assert flat.size == coffee.csr_map_len(l2g.shape[0], n)
+    assert np.sum(flat != 0xFFFFFFFF) == pos.size  # everything else is padding
 
 
 def test_sparsity_edge_cases():
@@ -108,7 +112,7 @@ def test_map_of_a_pattern_that_misses_entries_flags_an_error():
     m = coffee.csr_map(g, rowptr, colidx)
     with pytest.raises(coffee.CoffeeError):
         coffee.check_errors()
-    mm = m.cpu().numpy().view(np.uint32)
+    mm = coffee.csr_map_unblock(m, l2g.shape[0], l2g.shape[1])
     assert np.all(mm[:10] < colidx.numel()) and np.any(mm[10:] == 0xFFFFFFFF)
 
 
