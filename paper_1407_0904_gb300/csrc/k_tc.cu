@@ -22,7 +22,7 @@
 //                         16-byte stores of a thread's own row (cells on the lanes, for
 //                         element matrices of at most 128 entries).
 // T^T (the A operand) stays resident in shared memory for the whole launch.
-// Every mbarrier wait is bounded (about 2 s of %globaltimer); on expiry the
+// Every mbarrier wait is bounded (about 2 s of SM cycles); on expiry the
 // kernel sets the error word and unwinds, freeing its TMEM.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>

@@ -205,10 +205,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
     uint32_t rc = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++rc) {
       const uint32_t slot = rc % NSLOT, round = rc / NSLOT;
-      if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) break;
-      tc_fence_after();
       const int64_t cell = t * BN + q * 32 + lane;
       const bool live = cell < p.ncells;
+      // the cell's u is gathered before waiting for its accumulator, so the loads overlap the wait
       float u[NS][D];
 #pragma unroll
       for (int r = 0; r < NS; ++r) {
@@ -217,26 +216,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
 #pragma unroll
         for (int c = 0; c < D; ++c) u[r][c] = okid ? (float)__ldg(p.coef + (int64_t)id * D + c) : 0.f;
       }
+      if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) break;
+      tc_fence_after();
       float R[D][NS];
 #pragma unroll
       for (int c = 0; c < D; ++c)
 #pragma unroll
         for (int i = 0; i < NS; ++i) R[c][i] = 0.f;
       if (t * BN + q * 32 < p.ncells) {  // warp-uniform
+        // 32 accumulator columns per TMEM wait (two 16-column loads)
 #pragma unroll
-        for (int o0 = 0; o0 < NPAD; o0 += 16) {
-          uint32_t v[16];
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + slot * SLOTW + o0, v);
+        for (int o0 = 0; o0 < NPAD; o0 += 32) {
+          uint32_t v[2][16];
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + slot * SLOTW + o0, v[0]);
+          if (o0 + 16 < NPAD) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + slot * SLOTW + o0 + 16, v[1]);
           tmem_wait_ld();
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int o = o0 + jj;
-            if (o < S::NBLK) {
-              const int i = o / NS, s = o % NS;
+          for (int h = 0; h < 2; ++h)
 #pragma unroll
-              for (int c = 0; c < D; ++c) R[c][i] = fmaf(__uint_as_float(v[jj]), u[s][c], R[c][i]);
+            for (int jj = 0; jj < 16; ++jj) {
+              const int o = o0 + 16 * h + jj;
+              if (o < S::NBLK) {
+                const int i = o / NS, s = o % NS;
+#pragma unroll
+                for (int c = 0; c < D; ++c) R[c][i] = fmaf(__uint_as_float(v[h][jj]), u[s][c], R[c][i]);
+              }
             }
-          }
         }
       }
       tc_fence_before();

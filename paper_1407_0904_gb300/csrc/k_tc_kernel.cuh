@@ -12,12 +12,14 @@ namespace {
 
 using namespace tc;
 
-// Global-assembly (CSR) epilogue: each epilogue warp streams the entry-map rows of its 32
-// outputs for 32 cells at a time (one 4 KB stage) from global memory into shared memory with
-// bulk asynchronous copies, CSR_AHEAD chunks ahead of the chunk it adds.
-constexpr int CSR_STAGES = 4, CSR_AHEAD = CSR_STAGES - 1;
-constexpr int CSR_STAGE_BYTES = 32 * 32 * 4;
-constexpr int CSR_SMEM = 128 + EPI_WARPS * CSR_STAGES * CSR_STAGE_BYTES + 128;  // barriers, ring, slack
+// Global-assembly (CSR) epilogue: each epilogue warp streams the entry-map blocks of its 32
+// outputs for one accumulator's cells (up to 128 cells, one 16 KB stage) from global memory into
+// shared memory with bulk asynchronous copies, one accumulator ahead of the one it adds. The
+// hand-off (an mbarrier with a transaction count) is paid once per accumulator, not per 32 cells.
+constexpr int CSR_STAGES = 2;
+constexpr int CSR_STAGE_BYTES = BN * 32 * 4;
+constexpr int CSR_BAR_BYTES = 128;
+constexpr int CSR_SMEM = CSR_BAR_BYTES + EPI_WARPS * CSR_STAGES * CSR_STAGE_BYTES + 128;  // barriers, ring, slack
 
 __device__ __forceinline__ void csr_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -279,73 +281,71 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
     // ---------------- epilogue, global assembly: entries added into the CSR values ----------------
     const int q = warp;  // TMEM lane quadrant
     const int W = p.subw, nslot = 512 / W;
-    const int Np = (N + 3) & ~3;  // map row stride (entries of one cell, padded to 16 bytes)
+    const int Np = (N + 3) & ~3;  // entries per cell in the map (padded to 16 bytes)
     uint8_t* ring_base = reinterpret_cast<uint8_t*>(bars) + round_up((int)sizeof(Barriers), 128);
     uint64_t* rbar = reinterpret_cast<uint64_t*>(ring_base) + q * CSR_STAGES;
-    uint8_t* rbuf = ring_base + 128 + q * CSR_STAGES * CSR_STAGE_BYTES;
-    // chunk = (tile, sub-tile, M-tile, 32-cell column group): the consumer's order
-    struct Chunk {
+    uint8_t* rbuf = ring_base + CSR_BAR_BYTES + q * CSR_STAGES * CSR_STAGE_BYTES;
+    // accumulator = (tile, sub-tile, M-tile): the consumer's order
+    struct Acc {
       int64_t t;
-      int j, m, c;
+      int j, m;
     };
-    auto advance = [&](Chunk& k) {
-      k.c += 32;
-      if (k.c >= W) {
-        k.c = 0;
-        if (++k.m >= p.mtiles) {
-          k.m = 0;
-          if (++k.j >= BN / W) {
-            k.j = 0;
-            k.t += gridDim.x;
-          }
+    auto advance = [&](Acc& k) {
+      if (++k.m >= p.mtiles) {
+        k.m = 0;
+        if (++k.j >= BN / W) {
+          k.j = 0;
+          k.t += gridDim.x;
         }
       }
     };
-    // the map block of the chunk's 32 cells x this warp's 32 outputs -> stage (one bulk copy;
-    // the map is stored blocked in exactly these [32 cells][width] blocks)
-    auto issue = [&](const Chunk& k, int stage) {
+    // the map blocks ([32 cells][width] each, stored contiguously) of this warp's 32 outputs for
+    // the accumulator's cells -> stage: one bulk copy per 32-cell block, one transaction count
+    auto issue = [&](const Acc& k, int stage) {
+      if (lane != 0) return;
       const uint32_t bar = smem_u32(rbar + stage);
-      const int64_t cb = k.t * BN + k.j * W + k.c;  // a multiple of 32
+      const int64_t c0 = k.t * BN + k.j * W;  // first cell, a multiple of 32
       const int ob = k.m * 4 + q;
       const int bw = Np - ob * 32 < 32 ? Np - ob * 32 : 32;
-      if (lane == 0) {
-        if (k.t < ntiles && cb < p.ncells && bw > 0) {
-          csr_expect_tx(bar, (uint32_t)(32 * bw * 4));
-          csr_bulk_g2s(smem_u32(rbuf + stage * CSR_STAGE_BYTES), p.map + 32 * ((cb >> 5) * (int64_t)Np + 32 * ob),
-                       (uint32_t)(32 * bw * 4), bar);
-        } else {
-          mbar_arrive(bar);
-        }
+      const int64_t rem = k.t < ntiles ? p.ncells - c0 : 0;
+      const int nblk = rem <= 0 || bw <= 0 ? 0 : (int)((rem < W ? rem : W) + 31) / 32;
+      if (nblk == 0) {
+        mbar_arrive(bar);
+        return;
       }
+      const uint32_t bytes = (uint32_t)(32 * bw * 4);
+      csr_expect_tx(bar, bytes * nblk);
+      for (int b = 0; b < nblk; ++b)
+        csr_bulk_g2s(smem_u32(rbuf + stage * CSR_STAGE_BYTES + b * bytes),
+                     p.map + 32 * (((c0 >> 5) + b) * (int64_t)Np + 32 * ob), bytes, bar);
     };
-    Chunk prod{(int64_t)blockIdx.x, 0, 0, 0};
-    for (int k = 0; k < CSR_AHEAD; ++k) {
-      issue(prod, k);
-      advance(prod);
-    }
-    uint32_t n = 0;  // chunks consumed
-    uint32_t rc = 0;
+    Acc prod{(int64_t)blockIdx.x, 0, 0};
+    issue(prod, 0);
+    advance(prod);
+    uint32_t issued = 1, n = 0;  // accumulators whose map blocks were requested / consumed
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       for (int j = 0; j < BN / W && ok; ++j)
-      for (int m = 0; m < p.mtiles && ok; ++m, ++rc) {
-        const uint32_t slot = rc % nslot, round = rc / nslot;
+      for (int m = 0; m < p.mtiles && ok; ++m, ++n) {
+        const uint32_t slot = n % nslot, round = n / nslot;
+        const int stage = (int)(n % CSR_STAGES);
+        issue(prod, (int)((n + 1) % CSR_STAGES));  // refills the stage consumed last
+        advance(prod);
+        ++issued;
         if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) { ok = false; break; }
+        if (!mbar_wait(smem_u32(rbar + stage), (n / CSR_STAGES) & 1u, p.err)) { ok = false; ++n; break; }
         tc_fence_after();
         const int o = m * BM + q * 32 + lane;
-        for (int c = 0; c < W; c += 32, ++n) {
-          const int stage = (int)(n % CSR_STAGES);
-          issue(prod, (int)((n + CSR_AHEAD) % CSR_STAGES));  // refills the stage consumed last
-          advance(prod);
-          if (!mbar_wait(smem_u32(rbar + stage), (n / CSR_STAGES) & 1u, p.err)) { ok = false; ++n; break; }
+        const int ob = m * 4 + q, bw = Np - ob * 32 < 32 ? Np - ob * 32 : 32;
+        const uint32_t* sp0 = reinterpret_cast<const uint32_t*>(rbuf + stage * CSR_STAGE_BYTES) + (lane < bw ? lane : 0);
+        for (int c = 0; c < W; c += 32) {
           const int64_t cbase = t * BN + j * W + c;
           const int64_t rem = p.ncells - cbase;
           const int ncol = rem <= 0 ? 0 : (rem < 32 ? (int)rem : 32);
           if (m * BM + q * 32 < N && ncol > 0) {  // warp-uniform
             uint32_t v[32], pos[32];
             tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + slot * W + c, v);
-            const int ob = m * 4 + q, bw = Np - ob * 32 < 32 ? Np - ob * 32 : 32;
-            const uint32_t* sp = reinterpret_cast<const uint32_t*>(rbuf + stage * CSR_STAGE_BYTES) + (lane < bw ? lane : 0);
+            const uint32_t* sp = sp0 + (c >> 5) * 32 * bw;
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) pos[jj] = sp[jj * bw];
             tmem_wait_ld();
@@ -358,17 +358,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
                 }
             }
           }
-          fence_proxy_async();  // this stage's reads precede its next asynchronous refill
-          __syncwarp();
         }
+        fence_proxy_async();  // this stage's reads precede its next asynchronous refill
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
       }
     }
-    // copies still in flight: chunks n .. n + CSR_AHEAD - 1 (bounded waits)
-    for (int k = 0; k < CSR_AHEAD; ++k, ++n)
-      mbar_wait(smem_u32(rbar + n % CSR_STAGES), (n / CSR_STAGES) & 1u, p.err);
+    // copies requested but not consumed (bounded waits)
+    for (; n < issued; ++n) mbar_wait(smem_u32(rbar + n % CSR_STAGES), (n / CSR_STAGES) & 1u, p.err);
   }
 
   tc_fence_before();

@@ -31,7 +31,7 @@ constexpr int RING = 4;             // TMEM accumulator slots of BN columns
 constexpr int TMEM_COLS = RING * BN;
 constexpr int MAX_SLOTS = 16;       // accumulator slots of 32 columns (narrowest sub-tile)
 constexpr int MAX_STAGES = 4;
-constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr long long WAIT_CYCLES = 4000000000ll;  // about 2 s at 2 GHz
 constexpr float KAPPA_FP64 = 32.0f;  // Frobenius condition number above which geometry is FP64
 
 // ---------------------------------------------------------------- PTX helpers
@@ -55,19 +55,17 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 // Bounded wait: true when the phase completed, false (and the error word set) on expiry.
+// The bound is counted on the SM's own cycle counter: reading the global nanosecond timer
+// costs a long-latency round trip, which a wait that is polled often (a pipeline hand-off that
+// is not yet complete) would add to every hand-off.
 static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned* err) {
   if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
+  const long long t0 = clock64();
   for (;;) {
     for (int i = 0; i < 64; ++i)
       if (mbar_try(bar, parity)) return true;
-    if (global_ns() - t0 > WAIT_NS) {
+    if (clock64() - t0 > WAIT_CYCLES) {
       atomicOr(err, ERR_TIMEOUT);
       return false;
     }
