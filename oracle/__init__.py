@@ -20,7 +20,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC = 0, 1, 2, 3
-TRIANGLE, TETRAHEDRON = 0, 1
+TRIANGLE, TETRAHEDRON, PRISM = 0, 1, 2
 
 
 def build(force=False):
@@ -48,6 +48,10 @@ def _load():
         lib.oracle_assemble_cells.argtypes = [I, I, I, D, P, P, P, P, L, P, L, P, I]
         lib.oracle_burgers_residual.argtypes = [I, I, D, P, P, P, P, L, L, P]
         lib.oracle_assemble_backward.argtypes = [I, I, I, D, P, P, P, P, L, L, P, P, P, I]
+        lib.oracle_prism_ndof.argtypes = [I]
+        lib.oracle_prism_rule.argtypes = [I, P, P]
+        lib.oracle_prism_basis.argtypes = [I, I, P, P, P]
+        lib.oracle_prism_assemble.argtypes = [I, I, P, P, L, P, I]
         _lib = lib
     return _lib
 
@@ -217,3 +221,41 @@ def csr_dense(rowptr, colidx, vals):
     r = np.repeat(np.arange(nrows), np.diff(rowptr))
     A[r, colidx] = vals
     return A
+
+
+# ---------------------------------------------------------------- prisms
+# The paper's third element shape (section 5.2): triangle x interval, degree-k tensor-product
+# Lagrange space, geometry by the degree-1 prism functions (not affine), quadrature fixed as
+# n = k+2 Gauss-Legendre points per direction, the triangle factor collapsed by the Duffy map.
+
+def prism_ndof(k):
+    return _load().oracle_prism_ndof(k)
+
+
+def prism_rule(k):
+    """(pts [nq, 3], wts [nq]) of the prism quadrature rule."""
+    L = _load()
+    nq = L.oracle_prism_rule(k, None, None)
+    pts, wts = np.zeros((nq, 3)), np.zeros(nq)
+    L.oracle_prism_rule(k, _p(pts), _p(wts))
+    return pts, wts
+
+
+def prism_basis(k, x):
+    """(phi [npts, n], dphi [npts, n, 3]) of the degree-k prism basis at reference points x [npts, 3]."""
+    x = _f64(np.atleast_2d(x))
+    n = prism_ndof(k)
+    phi, dphi = np.zeros((x.shape[0], n)), np.zeros((x.shape[0], n, 3))
+    if _load().oracle_prism_basis(k, x.shape[0], _p(x), _p(phi), _p(dphi)) != 0:
+        raise ValueError("oracle_prism_basis failed")
+    return phi, dphi
+
+
+def prism_assemble(form, k, coords, c2v, threads=0):
+    """Element matrices [ncells, n, n] of MASS or HELMHOLTZ on prisms (c2v [ncells, 6])."""
+    coords, c2v = _f64(coords), _i32(c2v)
+    n = prism_ndof(k)
+    out = np.zeros((c2v.shape[0], n, n))
+    if _load().oracle_prism_assemble(form, k, _p(coords), _p(c2v), c2v.shape[0], _p(out), threads) != 0:
+        raise ValueError("oracle_prism_assemble failed")
+    return out

@@ -468,6 +468,139 @@ bool valid(int form, int k, int cell) {
   return form >= 0 && form <= 3 && (cell == CELL_TRI || cell == CELL_TET) && k >= 1 && k <= 4;
 }
 
+// ---------------------------------------------------------------------------
+// Prisms: the paper's third element shape (section 5.2 tests triangles, tetrahedra and
+// prisms). Reference prism: the reference triangle (0,0),(1,0),(0,1) times [0,1] in zeta;
+// vertices 0,1,2 at zeta = 0 and 3,4,5 above them at zeta = 1. The degree-k Lagrange space is
+// the tensor product of the degree-k triangle space and the degree-k interval space; node
+// (a,b,c) sits at (a/k, b/k, c/k), ordered with the zeta level c slowest and the triangle's
+// lattice order inside a level. The geometry x(xi) = sum_v N_v(xi) X_v uses the degree-1
+// prism functions N_v, so J varies over the cell (the cell is not affine) and the element
+// matrix is the quadrature sum itself.
+// Quadrature (this definition is the one the library implements too): n = k+2 Gauss-Legendre
+// points per direction on [0,1]; the triangle factor collapsed by (s,t) -> (s, t(1-s)) with
+// weight w_s w_t (1-s); zeta = r with weight w_r. It integrates the mass integrand of any
+// prism exactly (degree <= 2k+1 in the triangle variables and <= 2k+2 in zeta).
+// ---------------------------------------------------------------------------
+Rule prism_rule(int k) {
+  const int n = k + 2;
+  std::vector<double> x, w;
+  gauss_legendre01(n, x, w);
+  Rule R;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int l = 0; l < n; ++l) {
+        const double s = x[i], t = x[j], r = x[l];
+        R.pts.push_back(s);
+        R.pts.push_back(t * (1.0 - s));
+        R.pts.push_back(r);
+        R.wts.push_back(w[i] * w[j] * (1.0 - s) * w[l]);
+      }
+  R.nq = (int)R.wts.size();
+  return R;
+}
+
+// interval Lagrange function c of degree k on the nodes m/k, and its derivative
+void line_lagrange(int k, int c, double z, double& v, double& dv) {
+  v = 1.0;
+  dv = 0.0;
+  for (int m = 0; m <= k; ++m) {
+    if (m == c) continue;
+    const double den = (double)(c - m) / k, fac = (z - (double)m / k) / den;
+    dv = dv * fac + v / den;  // product rule, one factor at a time
+    v *= fac;
+  }
+}
+
+int prism_ndof(int k) { return (k + 1) * (k + 2) / 2 * (k + 1); }
+
+// values phi[i] and reference derivatives dphi[i*3 + a] of the prism basis at x
+void eval_prism_basis(const Basis& T, int k, const double* x, double* phi, double* dphi) {
+  const int nt = T.n;
+  std::vector<double> pt(nt), dpt((size_t)nt * 2);
+  eval_basis(T, x, pt.data(), dpt.data());
+  for (int c = 0; c <= k; ++c) {
+    double L, dL;
+    line_lagrange(k, c, x[2], L, dL);
+    for (int t = 0; t < nt; ++t) {
+      const int i = c * nt + t;
+      if (phi) phi[i] = pt[t] * L;
+      if (dphi) {
+        dphi[(size_t)i * 3 + 0] = dpt[(size_t)t * 2 + 0] * L;
+        dphi[(size_t)i * 3 + 1] = dpt[(size_t)t * 2 + 1] * L;
+        dphi[(size_t)i * 3 + 2] = pt[t] * dL;
+      }
+    }
+  }
+}
+
+// Jacobian of the prism map at xi: J[r][c] = sum_v X[v][r] dN_v/dxi_c
+void prism_jacobian(const double* X, const double* xi, double J[3][3]) {
+  const double s = xi[0], t = xi[1], z = xi[2];
+  const double lam[3] = {1.0 - s - t, s, t};
+  const double dlam[3][2] = {{-1.0, -1.0}, {1.0, 0.0}, {0.0, 1.0}};
+  double dN[6][3];
+  for (int v = 0; v < 3; ++v) {
+    dN[v][0] = dlam[v][0] * (1.0 - z);
+    dN[v][1] = dlam[v][1] * (1.0 - z);
+    dN[v][2] = -lam[v];
+    dN[v + 3][0] = dlam[v][0] * z;
+    dN[v + 3][1] = dlam[v][1] * z;
+    dN[v + 3][2] = lam[v];
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0.0;
+      for (int v = 0; v < 6; ++v) acc += X[v * 3 + r] * dN[v][c];
+      J[r][c] = acc;
+    }
+}
+
+// Element matrix of one prism (MASS or HELMHOLTZ): the quadrature loop nest of section 2,
+// with the Jacobian, its determinant and inverse evaluated at every point.
+void prism_matrix(int form, int k, const Basis& T, const Rule& R, const double* phiq, const double* dphiq,
+                  const double* X, double* A) {
+  const int n = prism_ndof(k);
+  std::fill(A, A + (size_t)n * n, 0.0);
+  std::vector<double> grad((size_t)n * 3);
+  for (int q = 0; q < R.nq; ++q) {
+    double J[3][3];
+    prism_jacobian(X, &R.pts[(size_t)q * 3], J);
+    // inverse by the adjugate: K[a][c] = cofactor(c,a) / det
+    const double C00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double C01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double C02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * C00 + J[0][1] * C01 + J[0][2] * C02;
+    double K[3][3];
+    K[0][0] = C00 / det;
+    K[1][0] = C01 / det;
+    K[2][0] = C02 / det;
+    K[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    K[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    K[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    K[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    K[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    K[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    const double* phi = phiq + (size_t)q * n;
+    const double* dphi = dphiq + (size_t)q * n * 3;
+    for (int i = 0; i < n; ++i)
+      for (int c = 0; c < 3; ++c) {
+        double g = 0.0;
+        for (int a = 0; a < 3; ++a) g += K[a][c] * dphi[(size_t)i * 3 + a];
+        grad[(size_t)i * 3 + c] = g;
+      }
+    const double wd = R.wts[q] * std::fabs(det);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double v = phi[i] * phi[j];
+        if (form == FORM_HELMHOLTZ)
+          v += grad[(size_t)i * 3] * grad[(size_t)j * 3] + grad[(size_t)i * 3 + 1] * grad[(size_t)j * 3 + 1] +
+               grad[(size_t)i * 3 + 2] * grad[(size_t)j * 3 + 2];
+        A[(size_t)i * n + j] += wd * v;
+      }
+  }
+}
+
 void set_threads(int nthreads) {
 #ifdef _OPENMP
   omp_set_num_threads(nthreads > 0 ? nthreads : omp_get_num_procs());
@@ -625,6 +758,51 @@ int oracle_assemble_backward(int form, int degree, int cell, double nu, const do
         for (int a = 0; a < d; ++a) d_coef[id * d + a] += L[nx + rr * d + a];
       }
     }
+  }
+  return 0;
+}
+
+// ---- prisms ----
+int oracle_prism_ndof(int degree) { return (degree >= 1 && degree <= 4) ? prism_ndof(degree) : -1; }
+
+// the prism quadrature rule: pts [nq][3], wts [nq]; NULL pointers query nq
+int oracle_prism_rule(int degree, double* pts, double* wts) {
+  if (degree < 1 || degree > 4) return -1;
+  Rule R = prism_rule(degree);
+  if (pts) std::memcpy(pts, R.pts.data(), R.pts.size() * sizeof(double));
+  if (wts) std::memcpy(wts, R.wts.data(), R.wts.size() * sizeof(double));
+  return R.nq;
+}
+
+// prism basis values [npts][n] and reference derivatives [npts][n][3] at x [npts][3]
+int oracle_prism_basis(int degree, int npts, const double* x, double* phi, double* dphi) {
+  if (degree < 1 || degree > 4) return -1;
+  Basis T = lagrange(CELL_TRI, degree);
+  const int n = prism_ndof(degree);
+  for (int p = 0; p < npts; ++p)
+    eval_prism_basis(T, degree, x + (size_t)p * 3, phi ? phi + (size_t)p * n : nullptr,
+                     dphi ? dphi + (size_t)p * n * 3 : nullptr);
+  return 0;
+}
+
+// element matrices [ncells][n][n] of MASS or HELMHOLTZ on prisms: coords [nverts][3],
+// cell2vert [ncells][6] (bottom triangle, then the top vertices above it)
+int oracle_prism_assemble(int form, int degree, const double* coords, const int32_t* c2v, int64_t ncells,
+                          double* out, int nthreads) {
+  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ) || degree < 1 || degree > 4 || ncells < 0) return -1;
+  Basis T = lagrange(CELL_TRI, degree);
+  Rule R = prism_rule(degree);
+  const int n = prism_ndof(degree);
+  std::vector<double> phiq((size_t)R.nq * n), dphiq((size_t)R.nq * n * 3);
+  for (int q = 0; q < R.nq; ++q)
+    eval_prism_basis(T, degree, &R.pts[(size_t)q * 3], &phiq[(size_t)q * n], &dphiq[(size_t)q * n * 3]);
+  set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < ncells; ++e) {
+    double X[18];
+    for (int v = 0; v < 6; ++v)
+      for (int r = 0; r < 3; ++r) X[v * 3 + r] = coords[(int64_t)c2v[e * 6 + v] * 3 + r];
+    prism_matrix(form, degree, T, R, phiq.data(), dphiq.data(), X, out + e * (int64_t)n * n);
   }
   return 0;
 }

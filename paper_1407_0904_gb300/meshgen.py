@@ -17,12 +17,16 @@ Conventions:
     vertices stay fixed, so the mesh still tiles the unit square/cube exactly;
   * a degree-k node of a cell with grid vertices V0..Vd and lattice index (a,b,c)
     is the integer point k*V0 + a(V1-V0) + b(V2-V0) + c(V3-V0) of the (k*n+1)^d
-    lattice, which makes the numbering conforming across cells.
+    lattice, which makes the numbering conforming across cells;
+  * prisms: the triangle mesh of the unit square extruded through nz layers of the unit
+    cube; a prism's vertices are its bottom triangle, then the three vertices above it;
+    its degree-k node (a,b) at level c is the integer point k*V0 + a(V1-V0) + b(V2-V0)
+    + c*(V3-V0) (with V3 above V0), zeta level slowest.
 """
 import itertools
 import numpy as np
 
-TRIANGLE, TETRAHEDRON = 0, 1
+TRIANGLE, TETRAHEDRON, PRISM = 0, 1, 2
 
 _PERMS3 = list(itertools.permutations(range(3)))
 
@@ -41,6 +45,11 @@ class Mesh:
     @property
     def dim(self):
         return 2 if self.cell == TRIANGLE else 3
+
+    @property
+    def nvc(self):
+        """vertices per cell"""
+        return {TRIANGLE: 3, TETRAHEDRON: 4, PRISM: 6}[self.cell]
 
     @property
     def ncells(self):
@@ -104,6 +113,29 @@ def tet_mesh(nx, ny=None, nz=None, perturb=0.15, seed=2, ncells=None):
     return Mesh(TETRAHEDRON, np.ascontiguousarray(coords), c2v.astype(np.int32), grid, (nx, ny, nz))
 
 
+def prism_mesh(n, nz=None, perturb=0.15, seed=6):
+    """Unit cube: the n x n two-triangle mesh of the square extruded through nz layers
+    (2 n^2 nz prisms); interior vertices perturbed, so the quadrilateral faces are not
+    planar and the prisms are not affine."""
+    nz = n if nz is None else nz
+    rng = np.random.default_rng(seed)
+    kk, jj, ii = np.meshgrid(np.arange(nz + 1), np.arange(n + 1), np.arange(n + 1), indexing="ij")
+    pts = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1).astype(np.int64)
+    coords = _perturb(pts.astype(np.float64), (n, n, nz), perturb, rng)
+    ck, cj, ci = np.meshgrid(np.arange(nz), np.arange(n), np.arange(n), indexing="ij")
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    b00 = np.stack([ci, cj, ck], axis=1)
+    ex, ey, ez = np.array([1, 0, 0]), np.array([0, 1, 0]), np.array([0, 0, 1])
+    corners = np.empty((b00.shape[0], 2, 6, 3), dtype=np.int64)
+    for half, tri in enumerate(((0 * ex, ex, ex + ey), (0 * ex, ex + ey, ey))):
+        for v in range(3):
+            corners[:, half, v] = b00 + tri[v]
+            corners[:, half, v + 3] = b00 + tri[v] + ez
+    grid = corners.reshape(-1, 6, 3)
+    c2v = grid[..., 0] + (n + 1) * (grid[..., 1] + (n + 1) * grid[..., 2])
+    return Mesh(PRISM, np.ascontiguousarray(coords), c2v.astype(np.int32), grid, (n, n, nz))
+
+
 def lattice(cell, k):
     """Lattice multi-indices (a,b[,c]), a+b+c <= k, c slowest then b then a."""
     out = []
@@ -120,10 +152,15 @@ def cell2dof(mesh, k, permute_seed=None):
 
     With permute_seed the global node ids are shuffled by a seeded permutation
     (a gather-locality stress case)."""
-    L = lattice(mesh.cell, k)  # [ns, d]
-    g = mesh.grid  # [ncells, d+1, d]
+    g = mesh.grid  # [ncells, nvc, d]
     V0 = g[:, 0]
-    E = g[:, 1:] - V0[:, None, :]  # [ncells, d, d] rows = V_{a+1}-V0
+    if mesh.cell == PRISM:
+        T = lattice(TRIANGLE, k)
+        L = np.array([(a, b, c) for c in range(k + 1) for (a, b) in T], dtype=np.int64)
+        E = np.stack([g[:, 1] - V0, g[:, 2] - V0, g[:, 3] - V0], axis=1)  # V3 is above V0
+    else:
+        L = lattice(mesh.cell, k)  # [ns, d]
+        E = g[:, 1:] - V0[:, None, :]  # [ncells, d, d] rows = V_{a+1}-V0
     pts = k * V0[:, None, :] + np.einsum("na,cad->cnd", L, E)  # [ncells, ns, d]
     dims = [k * s + 1 for s in mesh.shape]
     ids = np.zeros(pts.shape[:2], dtype=np.int64)
