@@ -37,7 +37,8 @@ L2_BYTES = 129 * 2 ** 20
 TRAFFIC = {"5b6fc9e0fe78759c": 2.492e9}  # 31.86 MB read + 2.46 GB written per launch (two launches)
 
 MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC, BURGERS_RESIDUAL = 0, 1, 2, 3, 4
-TRIANGLE, TETRAHEDRON = 0, 1
+TRIANGLE, TETRAHEDRON, PRISM = 0, 1, 2
+FP64_PEAK_TFLOPS = 1.25  # FP64 FMA throughput measured on this GPU model by a standalone probe
 
 
 class Workload:
@@ -69,6 +70,10 @@ def _kuhn2pow20(mg, nx):
     return mg.tet_mesh(64, 64, 43, perturb=0.15, seed=3, ncells=2 ** 20)
 
 
+def _prism48(mg, nx):
+    return mg.prism_mesh(nx or 48, nx or 48, perturb=0.15, seed=6)
+
+
 def _tri64(mg, nx):
     return mg.tri_mesh(nx or 64, perturb=0.2, seed=1)
 
@@ -87,6 +92,9 @@ WORKLOADS["burgers-p2-tet"] = Workload("burgers-p2-tet", BURGERS_JAC, 2, TETRAHE
 WORKLOADS["burgers-residual-p2-tet"] = Workload("burgers-residual-p2-tet", BURGERS_RESIDUAL, 2, TETRAHEDRON,
                                                 "Kuhn 64x64x43 truncated to 2^20 tets, perturbed 0.15h (seed 3), "
                                                 "vector P2 u~N(0,1), nu=0.01; element vectors", _kuhn2pow20)
+WORKLOADS["helmholtz-p2-prism"] = Workload("helmholtz-p2-prism", HELMHOLTZ, 2, PRISM,
+                                           "unit cube, 48x48 two-triangle columns x 48 layers = 221,184 "
+                                           "twisted prisms perturbed 0.15h (seed 6); FP64", _prism48)
 WORKLOADS["helmholtz-p1-tri"] = Workload("helmholtz-p1-tri", HELMHOLTZ, 1, TRIANGLE,
                                          "unit square 64x64x2 triangles perturbed 0.2h (seed 1)", _tri64)
 
@@ -146,7 +154,7 @@ def out_entries(wl, ndof):
 def alg_bytes_per_cell(wl, mesh, c2d, coef, ndof, out_bytes):
     """Algorithmic HBM bytes per cell: every input once, plus the element matrix (or vector)."""
     d = 2 if wl.cell == TRIANGLE else 3
-    b = 4 * (d + 1) + 8 * d * mesh.nverts / mesh.ncells + out_bytes * out_entries(wl, ndof)
+    b = 4 * mesh.nvc + 8 * d * mesh.nverts / mesh.ncells + out_bytes * out_entries(wl, ndof)
     if c2d is not None:
         b += 4 * c2d.shape[1] + 8 * coef.size / mesh.ncells
     return b
@@ -213,6 +221,8 @@ def kernel_source_sha():
 
 def oracle_cells(wl, mesh, coef, c2d, sel, threads=0):
     import oracle
+    if wl.cell == PRISM:
+        return oracle.prism_assemble(wl.form, wl.degree, mesh.coords, mesh.cell2vert[sel], threads=threads)
     if wl.form == BURGERS_RESIDUAL:
         d = 2 if wl.cell == TRIANGLE else 3
         return oracle.burgers_residual(wl.degree, wl.cell, mesh.coords, mesh.cell2vert[sel], coef.reshape(-1, d),
@@ -245,7 +255,7 @@ def metric_of(wl):
     if wl.form == BURGERS_RESIDUAL:
         return "Burgers residual P%d-%s element vectors/s" % (wl.degree, "tri" if wl.cell == TRIANGLE else "tet")
     return "%s P%d-%s element matrices/s" % (["Mass", "Helmholtz", "Advection-diffusion", "Burgers Jacobian"][wl.form],
-                                             wl.degree, "tri" if wl.cell == TRIANGLE else "tet")
+                                             wl.degree, ["tri", "tet", "prism"][wl.cell])
 
 
 def mesh_desc_of(wl, nx, mesh):
@@ -385,6 +395,15 @@ def run_ours(args):
             "alg_bytes_per_cell": per_cell, "kernel_ms": launch_ms}
     if prec == coffee.FP64:
         roof["note"] = "FP64 kernel: bound by the FP64 ALU (1.25 TFLOP/s measured); HBM fraction for context"
+    if cell == PRISM:
+        # non-affine cells: the contraction over all quadrature points (K = 7 Q) dominates
+        Q = (degree + 2) ** 3
+        flops = 2.0 * (Q * (7 if form == HELMHOLTZ else 1)) * ndof * ndof + 250.0 * Q
+        tf = flops * ncells / (launch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 FMA probe (not in the measured-peaks file)", "flops_per_cell": flops,
+                "kernel_ms": launch_ms, "hbm_gbs": achieved}
 
     fp64 = None
     if prec != coffee.FP64 and not args.no_fp64:

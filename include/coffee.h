@@ -61,7 +61,14 @@ extern "C" {
 /* Same type as cudaStream_t (struct CUstream_st*), declared without CUDA headers. */
 typedef struct CUstream_st* coffee_stream_t;
 
-typedef enum { COFFEE_TRIANGLE = 0, COFFEE_TETRAHEDRON = 1 } coffee_cell;
+/* Prisms (the paper's third element shape): reference triangle x [0,1]; cell2vert rows are
+ * the bottom triangle's vertices, then the three vertices above them; degree-k tensor-product
+ * Lagrange space (node (a,b,c) at (a/k, b/k, c/k), zeta level c slowest); the map uses the
+ * degree-1 prism functions, so it is not affine and the element matrix is the quadrature sum
+ * of a fixed rule: n = k+2 Gauss-Legendre points per direction on [0,1], the triangle factor
+ * collapsed by (s,t) -> (s, t(1-s)) with weight w_s w_t (1-s). Prisms support MASS and
+ * HELMHOLTZ in FP64 (coffee_assemble_ex, coffee_assemble_csr). */
+typedef enum { COFFEE_TRIANGLE = 0, COFFEE_TETRAHEDRON = 1, COFFEE_PRISM = 2 } coffee_cell;
 
 typedef enum {
   COFFEE_MASS = 0,
@@ -111,8 +118,8 @@ typedef enum {
 #define COFFEE_FLAG_CELL_LANES 64u
 
 /* Number of rows of the element matrix (or length of the element vector): (k+1)(k+2)/2
- * (triangle) or (k+1)(k+2)(k+3)/6 (tetrahedron), times d for BURGERS_JAC and
- * BURGERS_RESIDUAL. Negative on error. */
+ * (triangle), (k+1)(k+2)(k+3)/6 (tetrahedron) or (k+1)^2(k+2)/2 (prism), times d for
+ * BURGERS_JAC and BURGERS_RESIDUAL. Negative on error. */
 int coffee_ndof(int form, int degree, int cell);
 
 /* Reference-element tabulation (section 2, step 2: the static basis tables W, X_D10,
@@ -135,7 +142,7 @@ int coffee_reference_tensor(int form, int degree, int cell, int* K, int* N, doub
 
 /* FP64 local assembly (plain one-thread-per-cell kernel), all pointers on the device:
  *   coords    [nverts][d] double
- *   cell2vert [ncells][d+1] int32
+ *   cell2vert [ncells][d+1] int32 (prisms: [ncells][6])
  *   coef      ADVDIFF: [ncoefnodes][1+d] double, row = (eps, b_0, .., b_{d-1})
  *             BURGERS_JAC: u [ncoefnodes][d] double (viscosity nu = 0.01)
  *             MASS/HELMHOLTZ: NULL

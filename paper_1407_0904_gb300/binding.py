@@ -13,7 +13,7 @@ import torch
 
 MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC = 0, 1, 2, 3
 BURGERS_RESIDUAL = 4  # element vectors [ncells, d*ns] of the residual whose Jacobian is BURGERS_JAC
-TRIANGLE, TETRAHEDRON = 0, 1
+TRIANGLE, TETRAHEDRON, PRISM = 0, 1, 2
 FP64, TF32, TF32X3, BF16, BF16X3 = 0, 1, 2, 3, 4
 FLAG_VALIDATE = 1
 FLAG_OUTPUT_LANES = 2   # tuning knob: element-matrix entries on the TMEM lanes
@@ -80,6 +80,10 @@ def _check(rc):
 
 def dim(cell):
     return 2 if cell == TRIANGLE else 3
+
+
+def verts_per_cell(cell):
+    return {TRIANGLE: 3, TETRAHEDRON: 4, PRISM: 6}[cell]
 
 
 def ndof(form, degree, cell):
@@ -166,8 +170,9 @@ def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, p
     cell2dof = _dev(cell2dof, torch.int32, "cell2dof")
     d = dim(cell)
     ncells = cell2vert.shape[0]
-    if cell2vert.dim() != 2 or cell2vert.shape[1] != d + 1:
-        raise ValueError("cell2vert must be [ncells, %d]" % (d + 1))
+    nv = verts_per_cell(cell)
+    if cell2vert.dim() != 2 or cell2vert.shape[1] != nv:
+        raise ValueError("cell2vert must be [ncells, %d]" % nv)
     n = ndof(form, degree, cell)
     odt = torch.float64 if precision == FP64 else torch.float32
     shape = (ncells, n) if form == BURGERS_RESIDUAL else (ncells, n, n)  # element vectors or matrices

@@ -67,7 +67,15 @@ int fp64_table(DeviceCache& c, int form, int degree, int cell, const double** T)
     return COFFEE_OK;
   }
   std::vector<double> h;
-  reference_tensor(form, degree, cell, h);
+  if (cell == CELL_PRISM) {
+    // per-point tensors, then the rule's points and weights (read by the prism kernel)
+    std::vector<double> pts, wts;
+    prism_tensor(form, degree, h, pts, wts);
+    h.insert(h.end(), pts.begin(), pts.end());
+    h.insert(h.end(), wts.begin(), wts.end());
+  } else {
+    reference_tensor(form, degree, cell, h);
+  }
   double* d = nullptr;
   cudaError_t e = cudaMalloc(&d, h.size() * sizeof(double));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(reference tensor)");
@@ -99,7 +107,7 @@ int tc_table(DeviceCache& c, int form, int degree, int cell, int prec, TcTable* 
 
 bool valid_fdc(int form, int degree, int cell) {
   return form >= FORM_MASS && form <= FORM_BURGERS_RES && degree >= 1 && degree <= 4 &&
-         (cell == CELL_TRI || cell == CELL_TET);
+         (cell == CELL_TRI || cell == CELL_TET || cell == CELL_PRISM);
 }
 
 int check_args(const coffee_assemble_args* a) {
@@ -133,9 +141,32 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
   DeviceCache* c = nullptr;
   if ((rc = device_cache(&c)) != COFFEE_OK) return rc;
   const int d = a->cell == CELL_TRI ? 2 : 3;
+  const bool validate = (a->flags & COFFEE_FLAG_VALIDATE) != 0;
+  if (a->cell == CELL_PRISM) {
+    if (!(a->form == FORM_MASS || a->form == FORM_HELMHOLTZ) || a->precision != PREC_FP64)
+      return fail(COFFEE_ERR_UNSUPPORTED, "prisms: MASS and HELMHOLTZ in FP64 only");
+    const double* T = nullptr;
+    if ((rc = fp64_table(*c, a->form, a->degree, a->cell, &T)) != COFFEE_OK) return rc;
+    const int n = prism_nnodes(a->degree);
+    PrismParams p{};
+    p.coords = a->coords;
+    p.c2v = a->cell2vert;
+    p.T = T;
+    p.out = a->out;
+    p.err = c->err;
+    p.ncells = a->ncells;
+    p.nverts = a->nverts;
+    p.Q = (a->degree + 2) * (a->degree + 2) * (a->degree + 2);
+    p.N = n * n;
+    p.validate = validate ? 1 : 0;
+    p.map = map;
+    p.nnz = nnz;
+    cudaError_t e = (cudaError_t)launch_prism(a->form, p, c->num_sms, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch(assemble_prism)");
+    return COFFEE_OK;
+  }
   const int ns = nnodes(a->cell, a->degree);
   const int ndof = burgers_like(a->form) ? d * ns : ns;
-  const bool validate = (a->flags & COFFEE_FLAG_VALIDATE) != 0;
   if (a->precision == PREC_FP64) {
     const double* T = nullptr;
     if ((rc = fp64_table(*c, a->form, a->degree, a->cell, &T)) != COFFEE_OK) return rc;
@@ -211,8 +242,9 @@ using namespace coffee;
 extern "C" {
 
 int coffee_ndof(int form, int degree, int cell) {
-  if (!(form >= 0 && form <= 4 && degree >= 1 && degree <= 6 && (cell == 0 || cell == 1)))
+  if (!(form >= 0 && form <= 4 && degree >= 1 && degree <= 6 && (cell == 0 || cell == 1 || cell == 2)))
     return fail(COFFEE_ERR_INVALID_ARG, "form/degree/cell out of range");
+  if (cell == CELL_PRISM) return burgers_like(form) ? 3 * prism_nnodes(degree) : prism_nnodes(degree);
   int ns = nnodes(cell, degree);
   return burgers_like(form) ? (cell == CELL_TRI ? 2 : 3) * ns : ns;
 }
@@ -248,6 +280,7 @@ int coffee_reference_tensor(int form, int degree, int cell, int* K, int* N, doub
 
 int coffee_supported(int form, int degree, int cell, int precision) {
   if (!valid_fdc(form, degree, cell) || precision < PREC_FP64 || precision > PREC_BF16X3) return 0;
+  if (cell == CELL_PRISM) return (form == FORM_MASS || form == FORM_HELMHOLTZ) && precision == PREC_FP64;
   if (precision == PREC_FP64) return 1;
   return tc_supported(form, degree, cell, precision);
 }
@@ -320,6 +353,7 @@ int coffee_csr_map(const int32_t* l2g, int64_t ncells, int nloc, const int64_t* 
 int coffee_csr_supported(int form, int degree, int cell, int precision) {
   if (!valid_fdc(form, degree, cell) || precision < PREC_FP64 || precision > PREC_BF16X3) return 0;
   if (form == FORM_BURGERS_RES) return 0;
+  if (cell == CELL_PRISM) return coffee_supported(form, degree, cell, precision);
   return precision == PREC_FP64 ? 1 : tc_csr_supported(form, degree, cell, precision);
 }
 
@@ -363,6 +397,7 @@ int coffee_assemble_backward(const coffee_assemble_args* a, const void* dout, do
   if (rc != COFFEE_OK || a->ncells == 0) return rc;
   if (burgers_like(a->form))
     return fail(COFFEE_ERR_UNSUPPORTED, "no GPU adjoint for the Burgers forms");
+  if (a->cell == CELL_PRISM) return fail(COFFEE_ERR_UNSUPPORTED, "no GPU adjoint on prisms");
   if (!dout || !d_coords) return fail(COFFEE_ERR_INVALID_ARG, "dout and d_coords must be non-NULL");
   if (deterministic && (a->nverts <= 0 || (a->form == FORM_ADVDIFF && d_coef && a->ncoefnodes <= 0)))
     return fail(COFFEE_ERR_INVALID_ARG, "deterministic mode needs nverts (and ncoefnodes)");
@@ -476,8 +511,8 @@ int coffee_batch_plan(const coffee_assemble_args* groups, int ngroups, int grid,
     int rc = check_args(&groups[i]);
     if (rc != COFFEE_OK) return rc;
     if (groups[i].precision != prec) return fail(COFFEE_ERR_INVALID_ARG, "all groups must share one precision");
-    if (burgers_like(groups[i].form))
-      return fail(COFFEE_ERR_UNSUPPORTED, "the mixed batch covers MASS, HELMHOLTZ and ADVDIFF");
+    if (burgers_like(groups[i].form) || groups[i].cell == CELL_PRISM)
+      return fail(COFFEE_ERR_UNSUPPORTED, "the mixed batch covers MASS, HELMHOLTZ and ADVDIFF on simplices");
   }
   if (item_overhead < 0) item_overhead = 16384.0;
   std::lock_guard<std::mutex> lock(g_mu);

@@ -12,7 +12,7 @@
 
 namespace coffee {
 
-enum { CELL_TRI = 0, CELL_TET = 1 };
+enum { CELL_TRI = 0, CELL_TET = 1, CELL_PRISM = 2 };
 enum { FORM_MASS = 0, FORM_HELMHOLTZ = 1, FORM_ADVDIFF = 2, FORM_BURGERS = 3, FORM_BURGERS_RES = 4 };
 // the Burgers residual (an element vector) uses the Burgers Jacobian's reference tensors
 inline int table_form(int form) { return form == FORM_BURGERS_RES ? FORM_BURGERS : form; }
@@ -35,6 +35,12 @@ void quadrature_rule(int cell, int degree, std::vector<double>& pts, std::vector
 void lagrange_basis(int cell, int k, int npts, const double* x, double* phi, double* grads);
 void reference_tensor(int form, int k, int cell, std::vector<double>& T);
 
+// prisms (tabulate.cpp): rule, basis, per-point reference tensors
+int prism_nnodes(int k);
+void prism_rule(int k, std::vector<double>& pts, std::vector<double>& wts);
+void prism_basis(int k, int npts, const double* x, double* phi, double* grads);
+void prism_tensor(int form, int k, std::vector<double>& T, std::vector<double>& pts, std::vector<double>& wts);
+
 // ---- error reporting (api.cu) ----
 int fail(int status, const std::string& msg);
 
@@ -56,6 +62,21 @@ struct Fp64Params {
 };
 // returns cudaError_t as int
 int launch_fp64(int form, int cell, const Fp64Params& p, void* stream);
+
+// ---- FP64 prism kernel (k_prism.cu) ----
+struct PrismParams {
+  const double* coords;  // [nverts][3]
+  const int32_t* c2v;    // [ncells][6]
+  const double* T;       // [Q*KQ][N] per-point tensors, then points [Q][3], then weights [Q]
+  void* out;             // double [ncells][N], or the CSR values when map is set
+  unsigned* err;
+  int64_t ncells, nverts;
+  int Q, N;
+  int validate;
+  const uint32_t* map;   // global assembly (blocked entry map), else NULL
+  int64_t nnz;
+};
+int launch_prism(int form, const PrismParams& p, int num_sms, void* stream);
 
 // ---- adjoint (k_bwd.cu) ----
 struct BwdParams {

@@ -254,3 +254,90 @@ void reference_tensor(int form, int k, int cell, std::vector<double>& T) {
 }
 
 }  // namespace coffee
+
+// ---------------------------------------------------------------------------------------
+// Prisms (the paper's third element shape, section 5.2): reference triangle x [0,1].
+// Degree-k space: triangle Lagrange functions (Silvester) times interval Lagrange functions
+// on the nodes c/k; dof (a,b,c) at (a/k, b/k, c/k), zeta level c slowest, triangle lattice
+// order inside a level. The prism map is not affine, so the quadrature is not pre-summed:
+// the reference tensors keep one block per quadrature point (see prism_tensor).
+// Rule: n = k+2 Gauss-Legendre points per direction on [0,1]; triangle points (s, t(1-s)),
+// weight w_s w_t (1-s); zeta = r, weight w_r.
+// ---------------------------------------------------------------------------------------
+namespace coffee {
+
+int prism_nnodes(int k) { return (k + 1) * (k + 2) / 2 * (k + 1); }
+
+void prism_rule(int k, std::vector<double>& pts, std::vector<double>& wts) {
+  const int n = k + 2;
+  std::vector<double> g, w;
+  gauss_jacobi01(n, 0, g, w);  // alpha = 0: Gauss-Legendre
+  pts.clear();
+  wts.clear();
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int l = 0; l < n; ++l) {
+        pts.push_back(g[i]);
+        pts.push_back(g[j] * (1.0 - g[i]));
+        pts.push_back(g[l]);
+        wts.push_back(w[i] * w[j] * (1.0 - g[i]) * w[l]);
+      }
+}
+
+void prism_basis(int k, int npts, const double* x, double* phi, double* grads) {
+  const int nt = (k + 1) * (k + 2) / 2, n = prism_nnodes(k);
+  std::vector<double> tp(nt), tg((size_t)nt * 2);
+  for (int p = 0; p < npts; ++p) {
+    const double* xp = x + (size_t)p * 3;
+    lagrange_basis(0, k, 1, xp, tp.data(), tg.data());
+    for (int c = 0; c <= k; ++c) {
+      // interval Lagrange function on the nodes m/k: prod_{m != c} (k z - m) / (c - m)
+      double L = 1.0, dL = 0.0;
+      for (int m = 0; m <= k; ++m) {
+        if (m == c) continue;
+        const double f = (k * xp[2] - m) / (double)(c - m), df = k / (double)(c - m);
+        dL = dL * f + L * df;
+        L *= f;
+      }
+      for (int t = 0; t < nt; ++t) {
+        const size_t i = (size_t)p * n + (size_t)c * nt + t;
+        if (phi) phi[i] = tp[t] * L;
+        if (grads) {
+          grads[i * 3 + 0] = tg[(size_t)t * 2 + 0] * L;
+          grads[i * 3 + 1] = tg[(size_t)t * 2 + 1] * L;
+          grads[i * 3 + 2] = tp[t] * dL;
+        }
+      }
+    }
+  }
+}
+
+// Per-point reference tensors of MASS (KQ = 1) and HELMHOLTZ (KQ = 7) on prisms:
+//   T[q*KQ + 0][i*n+j]     = phi_i(x_q) phi_j(x_q)
+//   T[q*KQ + 1 + p][i*n+j] = d_a phi_i d_b phi_j + [a!=b] d_b phi_i d_a phi_j   (p-th pair a<=b)
+// so that A_e = sum_q sum_kq G_e[q][kq] T[q*KQ+kq] with G_e[q] = w_q |det J(x_q)| (1, (K K^T)_ab).
+void prism_tensor(int form, int k, std::vector<double>& T, std::vector<double>& pts, std::vector<double>& wts) {
+  prism_rule(k, pts, wts);
+  const int Q = (int)wts.size(), n = prism_nnodes(k), N = n * n, KQ = form == FORM_HELMHOLTZ ? 7 : 1;
+  std::vector<double> phi((size_t)Q * n), g((size_t)Q * n * 3);
+  prism_basis(k, Q, pts.data(), phi.data(), g.data());
+  T.assign((size_t)Q * KQ * N, 0.0);
+  for (int q = 0; q < Q; ++q) {
+    const double* ph = &phi[(size_t)q * n];
+    const double* gr = &g[(size_t)q * n * 3];
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        T[((size_t)q * KQ) * N + (size_t)i * n + j] = ph[i] * ph[j];
+        if (KQ == 7)
+          for (int pp = 0; pp < 6; ++pp) {
+            int a, b;
+            pair_index(3, pp, a, b);
+            double v = gr[(size_t)i * 3 + a] * gr[(size_t)j * 3 + b];
+            if (a != b) v += gr[(size_t)i * 3 + b] * gr[(size_t)j * 3 + a];
+            T[((size_t)q * KQ + 1 + pp) * N + (size_t)i * n + j] = v;
+          }
+      }
+  }
+}
+
+}  // namespace coffee
