@@ -398,12 +398,31 @@ def run_ours(args):
     if cell == PRISM:
         # non-affine cells: the contraction over all quadrature points (K = 7 Q) dominates
         Q = (degree + 2) ** 3
-        flops = 2.0 * (Q * (7 if form == HELMHOLTZ else 1)) * ndof * ndof + 250.0 * Q
-        tf = flops * ncells / (launch_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 FMA probe (not in the measured-peaks file)", "flops_per_cell": flops,
-                "kernel_ms": launch_ms, "hbm_gbs": achieved}
+        K = Q * (7 if form == HELMHOLTZ else 1)
+        flops = 2.0 * K * ndof * ndof + 250.0 * Q  # algorithmic, per cell
+        if prec == coffee.FP64:
+            tf = flops * ncells / (launch_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "FP64 FMA probe (not in the measured-peaks file)", "flops_per_cell": flops,
+                    "kernel_ms": launch_ms, "hbm_gbs": achieved}
+        else:
+            # tensor pipe: executed MMA flops (K padded to the 64-byte chunk, outputs to 128-row
+            # slices, three passes for the split precisions) against the tf32/bf16 dense peak
+            tf32 = prec in (coffee.TF32, coffee.TF32X3)
+            kc = 16 if tf32 else 32
+            kpad = -(-K // kc) * kc
+            npad = -(-(ndof * ndof) // 128) * 128
+            passes = 3 if prec in (coffee.TF32X3, coffee.BF16X3) else 1
+            executed = 2.0 * kpad * npad * passes
+            bf16 = float(peaks.get("bf16_tflops", 1990.0))
+            peak_t = bf16 * (1.1 / 2.25) if tf32 else bf16
+            tf = executed * ncells / (launch_ms / 1e3) / 1e12
+            roof = {"bound": "tensor", "achieved": tf, "peak": peak_t, "unit": "TFLOP/s", "frac": tf / peak_t,
+                    "traffic": None, "peak_source": ("measured bf16 x nominal tf32/bf16 ratio 1.1/2.25" if tf32
+                                                     else "measured bf16"),
+                    "executed_flops_per_cell": executed, "algorithmic_flops_per_cell": flops,
+                    "kernel_ms": launch_ms, "hbm_gbs": achieved}
 
     fp64 = None
     if prec != coffee.FP64 and not args.no_fp64:

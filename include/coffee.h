@@ -67,7 +67,9 @@ typedef struct CUstream_st* coffee_stream_t;
  * degree-1 prism functions, so it is not affine and the element matrix is the quadrature sum
  * of a fixed rule: n = k+2 Gauss-Legendre points per direction on [0,1], the triangle factor
  * collapsed by (s,t) -> (s, t(1-s)) with weight w_s w_t (1-s). Prisms support MASS and
- * HELMHOLTZ in FP64 (coffee_assemble_ex, coffee_assemble_csr). */
+ * HELMHOLTZ: FP64 for P1-P4 (coffee_assemble_ex, coffee_assemble_csr) and the tensor-core
+ * precisions for P1-P2 (coffee_assemble_ex; the contraction over all quadrature points is
+ * streamed through shared memory in K-chunks). */
 typedef enum { COFFEE_TRIANGLE = 0, COFFEE_TETRAHEDRON = 1, COFFEE_PRISM = 2 } coffee_cell;
 
 typedef enum {

@@ -77,6 +77,10 @@ struct PrismParams {
   int64_t nnz;
 };
 int launch_prism(int form, const PrismParams& p, int num_sms, void* stream);
+// tensor-core prisms (k_prism_tc.cu): K-chunked streamed contraction, MASS/HELMHOLTZ P1-P2
+struct TcParams;
+struct TcTable;
+int prism_tc_supported(int form, int degree, int precision);
 
 // ---- adjoint (k_bwd.cu) ----
 struct BwdParams {
@@ -136,6 +140,7 @@ struct TcParams {
   double nu;
   const uint32_t* map;   // global assembly: CSR position of every entry (blocked, csr_map_index); out = CSR values
   int64_t nnz;           // length of the CSR value array when map is set
+  int nkc;               // prisms: K-chunks of the streamed contraction
 };
 int tc_supported(int form, int degree, int cell, int precision);
 int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
@@ -183,6 +188,8 @@ int launch_sparsity(const int32_t* l2g, int64_t ncells, int nloc, int64_t nrows,
 int launch_csr_map(const int32_t* l2g, int64_t ncells, int nloc, const int64_t* rowptr, const int32_t* colidx,
                    int64_t nrows, uint32_t* map, unsigned* err, int num_sms, void* stream);
 int tc_csr_supported(int form, int degree, int cell, int precision);
+void build_prism_tc_image(int form, int degree, int prec, std::vector<uint8_t>& img, TcTable& meta);
+int launch_prism_tc(int form, int degree, const TcParams& p, int num_sms, void* stream, std::string& why);
 int launch_tc_csr(int form, int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
 
 // Build the operand image on the host

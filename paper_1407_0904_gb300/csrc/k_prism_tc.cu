@@ -1,0 +1,455 @@
+// tcgen05 local assembly on prisms (the paper's third element shape, section 5.2).
+//
+// A prism's map is not affine, so the Jacobian is evaluated at every quadrature point and the
+// element matrix is a quadrature sum: A_e[o] = sum_{q,f} G_e[q][f] T[q*KQ+f][o] with
+// G_e[q] = w_q |det J_q| (1, (K_q K_q^T)_ab), KQ = 1 (mass) or 7 (Helmholtz). The contraction
+// over K = Q*KQ (189 at P1, 448 at P2) is too deep to keep either operand resident, so both are
+// streamed through shared memory in K-chunks of 64 bytes per row (16 tf32 / 32 bf16 columns):
+//   loader warp 8       one bulk copy per chunk of T^T (all 128-output slices, hi and lo),
+//                       completion counted on the stage's mbarrier (transaction bytes);
+//   producer warps 4-7  one cell per thread: the chunk's columns of G_e, geometry evaluated per
+//                       point in FP32 as the columns are formed, split into the B operand;
+//   MMA warp 12         per chunk and slice, tcgen05.mma accumulating in TMEM (D[o][cell]);
+//   epilogue warps 0-3  one 128-output slice at a time: TMEM -> 128-byte warp stores.
+// Every wait is bounded; on expiry the kernel sets the error word and unwinds.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstring>
+#include <cmath>
+#include "coffee_internal.h"
+#include "tc_common.cuh"
+
+namespace coffee {
+namespace {
+using namespace tc;
+
+constexpr int PCB = 64;          // bytes per operand row in one K-chunk (two MMA K-steps)
+constexpr int PROD0 = 4;         // producer warps 4..7
+constexpr int LOADER = 8;        // loader warp
+constexpr int PMAX_STAGES = 6;
+
+struct alignas(8) PBars {
+  uint64_t full[PMAX_STAGES];
+  uint64_t empty[PMAX_STAGES];
+  uint64_t tfull[RING];
+  uint64_t tempty[RING];
+  uint64_t done;
+  uint32_t tmem_base;
+};
+
+__device__ __forceinline__ void prism_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void prism_bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// p.N outputs, p.mtiles slices, p.nkc chunks, p.ksteps_off = KQ, p.ns = Q; the image holds the
+// chunks of T^T ([chunk][slice][part][128 rows x 64 B]) followed by the points (s,t,z,w) [Q][4].
+template <int PREC>
+__global__ void __launch_bounds__(NTHREADS, 1) k_assemble_prism_tc(const TcParams p, int nstages) {
+  using PT = PrecTraits<PREC>;
+  constexpr int PARTS = PT::split ? 2 : 1;
+  constexpr int KC = PT::tf32 ? 16 : 32;  // K columns per chunk
+  constexpr int TB = BM * PCB;            // bytes of one 128-row part of one chunk
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int MT = p.mtiles, NKC = p.nkc, KQ = p.ksteps_off, Q = p.ns, N = p.N;
+  const int a_chunk = MT * PARTS * TB;          // T^T part of a stage
+  const int stage_bytes = a_chunk + PARTS * TB;  // + the G part
+  PBars* bars = reinterpret_cast<PBars*>(smem + nstages * stage_bytes);
+  const float4* qpts = reinterpret_cast<const float4*>(p.image + (size_t)NKC * a_chunk);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (p.ncells + BN - 1) / BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      mbar_init(smem_u32(&bars->full[s]), 128 + 1);  // producers + the loader's arrival
+      mbar_init(smem_u32(&bars->empty[s]), 1);
+    }
+    for (int r = 0; r < RING; ++r) {
+      mbar_init(smem_u32(&bars->tfull[r]), 1);
+      mbar_init(smem_u32(&bars->tempty[r]), EPI_WARPS);
+    }
+    mbar_init(smem_u32(&bars->done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&bars->tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+
+  if (warp >= PROD0 && warp < LOADER) {
+    // ---------------- producers: the G columns of every chunk, one cell per thread ----------------
+    const int row = ((warp - PROD0) << 5) + lane;
+    uint32_t c = 0;  // chunk counter (all tiles)
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int64_t e = t * BN + row;
+      bool live = e < p.ncells;
+      // vertex positions relative to vertex 0, differenced in FP64 before rounding to FP32: the
+      // Jacobian only sees differences (sum_v dN_v = 0), which keep their relative accuracy
+      float X[6][3];
+      if (live) {
+        bool bad = false;
+        double X0[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int v = 0; v < 6; ++v) {
+          int vid = __ldg(p.c2v + e * 6 + v);
+          if (p.validate && (vid < 0 || vid >= p.nverts)) {
+            bad = true;
+            vid = 0;
+          }
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const double x = __ldg(p.coords + (int64_t)vid * 3 + r);
+            if (v == 0) X0[r] = x;
+            X[v][r] = (float)(x - X0[r]);
+          }
+        }
+        if (bad) {
+          atomicOr(p.err, ERR_INDEX);
+          live = false;
+        }
+      }
+      int gq = -1;      // point whose factors are cached
+      float gf[7] = {};  // w |det| (1, K K^T pairs) at point gq
+      for (int kc = 0; kc < NKC; ++kc, ++c) {
+        const int s = (int)(c % nstages);
+        if (!mbar_wait(smem_u32(&bars->empty[s]), ((c / nstages) & 1u) ^ 1u, p.err)) { ok = false; break; }
+        auto factor = [&](int kcol) -> float {
+          const int k = kc * KC + kcol;
+          const int q = k / KQ, f = k - (k / KQ) * KQ;
+          if (!live || q >= Q) return 0.f;
+          if (q != gq) {
+            gq = q;
+            const float4 pt = __ldg(qpts + q);  // (s, t, z, w)
+            const float lam[3] = {1.f - pt.x - pt.y, pt.x, pt.y};
+            const float dls[3] = {-1.f, 1.f, 0.f}, dlt[3] = {-1.f, 0.f, 1.f};
+            float J[3][3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              float js = 0.f, jt = 0.f, jz = 0.f;
+#pragma unroll
+              for (int v = 0; v < 3; ++v) {
+                const float mid = (1.f - pt.z) * X[v][r] + pt.z * X[v + 3][r];
+                js = fmaf(dls[v], mid, js);
+                jt = fmaf(dlt[v], mid, jt);
+                jz = fmaf(lam[v], X[v + 3][r] - X[v][r], jz);
+              }
+              J[r][0] = js;
+              J[r][1] = jt;
+              J[r][2] = jz;
+            }
+            const float adj[3][3] = {{J[1][1] * J[2][2] - J[1][2] * J[2][1], J[0][2] * J[2][1] - J[0][1] * J[2][2],
+                                      J[0][1] * J[1][2] - J[0][2] * J[1][1]},
+                                     {J[1][2] * J[2][0] - J[1][0] * J[2][2], J[0][0] * J[2][2] - J[0][2] * J[2][0],
+                                      J[0][2] * J[1][0] - J[0][0] * J[1][2]},
+                                     {J[1][0] * J[2][1] - J[1][1] * J[2][0], J[0][1] * J[2][0] - J[0][0] * J[2][1],
+                                      J[0][0] * J[1][1] - J[0][1] * J[1][0]}};
+            const float adet = fabsf(J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0]);
+            gf[0] = pt.w * adet;
+            int pp = 1;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+              for (int b = a; b < 3; ++b) {
+                float acc = 0.f;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) acc = fmaf(adj[a][r], adj[b][r], acc);
+                gf[pp++] = pt.w * acc / adet;
+              }
+          }
+          float v = gf[0];
+#pragma unroll
+          for (int i = 1; i < 7; ++i)
+            if (f == i) v = gf[i];
+          return v;
+        };
+        uint8_t* b = smem + (size_t)s * stage_bytes + a_chunk;  // G part of the stage
+        if constexpr (PT::tf32) {
+#pragma unroll
+          for (int cc = 0; cc < KC / 4; ++cc) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+              const float x = factor(cc * 4 + qq);
+              h[qq] = tf32_rna(x);
+              l[qq] = tf32_rna(x - __uint_as_float(h[qq]));
+            }
+            const uint32_t off = canon_off(row, cc * 16, PCB);
+            *reinterpret_cast<uint4*>(b + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            if constexpr (PT::split) *reinterpret_cast<uint4*>(b + TB + off) = make_uint4(l[0], l[1], l[2], l[3]);
+          }
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < KC / 8; ++cc) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+              const float x0 = factor(cc * 8 + 2 * qq), x1 = factor(cc * 8 + 2 * qq + 1);
+              const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+              const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+              const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+              h[qq] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+              l[qq] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            const uint32_t off = canon_off(row, cc * 16, PCB);
+            *reinterpret_cast<uint4*>(b + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            if constexpr (PT::split) *reinterpret_cast<uint4*>(b + TB + off) = make_uint4(l[0], l[1], l[2], l[3]);
+          }
+        }
+        fence_proxy_async();
+        mbar_arrive(smem_u32(&bars->full[s]));
+      }
+    }
+  } else if (warp == LOADER) {
+    // ---------------- loader: one bulk copy of T^T per chunk ----------------
+    if (lane == 0) {
+      uint32_t c = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+        for (int kc = 0; kc < NKC; ++kc, ++c) {
+          const int s = (int)(c % nstages);
+          if (!mbar_wait(smem_u32(&bars->empty[s]), ((c / nstages) & 1u) ^ 1u, p.err)) { ok = false; break; }
+          const uint32_t bar = smem_u32(&bars->full[s]);
+          prism_expect_tx(bar, (uint32_t)a_chunk);
+          prism_bulk_g2s(smem_u32(smem + (size_t)s * stage_bytes), p.image + (size_t)kc * a_chunk, (uint32_t)a_chunk,
+                         bar);
+        }
+      // every issued copy is consumed by the MMA warp's wait on its stage (or the kernel timed out)
+    }
+    __syncwarp();
+  } else if (warp == MMA_WARP) {
+    // ---------------- MMA issuer: D[o][cell] += T^T[o][k] G[cell][k], chunk by chunk ----------------
+    if (lane == 0) {
+      const uint32_t sbo = 8u * PCB;
+      const uint32_t idesc = make_idesc(PT::tf32 ? 2 : 1, BM, BN);
+      const uint32_t s0 = smem_u32(smem);
+      uint32_t c = 0, rc = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, rc += MT) {
+        for (int m = 0; m < MT && ok; ++m) {
+          const uint32_t r = rc + m;
+          if (!mbar_wait(smem_u32(&bars->tempty[r % RING]), ((r / RING) & 1u) ^ 1u, p.err)) ok = false;
+        }
+        if (!ok) break;
+        tc_fence_after();
+        for (int kc = 0; kc < NKC; ++kc, ++c) {
+          const int s = (int)(c % nstages);
+          if (!mbar_wait(smem_u32(&bars->full[s]), (c / nstages) & 1u, p.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t st = s0 + (uint32_t)(s * stage_bytes);
+          const uint32_t g = st + (uint32_t)a_chunk;
+          for (int m = 0; m < MT; ++m) {
+            const uint32_t d = tmem + ((rc + m) % RING) * BN;
+            const uint32_t a = st + (uint32_t)(m * PARTS * TB);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              const uint32_t ko = (uint32_t)ks * 256u;
+              uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+              if constexpr (PT::split) {
+                mma<PT::tf32>(d, make_desc(a + ko, sbo), make_desc(g + TB + ko, sbo), idesc, acc);
+                acc = 1;
+                mma<PT::tf32>(d, make_desc(a + TB + ko, sbo), make_desc(g + ko, sbo), idesc, 1);
+              }
+              mma<PT::tf32>(d, make_desc(a + ko, sbo), make_desc(g + ko, sbo), idesc, acc);
+            }
+          }
+          tc_commit(smem_u32(&bars->empty[s]));
+        }
+        if (!ok) break;
+        for (int m = 0; m < MT; ++m) tc_commit(smem_u32(&bars->tfull[(rc + m) % RING]));
+      }
+      tc_commit(smem_u32(&bars->done));
+      mbar_wait(smem_u32(&bars->done), 0, p.err);
+    }
+    __syncwarp();
+  } else if (warp < EPI_WARPS) {
+    // ---------------- epilogue: 128-byte warp stores of 32 outputs of one cell ----------------
+    const int q = warp;
+    uint32_t rc = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+      for (int m = 0; m < MT; ++m, ++rc) {
+        const uint32_t slot = rc % RING;
+        if (!mbar_wait(smem_u32(&bars->tfull[slot]), (rc / RING) & 1u, p.err)) { ok = false; break; }
+        tc_fence_after();
+        const int o = m * BM + q * 32 + lane;
+        for (int cc = 0; cc < BN; cc += 64) {
+          const int64_t cbase = t * BN + cc;
+          const int64_t rem = p.ncells - cbase;
+          const int ncol = rem <= 0 ? 0 : (rem < 64 ? (int)rem : 64);
+          if (m * BM + q * 32 < N && ncol > 0) {  // warp-uniform
+            uint32_t v0[32], v1[32];
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + slot * BN + cc;
+            tmem_ld32(taddr, v0);
+            tmem_ld32(taddr + 32, v1);
+            tmem_wait_ld();
+            if (o < N) {
+              float* dst = p.out + cbase * N + o;
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj)
+                if (jj < ncol) __stcs(dst + (int64_t)jj * N, __uint_as_float(v0[jj]));
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj)
+                if (32 + jj < ncol) __stcs(dst + (int64_t)(32 + jj) * N, __uint_as_float(v1[jj]));
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
+      }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+struct PGeom {
+  int n, N, mtiles, KQ, Q, K, nkc, parts, kc, elem, a_chunk, stage;
+};
+
+bool pgeom(int form, int degree, int prec, PGeom& g) {
+  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ) || degree < 1 || degree > 2) return false;
+  if (prec == PREC_FP64 || prec < 0 || prec > PREC_BF16X3) return false;
+  const bool tf32 = prec == PREC_TF32 || prec == PREC_TF32X3;
+  g.n = prism_nnodes(degree);
+  g.N = g.n * g.n;
+  g.mtiles = (g.N + BM - 1) / BM;
+  g.KQ = form == FORM_HELMHOLTZ ? 7 : 1;
+  g.Q = (degree + 2) * (degree + 2) * (degree + 2);
+  g.K = g.Q * g.KQ;
+  g.elem = tf32 ? 4 : 2;
+  g.kc = PCB / g.elem;
+  g.nkc = (g.K + g.kc - 1) / g.kc;
+  g.parts = (prec == PREC_TF32X3 || prec == PREC_BF16X3) ? 2 : 1;
+  g.a_chunk = g.mtiles * g.parts * BM * PCB;
+  g.stage = g.a_chunk + g.parts * BM * PCB;
+  return g.mtiles <= 3;
+}
+
+constexpr int P_SMEM_LIMIT = 227 * 1024;
+
+int pstages(const PGeom& g) {
+  const int fixed = (int)sizeof(PBars) + 1024 + 64;
+  int s = PMAX_STAGES;
+  while (s >= 2 && fixed + s * g.stage > P_SMEM_LIMIT) --s;
+  return s >= 2 ? s : 0;
+}
+
+template <int PREC>
+cudaError_t launch_p(const TcParams& p, int num_sms, cudaStream_t s, int nst, int smem) {
+  auto kern = k_assemble_prism_tc<PREC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (p.ncells + BN - 1) / BN;
+  const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
+  kern<<<grid, NTHREADS, smem, s>>>(p, nst);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int prism_tc_supported(int form, int degree, int precision) {
+  PGeom g;
+  return pgeom(form, degree, precision, g) && pstages(g) > 0 ? 1 : 0;
+}
+
+// T^T chunks [chunk][slice][part][128 rows x 64 B canonical], then the points (s,t,z,w) [Q]
+void build_prism_tc_image(int form, int degree, int prec, std::vector<uint8_t>& img, TcTable& meta) {
+  PGeom g;
+  pgeom(form, degree, prec, g);
+  std::vector<double> T, pts, wts;
+  prism_tensor(form, degree, T, pts, wts);
+  const bool tf32 = g.elem == 4;
+  const size_t tb = (size_t)BM * PCB;
+  img.assign((size_t)g.nkc * g.a_chunk + (size_t)g.Q * 16, 0);
+  for (int kc = 0; kc < g.nkc; ++kc)
+    for (int m = 0; m < g.mtiles; ++m)
+      for (int r = 0; r < BM; ++r) {
+        const int o = m * BM + r;
+        for (int j = 0; j < g.kc; ++j) {
+          const int k = kc * g.kc + j;
+          const double x = (o < g.N && k < g.K) ? T[(size_t)k * g.N + o] : 0.0;
+          const uint32_t off = canon_off(r, j * g.elem, PCB);
+          uint8_t* hi = img.data() + (size_t)kc * g.a_chunk + (size_t)(m * g.parts) * tb;
+          uint8_t* lo = hi + tb;
+          if (tf32) {
+            const uint32_t h = host_tf32_rna((float)x);
+            const uint32_t l = host_tf32_rna((float)(x - (double)host_f(h)));
+            std::memcpy(hi + off, &h, 4);
+            if (g.parts == 2) std::memcpy(lo + off, &l, 4);
+          } else {
+            const uint16_t h = host_bf16_rn((float)x);
+            const uint16_t l = host_bf16_rn((float)(x - (double)host_bf16_f(h)));
+            std::memcpy(hi + off, &h, 2);
+            if (g.parts == 2) std::memcpy(lo + off, &l, 2);
+          }
+        }
+      }
+  float* qp = reinterpret_cast<float*>(img.data() + (size_t)g.nkc * g.a_chunk);
+  for (int q = 0; q < g.Q; ++q) {
+    qp[q * 4 + 0] = (float)pts[(size_t)q * 3 + 0];
+    qp[q * 4 + 1] = (float)pts[(size_t)q * 3 + 1];
+    qp[q * 4 + 2] = (float)pts[(size_t)q * 3 + 2];
+    qp[q * 4 + 3] = (float)wts[q];
+  }
+  meta = TcTable{};
+  meta.mtiles = g.mtiles;
+  meta.kbytes = PCB;
+  meta.kelems = g.nkc * g.kc;
+  meta.K = g.K;
+  meta.parts = g.parts;
+  meta.ksteps_off = g.KQ;
+  meta.tile_bytes = (int64_t)tb;
+}
+
+int launch_prism_tc(int form, int degree, const TcParams& p, int num_sms, void* stream, std::string& why) {
+  if (p.ncells == 0) return (int)cudaSuccess;
+  PGeom g;
+  if (!pgeom(form, degree, p.precision, g)) {
+    why = "no tensor-core prism kernel for this form/degree";
+    return (int)cudaErrorInvalidValue;
+  }
+  const int nst = pstages(g);
+  if (nst == 0) {
+    why = "operands do not fit in shared memory";
+    return (int)cudaErrorInvalidValue;
+  }
+  TcParams q = p;
+  q.mtiles = g.mtiles;
+  q.nkc = g.nkc;
+  q.ksteps_off = g.KQ;
+  q.ns = g.Q;
+  q.N = g.N;
+  int smem = nst * g.stage + (int)sizeof(PBars) + 1024 + 64;
+  if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA (one TMEM owner) per SM
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (p.precision) {
+    case PREC_TF32: return (int)launch_p<PREC_TF32>(q, num_sms, s, nst, smem);
+    case PREC_TF32X3: return (int)launch_p<PREC_TF32X3>(q, num_sms, s, nst, smem);
+    case PREC_BF16: return (int)launch_p<PREC_BF16>(q, num_sms, s, nst, smem);
+    case PREC_BF16X3: return (int)launch_p<PREC_BF16X3>(q, num_sms, s, nst, smem);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace coffee

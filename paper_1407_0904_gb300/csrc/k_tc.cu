@@ -79,6 +79,10 @@ int tc_supported(int form, int degree, int cell, int precision) {
 }
 
 void build_tc_image(int form, int degree, int cell, int prec, std::vector<uint8_t>& img, TcTable& meta) {
+  if (cell == CELL_PRISM) {
+    build_prism_tc_image(form, degree, prec, img, meta);
+    return;
+  }
   if (form == FORM_BURGERS) {
     build_burgers_image(degree, cell, prec, img, meta);
     return;

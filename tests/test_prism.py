@@ -55,8 +55,8 @@ def test_prism_global_assembly_fp64(k):
 def test_prism_errors():
     mesh = meshgen.prism_mesh(3, 2, seed=1)
     x, c2v = to_dev(mesh)
-    with pytest.raises(coffee.CoffeeError):  # no tensor-core prisms
-        coffee.assemble(HELMHOLTZ, 1, PRISM, x, c2v, precision=coffee.TF32X3)
+    with pytest.raises(coffee.CoffeeError):  # tensor-core prisms stop at P2
+        coffee.assemble(HELMHOLTZ, 3, PRISM, x, c2v, precision=coffee.TF32X3)
     with pytest.raises(coffee.CoffeeError):  # prisms cover MASS and HELMHOLTZ
         coffee.assemble(coffee.ADVDIFF, 1, PRISM, x, c2v, torch.zeros(64, dtype=torch.float64, device=DEV),
                         c2v[:, :4].contiguous(), precision=coffee.FP64)
@@ -67,3 +67,36 @@ def test_prism_errors():
         coffee.check_errors()
     empty = coffee.assemble(MASS, 2, PRISM, x, c2v[:0].contiguous(), precision=coffee.FP64)
     assert empty.shape == (0, 18, 18)
+
+
+TC_TOL = {coffee.TF32X3: 1e-5, coffee.BF16X3: 1e-4, coffee.TF32: 1e-2, coffee.BF16: 2e-2}
+
+
+@pytest.mark.parametrize("form", [MASS, HELMHOLTZ])
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("prec", [coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16])
+def test_prism_tensor_cores_match_oracle(form, k, prec):
+    """K-chunked streamed contraction on the tensor cores (972 cells: 7 tiles + a ragged one)."""
+    mesh = meshgen.prism_mesh(9, 6, perturb=0.15, seed=30 + k)
+    ref = oracle.prism_assemble(form, k, mesh.coords, mesh.cell2vert)
+    x, c2v = to_dev(mesh)
+    out = coffee.assemble(form, k, PRISM, x, c2v, precision=prec, validate=True)
+    coffee.check_errors()
+    assert out.dtype == torch.float32 and out.shape == ref.shape
+    err = rel_err_per_cell(out.cpu().numpy(), ref)
+    print("prism TC %s P%d %s: %.3e" % (coffee.FORM_NAMES[form], k, coffee.PRECISION_NAMES[prec], err))
+    assert err < TC_TOL[prec]
+
+
+def test_prism_tc_full_size_sampled():
+    """The benchmark's 221,184 twisted P2 prisms (48 x 48 x 2 x 48, seed 6), TF32X3: 512 sampled
+    cells against the oracle."""
+    mesh = meshgen.prism_mesh(48, 48, perturb=0.15, seed=6)
+    x, c2v = to_dev(mesh)
+    out = coffee.assemble(HELMHOLTZ, 2, PRISM, x, c2v, precision=coffee.TF32X3)
+    coffee.check_errors()
+    sel = np.sort(np.random.default_rng(6).choice(mesh.ncells, 512, replace=False))
+    ref = oracle.prism_assemble(HELMHOLTZ, 2, mesh.coords, mesh.cell2vert[sel])
+    err = rel_err_per_cell(out[torch.from_numpy(sel).to(DEV)].cpu().numpy(), ref)
+    print("prism TC full size: %.3e" % err)
+    assert err < TC_TOL[coffee.TF32X3]
