@@ -5,10 +5,11 @@
 // G_e[q] = w_q |det J_q| (1, (K_q K_q^T)_ab), KQ = 1 (mass) or 7 (Helmholtz). The contraction
 // over K = Q*KQ (189 at P1, 448 at P2) is too deep to keep either operand resident, so both are
 // streamed through shared memory in K-chunks of 64 bytes per row (16 tf32 / 32 bf16 columns):
-//   loader warp 8       one bulk copy per chunk of T^T (all 128-output slices, hi and lo),
+//   loader warp 13      one bulk copy per chunk of T^T (all 128-output slices, hi and lo),
 //                       completion counted on the stage's mbarrier (transaction bytes);
-//   producer warps 4-7  one cell per thread: the chunk's columns of G_e, geometry evaluated per
-//                       point in FP32 as the columns are formed, split into the B operand;
+//   producer warps 4-11 two threads per cell, each forming half of the chunk's columns of G_e
+//                       (geometry per point in FP32, J from per-cell bilinear coefficients),
+//                       split into the B operand;
 //   MMA warp 12         per chunk and slice, tcgen05.mma accumulating in TMEM (D[o][cell]);
 //   epilogue warps 0-3  one 128-output slice at a time: TMEM -> 128-byte warp stores.
 // Every wait is bounded; on expiry the kernel sets the error word and unwinds.
@@ -25,8 +26,10 @@ namespace {
 using namespace tc;
 
 constexpr int PCB = 64;          // bytes per operand row in one K-chunk (two MMA K-steps)
-constexpr int PROD0 = 4;         // producer warps 4..7
-constexpr int LOADER = 8;        // loader warp
+constexpr int PROD0 = 4;         // producer warps 4..11
+constexpr int NPROD = 256;       // producer threads: two per cell
+constexpr int LOADER = 13;       // loader warp
+constexpr int PTHREADS = 14 * 32;
 constexpr int PMAX_STAGES = 6;
 
 struct alignas(8) PBars {
@@ -37,6 +40,7 @@ struct alignas(8) PBars {
   uint64_t done;
   uint32_t tmem_base;
 };
+static_assert(sizeof(PBars) <= 256, "the point table follows the barriers at +256 bytes");
 
 __device__ __forceinline__ void prism_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -50,7 +54,7 @@ __device__ __forceinline__ void prism_bulk_g2s(uint32_t dst, const void* src, ui
 // p.N outputs, p.mtiles slices, p.nkc chunks, p.ksteps_off = KQ, p.ns = Q; the image holds the
 // chunks of T^T ([chunk][slice][part][128 rows x 64 B]) followed by the points (s,t,z,w) [Q][4].
 template <int PREC>
-__global__ void __launch_bounds__(NTHREADS, 1) k_assemble_prism_tc(const TcParams p, int nstages) {
+__global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParams p, int nstages) {
   using PT = PrecTraits<PREC>;
   constexpr int PARTS = PT::split ? 2 : 1;
   constexpr int KC = PT::tf32 ? 16 : 32;  // K columns per chunk
@@ -61,14 +65,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_prism_tc(const TcParam
   const int a_chunk = MT * PARTS * TB;          // T^T part of a stage
   const int stage_bytes = a_chunk + PARTS * TB;  // + the G part
   PBars* bars = reinterpret_cast<PBars*>(smem + nstages * stage_bytes);
-  const float4* qpts = reinterpret_cast<const float4*>(p.image + (size_t)NKC * a_chunk);
+  float4* qsm = reinterpret_cast<float4*>(reinterpret_cast<uint8_t*>(bars) + 256);  // points (s,t,z,w) [Q]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (p.ncells + BN - 1) / BN;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < nstages; ++s) {
-      mbar_init(smem_u32(&bars->full[s]), 128 + 1);  // producers + the loader's arrival
+      mbar_init(smem_u32(&bars->full[s]), NPROD + 1);  // producers + the loader's arrival
       mbar_init(smem_u32(&bars->empty[s]), 1);
     }
     for (int r = 0; r < RING; ++r) {
@@ -85,25 +89,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_prism_tc(const TcParam
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  {
+    const float4* qg = reinterpret_cast<const float4*>(p.image + (size_t)NKC * a_chunk);
+    for (int i = threadIdx.x; i < Q; i += PTHREADS) qsm[i] = __ldg(qg + i);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
 
-  if (warp >= PROD0 && warp < LOADER) {
-    // ---------------- producers: the G columns of every chunk, one cell per thread ----------------
-    const int row = ((warp - PROD0) << 5) + lane;
+  if (warp >= PROD0 && warp < MMA_WARP) {
+    // ---------------- producers: the G columns of every chunk, two threads per cell ----------------
+    const int pt_id = threadIdx.x - PROD0 * 32;
+    const int row = pt_id & (BN - 1), half = pt_id >> 7;  // cell of the tile, half of the chunk
     uint32_t c = 0;  // chunk counter (all tiles)
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const int64_t e = t * BN + row;
       bool live = e < p.ncells;
-      // vertex positions relative to vertex 0, differenced in FP64 before rounding to FP32: the
-      // Jacobian only sees differences (sum_v dN_v = 0), which keep their relative accuracy
-      float X[6][3];
+      // J(s,t,z) is bilinear: columns d/ds = A + z B, d/dt = C + z D, d/dz = E + s F + t G with
+      // vertex differences taken in FP64 before rounding to FP32
+      float JA[3], JB[3], JC[3], JD[3], JE[3], JF[3], JG[3];
       if (live) {
         bool bad = false;
-        double X0[3] = {0.0, 0.0, 0.0};
+        double Xd[6][3];
 #pragma unroll
         for (int v = 0; v < 6; ++v) {
           int vid = __ldg(p.c2v + e * 6 + v);
@@ -112,15 +121,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_prism_tc(const TcParam
             vid = 0;
           }
 #pragma unroll
-          for (int r = 0; r < 3; ++r) {
-            const double x = __ldg(p.coords + (int64_t)vid * 3 + r);
-            if (v == 0) X0[r] = x;
-            X[v][r] = (float)(x - X0[r]);
-          }
+          for (int r = 0; r < 3; ++r) Xd[v][r] = __ldg(p.coords + (int64_t)vid * 3 + r);
         }
         if (bad) {
-          atomicOr(p.err, ERR_INDEX);
+          if (half == 0) atomicOr(p.err, ERR_INDEX);
           live = false;
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const double b1 = Xd[1][r] - Xd[0][r], b2 = Xd[2][r] - Xd[0][r];  // bottom edges
+          const double t1 = Xd[4][r] - Xd[3][r], t2 = Xd[5][r] - Xd[3][r];  // top edges
+          const double h0 = Xd[3][r] - Xd[0][r], h1 = Xd[4][r] - Xd[1][r], h2 = Xd[5][r] - Xd[2][r];
+          JA[r] = (float)b1;
+          JB[r] = (float)(t1 - b1);
+          JC[r] = (float)b2;
+          JD[r] = (float)(t2 - b2);
+          JE[r] = (float)h0;
+          JF[r] = (float)(h1 - h0);
+          JG[r] = (float)(h2 - h0);
         }
       }
       int gq = -1;      // point whose factors are cached
@@ -134,23 +152,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_prism_tc(const TcParam
           if (!live || q >= Q) return 0.f;
           if (q != gq) {
             gq = q;
-            const float4 pt = __ldg(qpts + q);  // (s, t, z, w)
-            const float lam[3] = {1.f - pt.x - pt.y, pt.x, pt.y};
-            const float dls[3] = {-1.f, 1.f, 0.f}, dlt[3] = {-1.f, 0.f, 1.f};
+            const float4 pq = qsm[q];  // (s, t, z, w)
             float J[3][3];
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-              float js = 0.f, jt = 0.f, jz = 0.f;
-#pragma unroll
-              for (int v = 0; v < 3; ++v) {
-                const float mid = (1.f - pt.z) * X[v][r] + pt.z * X[v + 3][r];
-                js = fmaf(dls[v], mid, js);
-                jt = fmaf(dlt[v], mid, jt);
-                jz = fmaf(lam[v], X[v + 3][r] - X[v][r], jz);
-              }
-              J[r][0] = js;
-              J[r][1] = jt;
-              J[r][2] = jz;
+              J[r][0] = fmaf(pq.z, JB[r], JA[r]);
+              J[r][1] = fmaf(pq.z, JD[r], JC[r]);
+              J[r][2] = fmaf(pq.x, JF[r], fmaf(pq.y, JG[r], JE[r]));
             }
             const float adj[3][3] = {{J[1][1] * J[2][2] - J[1][2] * J[2][1], J[0][2] * J[2][1] - J[0][1] * J[2][2],
                                       J[0][1] * J[1][2] - J[0][2] * J[1][1]},
@@ -159,7 +167,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_prism_tc(const TcParam
                                      {J[1][0] * J[2][1] - J[1][1] * J[2][0], J[0][1] * J[2][0] - J[0][0] * J[2][1],
                                       J[0][0] * J[1][1] - J[0][1] * J[1][0]}};
             const float adet = fabsf(J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0]);
-            gf[0] = pt.w * adet;
+            gf[0] = pq.w * adet;
+            const float wi = pq.w / adet;
             int pp = 1;
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -168,7 +177,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_prism_tc(const TcParam
                 float acc = 0.f;
 #pragma unroll
                 for (int r = 0; r < 3; ++r) acc = fmaf(adj[a][r], adj[b][r], acc);
-                gf[pp++] = pt.w * acc / adet;
+                gf[pp++] = wi * acc;
               }
           }
           float v = gf[0];
@@ -178,34 +187,37 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_prism_tc(const TcParam
           return v;
         };
         uint8_t* b = smem + (size_t)s * stage_bytes + a_chunk;  // G part of the stage
+        // this thread's half of the chunk: 32 bytes of the row (two 16-byte stores per part)
         if constexpr (PT::tf32) {
 #pragma unroll
-          for (int cc = 0; cc < KC / 4; ++cc) {
+          for (int cc = 0; cc < 2; ++cc) {
+            const int c16 = half * 2 + cc;  // 16-byte unit of the 64-byte row
             uint32_t h[4], l[4];
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
-              const float x = factor(cc * 4 + qq);
+              const float x = factor(c16 * 4 + qq);
               h[qq] = tf32_rna(x);
               l[qq] = tf32_rna(x - __uint_as_float(h[qq]));
             }
-            const uint32_t off = canon_off(row, cc * 16, PCB);
+            const uint32_t off = canon_off(row, c16 * 16, PCB);
             *reinterpret_cast<uint4*>(b + off) = make_uint4(h[0], h[1], h[2], h[3]);
             if constexpr (PT::split) *reinterpret_cast<uint4*>(b + TB + off) = make_uint4(l[0], l[1], l[2], l[3]);
           }
         } else {
 #pragma unroll
-          for (int cc = 0; cc < KC / 8; ++cc) {
+          for (int cc = 0; cc < 2; ++cc) {
+            const int c16 = half * 2 + cc;
             uint32_t h[4], l[4];
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
-              const float x0 = factor(cc * 8 + 2 * qq), x1 = factor(cc * 8 + 2 * qq + 1);
+              const float x0 = factor(c16 * 8 + 2 * qq), x1 = factor(c16 * 8 + 2 * qq + 1);
               const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
               const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
               const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
               h[qq] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
               l[qq] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
             }
-            const uint32_t off = canon_off(row, cc * 16, PCB);
+            const uint32_t off = canon_off(row, c16 * 16, PCB);
             *reinterpret_cast<uint4*>(b + off) = make_uint4(h[0], h[1], h[2], h[3]);
             if constexpr (PT::split) *reinterpret_cast<uint4*>(b + TB + off) = make_uint4(l[0], l[1], l[2], l[3]);
           }
@@ -215,8 +227,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_prism_tc(const TcParam
       }
     }
   } else if (warp == LOADER) {
-    // ---------------- loader: one bulk copy of T^T per chunk ----------------
     if (lane == 0) {
+      // ---------------- loader: one bulk copy of T^T per chunk ----------------
       uint32_t c = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
@@ -228,7 +240,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_prism_tc(const TcParam
           prism_bulk_g2s(smem_u32(smem + (size_t)s * stage_bytes), p.image + (size_t)kc * a_chunk, (uint32_t)a_chunk,
                          bar);
         }
-      // every issued copy is consumed by the MMA warp's wait on its stage (or the kernel timed out)
+      // every issued copy is consumed by the MMA thread's wait on its stage (or the kernel timed out)
     }
     __syncwarp();
   } else if (warp == MMA_WARP) {
@@ -349,7 +361,7 @@ bool pgeom(int form, int degree, int prec, PGeom& g) {
 constexpr int P_SMEM_LIMIT = 227 * 1024;
 
 int pstages(const PGeom& g) {
-  const int fixed = (int)sizeof(PBars) + 1024 + 64;
+  const int fixed = 256 + g.Q * 16 + 1024 + 64;  // barriers (256 B), point table
   int s = PMAX_STAGES;
   while (s >= 2 && fixed + s * g.stage > P_SMEM_LIMIT) --s;
   return s >= 2 ? s : 0;
@@ -362,7 +374,7 @@ cudaError_t launch_p(const TcParams& p, int num_sms, cudaStream_t s, int nst, in
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (p.ncells + BN - 1) / BN;
   const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
-  kern<<<grid, NTHREADS, smem, s>>>(p, nst);
+  kern<<<grid, PTHREADS, smem, s>>>(p, nst);
   return cudaGetLastError();
 }
 
@@ -440,7 +452,7 @@ int launch_prism_tc(int form, int degree, const TcParams& p, int num_sms, void* 
   q.ksteps_off = g.KQ;
   q.ns = g.Q;
   q.N = g.N;
-  int smem = nst * g.stage + (int)sizeof(PBars) + 1024 + 64;
+  int smem = nst * g.stage + 256 + g.Q * 16 + 1024 + 64;
   if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA (one TMEM owner) per SM
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   switch (p.precision) {
