@@ -51,7 +51,7 @@ def _load():
         lib.oracle_prism_ndof.argtypes = [I]
         lib.oracle_prism_rule.argtypes = [I, P, P]
         lib.oracle_prism_basis.argtypes = [I, I, P, P, P]
-        lib.oracle_prism_assemble.argtypes = [I, I, P, P, L, P, I]
+        lib.oracle_prism_assemble.argtypes = [I, I, P, P, P, P, L, P, I]
         _lib = lib
     return _lib
 
@@ -251,11 +251,13 @@ def prism_basis(k, x):
     return phi, dphi
 
 
-def prism_assemble(form, k, coords, c2v, threads=0):
-    """Element matrices [ncells, n, n] of MASS or HELMHOLTZ on prisms (c2v [ncells, 6])."""
-    coords, c2v = _f64(coords), _i32(c2v)
+def prism_assemble(form, k, coords, c2v, coef=None, c2d=None, threads=0):
+    """Element matrices [ncells, n, n] of MASS, HELMHOLTZ or ADVDIFF on prisms (c2v [ncells, 6];
+    ADVDIFF: coef rows (eps, b0, b1, b2) per node, c2d [ncells, 6])."""
+    coords, c2v, coef, c2d = _f64(coords), _i32(c2v), _f64(coef), _i32(c2d)
     n = prism_ndof(k)
     out = np.zeros((c2v.shape[0], n, n))
-    if _load().oracle_prism_assemble(form, k, _p(coords), _p(c2v), c2v.shape[0], _p(out), threads) != 0:
+    if _load().oracle_prism_assemble(form, k, _p(coords), _p(c2v), _p(coef), _p(c2d), c2v.shape[0], _p(out),
+                                     threads) != 0:
         raise ValueError("oracle_prism_assemble failed")
     return out

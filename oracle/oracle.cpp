@@ -556,10 +556,12 @@ void prism_jacobian(const double* X, const double* xi, double J[3][3]) {
     }
 }
 
-// Element matrix of one prism (MASS or HELMHOLTZ): the quadrature loop nest of section 2,
-// with the Jacobian, its determinant and inverse evaluated at every point.
+// Element matrix of one prism (MASS, HELMHOLTZ or ADVDIFF): the quadrature loop nest of
+// section 2, with the Jacobian, its determinant and inverse evaluated at every point. For
+// ADVDIFF, cf holds (eps, b_0, b_1, b_2) at the six vertices; eps and b are degree-1 prism
+// fields, evaluated at each point with the prism's own vertex functions N_v.
 void prism_matrix(int form, int k, const Basis& T, const Rule& R, const double* phiq, const double* dphiq,
-                  const double* X, double* A) {
+                  const double* X, const double* cf, double* A) {
   const int n = prism_ndof(k);
   std::fill(A, A + (size_t)n * n, 0.0);
   std::vector<double> grad((size_t)n * 3);
@@ -590,12 +592,26 @@ void prism_matrix(int form, int k, const Basis& T, const Rule& R, const double* 
         grad[(size_t)i * 3 + c] = g;
       }
     const double wd = R.wts[q] * std::fabs(det);
+    double eps = 0.0, b[3] = {0.0, 0.0, 0.0};
+    if (form == FORM_ADVDIFF) {
+      const double* x = &R.pts[(size_t)q * 3];
+      const double lam[3] = {1.0 - x[0] - x[1], x[0], x[1]};
+      for (int v = 0; v < 6; ++v) {
+        const double Nv = v < 3 ? lam[v] * (1.0 - x[2]) : lam[v - 3] * x[2];
+        eps += Nv * cf[v * 4];
+        for (int r = 0; r < 3; ++r) b[r] += Nv * cf[v * 4 + 1 + r];
+      }
+    }
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) {
-        double v = phi[i] * phi[j];
-        if (form == FORM_HELMHOLTZ)
-          v += grad[(size_t)i * 3] * grad[(size_t)j * 3] + grad[(size_t)i * 3 + 1] * grad[(size_t)j * 3 + 1] +
-               grad[(size_t)i * 3 + 2] * grad[(size_t)j * 3 + 2];
+        const double gg = grad[(size_t)i * 3] * grad[(size_t)j * 3] + grad[(size_t)i * 3 + 1] * grad[(size_t)j * 3 + 1] +
+                          grad[(size_t)i * 3 + 2] * grad[(size_t)j * 3 + 2];
+        double v;
+        if (form == FORM_ADVDIFF)
+          v = eps * gg + phi[i] * (b[0] * grad[(size_t)j * 3] + b[1] * grad[(size_t)j * 3 + 1] +
+                                   b[2] * grad[(size_t)j * 3 + 2]);
+        else
+          v = phi[i] * phi[j] + (form == FORM_HELMHOLTZ ? gg : 0.0);
         A[(size_t)i * n + j] += wd * v;
       }
   }
@@ -785,11 +801,15 @@ int oracle_prism_basis(int degree, int npts, const double* x, double* phi, doubl
   return 0;
 }
 
-// element matrices [ncells][n][n] of MASS or HELMHOLTZ on prisms: coords [nverts][3],
-// cell2vert [ncells][6] (bottom triangle, then the top vertices above it)
-int oracle_prism_assemble(int form, int degree, const double* coords, const int32_t* c2v, int64_t ncells,
-                          double* out, int nthreads) {
-  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ) || degree < 1 || degree > 4 || ncells < 0) return -1;
+// element matrices [ncells][n][n] of MASS, HELMHOLTZ or ADVDIFF on prisms: coords [nverts][3],
+// cell2vert [ncells][6] (bottom triangle, then the top vertices above it); ADVDIFF: coef rows
+// (eps, b_0, b_1, b_2) per coefficient node, cell2dof [ncells][6] (the cell's vertices)
+int oracle_prism_assemble(int form, int degree, const double* coords, const int32_t* c2v, const double* coef,
+                          const int32_t* c2d, int64_t ncells, double* out, int nthreads) {
+  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF) || degree < 1 || degree > 4 ||
+      ncells < 0)
+    return -1;
+  if (form == FORM_ADVDIFF && (!coef || !c2d)) return -1;
   Basis T = lagrange(CELL_TRI, degree);
   Rule R = prism_rule(degree);
   const int n = prism_ndof(degree);
@@ -799,10 +819,13 @@ int oracle_prism_assemble(int form, int degree, const double* coords, const int3
   set_threads(nthreads);
 #pragma omp parallel for schedule(static)
   for (int64_t e = 0; e < ncells; ++e) {
-    double X[18];
+    double X[18], cf[24] = {0};
     for (int v = 0; v < 6; ++v)
       for (int r = 0; r < 3; ++r) X[v * 3 + r] = coords[(int64_t)c2v[e * 6 + v] * 3 + r];
-    prism_matrix(form, degree, T, R, phiq.data(), dphiq.data(), X, out + e * (int64_t)n * n);
+    if (form == FORM_ADVDIFF)
+      for (int v = 0; v < 6; ++v)
+        for (int r = 0; r < 4; ++r) cf[v * 4 + r] = coef[(int64_t)c2d[e * 6 + v] * 4 + r];
+    prism_matrix(form, degree, T, R, phiq.data(), dphiq.data(), X, cf, out + e * (int64_t)n * n);
   }
   return 0;
 }

@@ -172,3 +172,62 @@ def test_prism_mesh_global_mass_is_the_unit_cube_and_numbering_conforms(k):
     assert abs(M.sum() - 1.0) < 1e-13
     rows = np.repeat(np.arange(nn), np.diff(rp))
     np.testing.assert_allclose(np.bincount(rows, weights=H - M, minlength=nn), 0.0, atol=1e-12 * np.abs(H).max())
+
+
+ADVDIFF = oracle.ADVDIFF
+
+
+def vertex_coef(rng, X):
+    """(eps, b) rows per prism vertex: eps = a0 + a.x and b = B x + c, linear in the position."""
+    a0, a = 1.0 + 0.2 * rng.random(), 0.3 * rng.standard_normal(3)
+    Bm, cvec = 0.5 * rng.standard_normal((3, 3)), rng.standard_normal(3)
+    eps = a0 + X @ a
+    b = X @ Bm.T + cvec
+    return np.concatenate([eps[:, None], b], axis=1), (a0, a, Bm, cvec)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_twisted_prism_advdiff_annihilates_constants_linear_and_reduces_to_stiffness(k):
+    rng = np.random.default_rng(90 + k)
+    X = np.array([[float(v) for v in row] for row in rational_prism(rng, twisted=True)])
+    c2v = np.arange(6, dtype=np.int32)[None]
+    c2d = c2v.copy()
+    coef1, _ = vertex_coef(rng, X)
+    coef2, _ = vertex_coef(rng, X)
+    A1 = oracle.prism_assemble(ADVDIFF, k, X, c2v, coef1.ravel(), c2d)[0]
+    A2 = oracle.prism_assemble(ADVDIFF, k, X, c2v, coef2.ravel(), c2d)[0]
+    A12 = oracle.prism_assemble(ADVDIFF, k, X, c2v, (0.3 * coef1 - 1.7 * coef2).ravel(), c2d)[0]
+    np.testing.assert_allclose(A1.sum(axis=1), 0.0, atol=1e-12 * np.abs(A1).max())  # A 1 = 0
+    np.testing.assert_allclose(A12, 0.3 * A1 - 1.7 * A2, atol=1e-13 * np.abs(A12).max())
+    unit = np.zeros((6, 4))
+    unit[:, 0] = 1.0  # eps = 1, b = 0: the stiffness part of Helmholtz
+    S = oracle.prism_assemble(ADVDIFF, k, X, c2v, unit.ravel(), c2d)[0]
+    H = oracle.prism_assemble(HELMHOLTZ, k, X, c2v)[0] - oracle.prism_assemble(MASS, k, X, c2v)[0]
+    np.testing.assert_allclose(S, H, atol=1e-13 * np.abs(H).max())
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_affine_prism_advdiff_bilinear_identity_exact(k):
+    """Sheared right prism, eps and b linear in x: Q^T A P = int eps grad p.grad q + q (b.grad p)."""
+    rng = np.random.default_rng(110 + k)
+    Xs = rational_prism(rng, twisted=False)
+    X = np.array([[float(v) for v in row] for row in Xs])
+    coef, (a0, a, Bm, cvec) = vertex_coef(rng, X)
+    xs = exact.symbols(3)
+    p, q = exact.random_poly(xs, k, rng), exact.random_poly(xs, k, rng)
+    eps = a0 + sum(float(a[r]) * xs[r] for r in range(3))
+    b = [sum(float(Bm[c, r]) * xs[r] for r in range(3)) + float(cvec[c]) for c in range(3)]
+    xi = sp.symbols("s t z")
+    phys = sym_map(Xs, xi)
+    J = sp.Matrix(3, 3, lambda r, c: sp.diff(phys[r], xi[c]))
+    det = sp.simplify(J.det())
+    gp = [sp.diff(p, x) for x in xs]
+    gq = [sp.diff(q, x) for x in xs]
+    integrand = eps * sum(u * v for u, v in zip(gp, gq)) + q * sum(bb * g for bb, g in zip(b, gp))
+    ex = float(integrate_ref_prism(sp.expand(integrand.subs(dict(zip(xs, phys)), simultaneous=True)) * abs(det), xi))
+    nodes = prism_map(X, prism_nodes_ref(k))
+    P = np.array([float(p.subs(dict(zip(xs, n)))) for n in nodes])
+    Q = np.array([float(q.subs(dict(zip(xs, n)))) for n in nodes])
+    A = oracle.prism_assemble(ADVDIFF, k, X, np.arange(6, dtype=np.int32)[None], coef.ravel(),
+                              np.arange(6, dtype=np.int32)[None])[0]
+    assert abs(Q @ A @ P - ex) < 1e-11 * (np.abs(Q) @ np.abs(A) @ np.abs(P))
