@@ -95,6 +95,10 @@ WORKLOADS["burgers-residual-p2-tet"] = Workload("burgers-residual-p2-tet", BURGE
 WORKLOADS["helmholtz-p2-prism"] = Workload("helmholtz-p2-prism", HELMHOLTZ, 2, PRISM,
                                            "unit cube, 48x48 two-triangle columns x 48 layers = 221,184 "
                                            "twisted prisms perturbed 0.15h (seed 6); FP64", _prism48)
+WORKLOADS["advdiff-p2-prism"] = Workload("advdiff-p2-prism", ADVDIFF, 2, PRISM,
+                                         "unit cube, 48x48 two-triangle columns x 48 layers = 221,184 "
+                                         "twisted prisms perturbed 0.15h (seed 6), eps~U[0.5,1.5], "
+                                         "b~U[-1,1]^3 per vertex", _prism48)
 WORKLOADS["helmholtz-p1-tri"] = Workload("helmholtz-p1-tri", HELMHOLTZ, 1, TRIANGLE,
                                          "unit square 64x64x2 triangles perturbed 0.2h (seed 1)", _tri64)
 
@@ -222,7 +226,8 @@ def kernel_source_sha():
 def oracle_cells(wl, mesh, coef, c2d, sel, threads=0):
     import oracle
     if wl.cell == PRISM:
-        return oracle.prism_assemble(wl.form, wl.degree, mesh.coords, mesh.cell2vert[sel], threads=threads)
+        extra = (coef, c2d[sel]) if wl.form == ADVDIFF else ()
+        return oracle.prism_assemble(wl.form, wl.degree, mesh.coords, mesh.cell2vert[sel], *extra, threads=threads)
     if wl.form == BURGERS_RESIDUAL:
         d = 2 if wl.cell == TRIANGLE else 3
         return oracle.burgers_residual(wl.degree, wl.cell, mesh.coords, mesh.cell2vert[sel], coef.reshape(-1, d),
@@ -396,9 +401,9 @@ def run_ours(args):
     if prec == coffee.FP64:
         roof["note"] = "FP64 kernel: bound by the FP64 ALU (1.25 TFLOP/s measured); HBM fraction for context"
     if cell == PRISM:
-        # non-affine cells: the contraction over all quadrature points (K = 7 Q) dominates
+        # non-affine cells: the contraction over all quadrature points (K = KQ Q) dominates
         Q = (degree + 2) ** 3
-        K = Q * (7 if form == HELMHOLTZ else 1)
+        K = Q * {HELMHOLTZ: 7, ADVDIFF: 9}.get(form, 1)
         flops = 2.0 * K * ndof * ndof + 250.0 * Q  # algorithmic, per cell
         if prec == coffee.FP64:
             tf = flops * ncells / (launch_ms / 1e3) / 1e12

@@ -143,13 +143,16 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
   const int d = a->cell == CELL_TRI ? 2 : 3;
   const bool validate = (a->flags & COFFEE_FLAG_VALIDATE) != 0;
   if (a->cell == CELL_PRISM && a->precision != PREC_FP64) {
-    if (map || !prism_tc_supported(a->form, a->degree, a->precision))
-      return fail(COFFEE_ERR_UNSUPPORTED, "tensor-core prisms: local assembly of MASS and HELMHOLTZ, P1-P2");
+    if (!prism_tc_supported(a->form, a->degree, a->precision))
+      return fail(COFFEE_ERR_UNSUPPORTED, "tensor-core prisms: MASS, HELMHOLTZ and ADVDIFF, P1-P2");
     TcTable meta{};
     if ((rc = tc_table(*c, a->form, a->degree, a->cell, a->precision, &meta)) != COFFEE_OK) return rc;
     TcParams p{};
     p.coords = a->coords;
     p.c2v = a->cell2vert;
+    p.coef = a->coef;
+    p.c2d = a->cell2dof;
+    p.ncoefnodes = a->ncoefnodes;
     p.image = meta.image;
     p.out = static_cast<float*>(a->out);
     p.err = c->err;
@@ -157,20 +160,25 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
     p.nverts = a->nverts;
     p.precision = a->precision;
     p.validate = validate ? 1 : 0;
+    p.map = map;
+    p.nnz = nnz;
     std::string why;
     cudaError_t e = (cudaError_t)launch_prism_tc(a->form, a->degree, p, c->num_sms, stream, why);
     if (e != cudaSuccess) return cuda_fail(e, ("launch(assemble_prism_tc) " + why).c_str());
     return COFFEE_OK;
   }
   if (a->cell == CELL_PRISM) {
-    if (!(a->form == FORM_MASS || a->form == FORM_HELMHOLTZ))
-      return fail(COFFEE_ERR_UNSUPPORTED, "prisms: MASS and HELMHOLTZ");
+    if (!(a->form == FORM_MASS || a->form == FORM_HELMHOLTZ || a->form == FORM_ADVDIFF))
+      return fail(COFFEE_ERR_UNSUPPORTED, "prisms: MASS, HELMHOLTZ and ADVDIFF");
     const double* T = nullptr;
     if ((rc = fp64_table(*c, a->form, a->degree, a->cell, &T)) != COFFEE_OK) return rc;
     const int n = prism_nnodes(a->degree);
     PrismParams p{};
     p.coords = a->coords;
     p.c2v = a->cell2vert;
+    p.coef = a->coef;
+    p.c2d = a->cell2dof;
+    p.ncoefnodes = a->ncoefnodes;
     p.T = T;
     p.out = a->out;
     p.err = c->err;
@@ -301,7 +309,8 @@ int coffee_reference_tensor(int form, int degree, int cell, int* K, int* N, doub
 int coffee_supported(int form, int degree, int cell, int precision) {
   if (!valid_fdc(form, degree, cell) || precision < PREC_FP64 || precision > PREC_BF16X3) return 0;
   if (cell == CELL_PRISM)
-    return (form == FORM_MASS || form == FORM_HELMHOLTZ) && (precision == PREC_FP64 || prism_tc_supported(form, degree, precision));
+    return (form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF) &&
+           (precision == PREC_FP64 || prism_tc_supported(form, degree, precision));
   if (precision == PREC_FP64) return 1;
   return tc_supported(form, degree, cell, precision);
 }
@@ -374,7 +383,9 @@ int coffee_csr_map(const int32_t* l2g, int64_t ncells, int nloc, const int64_t* 
 int coffee_csr_supported(int form, int degree, int cell, int precision) {
   if (!valid_fdc(form, degree, cell) || precision < PREC_FP64 || precision > PREC_BF16X3) return 0;
   if (form == FORM_BURGERS_RES) return 0;
-  if (cell == CELL_PRISM) return (form == FORM_MASS || form == FORM_HELMHOLTZ) && precision == PREC_FP64;
+  if (cell == CELL_PRISM)
+    return precision == PREC_FP64 ? (form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF)
+                                  : prism_tc_supported(form, degree, precision);
   return precision == PREC_FP64 ? 1 : tc_csr_supported(form, degree, cell, precision);
 }
 

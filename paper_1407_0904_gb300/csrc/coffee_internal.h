@@ -67,6 +67,9 @@ int launch_fp64(int form, int cell, const Fp64Params& p, void* stream);
 struct PrismParams {
   const double* coords;  // [nverts][3]
   const int32_t* c2v;    // [ncells][6]
+  const double* coef;    // ADVDIFF: rows (eps, b0, b1, b2) per coefficient node
+  const int32_t* c2d;    // ADVDIFF: [ncells][6]
+  int64_t ncoefnodes;
   const double* T;       // [Q*KQ][N] per-point tensors, then points [Q][3], then weights [Q]
   void* out;             // double [ncells][N], or the CSR values when map is set
   unsigned* err;

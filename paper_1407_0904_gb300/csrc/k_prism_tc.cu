@@ -2,7 +2,9 @@
 //
 // A prism's map is not affine, so the Jacobian is evaluated at every quadrature point and the
 // element matrix is a quadrature sum: A_e[o] = sum_{q,f} G_e[q][f] T[q*KQ+f][o] with
-// G_e[q] = w_q |det J_q| (1, (K_q K_q^T)_ab), KQ = 1 (mass) or 7 (Helmholtz). The contraction
+// G_e[q] = w_q |det J_q| (1, (K_q K_q^T)_ab), KQ = 1 (mass) or 7 (Helmholtz), or
+// G_e[q] = w_q |det J_q| (eps_q (K_q K_q^T)_ab, (K_q b_q)_a), KQ = 9 (advection-diffusion with
+// degree-1 prism fields eps, b given at the six vertices). The contraction
 // over K = Q*KQ (189 at P1, 448 at P2) is too deep to keep either operand resident, so both are
 // streamed through shared memory in K-chunks of 64 bytes per row (16 tf32 / 32 bf16 columns):
 //   loader warp 13      one bulk copy per chunk of T^T (all 128-output slices, hi and lo),
@@ -53,7 +55,7 @@ __device__ __forceinline__ void prism_bulk_g2s(uint32_t dst, const void* src, ui
 
 // p.N outputs, p.mtiles slices, p.nkc chunks, p.ksteps_off = KQ, p.ns = Q; the image holds the
 // chunks of T^T ([chunk][slice][part][128 rows x 64 B]) followed by the points (s,t,z,w) [Q][4].
-template <int PREC>
+template <int PREC, int KQ, bool CSR>
 __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParams p, int nstages) {
   using PT = PrecTraits<PREC>;
   constexpr int PARTS = PT::split ? 2 : 1;
@@ -61,7 +63,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
   constexpr int TB = BM * PCB;            // bytes of one 128-row part of one chunk
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int MT = p.mtiles, NKC = p.nkc, KQ = p.ksteps_off, Q = p.ns, N = p.N;
+  const int MT = p.mtiles, NKC = p.nkc, Q = p.ns, N = p.N;
   const int a_chunk = MT * PARTS * TB;          // T^T part of a stage
   const int stage_bytes = a_chunk + PARTS * TB;  // + the G part
   PBars* bars = reinterpret_cast<PBars*>(smem + nstages * stage_bytes);
@@ -110,6 +112,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
       // J(s,t,z) is bilinear: columns d/ds = A + z B, d/dt = C + z D, d/dz = E + s F + t G with
       // vertex differences taken in FP64 before rounding to FP32
       float JA[3], JB[3], JC[3], JD[3], JE[3], JF[3], JG[3];
+      float CF[6][4];  // advection-diffusion: (eps, b) at the six vertices
       if (live) {
         bool bad = false;
         double Xd[6][3];
@@ -122,6 +125,18 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
           }
 #pragma unroll
           for (int r = 0; r < 3; ++r) Xd[v][r] = __ldg(p.coords + (int64_t)vid * 3 + r);
+        }
+        if constexpr (KQ == 9) {
+#pragma unroll
+          for (int v = 0; v < 6; ++v) {
+            int cid = __ldg(p.c2d + e * 6 + v);
+            if (p.validate && (cid < 0 || cid >= p.ncoefnodes)) {
+              bad = true;
+              cid = 0;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) CF[v][r] = (float)__ldg(p.coef + (int64_t)cid * 4 + r);
+          }
         }
         if (bad) {
           if (half == 0) atomicOr(p.err, ERR_INDEX);
@@ -142,7 +157,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
         }
       }
       int gq = -1;      // point whose factors are cached
-      float gf[7] = {};  // w |det| (1, K K^T pairs) at point gq
+      float gf[9] = {};  // the point's factors (see the kernel comment)
       for (int kc = 0; kc < NKC; ++kc, ++c) {
         const int s = (int)(c % nstages);
         if (!mbar_wait(smem_u32(&bars->empty[s]), ((c / nstages) & 1u) ^ 1u, p.err)) { ok = false; break; }
@@ -166,23 +181,43 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
                                       J[0][2] * J[1][0] - J[0][0] * J[1][2]},
                                      {J[1][0] * J[2][1] - J[1][1] * J[2][0], J[0][1] * J[2][0] - J[0][0] * J[2][1],
                                       J[0][0] * J[1][1] - J[0][1] * J[1][0]}};
-            const float adet = fabsf(J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0]);
-            gf[0] = pq.w * adet;
-            const float wi = pq.w / adet;
-            int pp = 1;
+            const float det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+            const float adet = fabsf(det);
+            float wi = pq.w / adet;
+            constexpr int P0 = KQ == 9 ? 0 : 1;  // first pair factor
+            if constexpr (KQ == 9) {
+              // eps and b at the point from the vertex values (degree-1 prism functions)
+              const float lam[3] = {1.f - pq.x - pq.y, pq.x, pq.y};
+              float eps = 0.f, bq[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
+              for (int v = 0; v < 6; ++v) {
+                const float Nv = v < 3 ? lam[v] * (1.f - pq.z) : lam[v - 3] * pq.z;
+                eps = fmaf(Nv, CF[v][0], eps);
 #pragma unroll
-              for (int b = a; b < 3; ++b) {
-                float acc = 0.f;
-#pragma unroll
-                for (int r = 0; r < 3; ++r) acc = fmaf(adj[a][r], adj[b][r], acc);
-                gf[pp++] = wi * acc;
+                for (int r = 0; r < 3; ++r) bq[r] = fmaf(Nv, CF[v][1 + r], bq[r]);
               }
+              const float sw = det < 0.f ? -pq.w : pq.w;
+#pragma unroll
+              for (int a = 0; a < 3; ++a) gf[6 + a] = sw * (adj[a][0] * bq[0] + adj[a][1] * bq[1] + adj[a][2] * bq[2]);
+              wi *= eps;
+            } else {
+              gf[0] = pq.w * adet;
+            }
+            if constexpr (KQ > 1) {
+#pragma unroll
+              for (int a = 0, pp = P0; a < 3; ++a)
+#pragma unroll
+                for (int b = a; b < 3; ++b, ++pp) {
+                  float acc = 0.f;
+#pragma unroll
+                  for (int r = 0; r < 3; ++r) acc = fmaf(adj[a][r], adj[b][r], acc);
+                  gf[pp] = wi * acc;
+                }
+            }
           }
           float v = gf[0];
 #pragma unroll
-          for (int i = 1; i < 7; ++i)
+          for (int i = 1; i < KQ; ++i)
             if (f == i) v = gf[i];
           return v;
         };
@@ -290,6 +325,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
     __syncwarp();
   } else if (warp < EPI_WARPS) {
     // ---------------- epilogue: 128-byte warp stores of 32 outputs of one cell ----------------
+    // (global assembly, p.map set: one reduction per entry at its CSR position instead)
     const int q = warp;
     uint32_t rc = 0;
     bool ok = true;
@@ -304,8 +340,32 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
           const int64_t rem = p.ncells - cbase;
           const int ncol = rem <= 0 ? 0 : (rem < 64 ? (int)rem : 64);
           if (m * BM + q * 32 < N && ncol > 0) {  // warp-uniform
-            uint32_t v0[32], v1[32];
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + slot * BN + cc;
+            if constexpr (CSR) {
+              // global assembly, 32 cells per TMEM wait: a warp reads each cell's 32 map entries
+              // (contiguous in the blocked layout) and adds the values at their CSR positions
+              const int npad = (N + 3) & ~3;
+              const int bw = npad - (o & ~31) < 32 ? npad - (o & ~31) : 32;  // width of this 32-output block
+              for (int h = 0; h < 2; ++h) {
+                uint32_t v[32], pos[32];
+                tmem_ld32(taddr + 32 * h, v);
+                // cells cbase + 32h + jj (cbase is a multiple of 32): csr_map_index = row + jj * bw
+                const uint32_t* row = p.map + csr_map_index(cbase + 32 * h, o, npad);
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) pos[jj] = (o < N && h * 32 + jj < ncol) ? __ldg(row + jj * bw) : 0u;
+                tmem_wait_ld();
+                if (o < N) {
+#pragma unroll
+                  for (int jj = 0; jj < 32; ++jj)
+                    if (h * 32 + jj < ncol) {
+                      if (pos[jj] < (uint64_t)p.nnz) atomicAdd(p.out + pos[jj], __uint_as_float(v[jj]));
+                      else atomicOr(p.err, ERR_INDEX);
+                    }
+                }
+              }
+              continue;
+            }
+            uint32_t v0[32], v1[32];
             tmem_ld32(taddr, v0);
             tmem_ld32(taddr + 32, v1);
             tmem_wait_ld();
@@ -340,13 +400,13 @@ struct PGeom {
 };
 
 bool pgeom(int form, int degree, int prec, PGeom& g) {
-  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ) || degree < 1 || degree > 2) return false;
+  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF) || degree < 1 || degree > 2) return false;
   if (prec == PREC_FP64 || prec < 0 || prec > PREC_BF16X3) return false;
   const bool tf32 = prec == PREC_TF32 || prec == PREC_TF32X3;
   g.n = prism_nnodes(degree);
   g.N = g.n * g.n;
   g.mtiles = (g.N + BM - 1) / BM;
-  g.KQ = form == FORM_HELMHOLTZ ? 7 : 1;
+  g.KQ = form == FORM_HELMHOLTZ ? 7 : form == FORM_ADVDIFF ? 9 : 1;
   g.Q = (degree + 2) * (degree + 2) * (degree + 2);
   g.K = g.Q * g.KQ;
   g.elem = tf32 ? 4 : 2;
@@ -367,15 +427,35 @@ int pstages(const PGeom& g) {
   return s >= 2 ? s : 0;
 }
 
-template <int PREC>
+template <int PREC, int KQ>
 cudaError_t launch_p(const TcParams& p, int num_sms, cudaStream_t s, int nst, int smem) {
-  auto kern = k_assemble_prism_tc<PREC>;
+  auto kern = p.map ? k_assemble_prism_tc<PREC, KQ, true> : k_assemble_prism_tc<PREC, KQ, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (p.ncells + BN - 1) / BN;
   const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
   kern<<<grid, PTHREADS, smem, s>>>(p, nst);
   return cudaGetLastError();
+}
+
+template <int KQ>
+cudaError_t launch_prec(const TcParams& q, int num_sms, cudaStream_t s, int nst, int smem) {
+  switch (q.precision) {
+    case PREC_TF32: return launch_p<PREC_TF32, KQ>(q, num_sms, s, nst, smem);
+    case PREC_TF32X3: return launch_p<PREC_TF32X3, KQ>(q, num_sms, s, nst, smem);
+    case PREC_BF16: return launch_p<PREC_BF16, KQ>(q, num_sms, s, nst, smem);
+    case PREC_BF16X3: return launch_p<PREC_BF16X3, KQ>(q, num_sms, s, nst, smem);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_kq(int KQ, const TcParams& q, int num_sms, cudaStream_t s, int nst, int smem) {
+  switch (KQ) {
+    case 1: return launch_prec<1>(q, num_sms, s, nst, smem);
+    case 7: return launch_prec<7>(q, num_sms, s, nst, smem);
+    case 9: return launch_prec<9>(q, num_sms, s, nst, smem);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -455,13 +535,7 @@ int launch_prism_tc(int form, int degree, const TcParams& p, int num_sms, void* 
   int smem = nst * g.stage + 256 + g.Q * 16 + 1024 + 64;
   if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA (one TMEM owner) per SM
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  switch (p.precision) {
-    case PREC_TF32: return (int)launch_p<PREC_TF32>(q, num_sms, s, nst, smem);
-    case PREC_TF32X3: return (int)launch_p<PREC_TF32X3>(q, num_sms, s, nst, smem);
-    case PREC_BF16: return (int)launch_p<PREC_BF16>(q, num_sms, s, nst, smem);
-    case PREC_BF16X3: return (int)launch_p<PREC_BF16X3>(q, num_sms, s, nst, smem);
-  }
-  return (int)cudaErrorInvalidValue;
+  return (int)launch_kq(g.KQ, q, num_sms, s, nst, smem);
 }
 
 }  // namespace coffee

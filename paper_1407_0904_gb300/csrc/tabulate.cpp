@@ -312,13 +312,16 @@ void prism_basis(int k, int npts, const double* x, double* phi, double* grads) {
   }
 }
 
-// Per-point reference tensors of MASS (KQ = 1) and HELMHOLTZ (KQ = 7) on prisms:
-//   T[q*KQ + 0][i*n+j]     = phi_i(x_q) phi_j(x_q)
-//   T[q*KQ + 1 + p][i*n+j] = d_a phi_i d_b phi_j + [a!=b] d_b phi_i d_a phi_j   (p-th pair a<=b)
-// so that A_e = sum_q sum_kq G_e[q][kq] T[q*KQ+kq] with G_e[q] = w_q |det J(x_q)| (1, (K K^T)_ab).
+// Per-point reference tensors on prisms, A_e = sum_q sum_kq G_e[q][kq] T[q*KQ+kq]:
+//  MASS (KQ = 1):      T[q] = phi_i phi_j;                      G = w |det|
+//  HELMHOLTZ (KQ = 7): T[q*7] = phi_i phi_j, T[q*7+1+p] = d_a phi_i d_b phi_j + [a!=b] d_b phi_i d_a phi_j
+//                      for the p-th pair a <= b;                G = w |det| (1, (K K^T)_ab)
+//  ADVDIFF (KQ = 9):   T[q*9+p] = the pair tensors, T[q*9+6+a] = phi_i d_a phi_j;
+//                      G = w |det| (eps_q (K K^T)_ab, (K b_q)_a)
 void prism_tensor(int form, int k, std::vector<double>& T, std::vector<double>& pts, std::vector<double>& wts) {
   prism_rule(k, pts, wts);
-  const int Q = (int)wts.size(), n = prism_nnodes(k), N = n * n, KQ = form == FORM_HELMHOLTZ ? 7 : 1;
+  const int Q = (int)wts.size(), n = prism_nnodes(k), N = n * n;
+  const int KQ = form == FORM_HELMHOLTZ ? 7 : form == FORM_ADVDIFF ? 9 : 1;
   std::vector<double> phi((size_t)Q * n), g((size_t)Q * n * 3);
   prism_basis(k, Q, pts.data(), phi.data(), g.data());
   T.assign((size_t)Q * KQ * N, 0.0);
@@ -327,15 +330,20 @@ void prism_tensor(int form, int k, std::vector<double>& T, std::vector<double>& 
     const double* gr = &g[(size_t)q * n * 3];
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) {
-        T[((size_t)q * KQ) * N + (size_t)i * n + j] = ph[i] * ph[j];
-        if (KQ == 7)
+        const size_t o = (size_t)i * n + j;
+        if (KQ != 9) T[((size_t)q * KQ) * N + o] = ph[i] * ph[j];
+        if (KQ >= 7) {
+          const int p0 = KQ == 7 ? 1 : 0;  // first pair column of the point
           for (int pp = 0; pp < 6; ++pp) {
             int a, b;
             pair_index(3, pp, a, b);
             double v = gr[(size_t)i * 3 + a] * gr[(size_t)j * 3 + b];
             if (a != b) v += gr[(size_t)i * 3 + b] * gr[(size_t)j * 3 + a];
-            T[((size_t)q * KQ + 1 + pp) * N + (size_t)i * n + j] = v;
+            T[((size_t)q * KQ + p0 + pp) * N + o] = v;
           }
+        }
+        if (KQ == 9)
+          for (int a = 0; a < 3; ++a) T[((size_t)q * KQ + 6 + a) * N + o] = ph[i] * gr[(size_t)j * 3 + a];
       }
   }
 }
