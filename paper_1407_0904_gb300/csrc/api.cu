@@ -87,7 +87,6 @@ int fp64_table(DeviceCache& c, int form, int degree, int cell, const double** T)
 }
 
 int tc_table(DeviceCache& c, int form, int degree, int cell, int prec, TcTable* meta) {
-  form = table_form(form);
   auto key = std::make_tuple(form, degree, cell, prec);
   auto it = c.tc.find(key);
   if (it == c.tc.end()) {
@@ -243,6 +242,8 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
   p.kbytes = meta.kbytes;
   p.parts = meta.parts;
   p.ksteps_off = meta.ksteps_off;
+  p.aexact = meta.aexact;
+  p.scale_off = meta.scale_off;
   p.tune = ((a->flags & COFFEE_FLAG_OUTPUT_LANES) ? TUNE_OUTPUT_LANES : 0u) |
            ((a->flags & COFFEE_FLAG_TWO_STAGES) ? TUNE_TWO_STAGES : 0u) |
            ((a->flags & COFFEE_FLAG_SUBTILE_64) ? TUNE_SUB64 : 0u) |

@@ -122,6 +122,9 @@ struct TcTable {
   int parts;             // 1 (single pass) or 2 (hi, lo)
   int ksteps_off;        // Burgers: K-steps of the off-diagonal component blocks
   int64_t tile_bytes;    // bytes of one part of one M-tile = 128 * kbytes
+  int aexact;            // 1: every A column is an integer vector times a scale, so A is held
+                         // exactly in one part and the scales (float [kelems]) follow the tiles
+  int64_t scale_off;     // byte offset of those scales in the image
 };
 
 struct TcParams {
@@ -144,12 +147,14 @@ struct TcParams {
   const uint32_t* map;   // global assembly: CSR position of every entry (blocked, csr_map_index); out = CSR values
   int64_t nnz;           // length of the CSR value array when map is set
   int nkc;               // prisms: K-chunks of the streamed contraction
+  int aexact;            // TcTable::aexact
+  int64_t scale_off;     // TcTable::scale_off
 };
 int tc_supported(int form, int degree, int cell, int precision);
 int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
 // Burgers-Jacobian tensor-core kernel (k_tc_burgers.cu)
 int burgers_tc_supported(int degree, int cell, int precision);
-void build_burgers_image(int degree, int cell, int prec, std::vector<uint8_t>& img, TcTable& meta);
+void build_burgers_image(int degree, int cell, int prec, bool exact_ok, std::vector<uint8_t>& img, TcTable& meta);
 int launch_burgers_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
 // Burgers-residual (element vector) tensor-core kernel (k_tc_burgers_res.cu)
 int burgers_res_tc_supported(int degree, int cell, int precision);

@@ -83,8 +83,8 @@ void build_tc_image(int form, int degree, int cell, int prec, std::vector<uint8_
     build_prism_tc_image(form, degree, prec, img, meta);
     return;
   }
-  if (form == FORM_BURGERS) {
-    build_burgers_image(degree, cell, prec, img, meta);
+  if (burgers_like(form)) {  // the Jacobian takes the exact integer form of A where it exists
+    build_burgers_image(degree, cell, prec, form == FORM_BURGERS, img, meta);
     return;
   }
   Geom g;

@@ -12,6 +12,11 @@
 // diagonal blocks over all of them. Producers build one block's factors per operand
 // stage (the per-block B operand), so the operand stages stay the size of one block.
 // Pipeline roles, TMEM ring and bounded waits are those of k_tc.cu.
+//
+// Exact A (AX): where every column k of A is an integer vector n_k times a scale c_k with
+// integers the operand type holds exactly (tf32: odd part < 2^11, bf16: < 2^8), A is stored
+// once as the integers and the producers multiply factor k by c_k. The split precisions then
+// need two passes (A B_hi + A B_lo) instead of three, and A takes half the shared memory.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -25,11 +30,13 @@ namespace coffee {
 namespace {
 using namespace tc;
 
-template <int D, int NS, int PREC>
+template <int D, int NS, int PREC, bool AX>
 __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, int nstages) {
   using S = BurgersShape<D, NS, PREC>;
   using PT = PrecTraits<PREC>;
   constexpr int NV = D + 1, P = S::P, KA1 = S::KA1, KD = S::KD, PARTS = S::PARTS;
+  constexpr int APARTS = AX ? 1 : PARTS;  // parts of the resident A operand
+  static_assert(KD * 4 <= SCALE_BYTES, "column scales exceed their shared-memory slot");
   constexpr int NB = D * D;
   constexpr uint32_t IDESC = make_idesc(PT::tf32 ? 2 : 1, BM, BN);
 
@@ -37,10 +44,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int kbytes = p.kbytes;  // = KD * ELEM
   const int tile_bytes = BM * kbytes;
-  const int a_bytes = S::MT * PARTS * tile_bytes;
+  const int a_bytes = S::MT * APARTS * tile_bytes;
+  constexpr int SPART = BN * S::CWB;  // bytes of one part of a chunk stage
   uint8_t* sA = smem;
   uint8_t* sB = smem + a_bytes;
-  Barriers* bars = reinterpret_cast<Barriers*>(sB + nstages * PARTS * tile_bytes);
+  Barriers* bars = reinterpret_cast<Barriers*>(sB + nstages * PARTS * SPART);
+  float* sc = reinterpret_cast<float*>(bars + 1);  // AX: scale of every A column
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (p.ncells + BN - 1) / BN;
@@ -68,6 +77,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
     const uint4* src = reinterpret_cast<const uint4*>(p.image);
     uint4* dst = reinterpret_cast<uint4*>(sA);
     for (int i = threadIdx.x; i < a_bytes / 16; i += NTHREADS) dst[i] = __ldg(src + i);
+    if constexpr (AX) {
+      const float* scg = reinterpret_cast<const float*>(p.image + p.scale_off);
+      for (int i = threadIdx.x; i < KD; i += NTHREADS) sc[i] = __ldg(scg + i);
+    }
   }
   fence_proxy_async();
   tc_fence_before();
@@ -76,7 +89,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
   const uint32_t tmem = bars->tmem_base;
 
   if (warp >= PROD_WARP0 && warp < MMA_WARP) {
-    // ---------------- producers: one cell per thread, one block per stage ----------------
+    // ---------------- producers: one cell per thread, one K-chunk of a block per stage ----------------
     const int pw = warp - PROD_WARP0;
     const int grp = pw >> 2, row = ((pw & 3) << 5) + lane;
     const int spg = nstages / PROD_GROUPS;
@@ -84,7 +97,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
     for (int64_t tl = grp; ok; tl += PROD_GROUPS) {  // local tile number; groups alternate
       const int64_t t = blockIdx.x + tl * gridDim.x;
       if (t >= ntiles) break;
-      int64_t li = (tl / PROD_GROUPS) * NB;  // index among this group's blocks
+      int64_t li = (tl / PROD_GROUPS) * S::NCHT;  // index among this group's chunks
       const int64_t e = t * BN + row;
       float u[NS][D], Pm[D][D], H[P];
       bool live = e < p.ncells, bad = false;
@@ -133,42 +146,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
             for (int c = 0; c < D; ++c) u[r][c] = (float)__ldg(p.coef + (int64_t)did[r] * D + c);
         }
       }
-#pragma unroll
-      for (int blk = 0; blk < NB; ++blk, ++li) {
-        const int ci = blk / D, cj = blk % D;
-        int s;
-        uint32_t use;
-        stage_of(li, grp, spg, s, use);
-        if (!mbar_wait(smem_u32(&bars->empty[s]), (use & 1u) ^ 1u, p.err)) { ok = false; break; }
+      // blocks and chunks as compile-time indices, so u[.][ci] and P[.][cj] stay in registers
+      static_for<NB>([&](auto BLK) -> bool {
+        constexpr int blk = decltype(BLK)::value;
+        constexpr int ci = blk / D, cj = blk % D;
+        constexpr int kblk = ci == cj ? KD : KA1;
         // factors of block (ci, cj): u[r][ci] P[a][cj] (T1 columns); on the diagonal also
         // Q[r][a] = sum_c u[r][c] P[a][c] (T2 columns) and nu H (T3 columns); zero padding
         auto factor = [&](int k) -> float {
-          if (!live) return 0.f;
-          if (k < S::K1) return u[k / D][ci] * Pm[k % D][cj];
-          if (k < KA1) return 0.f;
-          if (k < KA1 + S::K1) {
+          float v = 0.f;
+          if (!live) return v;
+          if (k < S::K1) v = u[k / D][ci] * Pm[k % D][cj];
+          else if (k < KA1) v = 0.f;
+          else if (k < KA1 + S::K1) {
             const int r = (k - KA1) / D, a = (k - KA1) % D;
-            float q = 0.f;
 #pragma unroll
-            for (int c = 0; c < D; ++c) q = fmaf(u[r][c], Pm[a][c], q);
-            return q;
-          }
-          if (k < KA1 + S::K1 + P) return H[k - KA1 - S::K1];
-          return 0.f;
+            for (int c = 0; c < D; ++c) v = fmaf(u[r][c], Pm[a][c], v);
+          } else if (k < KA1 + S::K1 + P) v = H[k - KA1 - S::K1];
+          if constexpr (AX) v *= sc[k];
+          return v;
         };
-        uint8_t* hi = sB + (size_t)s * PARTS * tile_bytes;
-        if (ci == cj)
-          store_operand_fn<PREC, KD>(hi, hi + tile_bytes, row, kbytes, factor);
-        else
-          store_operand_fn<PREC, KA1>(hi, hi + tile_bytes, row, kbytes, factor);
-        fence_proxy_async();
-        mbar_arrive(smem_u32(&bars->full[s]));
-      }
+        return static_for<(kblk + S::CW - 1) / S::CW>([&](auto CH) -> bool {
+          constexpr int ch = decltype(CH)::value;
+          int s;
+          uint32_t use;
+          stage_of(li++, grp, spg, s, use);
+          if (!mbar_wait(smem_u32(&bars->empty[s]), (use & 1u) ^ 1u, p.err)) return ok = false;
+          uint8_t* hi = sB + (size_t)s * PARTS * SPART;
+          store_chunk_fn<PREC, S::CW, S::CWB>(hi, hi + SPART, row, kblk - ch * S::CW,
+                                      [&](int l) { return factor(ch * S::CW + l); });
+          fence_proxy_async();
+          mbar_arrive(smem_u32(&bars->full[s]));
+          return true;
+        });
+      });
     }
   } else if (warp == MMA_WARP) {
     // ---------------- MMA issuer ----------------
+    // Per block: the MT accumulator slots are taken, every K-chunk of the block is
+    // contracted into them as its stage fills, then the slots are handed to the epilogue.
     if (lane == 0) {
-      const uint32_t sbo = 8u * (uint32_t)kbytes;
+      const uint32_t sbo_a = 8u * (uint32_t)kbytes, sbo_b = 8u * S::CWB;
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
       uint32_t rc = 0;
       const int spg = nstages / PROD_GROUPS;
@@ -176,35 +194,45 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
         const int grp = (int)(tl % PROD_GROUPS);
-        for (int blk = 0; blk < NB && ok; ++blk) {
-          const bool diag = (blk / D) == (blk % D);
-          const int ksteps = diag ? KD / S::KSTEP : KA1 / S::KSTEP;
-          int s;
-          uint32_t use;
-          stage_of((tl / PROD_GROUPS) * NB + blk, grp, spg, s, use);
-          if (!mbar_wait(smem_u32(&bars->full[s]), use & 1u, p.err)) { ok = false; break; }
-          tc_fence_after();
-          const uint32_t bstage = b0 + (uint32_t)(s * PARTS * tile_bytes);
-          for (int m = 0; m < S::MT; ++m, ++rc) {
-            const uint32_t slot = rc % RING, round = rc / RING;
-            if (!mbar_wait(smem_u32(&bars->tempty[slot]), (round & 1u) ^ 1u, p.err)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t d = tmem + slot * BN;
-            const uint32_t atile = a0 + (uint32_t)(m * PARTS * tile_bytes);
-            uint32_t acc = 0;
-            for (int ks = 0; ks < ksteps; ++ks) {
-              const uint32_t ko = (uint32_t)ks * 256u;
-              if constexpr (PT::split) {
-                mma<PT::tf32>(d, make_desc(atile + ko, sbo), make_desc(bstage + tile_bytes + ko, sbo), IDESC, acc);
-                acc = 1;
-                mma<PT::tf32>(d, make_desc(atile + tile_bytes + ko, sbo), make_desc(bstage + ko, sbo), IDESC, 1);
-              }
-              mma<PT::tf32>(d, make_desc(atile + ko, sbo), make_desc(bstage + ko, sbo), IDESC, acc);
-              acc = 1;
-            }
-            tc_commit(smem_u32(&bars->tfull[slot]));
+        int64_t li = (tl / PROD_GROUPS) * S::NCHT;
+        for (int blk = 0; blk < NB && ok; ++blk, rc += S::MT) {
+          const int kblk = (blk / D) == (blk % D) ? KD : KA1;
+          for (int m = 0; m < S::MT && ok; ++m) {
+            const uint32_t r = rc + m;
+            if (!mbar_wait(smem_u32(&bars->tempty[r % RING]), ((r / RING) & 1u) ^ 1u, p.err)) ok = false;
           }
-          tc_commit(smem_u32(&bars->empty[s]));
+          if (!ok) break;
+          tc_fence_after();
+          for (int ch = 0; ch * S::CW < kblk; ++ch, ++li) {
+            int s;
+            uint32_t use;
+            stage_of(li, grp, spg, s, use);
+            if (!mbar_wait(smem_u32(&bars->full[s]), use & 1u, p.err)) { ok = false; break; }
+            tc_fence_after();
+            const int ksteps = (kblk - ch * S::CW < S::CW ? kblk - ch * S::CW : S::CW) / S::KSTEP;
+            const uint32_t bstage = b0 + (uint32_t)(s * PARTS * SPART);
+            for (int m = 0; m < S::MT; ++m) {
+              const uint32_t d = tmem + ((rc + m) % RING) * BN;
+              // K-chunk ch of A: byte column ch * CWB of the row, core matrices 128 bytes apart
+              const uint32_t atile = a0 + (uint32_t)(m * APARTS * tile_bytes) + (uint32_t)ch * (S::CWB * 8u);
+              uint32_t acc = ch > 0 ? 1u : 0u;
+              for (int ks = 0; ks < ksteps; ++ks) {
+                const uint32_t ko = (uint32_t)ks * 256u;
+                if constexpr (PT::split) {
+                  mma<PT::tf32>(d, make_desc(atile + ko, sbo_a), make_desc(bstage + SPART + ko, sbo_b), IDESC, acc);
+                  acc = 1;
+                  if constexpr (!AX)
+                    mma<PT::tf32>(d, make_desc(atile + tile_bytes + ko, sbo_a), make_desc(bstage + ko, sbo_b), IDESC,
+                                  1);
+                }
+                mma<PT::tf32>(d, make_desc(atile + ko, sbo_a), make_desc(bstage + ko, sbo_b), IDESC, acc);
+                acc = 1;
+              }
+            }
+            tc_commit(smem_u32(&bars->empty[s]));
+          }
+          if (!ok) break;
+          for (int m = 0; m < S::MT; ++m) tc_commit(smem_u32(&bars->tfull[(rc + m) % RING]));
         }
       }
       tc_commit(smem_u32(&bars->done));
@@ -244,10 +272,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
             if (o < S::NBLK) {
               float* row = p.out + cbase * p.N + (int64_t)(ci * NS + i) * ndof + j;
 #pragma unroll
-              for (int jj = 0; jj < 16; ++jj)
+              for (int jj = 0; jj < 16; ++jj, row += p.N)
                 if (jj < ncol) {
 #pragma unroll
-                  for (int cj = 0; cj < D; ++cj) __stcs(row + (int64_t)jj * p.N + cj * NS, __uint_as_float(v[cj][jj]));
+                  for (int cj = 0; cj < D; ++cj) __stcs(row + cj * NS, __uint_as_float(v[cj][jj]));
                 }
             }
           }
@@ -287,13 +315,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
             if (o < S::NBLK) {
               const int i = o / NS, j = o - (o / NS) * NS;
               float* dst = p.out + cbase * p.N + (int64_t)(ci * NS + i) * ndof + cj * NS + j;
-              const int64_t stride = p.N;
 #pragma unroll
-              for (int jj = 0; jj < 32; ++jj)
-                if (jj < ncol) __stcs(dst + jj * stride, __uint_as_float(v0[jj]));
+              for (int jj = 0; jj < 32; ++jj, dst += p.N)
+                if (jj < ncol) __stcs(dst, __uint_as_float(v0[jj]));
 #pragma unroll
-              for (int jj = 0; jj < 32; ++jj)
-                if (32 + jj < ncol) __stcs(dst + (32 + jj) * stride, __uint_as_float(v1[jj]));
+              for (int jj = 0; jj < 32; ++jj, dst += p.N)
+                if (32 + jj < ncol) __stcs(dst, __uint_as_float(v1[jj]));
             }
           }
           }
@@ -316,7 +343,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
 
 template <int D, int NS, int PREC>
 cudaError_t launch_b(const TcParams& p, int num_sms, cudaStream_t s, int nst, int smem) {
-  auto kern = k_burgers_tc<D, NS, PREC>;
+  auto kern = p.aexact ? k_burgers_tc<D, NS, PREC, true> : k_burgers_tc<D, NS, PREC, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (p.ncells + BN - 1) / BN;
@@ -341,10 +368,43 @@ cudaError_t launch_bp(const TcParams& p, int num_sms, cudaStream_t s, int nst, i
 int burgers_tc_supported(int degree, int cell, int precision) {
   BGeom g;
   if (!bgeom(degree, cell, precision, g)) return 0;
-  return bstages(g) > 0 ? 1 : 0;
+  return cstages(g) > 0 ? 1 : 0;  // A in hi/lo parts: the larger of the two layouts
 }
 
-void build_burgers_image(int degree, int cell, int prec, std::vector<uint8_t>& img, TcTable& meta) {
+namespace {
+// Integer form of one A column: x[o] = n[o] * scale for all o, with integers the operand type
+// holds exactly (odd part below 2^11 for tf32, 2^8 for bf16). The smallest multiplier N of
+// x / max|x| that lands every entry on an integer (to 1e-9) is taken; the reconstruction
+// must then agree with x to 1e-13 of max|x|. False when no such N <= 2^11 exists.
+bool integer_column(const std::vector<double>& x, bool tf32, double& scale, std::vector<double>& n) {
+  double m = 0.0;
+  for (double v : x) m = std::max(m, std::fabs(v));
+  n.assign(x.size(), 0.0);
+  scale = 1.0;
+  if (m == 0.0) return true;
+  const int odd_limit = tf32 ? 2048 : 256;
+  for (int N = 1; N <= 2048; ++N) {
+    bool ok = true;
+    for (size_t o = 0; o < x.size() && ok; ++o) {
+      const double y = x[o] / m * N;
+      const double r = std::nearbyint(y);
+      if (std::fabs(y - r) > 1e-9) ok = false;
+      long long q = std::llabs((long long)r);
+      while (q && !(q & 1)) q >>= 1;
+      if (q >= odd_limit) ok = false;
+      n[o] = r;
+    }
+    if (!ok) continue;
+    scale = m / N;
+    for (size_t o = 0; o < x.size(); ++o)
+      if (std::fabs(n[o] * scale - x[o]) > 1e-13 * m) return false;
+    return true;
+  }
+  return false;
+}
+}  // namespace
+
+void build_burgers_image(int degree, int cell, int prec, bool exact_ok, std::vector<uint8_t>& img, TcTable& meta) {
   BGeom g;
   bgeom(degree, cell, prec, g);
   std::vector<double> T;
@@ -353,32 +413,52 @@ void build_burgers_image(int degree, int cell, int prec, std::vector<uint8_t>& i
   const int nb = g.ns * g.ns;
   const bool tf32 = g.elem == 4;
   const int64_t tile = (int64_t)BM * g.kbytes;
-  img.assign((size_t)(g.mtiles * g.parts * tile), 0);
+  // column k of A: the reference-tensor row feeding it, or -1 for zero padding
+  auto trow_of = [&](int k) {
+    if (k < g.K1) return k;
+    if (k >= g.KA1 && k < g.KA1 + g.K1) return g.ns * d + (k - g.KA1);
+    if (k >= g.KA1 + g.K1 && k < g.KA1 + g.K1 + P) return 2 * g.ns * d + (k - g.KA1 - g.K1);
+    return -1;
+  };
+  // exact form: every column an integer vector times a scale
+  std::vector<std::vector<double>> ints(g.KD);
+  std::vector<float> scales(g.KD, 1.0f);
+  bool exact = exact_ok && g.KD * 4 <= SCALE_BYTES;
+  for (int k = 0; k < g.KD && exact; ++k) {
+    const int tr = trow_of(k);
+    std::vector<double> col(nb, 0.0);
+    if (tr >= 0)
+      for (int o = 0; o < nb; ++o) col[o] = T[(size_t)tr * nb + o];
+    double sc = 1.0;
+    exact = integer_column(col, tf32, sc, ints[k]);
+    scales[k] = (float)sc;
+  }
+  const int aparts = exact ? 1 : g.parts;
+  const int64_t a_bytes = (int64_t)g.mtiles * aparts * tile;
+  img.assign((size_t)(a_bytes + (exact ? g.KD * 4 : 0)), 0);
   for (int m = 0; m < g.mtiles; ++m)
     for (int r = 0; r < BM; ++r) {
       const int o = m * BM + r;
       for (int k = 0; k < g.KD; ++k) {
-        int trow = -1;  // row of the reference tensor feeding A column k
-        if (k < g.K1) trow = k;
-        else if (k >= g.KA1 && k < g.KA1 + g.K1) trow = g.ns * d + (k - g.KA1);
-        else if (k >= g.KA1 + g.K1 && k < g.KA1 + g.K1 + P) trow = 2 * g.ns * d + (k - g.KA1 - g.K1);
-        const double x = (o < nb && trow >= 0) ? T[(size_t)trow * nb + o] : 0.0;
+        const int tr = trow_of(k);
+        const double x = (o >= nb || tr < 0) ? 0.0 : exact ? ints[k][o] : T[(size_t)tr * nb + o];
         const uint32_t off = canon_off(r, k * g.elem, g.kbytes);
-        uint8_t* hi = img.data() + (size_t)(m * g.parts) * tile;
+        uint8_t* hi = img.data() + (size_t)(m * aparts) * tile;
         uint8_t* lo = hi + tile;
         if (tf32) {
           const uint32_t h = host_tf32_rna((float)x);
           const uint32_t l = host_tf32_rna((float)(x - (double)host_f(h)));
           std::memcpy(hi + off, &h, 4);
-          if (g.parts == 2) std::memcpy(lo + off, &l, 4);
+          if (aparts == 2) std::memcpy(lo + off, &l, 4);
         } else {
           const uint16_t h = host_bf16_rn((float)x);
           const uint16_t l = host_bf16_rn((float)(x - (double)host_bf16_f(h)));
           std::memcpy(hi + off, &h, 2);
-          if (g.parts == 2) std::memcpy(lo + off, &l, 2);
+          if (aparts == 2) std::memcpy(lo + off, &l, 2);
         }
       }
     }
+  if (exact) std::memcpy(img.data() + a_bytes, scales.data(), (size_t)g.KD * 4);
   meta = TcTable{};
   meta.mtiles = g.mtiles;
   meta.kbytes = g.kbytes;
@@ -387,6 +467,8 @@ void build_burgers_image(int degree, int cell, int prec, std::vector<uint8_t>& i
   meta.parts = g.parts;
   meta.ksteps_off = g.KA1 / g.kstep;
   meta.tile_bytes = tile;
+  meta.aexact = exact ? 1 : 0;
+  meta.scale_off = exact ? a_bytes : 0;
 }
 
 int launch_burgers_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why) {
@@ -395,13 +477,16 @@ int launch_burgers_tc(int cell, const TcParams& p, int num_sms, void* stream, st
   BGeom g{};
   g.mtiles = p.mtiles;
   g.parts = p.parts;
+  g.aparts = p.aexact ? 1 : p.parts;
+  g.sbytes = p.aexact ? SCALE_BYTES : 0;
   g.kbytes = p.kbytes;
-  const int nst = bstages(g);
+  const int nst = cstages(g);
   if (nst == 0) {
     why = "operands do not fit in shared memory";
     return (int)cudaErrorInvalidValue;
   }
-  int smem = g.mtiles * g.parts * BM * g.kbytes + nst * g.parts * BN * g.kbytes + (int)sizeof(Barriers) + 1024 + 64;
+  int smem = g.mtiles * g.aparts * BM * g.kbytes + nst * g.parts * BN * g.kbytes + (int)sizeof(Barriers) + g.sbytes +
+             1024 + 64;
   if (smem < SMEM_ONE_CTA) smem = SMEM_ONE_CTA;
   if (cell == CELL_TRI) {
     switch (p.ns) {

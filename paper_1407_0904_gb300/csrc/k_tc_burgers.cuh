@@ -5,12 +5,25 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
+#include <utility>
+#include <type_traits>
 #include "coffee_internal.h"
 #include "tc_common.cuh"
 
 namespace coffee {
 namespace {
 using namespace tc;
+
+// Calls f(std::integral_constant<int, 0>), f(..1), .. up to N-1 while f returns true;
+// true when every call did.
+template <class F, int... I>
+__device__ __forceinline__ bool static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+  return (f(std::integral_constant<int, I>{}) && ...);
+}
+template <int N, class F>
+__device__ __forceinline__ bool static_for(F&& f) {
+  return static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
 
 template <int D, int NS, int PREC>
 struct BurgersShape {
@@ -24,6 +37,14 @@ struct BurgersShape {
   static constexpr int NBLK = NS * NS;
   static constexpr int MT = (NBLK + BM - 1) / BM;
   static constexpr int PARTS = PT::split ? 2 : 1;
+  // Jacobian kernel: the B operand of a block is staged in K-chunks of CWB bytes per row. A
+  // chunk is the whole block row: splitting it (more, smaller stages) was measured slower,
+  // every extra hand-off between producers and the MMA costing more than it overlaps.
+  static constexpr int CWB = KD * ELEM;
+  static constexpr int CW = KD;                            // columns per chunk
+  static constexpr int NCH_O = (KA1 + CW - 1) / CW;        // chunks of an off-diagonal block
+  static constexpr int NCH_D = (KD + CW - 1) / CW;         // chunks of a diagonal block
+  static constexpr int NCHT = D * NCH_D + (D * D - D) * NCH_O;  // chunks per tile
 };
 
 // One operand row (one cell): columns C0..NCOLS-1 whose k-th value is f(k), converted and
@@ -66,12 +87,50 @@ __device__ __forceinline__ void store_operand_fn(uint8_t* hi, uint8_t* lo, int r
   }
 }
 
+// One K-chunk of an operand row: columns 0..CW-1 of the chunk take f(l) for l < ncols (a
+// multiple of 4 tf32 / 8 bf16 columns; constant after unrolling) and are stored 16 bytes at a
+// time in the canonical layout of a CWB-byte row; columns past ncols are not written.
+template <int PREC, int CW, int CWB, class F>
+__device__ __forceinline__ void store_chunk_fn(uint8_t* hi, uint8_t* lo, int r, int ncols, F f) {
+  using PT = PrecTraits<PREC>;
+  constexpr int PER = PT::tf32 ? 4 : 8;  // columns per 16-byte store
+#pragma unroll
+  for (int c = 0; c < CW / PER; ++c) {
+    if (c * PER >= ncols) break;
+    uint32_t h[4], l[4];
+    if constexpr (PT::tf32) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float x = f(c * 4 + q);
+        h[q] = tf32_rna(x);
+        l[q] = tf32_rna(x - __uint_as_float(h[q]));
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float x0 = f(c * 8 + 2 * q), x1 = f(c * 8 + 2 * q + 1);
+        __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+        __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+        __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+        h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      }
+    }
+    const uint32_t off = canon_off(r, c * 16, CWB);
+    *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    if constexpr (PT::split) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
 constexpr int SMEM_LIMIT = 227 * 1024;
 constexpr int SMEM_ONE_CTA = 120 * 1024;
 
 struct BGeom {
   int ns, K1, KA1, KD, kstep, elem, parts, mtiles, kbytes;
+  int aparts;  // parts of the resident A operand (1 when A is held exactly)
+  int sbytes;  // shared-memory bytes of the A column scales (0 unless A is exact)
 };
+constexpr int SCALE_BYTES = 512;  // room for the column scales of any compiled shape
 
 bool bgeom(int degree, int cell, int prec, BGeom& g) {
   if (prec == PREC_FP64 || prec < 0 || prec > PREC_BF16X3) return false;
@@ -88,14 +147,26 @@ bool bgeom(int degree, int cell, int prec, BGeom& g) {
   g.parts = (prec == PREC_TF32X3 || prec == PREC_BF16X3) ? 2 : 1;
   g.mtiles = (g.ns * g.ns + BM - 1) / BM;
   g.kbytes = g.KD * g.elem;
+  g.aparts = g.parts;
+  g.sbytes = 0;
   return true;
 }
 
 int bstages(const BGeom& g) {
-  const int a = g.mtiles * g.parts * BM * g.kbytes;
+  const int a = g.mtiles * g.aparts * BM * g.kbytes;
   const int b = g.parts * BN * g.kbytes;
-  const int fixed = a + (int)sizeof(Barriers) + 1024 + 64;
+  const int fixed = a + (int)sizeof(Barriers) + g.sbytes + 1024 + 64;
   int s = MAX_STAGES;  // even: the stages are split between the two producer groups
+  while (s >= 2 && fixed + s * b > SMEM_LIMIT) s -= 2;
+  return s >= 2 ? s : 0;
+}
+
+// Stages of the Jacobian kernel: PARTS x BN x CWB bytes each (CWB = kbytes), an even count.
+int cstages(const BGeom& g) {
+  const int a = g.mtiles * g.aparts * BM * g.kbytes;
+  const int b = g.parts * BN * g.kbytes;
+  const int fixed = a + (int)sizeof(Barriers) + g.sbytes + 1024 + 64;
+  int s = MAX_STAGES;
   while (s >= 2 && fixed + s * b > SMEM_LIMIT) s -= 2;
   return s >= 2 ? s : 0;
 }

@@ -307,6 +307,7 @@ int launch_burgers_res_tc(int cell, const TcParams& p, int num_sms, void* stream
   BGeom g{};
   g.mtiles = p.mtiles;
   g.parts = p.parts;
+  g.aparts = p.parts;
   g.kbytes = p.kbytes;
   int nst = bstages(g);
   if (nst == 0) {
