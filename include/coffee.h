@@ -232,6 +232,12 @@ int coffee_assemble_backward_noalloc(const coffee_assemble_args* a, const void* 
  *   grid <= 0 selects one CTA per SM; item_overhead < 0 selects the default (16384). */
 int coffee_batch_plan(const coffee_assemble_args* groups, int ngroups, int grid, double item_overhead,
                       void** plan);
+/* The same plan with a measured cost per group instead of the byte model:
+ *   tile_cost  host [ngroups], the cost of one full 128-cell tile of group i in any unit
+ *              (e.g. its measured time); a ragged tile costs cells/128 of it. Every entry must
+ *              be positive and finite, else COFFEE_ERR_INVALID_ARG. Not retained. */
+int coffee_batch_plan_costs(const coffee_assemble_args* groups, int ngroups, int grid, const double* tile_cost,
+                            void** plan);
 int coffee_batch_launch(void* plan, coffee_stream_t stream);
 void coffee_batch_free(void* plan);
 

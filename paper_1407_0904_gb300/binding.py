@@ -375,12 +375,21 @@ class BatchPlan:
 
     groups: list of dicts with keys form, degree, cell, coords, cell2vert and optionally
     coef, cell2dof, out. All groups use `precision` (a tensor-core precision).
-    launch() only enqueues one kernel on the current stream (CUDA-graph capturable)."""
+    launch() only enqueues one kernel on the current stream (CUDA-graph capturable).
 
-    def __init__(self, groups, precision=TF32X3, grid=0, item_overhead=-1.0, validate=False):
+    Work is split over the CTAs by cost. costs="measured" (default) takes each group's time
+    per 128-cell tile from the autotuner's cache for this GPU (coffee_batch_plan_costs) and
+    falls back to the byte model (bytes written + item_overhead per 128-output slice,
+    coffee_batch_plan) when a group is not in the cache; costs="bytes" forces the byte
+    model; a list gives one tile cost per group."""
+
+    def __init__(self, groups, precision=TF32X3, grid=0, item_overhead=-1.0, validate=False,
+                 costs="measured"):
         L = lib()
         L.coffee_batch_plan.argtypes = [ctypes.POINTER(AssembleArgs), ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]
+        L.coffee_batch_plan_costs.argtypes = [ctypes.POINTER(AssembleArgs), ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p)]
         L.coffee_batch_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.coffee_batch_free.argtypes = [ctypes.c_void_p]
         self._keep = []
@@ -399,8 +408,38 @@ class BatchPlan:
                 item_overhead = float(_tune.load_batch().get("item_overhead", -1.0))
             except Exception:
                 item_overhead = -1.0
+        if isinstance(costs, str):
+            costs = self.measured_costs(groups, precision) if costs == "measured" else None
+        self.costs = costs
         self._plan = ctypes.c_void_p()
-        _check(L.coffee_batch_plan(arr, len(groups), grid, item_overhead, ctypes.byref(self._plan)))
+        if costs is not None:
+            c = (ctypes.c_double * len(groups))(*[float(x) for x in costs])
+            _check(L.coffee_batch_plan_costs(arr, len(groups), grid, c, ctypes.byref(self._plan)))
+        else:
+            _check(L.coffee_batch_plan(arr, len(groups), grid, item_overhead, ctypes.byref(self._plan)))
+
+    @staticmethod
+    def measured_costs(groups, precision):
+        """Per-group cost of a 128-cell tile from the autotuner's cache for this GPU: the batch
+        kernel's own time per tile for that group shape (tune --batch-tiles) when every group has
+        one, else the group's tuned single-group kernel time per tile; None if neither covers
+        every group."""
+        try:
+            from . import tune as _tune
+            entries = _tune.load_cache() or {}
+            tiles = _tune.load_batch().get("tile_ms", {}) if entries else {}
+        except Exception:
+            return None
+        keys = ["%d/%d/%d/%d" % (g["form"], g["degree"], g["cell"], precision) for g in groups]
+        if all(tiles.get(k, 0) > 0 for k in keys):
+            return [float(tiles[k]) for k in keys]
+        out = []
+        for k in keys:
+            ent = entries.get(k)
+            if not ent or not ent.get("ms") or not ent.get("ncells"):
+                return None
+            out.append(float(ent["ms"]) * 128.0 / float(ent["ncells"]))
+        return out
 
     def launch(self, stream=None):
         _check(lib().coffee_batch_launch(self._plan, _stream_handle(stream)))

@@ -2,6 +2,7 @@
 // validation, the per-device cache of reference tensors, and kernel dispatch.
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -533,8 +534,11 @@ struct BatchPlanImpl {
 };
 }  // namespace
 
-int coffee_batch_plan(const coffee_assemble_args* groups, int ngroups, int grid, double item_overhead,
-                      void** plan) {
+namespace {
+// Plan shared by both entry points: tile_cost (per group, one full 128-cell tile) when given,
+// else bytes written + item_overhead per 128-output slice.
+int batch_plan_impl(const coffee_assemble_args* groups, int ngroups, int grid, double item_overhead,
+                    const double* tile_cost, void** plan) {
   if (!plan) return fail(COFFEE_ERR_INVALID_ARG, "plan is NULL");
   *plan = nullptr;
   if (!groups || ngroups <= 0) return fail(COFFEE_ERR_INVALID_ARG, "no groups");
@@ -590,7 +594,8 @@ int coffee_batch_plan(const coffee_assemble_args* groups, int ngroups, int grid,
     const int64_t nt = (a->ncells + 127) / 128;
     for (int64_t t = 0; t < nt; ++t) {
       const int64_t cells = std::min<int64_t>(128, a->ncells - t * 128);
-      cost.push_back(4.0 * (double)cells * g.p.N + item_overhead * meta.mtiles);
+      cost.push_back(tile_cost ? tile_cost[i] * (double)cells / 128.0
+                               : 4.0 * (double)cells * g.p.N + item_overhead * meta.mtiles);
     }
     items += nt;
   }
@@ -638,6 +643,21 @@ int coffee_batch_plan(const coffee_assemble_args* groups, int ngroups, int grid,
   P->L.err = c->err;
   *plan = P;
   return COFFEE_OK;
+}
+}  // namespace
+
+int coffee_batch_plan(const coffee_assemble_args* groups, int ngroups, int grid, double item_overhead,
+                      void** plan) {
+  return batch_plan_impl(groups, ngroups, grid, item_overhead, nullptr, plan);
+}
+
+int coffee_batch_plan_costs(const coffee_assemble_args* groups, int ngroups, int grid, const double* tile_cost,
+                            void** plan) {
+  if (!tile_cost) return fail(COFFEE_ERR_INVALID_ARG, "tile_cost is NULL");
+  for (int i = 0; i < ngroups; ++i)
+    if (!(tile_cost[i] > 0.0) || !std::isfinite(tile_cost[i]))
+      return fail(COFFEE_ERR_INVALID_ARG, "tile_cost must be positive and finite");
+  return batch_plan_impl(groups, ngroups, grid, -1.0, tile_cost, plan);
 }
 
 int coffee_batch_launch(void* plan, coffee_stream_t stream) {

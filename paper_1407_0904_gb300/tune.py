@@ -143,6 +143,50 @@ def tune_all(forms=None, cells=(0, 1), degrees=(1, 2, 3, 4), precisions=None, nc
     return entries
 
 
+def tune_batch_tiles(ncells=2 ** 17, precisions=None, reps=20, log=print):
+    """Time per 128-cell tile (ms, on one SM) of every group shape inside the batch kernel:
+    each (form, degree, cell) runs alone as a one-group batch of `ncells` cells. These are the
+    per-group costs BatchPlan splits the work by (costs="measured")."""
+    import torch
+    from . import binding as coffee
+    from . import meshgen
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    precisions = precisions or (coffee.TF32X3,)
+    out = {}
+    for cell in (0, 1):
+        m = _mesh(cell, ncells)
+        x, c2v = torch.from_numpy(m.coords).to(dev), torch.from_numpy(m.cell2vert).to(dev)
+        coef, c2d, _ = meshgen.advdiff_coefficients(m, seed=4)
+        cf, cd = torch.from_numpy(coef).to(dev), torch.from_numpy(c2d).to(dev)
+        for form in (coffee.MASS, coffee.HELMHOLTZ, coffee.ADVDIFF):
+            for k in (1, 2, 3, 4):
+                for prec in precisions:
+                    g = dict(form=form, degree=k, cell=cell, coords=x, cell2vert=c2v)
+                    if form == coffee.ADVDIFF:
+                        g["coef"], g["cell2dof"] = cf, cd
+                    try:
+                        plan = coffee.BatchPlan([g], precision=prec, costs="bytes")
+                    except coffee.CoffeeError:
+                        continue  # shape not covered by the batch kernel
+                    for _ in range(3):
+                        plan.launch()
+                    torch.cuda.synchronize()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    for _ in range(reps):
+                        plan.launch()
+                    b.record()
+                    torch.cuda.synchronize()
+                    ms = a.elapsed_time(b) / reps
+                    plan.free()
+                    tiles = (m.ncells + 127) // 128
+                    key = "%d/%d/%d/%d" % (form, k, cell, prec)
+                    out[key] = ms * min(tiles, nsm) / tiles
+                    log("batch tile %s: %.3f us per tile (%.4f ms for %d cells)" % (key, out[key] * 1e3, ms, m.ncells))
+    return out
+
+
 def tune_batch(ncells_per_mesh=2 ** 17, log=print):
     """Per-item overhead of the batch plan's cost model, timed on a mixed batch."""
     import torch
@@ -170,7 +214,7 @@ def tune_batch(ncells_per_mesh=2 ** 17, log=print):
             groups.append(g)
     times = {}
     for ovh in (0.0, 4096.0, 16384.0, 65536.0, 262144.0):
-        plan = coffee.BatchPlan(groups, item_overhead=ovh)
+        plan = coffee.BatchPlan(groups, item_overhead=ovh, costs="bytes")
         for _ in range(3):
             plan.launch()
         torch.cuda.synchronize()
@@ -244,12 +288,24 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--out", default=None)
     ap.add_argument("--study", action="store_true", help="cost model vs the cached tuned choices (no GPU)")
+    ap.add_argument("--batch-tiles", action="store_true",
+                    help="only (re)measure the batch kernel's per-group tile costs into the existing cache")
     args = ap.parse_args(argv)
     if args.study:
         study()
         return 0
+    if args.batch_tiles:
+        with open(cache_path()) as f:
+            data = json.load(f)
+        data.setdefault("batch", {})["tile_ms"] = tune_batch_tiles()
+        out = args.out or cache_path()
+        with open(out, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        print("wrote", out)
+        return 0
     entries = tune_all(ncells=args.ncells, reps=args.reps)
     batch = tune_batch()
+    batch["tile_ms"] = tune_batch_tiles()
     data = {"version": CACHE_VERSION, "gpu": _gpu_name(), "entries": entries, "batch": batch}
     out = args.out or cache_path()
     with open(out, "w") as f:

@@ -61,6 +61,16 @@ def test_host_argument_errors_before_any_launch():
     a.coords = a.cell2vert = a.out = 16  # non-NULL, never dereferenced on the host
     assert lib.coffee_assemble_ex(ctypes.byref(a), None) == -1  # advdiff without coefficients
     assert lib.coffee_tabulate(5, 1, 2, None, None, None, None, None, None) == -1
+    # weighted batch plans reject missing or non-positive tile costs before touching a device
+    plan = ctypes.c_void_p()
+    P = ctypes.c_void_p
+    lib.coffee_batch_plan_costs.argtypes = [ctypes.POINTER(coffee.binding.AssembleArgs), ctypes.c_int,
+                                            ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(P)]
+    one = (coffee.binding.AssembleArgs * 1)(a)
+    assert lib.coffee_batch_plan_costs(one, 1, 0, None, ctypes.byref(plan)) == -1
+    for bad in (0.0, -1.0, float("inf"), float("nan")):
+        assert lib.coffee_batch_plan_costs(one, 1, 0, (ctypes.c_double * 1)(bad), ctypes.byref(plan)) == -1
+        assert b"tile_cost" in lib.coffee_last_error()
     assert lib.coffee_ndof(0, 9, 0) == -1
 
 

@@ -72,7 +72,14 @@ def test_batch_plan_options_do_not_change_results():
     dev, groups = make_batch(tri, tet, seed=6)
     a = [o.clone() for o in coffee.BatchPlan(groups).launch()]
     for grid, ovh in [(7, 0.0), (1, 1e6), (300, -1.0)]:
-        b = coffee.BatchPlan(groups, grid=grid, item_overhead=ovh).launch()
+        b = coffee.BatchPlan(groups, grid=grid, item_overhead=ovh, costs="bytes").launch()
+        torch.cuda.synchronize()
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    # measured tile costs (coffee_batch_plan_costs): other splits, the same matrices
+    rng = np.random.default_rng(1)
+    for grid, costs in [(0, "measured"), (5, list(rng.uniform(0.1, 10.0, len(groups)))), (0, [1.0] * len(groups))]:
+        b = coffee.BatchPlan(groups, grid=grid, costs=costs).launch()
         torch.cuda.synchronize()
         for x, y in zip(a, b):
             assert torch.equal(x, y)
