@@ -589,6 +589,7 @@ int batch_plan_impl(const coffee_assemble_args* groups, int ngroups, int grid, d
     g.form = a->form;
     g.cell = a->cell;
     g.degree = a->degree;
+    g.lanes = g.p.N <= 32 ? 1 : 0;
     kbytes_max = std::max(kbytes_max, meta.kbytes);
     parts = meta.parts;
     const int64_t nt = (a->ncells + 127) / 128;

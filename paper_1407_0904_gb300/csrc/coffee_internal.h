@@ -163,7 +163,8 @@ int launch_burgers_res_tc(int cell, const TcParams& p, int num_sms, void* stream
 struct BatchGroup {
   TcParams p;      // the group's inputs, output, table image, N, mtiles, kbytes
   int64_t item0;   // first work item (128-cell tile) of the group in the work list
-  int form, cell, degree, pad;
+  int form, cell, degree;
+  int lanes;       // 1: cells on the TMEM lanes (element matrices of at most 32 entries)
 };
 struct BatchLaunch {
   const BatchGroup* groups;  // device

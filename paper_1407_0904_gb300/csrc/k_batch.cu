@@ -6,13 +6,16 @@
 // parameters (section 4's cost-model figure). Here every group's cells are cut into
 // 128-cell tiles, the tiles of all groups form one work list, and each CTA takes a
 // contiguous, cost-balanced range of it (host plan). Per work item:
-//   producer warps 8..11  compute the group's factors G_e (runtime switch over form and
+//   producer warps 4..11  compute the group's factors G_e (runtime switch over form and
 //                         cell shape) into a B-operand stage laid out with that group's K;
 //   loader warp 13        streams the group's T^T operand, one 128-output M-tile at a
 //                         time, from global memory (L2-resident) into a two-slot ring with
 //                         cp.async.bulk, completion tracked by transaction-count mbarriers;
 //   MMA warp 12           issues tcgen05.mma per M-tile into the TMEM ring;
-//   epilogue warps 0..7   store the element matrices into the group's output.
+//   epilogue warps 0..3   store the element matrices into the group's output.
+// Groups of at most 32 entries put the cells on the TMEM lanes (D[cell][o] = G T, operands
+// swapped, N = outputs rounded up to 16), so all four epilogue warps write whole rows; the
+// others keep the outputs on the lanes (D[o][cell], 128-byte warp stores per cell).
 // Groups therefore need not share K, N or tables, and no group's table has to fit in
 // shared memory beside the others. All waits are bounded as in k_tc.cu.
 #include <cuda_runtime.h>
@@ -82,7 +85,6 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
                                            int64_t it1, int nstages, int kbytes_max, unsigned* err) {
   using PT = PrecTraits<PREC>;
   constexpr int PARTS = PT::split ? 2 : 1;
-  constexpr uint32_t IDESC = make_idesc(PT::tf32 ? 2 : 1, BM, BN);
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int slot_bytes = PARTS * BM * kbytes_max;  // one A slot or one B stage
@@ -195,6 +197,8 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
         const BatchGroup& g = groups[group_of(groups, ngroups, it)];
         const int kb = g.p.kbytes, ksteps = kb / 32;
         const uint32_t sbo = 8u * (uint32_t)kb, part = (uint32_t)(BM * kb);
+        const bool lanes = g.lanes != 0;
+        const uint32_t idesc = make_idesc(PT::tf32 ? 2 : 1, BM, lanes ? ((g.p.N + 15) & ~15) : BN);
         int s;
         uint32_t use;
         stage_of(k / PROD_GROUPS, k % PROD_GROUPS, nstages / PROD_GROUPS, s, use);
@@ -209,15 +213,20 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
           tc_fence_after();
           const uint32_t d = tmem + slot * BN;
           const uint32_t atile = a0 + j * (uint32_t)slot_bytes;
+          // outputs on lanes: A = T^T slice, B = G stage; cells on lanes: A = G, B = T^T
+          const uint32_t xo = lanes ? bstage : atile, xc = lanes ? atile : bstage;
           uint32_t acc = 0;
           for (int ks = 0; ks < ksteps; ++ks) {
             const uint32_t ko = (uint32_t)ks * 256u;
             if constexpr (PT::split) {
-              mma<PT::tf32>(d, make_desc(atile + ko, sbo), make_desc(bstage + part + ko, sbo), IDESC, acc);
+              // small terms first: T_hi G_lo, T_lo G_hi, then T_hi G_hi
+              const uint32_t ahl = lanes ? xo + part : xo, bhl = lanes ? xc : xc + part;
+              mma<PT::tf32>(d, make_desc(ahl + ko, sbo), make_desc(bhl + ko, sbo), idesc, acc);
               acc = 1;
-              mma<PT::tf32>(d, make_desc(atile + part + ko, sbo), make_desc(bstage + ko, sbo), IDESC, 1);
+              const uint32_t alh = lanes ? xo : xo + part, blh = lanes ? xc + part : xc;
+              mma<PT::tf32>(d, make_desc(alh + ko, sbo), make_desc(blh + ko, sbo), idesc, 1);
             }
-            mma<PT::tf32>(d, make_desc(atile + ko, sbo), make_desc(bstage + ko, sbo), IDESC, acc);
+            mma<PT::tf32>(d, make_desc(xo + ko, sbo), make_desc(xc + ko, sbo), idesc, acc);
             acc = 1;
           }
           tc_commit(smem_u32(&bars->tfull[slot]));
@@ -237,6 +246,40 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
     for (int64_t it = it0; it < it1 && ok; ++it) {
       const BatchGroup& g = groups[group_of(groups, ngroups, it)];
       const int N = g.p.N;
+      if (g.lanes) {
+        // cells on lanes: thread = cell, its row of N <= 32 outputs from one TMEM load
+        const uint32_t slot = rc % RING, round = rc / RING;
+        ++rc;
+        if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, err)) { ok = false; break; }
+        tc_fence_after();
+        const int64_t c0 = (it - g.item0) * BN + q * 32;
+        if (c0 < g.p.ncells) {  // warp-uniform
+          uint32_t v[32];
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + slot * BN;
+          if (N > 16) tmem_ld32(taddr, v);
+          else tmem_ld16(taddr, *reinterpret_cast<uint32_t(*)[16]>(v));
+          tmem_wait_ld();
+          if (c0 + lane < g.p.ncells) {
+            float* row = g.p.out + (c0 + lane) * N;
+            if ((N & 3) == 0 && (reinterpret_cast<uintptr_t>(g.p.out) & 15) == 0) {
+#pragma unroll
+              for (int k4 = 0; k4 < 8; ++k4)
+                if (4 * k4 < N)
+                  __stcs(reinterpret_cast<float4*>(row + 4 * k4),
+                         make_float4(__uint_as_float(v[4 * k4]), __uint_as_float(v[4 * k4 + 1]),
+                                     __uint_as_float(v[4 * k4 + 2]), __uint_as_float(v[4 * k4 + 3])));
+            } else {
+#pragma unroll
+              for (int k = 0; k < 32; ++k)
+                if (k < N) __stcs(row + k, __uint_as_float(v[k]));
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
+        continue;
+      }
       for (int m = 0; m < g.p.mtiles; ++m, ++rc) {
         const uint32_t slot = rc % RING, round = rc / RING;
         if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, err)) { ok = false; break; }
