@@ -38,7 +38,21 @@ TRAFFIC = {"30371560e4b53eac": 2.489e9}  # 31.86 MB read + 2.457 GB written per 
 
 MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC, BURGERS_RESIDUAL = 0, 1, 2, 3, 4
 TRIANGLE, TETRAHEDRON, PRISM = 0, 1, 2
-FP64_PEAK_TFLOPS = 1.25  # FP64 FMA throughput measured on this GPU model by a standalone probe
+_DEVICE_PEAKS = {}
+
+
+def device_peaks(coffee):
+    """FP64 FMA and tcgen05 MMA rates of this GPU, measured by the library's own loops
+    (coffee_peak_fp64 / coffee_peak_mma): the FP64 and tensor-core roofline denominators,
+    which the measured-peaks file (copy bandwidth, cuBLAS bf16) does not give."""
+    if not _DEVICE_PEAKS:
+        _DEVICE_PEAKS.update({
+            "fp64_tflops": coffee.peak_fp64(),
+            "tf32_tflops": coffee.peak_mma(coffee.TF32, 256),
+            "tf32_n128_tflops": coffee.peak_mma(coffee.TF32, 128),
+            "bf16_tflops": coffee.peak_mma(coffee.BF16, 256),
+            "source": "coffee_peak_fp64 / coffee_peak_mma (M=128, N=256 and 128, one CTA per SM)"})
+    return _DEVICE_PEAKS
 
 
 class Workload:
@@ -399,7 +413,8 @@ def run_ours(args):
             "traffic": traffic, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "alg_bytes_per_cell": per_cell, "kernel_ms": launch_ms}
     if prec == coffee.FP64:
-        roof["note"] = "FP64 kernel: bound by the FP64 ALU (1.25 TFLOP/s measured); HBM fraction for context"
+        roof["note"] = ("FP64 kernel: bound by the FP64 ALU (%.2f TFLOP/s measured by coffee_peak_fp64); "
+                        "HBM fraction for context" % device_peaks(coffee)["fp64_tflops"])
     if cell == PRISM:
         # non-affine cells: the contraction over all quadrature points (K = KQ Q) dominates
         Q = (degree + 2) ** 3
@@ -407,9 +422,10 @@ def run_ours(args):
         flops = 2.0 * K * ndof * ndof + 250.0 * Q  # algorithmic, per cell
         if prec == coffee.FP64:
             tf = flops * ncells / (launch_ms / 1e3) / 1e12
-            roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "FP64 FMA probe (not in the measured-peaks file)", "flops_per_cell": flops,
+            p64 = device_peaks(coffee)["fp64_tflops"]
+            roof = {"bound": "alu", "achieved": tf, "peak": p64, "unit": "TFLOP/s",
+                    "frac": tf / p64, "traffic": None,
+                    "peak_source": "FP64 FMA loop measured on this GPU (coffee_peak_fp64)", "flops_per_cell": flops,
                     "kernel_ms": launch_ms, "hbm_gbs": achieved}
         else:
             # tensor pipe: executed MMA flops (K padded to the 64-byte chunk, outputs to 128-row
@@ -420,12 +436,15 @@ def run_ours(args):
             npad = -(-(ndof * ndof) // 128) * 128
             passes = 3 if prec in (coffee.TF32X3, coffee.BF16X3) else 1
             executed = 2.0 * kpad * npad * passes
-            bf16 = float(peaks.get("bf16_tflops", 1990.0))
-            peak_t = bf16 * (1.1 / 2.25) if tf32 else bf16
+            if tf32:
+                peak_t = device_peaks(coffee)["tf32_tflops"]
+                src = "tcgen05 kind::tf32 loop measured on this GPU (coffee_peak_mma, N=256)"
+            else:
+                peak_t = float(peaks.get("bf16_tflops", 1990.0))
+                src = "measured bf16 (cuBLAS)"
             tf = executed * ncells / (launch_ms / 1e3) / 1e12
             roof = {"bound": "tensor", "achieved": tf, "peak": peak_t, "unit": "TFLOP/s", "frac": tf / peak_t,
-                    "traffic": None, "peak_source": ("measured bf16 x nominal tf32/bf16 ratio 1.1/2.25" if tf32
-                                                     else "measured bf16"),
+                    "traffic": None, "peak_source": src,
                     "executed_flops_per_cell": executed, "algorithmic_flops_per_cell": flops,
                     "kernel_ms": launch_ms, "hbm_gbs": achieved}
 
@@ -484,7 +503,7 @@ def run_ours(args):
                 "roofline": roof, "max_rel_err_vs_oracle": max_err, "fp64_kernel": fp64,
                 "tc_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
                 "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": args.steps,
-                "clocks": clocks, "kernel_sha": sha}
+                "clocks": clocks, "kernel_sha": sha, "device_peaks": device_peaks(coffee)}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -15,7 +15,7 @@ LIB = os.path.join(PKG, "libcoffee.so")
 
 CU_SOURCES = ["api.cu", "k_fp64.cu", "k_tc.cu", "k_tc_burgers.cu", "k_bwd.cu", "noalloc.cu", "k_batch.cu",
               "k_csr.cu", "k_tc_csr.cu", "k_tc_burgers_res.cu",
-              "k_prism.cu", "k_prism_tc.cu"]
+              "k_prism.cu", "k_prism_tc.cu", "k_peaks.cu"]
 CPP_SOURCES = ["tabulate.cpp"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"] + GENCODE
@@ -41,7 +41,7 @@ def build(force=False, verbose=False, extra_nvcc=()):
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in CU_SOURCES + CPP_SOURCES]
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))] + \
-        [os.path.join(PKG, "..", "include", "coffee.h"), os.path.abspath(__file__)]
+        [os.path.join(PKG, "..", "include", f) for f in ("coffee.h", "coffee_peaks.h")] + [os.path.abspath(__file__)]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(p) <= t for p in deps if os.path.exists(p)):

@@ -141,6 +141,25 @@ def reference_tensor(form, degree, cell):
     return T
 
 
+def peak_fp64():
+    """Measured FP64 FMA rate of the current GPU in TFLOP/s (coffee_peak_fp64)."""
+    L = lib()
+    L.coffee_peak_fp64.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    v = ctypes.c_double()
+    _check(L.coffee_peak_fp64(ctypes.byref(v)))
+    return v.value
+
+
+def peak_mma(precision=TF32, n=256):
+    """Measured tcgen05 MMA rate (M=128, N=n, one 32-byte K-step per instruction) in TFLOP/s
+    for precision TF32 (kind::tf32) or BF16 (kind::f16) (coffee_peak_mma)."""
+    L = lib()
+    L.coffee_peak_mma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    v = ctypes.c_double()
+    _check(L.coffee_peak_mma(int(precision), int(n), ctypes.byref(v)))
+    return v.value
+
+
 def _dev(t, dtype, name):
     if t is None:
         return None
