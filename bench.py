@@ -92,6 +92,10 @@ def _tri64(mg, nx):
     return mg.tri_mesh(nx or 64, perturb=0.2, seed=1)
 
 
+def _tri1024(mg, nx):
+    return mg.tri_mesh(nx or 1024, perturb=0.2, seed=1)
+
+
 WORKLOADS = {}
 for _k in (1, 2, 3, 4):
     WORKLOADS["helmholtz-p%d-tet" % _k] = Workload(
@@ -115,6 +119,9 @@ WORKLOADS["advdiff-p2-prism"] = Workload("advdiff-p2-prism", ADVDIFF, 2, PRISM,
                                          "b~U[-1,1]^3 per vertex", _prism48)
 WORKLOADS["helmholtz-p1-tri"] = Workload("helmholtz-p1-tri", HELMHOLTZ, 1, TRIANGLE,
                                          "unit square 64x64x2 triangles perturbed 0.2h (seed 1)", _tri64)
+# the same problem at a size where HBM, not the launch, sets the time (its roofline fraction)
+WORKLOADS["helmholtz-p1-tri-1024"] = Workload("helmholtz-p1-tri-1024", HELMHOLTZ, 1, TRIANGLE,
+                                              "unit square 1024x1024x2 triangles perturbed 0.2h (seed 1)", _tri1024)
 
 
 # workloads with their own step (not a single-group forward launch)
@@ -399,6 +406,34 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = reduce_over_ranks(ncells * args.steps, world, "sum", dev) / (total_ms / 1e3)
 
+    # launch-bound sizes (output under 64 MB): the kernel's own rate, from a CUDA graph of 100
+    # launches replayed 10 times, so host launch overhead is out of the measurement
+    graph = None
+    if ncells * out_entries(wl, ndof) * out_bytes < (64 << 20):
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                step(prec, out)
+        stream.wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(100):
+                step(prec, out)
+        g.replay()
+        torch.cuda.synchronize()
+        ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ga.record(stream)
+        for _ in range(10):
+            g.replay()
+        gb.record(stream)
+        torch.cuda.synchronize()
+        gms = ga.elapsed_time(gb)
+        graph = {"launches": 1000, "value": ncells * 1000 / (gms / 1e3), "unit": UNIT,
+                 "us_per_launch": gms, "note": "CUDA-graph replay; the step loop above includes host launch cost"}
+        del g
+        coffee.check_errors()
+
     # roofline of the dominant (only) kernel: algorithmic bytes per launch / launch time
     per_cell = alg_bytes_per_cell(wl, mesh, c2d_np, coef_np, ndof, out_bytes)
     achieved = per_cell * ncells / (launch_ms / 1e3) / 1e9
@@ -503,7 +538,8 @@ def run_ours(args):
                 "roofline": roof, "max_rel_err_vs_oracle": max_err, "fp64_kernel": fp64,
                 "tc_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
                 "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": args.steps,
-                "clocks": clocks, "kernel_sha": sha, "device_peaks": device_peaks(coffee)}
+                "clocks": clocks, "kernel_sha": sha, "device_peaks": device_peaks(coffee),
+                "graph_replay": graph}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
