@@ -41,7 +41,7 @@ def build(force=False, verbose=False, extra_nvcc=()):
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in CU_SOURCES + CPP_SOURCES]
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))] + \
-        [os.path.join(PKG, "..", "include", f) for f in ("coffee.h", "coffee_peaks.h")] + [os.path.abspath(__file__)]
+        [os.path.join(PKG, "..", "include", f) for f in ("coffee.h", "coffee_peaks.h", "coffee_diag.h")] + [os.path.abspath(__file__)]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(p) <= t for p in deps if os.path.exists(p)):

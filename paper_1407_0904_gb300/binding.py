@@ -141,6 +141,14 @@ def reference_tensor(form, degree, cell):
     return T
 
 
+def diag_wait_timeout(stream=None):
+    """Enqueue the diagnostic wait that runs out (coffee_diag_wait_timeout); the next
+    check_errors() raises CoffeeError with COFFEE_ERR_TIMEOUT."""
+    L = lib()
+    L.coffee_diag_wait_timeout.argtypes = [ctypes.c_void_p]
+    _check(L.coffee_diag_wait_timeout(_stream_handle(stream)))
+
+
 def peak_fp64():
     """Measured FP64 FMA rate of the current GPU in TFLOP/s (coffee_peak_fp64)."""
     L = lib()

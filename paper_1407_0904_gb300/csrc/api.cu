@@ -10,6 +10,7 @@
 #include <tuple>
 #include <vector>
 #include "../../include/coffee.h"
+#include "../../include/coffee_diag.h"
 #include "coffee_internal.h"
 
 namespace coffee {
@@ -524,6 +525,18 @@ int coffee_check_errors(coffee_stream_t stream) {
 }
 
 const char* coffee_last_error(void) { return g_last_error.c_str(); }
+
+int coffee_diag_wait_timeout(coffee_stream_t stream) {
+  DeviceCache* c = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    int rc = device_cache(&c);
+    if (rc != COFFEE_OK) return rc;
+  }
+  cudaError_t e = (cudaError_t)launch_diag_wait(c->err, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "launch(diag_wait)");
+  return COFFEE_OK;
+}
 
 namespace {
 struct BatchPlanImpl {

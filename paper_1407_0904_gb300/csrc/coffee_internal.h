@@ -174,6 +174,8 @@ struct BatchLaunch {
   unsigned* err;
 };
 int batch_smem(int kbytes_max, int parts, int* nstages);
+// diagnostic bounded wait that runs out (k_peaks.cu)
+int launch_diag_wait(unsigned* err, void* stream);
 int batch_prepare(int precision, int smem);
 int batch_launch(const BatchLaunch& L, void* stream);
 int stream_one_supported(int form, int kbytes, int parts);

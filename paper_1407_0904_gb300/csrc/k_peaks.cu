@@ -1,7 +1,7 @@
 // Throughput microbenchmarks of this GPU: the FP64 FMA rate and the tcgen05 MMA rate
 // (kind::tf32 and kind::f16 with bf16), the denominators of the FP64 and tensor-core
-// rooflines that the measured copy/GEMM peaks do not provide. Measurement tools only; no
-// assembly path calls them.
+// rooflines that the measured copy/GEMM peaks do not provide; and the diagnostic wait that
+// runs out. Tools only; no assembly path calls them.
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "../../include/coffee.h"
@@ -74,6 +74,18 @@ __global__ void __launch_bounds__(128, 1) k_peak_mma(int iters, unsigned* err) {
   }
 }
 
+// One thread waits on an mbarrier that nothing arrives at, through the library's bounded wait:
+// it gives up after the bound, sets the timeout bit of the error word and returns.
+__global__ void k_diag_wait(unsigned* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, err);
+}
+
 template <class L>
 int time_launch(L launch, float* ms) {
   cudaEvent_t a, b;
@@ -102,6 +114,12 @@ int run_mma(int sms, int iters, unsigned* err, float* ms) {
 }
 
 }  // namespace
+
+int launch_diag_wait(unsigned* err, void* stream) {
+  k_diag_wait<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(err);
+  return (int)cudaGetLastError();
+}
+
 }  // namespace coffee
 
 using namespace coffee;
