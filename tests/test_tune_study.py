@@ -27,3 +27,26 @@ def test_study_covers_every_tuned_entry_and_the_model_is_close():
                                      (400, 0), (1225, 0)])
 def test_model_rules(n, flags):
     assert tune.model_flags(n) == flags
+
+
+def test_batch_costs_prefer_in_batch_tile_times(monkeypatch):
+    """BatchPlan's measured costs: the batch kernel's own per-tile time for every group when the
+    cache has them, else the single-group kernel's time per 128-cell tile, else None (the plan
+    then falls back to the byte model)."""
+    entries = {"1/2/1/2": {"ms": 0.05, "ncells": 2 ** 19, "flags": 0},
+               "0/1/0/2": {"ms": 0.03, "ncells": 2 ** 19, "flags": 0}}
+    tiles = {"1/2/1/2": 0.0025, "0/1/0/2": 0.0022}
+    monkeypatch.setattr(tune, "load_cache", lambda *a, **k: entries)
+    monkeypatch.setattr(tune, "load_batch", lambda *a, **k: {"tile_ms": dict(tiles)})
+    groups = [dict(form=1, degree=2, cell=1), dict(form=0, degree=1, cell=0)]
+    assert coffee.BatchPlan.measured_costs(groups, coffee.TF32X3) == [0.0025, 0.0022]
+    # a group without an in-batch time: every group takes its single-group kernel time instead
+    del tiles["0/1/0/2"]
+    monkeypatch.setattr(tune, "load_batch", lambda *a, **k: {"tile_ms": dict(tiles)})
+    got = coffee.BatchPlan.measured_costs(groups, coffee.TF32X3)
+    assert got == pytest.approx([0.05 * 128 / 2 ** 19, 0.03 * 128 / 2 ** 19])
+    # a group in neither: no measured costs
+    groups.append(dict(form=2, degree=4, cell=0))
+    assert coffee.BatchPlan.measured_costs(groups, coffee.TF32X3) is None
+    # another precision has no entries at all
+    assert coffee.BatchPlan.measured_costs(groups[:1], coffee.BF16X3) is None
