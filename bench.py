@@ -113,6 +113,9 @@ WORKLOADS["burgers-residual-p2-tet"] = Workload("burgers-residual-p2-tet", BURGE
 WORKLOADS["helmholtz-p2-prism"] = Workload("helmholtz-p2-prism", HELMHOLTZ, 2, PRISM,
                                            "unit cube, 48x48 two-triangle columns x 48 layers = 221,184 "
                                            "twisted prisms perturbed 0.15h (seed 6); FP64", _prism48)
+WORKLOADS["helmholtz-p3-prism"] = Workload("helmholtz-p3-prism", HELMHOLTZ, 3, PRISM,
+                                           "unit cube, 48x48 two-triangle columns x 48 layers = 221,184 "
+                                           "twisted prisms perturbed 0.15h (seed 6)", _prism48)
 WORKLOADS["advdiff-p2-prism"] = Workload("advdiff-p2-prism", ADVDIFF, 2, PRISM,
                                          "unit cube, 48x48 two-triangle columns x 48 layers = 221,184 "
                                          "twisted prisms perturbed 0.15h (seed 6), eps~U[0.5,1.5], "

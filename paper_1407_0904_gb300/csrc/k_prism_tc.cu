@@ -33,6 +33,7 @@ constexpr int NPROD = 256;       // producer threads: two per cell
 constexpr int LOADER = 13;       // loader warp
 constexpr int PTHREADS = 14 * 32;
 constexpr int PMAX_STAGES = 6;
+constexpr int PSG = 3;           // slices per group (accumulators live together in TMEM)
 
 struct alignas(8) PBars {
   uint64_t full[PMAX_STAGES];
@@ -55,6 +56,10 @@ __device__ __forceinline__ void prism_bulk_g2s(uint32_t dst, const void* src, ui
 
 // p.N outputs, p.mtiles slices, p.nkc chunks, p.ksteps_off = KQ, p.ns = Q; the image holds the
 // chunks of T^T ([chunk][slice][part][128 rows x 64 B]) followed by the points (s,t,z,w) [Q][4].
+// A tile's slices are contracted in groups of at most PSG (their accumulators share the 512
+// TMEM columns): a tile with more slices (P3: 13) runs the chunk loop once per group, the
+// producers forming the factors again from the tile's geometry (computed once per tile) and
+// the loader bringing only the group's slices of each chunk (contiguous in the image).
 template <int PREC, int KQ, bool CSR>
 __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParams p, int nstages) {
   using PT = PrecTraits<PREC>;
@@ -64,7 +69,9 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int MT = p.mtiles, NKC = p.nkc, Q = p.ns, N = p.N;
-  const int a_chunk = MT * PARTS * TB;          // T^T part of a stage
+  const int SG = MT < PSG ? MT : PSG, NG = (MT + SG - 1) / SG;  // slices per group, groups
+  const int a_full = MT * PARTS * TB;            // T^T chunk in the image (all slices)
+  const int a_chunk = SG * PARTS * TB;           // T^T part of a stage (one group)
   const int stage_bytes = a_chunk + PARTS * TB;  // + the G part
   PBars* bars = reinterpret_cast<PBars*>(smem + nstages * stage_bytes);
   float4* qsm = reinterpret_cast<float4*>(reinterpret_cast<uint8_t*>(bars) + 256);  // points (s,t,z,w) [Q]
@@ -92,7 +99,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   {
-    const float4* qg = reinterpret_cast<const float4*>(p.image + (size_t)NKC * a_chunk);
+    const float4* qg = reinterpret_cast<const float4*>(p.image + (size_t)NKC * a_full);
     for (int i = threadIdx.x; i < Q; i += PTHREADS) qsm[i] = __ldg(qg + i);
   }
   tc_fence_before();
@@ -104,7 +111,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
     // ---------------- producers: the G columns of every chunk, two threads per cell ----------------
     const int pt_id = threadIdx.x - PROD0 * 32;
     const int row = pt_id & (BN - 1), half = pt_id >> 7;  // cell of the tile, half of the chunk
-    uint32_t c = 0;  // chunk counter (all tiles)
+    uint32_t c = 0;  // chunk counter (all items)
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const int64_t e = t * BN + row;
@@ -156,6 +163,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
           JG[r] = (float)(h2 - h0);
         }
       }
+      for (int gi = 0; gi < NG && ok; ++gi) {
       int gq = -1;      // point whose factors are cached
       float gf[9] = {};  // the point's factors (see the kernel comment)
       for (int kc = 0; kc < NKC; ++kc, ++c) {
@@ -260,6 +268,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
         fence_proxy_async();
         mbar_arrive(smem_u32(&bars->full[s]));
       }
+      }
     }
   } else if (warp == LOADER) {
     if (lane == 0) {
@@ -267,14 +276,18 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
       uint32_t c = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+      for (int gi = 0; gi < NG && ok; ++gi) {
+        const int m0 = gi * SG, mt = MT - m0 < SG ? MT - m0 : SG;  // the group's slices
+        const uint32_t bytes = (uint32_t)(mt * PARTS * TB);
         for (int kc = 0; kc < NKC; ++kc, ++c) {
           const int s = (int)(c % nstages);
           if (!mbar_wait(smem_u32(&bars->empty[s]), ((c / nstages) & 1u) ^ 1u, p.err)) { ok = false; break; }
           const uint32_t bar = smem_u32(&bars->full[s]);
-          prism_expect_tx(bar, (uint32_t)a_chunk);
-          prism_bulk_g2s(smem_u32(smem + (size_t)s * stage_bytes), p.image + (size_t)kc * a_chunk, (uint32_t)a_chunk,
-                         bar);
+          prism_expect_tx(bar, bytes);
+          prism_bulk_g2s(smem_u32(smem + (size_t)s * stage_bytes),
+                         p.image + (size_t)kc * a_full + (size_t)m0 * PARTS * TB, bytes, bar);
         }
+      }
       // every issued copy is consumed by the MMA thread's wait on its stage (or the kernel timed out)
     }
     __syncwarp();
@@ -286,8 +299,10 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
       const uint32_t s0 = smem_u32(smem);
       uint32_t c = 0, rc = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, rc += MT) {
-        for (int m = 0; m < MT && ok; ++m) {
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+      for (int gi = 0; gi < NG && ok; ++gi) {
+        const int m0 = gi * SG, mt = MT - m0 < SG ? MT - m0 : SG;
+        for (int m = 0; m < mt && ok; ++m) {
           const uint32_t r = rc + m;
           if (!mbar_wait(smem_u32(&bars->tempty[r % RING]), ((r / RING) & 1u) ^ 1u, p.err)) ok = false;
         }
@@ -299,7 +314,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
           tc_fence_after();
           const uint32_t st = s0 + (uint32_t)(s * stage_bytes);
           const uint32_t g = st + (uint32_t)a_chunk;
-          for (int m = 0; m < MT; ++m) {
+          for (int m = 0; m < mt; ++m) {
             const uint32_t d = tmem + ((rc + m) % RING) * BN;
             const uint32_t a = st + (uint32_t)(m * PARTS * TB);
 #pragma unroll
@@ -317,7 +332,8 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
           tc_commit(smem_u32(&bars->empty[s]));
         }
         if (!ok) break;
-        for (int m = 0; m < MT; ++m) tc_commit(smem_u32(&bars->tfull[(rc + m) % RING]));
+        for (int m = 0; m < mt; ++m) tc_commit(smem_u32(&bars->tfull[(rc + m) % RING]));
+        rc += mt;
       }
       tc_commit(smem_u32(&bars->done));
       mbar_wait(smem_u32(&bars->done), 0, p.err);
@@ -330,7 +346,10 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
     uint32_t rc = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
-      for (int m = 0; m < MT; ++m, ++rc) {
+    for (int gi = 0; gi < NG && ok; ++gi) {
+      const int m0 = gi * SG, mt = MT - m0 < SG ? MT - m0 : SG;
+      for (int mm = 0; mm < mt; ++mm, ++rc) {
+        const int m = m0 + mm;  // slice of the element matrix
         const uint32_t slot = rc % RING;
         if (!mbar_wait(smem_u32(&bars->tfull[slot]), (rc / RING) & 1u, p.err)) { ok = false; break; }
         tc_fence_after();
@@ -384,6 +403,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
       }
+    }
   }
 
   tc_fence_before();
@@ -396,11 +416,13 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
 }
 
 struct PGeom {
-  int n, N, mtiles, KQ, Q, K, nkc, parts, kc, elem, a_chunk, stage;
+  int n, N, mtiles, KQ, Q, K, nkc, parts, kc, elem;
+  int a_chunk;  // bytes of one chunk of T^T in the image (all slices)
+  int stage;    // bytes of one shared-memory stage (one slice group of T^T + the G part)
 };
 
 bool pgeom(int form, int degree, int prec, PGeom& g) {
-  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF) || degree < 1 || degree > 2) return false;
+  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF) || degree < 1 || degree > 3) return false;
   if (prec == PREC_FP64 || prec < 0 || prec > PREC_BF16X3) return false;
   const bool tf32 = prec == PREC_TF32 || prec == PREC_TF32X3;
   g.n = prism_nnodes(degree);
@@ -414,8 +436,9 @@ bool pgeom(int form, int degree, int prec, PGeom& g) {
   g.nkc = (g.K + g.kc - 1) / g.kc;
   g.parts = (prec == PREC_TF32X3 || prec == PREC_BF16X3) ? 2 : 1;
   g.a_chunk = g.mtiles * g.parts * BM * PCB;
-  g.stage = g.a_chunk + g.parts * BM * PCB;
-  return g.mtiles <= 3;
+  const int sg = g.mtiles < PSG ? g.mtiles : PSG;
+  g.stage = (sg + 1) * g.parts * BM * PCB;
+  return true;
 }
 
 constexpr int P_SMEM_LIMIT = 227 * 1024;

@@ -161,7 +161,7 @@ def test_burgers_reference_tensor_on_reference_cell_matches_oracle(cell, k):
 
 
 def test_support_queries_cover_prisms():
-    """Host-only queries: prisms take MASS, HELMHOLTZ and ADVDIFF (FP64 P1-P4, tensor cores P1-P2),
+    """Host-only queries: prisms take MASS, HELMHOLTZ and ADVDIFF (FP64 P1-P4, tensor cores P1-P3),
     locally and fused into CSR; the Burgers forms are simplex-only."""
     P = coffee.PRISM
     for form in (coffee.MASS, coffee.HELMHOLTZ, coffee.ADVDIFF):
@@ -169,8 +169,8 @@ def test_support_queries_cover_prisms():
             assert coffee.supported(form, k, P, coffee.FP64)
             assert coffee.csr_supported(form, k, P, coffee.FP64)
             for prec in (coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16):
-                assert bool(coffee.supported(form, k, P, prec)) == (k <= 2)
-                assert bool(coffee.csr_supported(form, k, P, prec)) == (k <= 2)
+                assert bool(coffee.supported(form, k, P, prec)) == (k <= 3)
+                assert bool(coffee.csr_supported(form, k, P, prec)) == (k <= 3)
     for form in (coffee.BURGERS_JAC, coffee.BURGERS_RESIDUAL):
         for prec in (coffee.FP64, coffee.TF32X3):
             assert not coffee.supported(form, 1, P, prec)
