@@ -54,12 +54,25 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
-// group of the work item `it` (groups are few; linear scan over their first items)
-__device__ __forceinline__ int group_of(const BatchGroup* gs, int ngroups, int64_t it) {
-  int g = 0;
-  while (g + 1 < ngroups && gs[g + 1].item0 <= it) ++g;
-  return g;
-}
+// Group of the work items a role visits in increasing order: found once by a scan, then moved
+// forward as the items pass the next group's first item (kept in a register), so a work item
+// costs one compare instead of a chain of loads over the group table.
+struct GroupCursor {
+  const BatchGroup* gs;
+  int ngroups, g;
+  int64_t next0;  // first item of group g + 1
+  __device__ GroupCursor(const BatchGroup* gs_, int n, int64_t it) : gs(gs_), ngroups(n), g(0) {
+    while (g + 1 < ngroups && gs[g + 1].item0 <= it) ++g;
+    next0 = g + 1 < ngroups ? gs[g + 1].item0 : INT64_MAX;
+  }
+  __device__ __forceinline__ int at(int64_t it) {
+    while (it >= next0) {
+      ++g;
+      next0 = g + 1 < ngroups ? gs[g + 1].item0 : INT64_MAX;
+    }
+    return g;
+  }
+};
 
 template <int PREC, int FORM, int D>
 __device__ __forceinline__ void produce_row(const BatchGroup& g, int64_t e, bool live, uint8_t* hi, uint8_t* lo,
@@ -127,9 +140,10 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
     const int pw = warp - PROD_WARP0;
     const int grp = pw >> 2, row = ((pw & 3) << 5) + lane;
     const int spg = nstages / PROD_GROUPS;
+    GroupCursor cur(groups, ngroups, it0);
     for (int64_t it = it0 + grp; it < it1; it += PROD_GROUPS) {
       const int64_t k = it - it0;
-      const int gi = group_of(groups, ngroups, it);
+      const int gi = cur.at(it);
       const BatchGroup& g = groups[gi];
       int s;
       uint32_t use;
@@ -158,8 +172,9 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
       int tag[ASLOTS] = {-1, -1};  // (group, slice) held by each slot: consecutive items of a
                                    // group find their slices already resident
       bool ok = true;
+      GroupCursor cur(groups, ngroups, it0);
       for (int64_t it = it0; it < it1 && ok; ++it) {
-        const int gi = group_of(groups, ngroups, it);
+        const int gi = cur.at(it);
         const BatchGroup& g = groups[gi];
         const uint32_t part_bytes = (uint32_t)(BM * g.p.kbytes);
         for (int m = 0; m < g.p.mtiles; ++m, ++la) {
@@ -193,8 +208,9 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
       uint32_t rc = 0, ma = 0;
       int k = 0;
       bool ok = true;
+      GroupCursor cur(groups, ngroups, it0);
       for (int64_t it = it0; it < it1 && ok; ++it, ++k) {
-        const BatchGroup& g = groups[group_of(groups, ngroups, it)];
+        const BatchGroup& g = groups[cur.at(it)];
         const int kb = g.p.kbytes, ksteps = kb / 32;
         const uint32_t sbo = 8u * (uint32_t)kb, part = (uint32_t)(BM * kb);
         const bool lanes = g.lanes != 0;
@@ -243,8 +259,9 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
     const int q = warp;  // TMEM lane quadrant
     uint32_t rc = 0;
     bool ok = true;
+    GroupCursor cur(groups, ngroups, it0);
     for (int64_t it = it0; it < it1 && ok; ++it) {
-      const BatchGroup& g = groups[group_of(groups, ngroups, it)];
+      const BatchGroup& g = groups[cur.at(it)];
       const int N = g.p.N;
       if (g.lanes) {
         // cells on lanes: thread = cell, its row of N <= 32 outputs from one TMEM load
