@@ -141,6 +141,9 @@ int coffee_tabulate(int cell, int degree, int quad_degree, int* nq, int* ndof,
 /* Reference tensors of a form (host-only, FP64): T [K][N] with N = ns*ns, where the
  * element matrix (or, for BURGERS_JAC, each of its d*d component blocks) is
  * sum_k G_e[k] T[k] for per-cell geometry/coefficient factors G_e.
+ * BURGERS_RESIDUAL returns the BURGERS_JAC tensors (the residual contracts the same ones).
+ * Triangles and tetrahedra only: a prism's Jacobian varies over the cell, so it has no
+ * reference tensor (COFFEE_ERR_UNSUPPORTED).
  * Pass T = NULL to query *K and *N. */
 int coffee_reference_tensor(int form, int degree, int cell, int* K, int* N, double* T);
 

@@ -82,7 +82,10 @@ int fp64_table(DeviceCache& c, int form, int degree, int cell, const double** T)
   cudaError_t e = cudaMalloc(&d, h.size() * sizeof(double));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(reference tensor)");
   e = cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(reference tensor)");
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_fail(e, "cudaMemcpy(reference tensor)");
+  }
   c.fp64[key] = d;
   *T = d;
   return COFFEE_OK;
@@ -98,7 +101,10 @@ int tc_table(DeviceCache& c, int form, int degree, int cell, int prec, TcTable* 
     cudaError_t e = cudaMalloc(&ent.image, img.size());
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(tensor-core table)");
     e = cudaMemcpy(ent.image, img.data(), img.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(tensor-core table)");
+    if (e != cudaSuccess) {
+      cudaFree(ent.image);
+      return cuda_fail(e, "cudaMemcpy(tensor-core table)");
+    }
     ent.meta.image = ent.image;
     it = c.tc.emplace(key, ent).first;
   }
@@ -114,7 +120,7 @@ bool valid_fdc(int form, int degree, int cell) {
 int check_args(const coffee_assemble_args* a) {
   if (!a) return fail(COFFEE_ERR_INVALID_ARG, "args is NULL");
   if (!valid_fdc(a->form, a->degree, a->cell))
-    return fail(COFFEE_ERR_INVALID_ARG, "form/degree/cell out of range (degree 1..4, tri/tet)");
+    return fail(COFFEE_ERR_INVALID_ARG, "form/degree/cell out of range (degree 1..4, tri/tet/prism)");
   if (a->precision < PREC_FP64 || a->precision > PREC_BF16X3)
     return fail(COFFEE_ERR_INVALID_ARG, "precision out of range");
   if (a->ncells < 0) return fail(COFFEE_ERR_INVALID_ARG, "ncells < 0");
@@ -298,6 +304,10 @@ int coffee_tabulate(int cell, int degree, int quad_degree, int* nq, int* ndof, d
 
 int coffee_reference_tensor(int form, int degree, int cell, int* K, int* N, double* T) {
   if (!valid_fdc(form, degree, cell)) return fail(COFFEE_ERR_INVALID_ARG, "form/degree/cell out of range");
+  if (cell == CELL_PRISM)
+    return fail(COFFEE_ERR_UNSUPPORTED, "prisms are not affine: their Jacobian varies over the cell, so no "
+                                        "reference tensor exists (the prism kernels contract per quadrature point)");
+  form = table_form(form);
   const int ns = nnodes(cell, degree);
   if (K) *K = form_K(form, degree, cell);
   if (N) *N = ns * ns;

@@ -175,3 +175,15 @@ def test_support_queries_cover_prisms():
         for prec in (coffee.FP64, coffee.TF32X3):
             assert not coffee.supported(form, 1, P, prec)
             assert not coffee.csr_supported(form, 1, P, prec)
+
+
+def test_reference_tensor_queries_for_residual_and_prisms():
+    """Host-only: the residual contracts the Jacobian's reference tensors; prisms, whose
+    Jacobian varies over the cell, have none and are rejected."""
+    for cell, k in ((0, 2), (1, 1), (1, 2)):
+        R = coffee.reference_tensor(coffee.BURGERS_RESIDUAL, k, cell)
+        J = coffee.reference_tensor(coffee.BURGERS_JAC, k, cell)
+        assert R.shape == J.shape and R.shape[0] > 0
+        assert np.array_equal(R, J)
+    with pytest.raises(coffee.CoffeeError):
+        coffee.reference_tensor(coffee.HELMHOLTZ, 2, coffee.PRISM)
