@@ -189,17 +189,47 @@ def _stream_handle(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def coef_width(form, degree, cell):
+    """Columns of cell2dof for a form: the cell's vertices for ADVDIFF (P1 eps and b), the
+    scalar Pk nodes for the Burgers forms (u), 0 for forms without a coefficient."""
+    if form == ADVDIFF:
+        return verts_per_cell(cell)
+    if form in (BURGERS_JAC, BURGERS_RESIDUAL):
+        return nnodes(cell, degree)
+    return 0
+
+
+def check_shapes(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None):
+    """Shape checks of the inputs against the layouts of include/coffee.h, made before any
+    pointer is passed: the library receives bare pointers and cannot check extents."""
+    d = dim(cell)
+    nv = verts_per_cell(cell)
+    if cell2vert.dim() != 2 or cell2vert.shape[1] != nv:
+        raise ValueError("cell2vert must be [ncells, %d]" % nv)
+    if coords.dim() != 2 or coords.shape[1] != d:
+        raise ValueError("coords must be [nverts, %d]" % d)
+    w = coef_width(form, degree, cell)
+    if w == 0:
+        return
+    if coef is None or cell2dof is None:
+        return  # the library rejects the missing pointers itself
+    if cell2dof.dim() != 2 or cell2dof.shape[0] != cell2vert.shape[0] or cell2dof.shape[1] != w:
+        raise ValueError("cell2dof must be [ncells, %d] = [%d, %d], got %s"
+                         % (w, cell2vert.shape[0], w, list(cell2dof.shape)))
+    row = 1 + d if form == ADVDIFF else d
+    if coef.numel() % row != 0:
+        raise ValueError("coef must be [ncoefnodes, %d]" % row)
+
+
 def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
               out=None, nu=0.01, validate=False, ncoefnodes=None, tune=0, alloc_out=True):
     coords = _dev(coords, torch.float64, "coords")
     cell2vert = _dev(cell2vert, torch.int32, "cell2vert")
     coef = _dev(coef, torch.float64, "coef")
     cell2dof = _dev(cell2dof, torch.int32, "cell2dof")
+    check_shapes(form, degree, cell, coords, cell2vert, coef, cell2dof)
     d = dim(cell)
     ncells = cell2vert.shape[0]
-    nv = verts_per_cell(cell)
-    if cell2vert.dim() != 2 or cell2vert.shape[1] != nv:
-        raise ValueError("cell2vert must be [ncells, %d]" % nv)
     n = ndof(form, degree, cell)
     odt = torch.float64 if precision == FP64 else torch.float32
     shape = (ncells, n) if form == BURGERS_RESIDUAL else (ncells, n, n)  # element vectors or matrices

@@ -187,3 +187,35 @@ def test_reference_tensor_queries_for_residual_and_prisms():
         assert np.array_equal(R, J)
     with pytest.raises(coffee.CoffeeError):
         coffee.reference_tensor(coffee.HELMHOLTZ, 2, coffee.PRISM)
+
+
+def test_binding_checks_input_extents_before_any_pointer_is_passed():
+    """The C ABI sees bare pointers; the binding checks the extents it can see (CPU tensors
+    suffice: check_shapes looks at shapes only)."""
+    import torch
+    from paper_1407_0904_gb300 import meshgen
+    from paper_1407_0904_gb300.binding import check_shapes
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a))
+    for cell, mesh in ((0, meshgen.tri_mesh(4, seed=1)), (1, meshgen.tet_mesh(3, seed=1)),
+                       (2, meshgen.prism_mesh(3, 2, seed=1))):
+        x, c2v = t(mesh.coords), t(mesh.cell2vert)
+        coef, c2d, _ = meshgen.advdiff_coefficients(mesh, 3)
+        check_shapes(coffee.ADVDIFF, 2, cell, x, c2v, t(coef), t(c2d))
+        with pytest.raises(ValueError):  # fewer cell2dof rows than cells
+            check_shapes(coffee.ADVDIFF, 2, cell, x, c2v, t(coef), t(c2d[:-1]))
+        with pytest.raises(ValueError):  # a column short
+            check_shapes(coffee.ADVDIFF, 2, cell, x, c2v, t(coef), t(c2d[:, :-1]))
+        with pytest.raises(ValueError):  # coef rows are (eps, b_0 .. b_{d-1})
+            check_shapes(coffee.ADVDIFF, 2, cell, x, c2v, t(coef.ravel()[:-1]), t(c2d))
+        with pytest.raises(ValueError):
+            check_shapes(coffee.HELMHOLTZ, 2, cell, x[:, :1], c2v)
+        with pytest.raises(ValueError):
+            check_shapes(coffee.HELMHOLTZ, 2, cell, x, c2v[:, :-1])
+        if cell == 2:
+            continue
+        for k in (1, 2, 3):
+            u, c2d, _ = meshgen.burgers_coefficients(mesh, k, 3)
+            for form in (coffee.BURGERS_JAC, coffee.BURGERS_RESIDUAL):
+                check_shapes(form, k, cell, x, c2v, t(u.ravel()), t(c2d))
+                with pytest.raises(ValueError):  # the map of another degree
+                    check_shapes(form, k + 1, cell, x, c2v, t(u.ravel()), t(c2d))
