@@ -119,3 +119,28 @@ def test_config4_full_size_sampled():
     outs = plan.launch()
     coffee.check_errors()
     check_groups(dev, groups, outs, coffee.TF32X3, 1e-5, sample=200)
+
+
+def test_batch_validation_reports_a_bad_index_and_leaves_the_rest_intact():
+    """validate=True: an out-of-range vertex id in one group is reported through check_errors,
+    that cell's matrix is zero and every other cell of every group is unchanged."""
+    tri = meshgen.tri_mesh(24, perturb=0.2, seed=6)
+    tet = meshgen.tet_mesh(6, perturb=0.15, seed=7)
+    dev, groups = make_batch(tri, tet, seed=6)
+    clean = [o.clone() for o in coffee.BatchPlan(groups, validate=True).launch()]
+    coffee.check_errors()
+    gi = max(range(len(groups)), key=lambda i: groups[i]["spec"]["count"])
+    bad = groups[gi]["cell2vert"].clone()
+    bad[3, 1] = dev[groups[gi]["cell"]]["mesh"].nverts + 5
+    groups[gi] = dict(groups[gi], cell2vert=bad)
+    outs = coffee.BatchPlan(groups, validate=True).launch()
+    with pytest.raises(coffee.CoffeeError) as ei:
+        coffee.check_errors()
+    assert ei.value.status == -4
+    for i, (a, b) in enumerate(zip(clean, outs)):
+        if i != gi:
+            assert torch.equal(a, b)
+    assert torch.count_nonzero(outs[gi][3]) == 0
+    keep = torch.ones(outs[gi].shape[0], dtype=torch.bool, device=DEV)
+    keep[3] = False
+    assert torch.equal(outs[gi][keep], clean[gi][keep])
