@@ -190,6 +190,27 @@ int coffee_supported(int form, int degree, int cell, int precision);
  * Returns COFFEE_ERR_UNSUPPORTED for combinations without a kernel. */
 int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream);
 
+/* Local assembly of data held in HOST memory (the same kernels as coffee_assemble_ex, with
+ * the copies around them). a->coords, a->cell2vert, a->coef, a->cell2dof and a->out are HOST
+ * pointers with the layouts of coffee_assemble; out is [ncells][ndof][ndof] (BURGERS_RESIDUAL:
+ * [ncells][ndof]), double for FP64 and float otherwise. a->nverts, and a->ncoefnodes for the
+ * forms with a coefficient, must be > 0: they size the copies.
+ * The coordinates and coefficients are copied to the device once; the cells are assembled in
+ * `chunks` launches (chunk boundaries on 128-cell tiles), each chunk's inputs copied in and its
+ * results copied back on a second, library-owned stream while the next chunk computes.
+ * Page-locked host memory lets the copies overlap the kernels; pageable memory works but
+ * serialises them. Device staging comes from a library-owned stream-ordered memory pool that
+ * keeps its largest size for reuse (coffee_host_pool_trim releases it).
+ * Asynchronous: a->out is complete once `stream` has reached the end of this call's work
+ * (synchronise `stream`, or wait on an event recorded on it, before reading it).
+ * Errors: as coffee_assemble_ex; COFFEE_ERR_INVALID_ARG also for chunks < 1 or a missing size;
+ * COFFEE_ERR_NOMEM when the staging buffers cannot be allocated. */
+int coffee_assemble_host(const coffee_assemble_args* a, int chunks, coffee_stream_t stream);
+
+/* Releases the device memory the host-buffer pool of the current device holds beyond what
+ * pending work still uses. Host-only; returns COFFEE_OK. */
+int coffee_host_pool_trim(void);
+
 /* Adjoint of local assembly (new; the paper has no backward pass).
  * Given dout = dL/dA ([ncells][ndof][ndof], double for FP64, float otherwise),
  * ACCUMULATES (+=) dL/dcoords into d_coords [nverts][d] and dL/dcoef into d_coef

@@ -309,53 +309,65 @@ def check_errors(stream=None):
     _check(lib().coffee_check_errors(_stream_handle(stream)))
 
 
-_copy_streams = {}
+def _host(t, dtype, name):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("%s must be a host (CPU) tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t
 
 
 def assemble_host(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
-                  out=None, nu=0.01, chunks=4, device=None):
-    """Local assembly from HOST (ideally pinned) tensors into a host tensor.
+                  out=None, nu=0.01, chunks=4, device=None, validate=False, tune=None):
+    """Local assembly from HOST tensors into a host tensor (coffee_assemble_host).
 
-    Inputs are copied to the device, the cell range is processed in `chunks` launches
-    and each chunk's element matrices are copied back on a second stream while the
-    next chunk computes. Returns the host tensor `out` (allocated pinned if None); it
-    is complete once the current CUDA stream has reached this point."""
+    The library copies the coordinates and coefficients to the device once, assembles the
+    cells in `chunks` launches and copies each chunk's results back on its own stream while
+    the next chunk computes (page-locked tensors let the copies overlap). Returns the host
+    tensor `out` (allocated page-locked if None); it is complete once the current CUDA stream
+    of `device` has reached this point."""
     dev = device or torch.device("cuda", torch.cuda.current_device())
-    main = torch.cuda.current_stream(dev)
-    if dev not in _copy_streams:
-        _copy_streams[dev] = torch.cuda.Stream(dev)
-    side = _copy_streams[dev]
-    d_coords = coords.to(dev, non_blocking=True)
-    d_c2v = cell2vert.to(dev, non_blocking=True)
-    d_coef = None if coef is None else coef.to(dev, non_blocking=True)
-    d_c2d = None if cell2dof is None else cell2dof.to(dev, non_blocking=True)
+    coords = _host(coords, torch.float64, "coords")
+    cell2vert = _host(cell2vert, torch.int32, "cell2vert")
+    coef = _host(coef, torch.float64, "coef")
+    cell2dof = _host(cell2dof, torch.int32, "cell2dof")
+    check_shapes(form, degree, cell, coords, cell2vert, coef, cell2dof)
     ncells = cell2vert.shape[0]
     n = ndof(form, degree, cell)
     odt = torch.float64 if precision == FP64 else torch.float32
     shape = (ncells, n) if form == BURGERS_RESIDUAL else (ncells, n, n)
     if out is None:
         out = torch.empty(shape, dtype=odt, pin_memory=True)
-    d_out = torch.empty(shape, dtype=odt, device=dev)
-    d_out.record_stream(side)
-    ncoef = None
-    if coef is not None:
-        ncoef = coef.numel() // (1 + dim(cell)) if form == ADVDIFF else coef.numel() // dim(cell)
-    bounds = np.linspace(0, ncells, max(1, chunks) + 1).astype(np.int64)
-    for i in range(len(bounds) - 1):
-        lo, hi = int(bounds[i]), int(bounds[i + 1])
-        if hi <= lo:
-            continue
-        a, _ = make_args(form, degree, cell, d_coords, d_c2v[lo:hi],
-                         d_coef, None if d_c2d is None else d_c2d[lo:hi], precision, d_out[lo:hi],
-                         nu, False, ncoef)
-        _check(lib().coffee_assemble_ex(ctypes.byref(a), ctypes.c_void_p(main.cuda_stream)))
-        ev = torch.cuda.Event()
-        ev.record(main)
-        side.wait_event(ev)
-        with torch.cuda.stream(side):
-            out[lo:hi].copy_(d_out[lo:hi], non_blocking=True)
-    main.wait_stream(side)
+    else:
+        _host(out, odt, "out")
+        if out.numel() != int(np.prod(shape)):
+            raise ValueError("out must hold %s elements" % "x".join(map(str, shape)))
+    if tune is None:
+        tune = _tuned_flags(form, degree, cell, precision)
+    d = dim(cell)
+    a = AssembleArgs()
+    a.form, a.degree, a.cell, a.precision, a.nu = form, degree, cell, precision, nu
+    a.coords, a.nverts = _ptr(coords), coords.shape[0]
+    a.cell2vert = _ptr(cell2vert)
+    a.coef = _ptr(coef)
+    a.ncoefnodes = 0 if coef is None else coef.numel() // ((1 + d) if form == ADVDIFF else d)
+    a.cell2dof = _ptr(cell2dof)
+    a.out, a.ncells = _ptr(out), ncells
+    a.flags = (FLAG_VALIDATE if validate else 0) | int(tune)
+    L = lib()
+    L.coffee_assemble_host.argtypes = [ctypes.POINTER(AssembleArgs), ctypes.c_int, ctypes.c_void_p]
+    with torch.cuda.device(dev):
+        _check(L.coffee_assemble_host(ctypes.byref(a), int(chunks), _stream_handle(None)))
     return out
+
+
+def host_pool_trim():
+    """Release the device staging memory kept by assemble_host's pool (coffee_host_pool_trim)."""
+    _check(lib().coffee_host_pool_trim())
 
 
 def assemble_backward(form, degree, cell, coords, cell2vert, dout, coef=None, cell2dof=None,

@@ -219,3 +219,27 @@ def test_binding_checks_input_extents_before_any_pointer_is_passed():
                 check_shapes(form, k, cell, x, c2v, t(u.ravel()), t(c2d))
                 with pytest.raises(ValueError):  # the map of another degree
                     check_shapes(form, k + 1, cell, x, c2v, t(u.ravel()), t(c2d))
+
+
+def test_host_buffer_entry_point_rejects_bad_arguments_before_any_cuda_call():
+    """coffee_assemble_host: argument checks come before the first CUDA call (no device here)."""
+    lib = coffee.lib()
+    A = coffee.binding.AssembleArgs
+    lib.coffee_assemble_host.argtypes = [ctypes.POINTER(A), ctypes.c_int, ctypes.c_void_p]
+    assert lib.coffee_assemble_host(None, 4, None) == -1
+    a = A()
+    a.form, a.degree, a.cell, a.precision, a.ncells = coffee.HELMHOLTZ, 3, coffee.TETRAHEDRON, coffee.TF32X3, 0
+    assert lib.coffee_assemble_host(ctypes.byref(a), 0, None) == -1
+    assert b"chunks" in lib.coffee_last_error()
+    assert lib.coffee_assemble_host(ctypes.byref(a), 4, None) == 0  # empty: nothing to copy
+    a.ncells = 10
+    assert lib.coffee_assemble_host(ctypes.byref(a), 4, None) == -1  # NULL host pointers
+    a.coords = a.cell2vert = a.out = 16  # non-NULL, never dereferenced before the size checks
+    assert lib.coffee_assemble_host(ctypes.byref(a), 4, None) == -1
+    assert b"nverts" in lib.coffee_last_error()
+    a.form, a.nverts = coffee.ADVDIFF, 20
+    assert lib.coffee_assemble_host(ctypes.byref(a), 4, None) == -1
+    assert b"coef" in lib.coffee_last_error()
+    a.form, a.degree = coffee.HELMHOLTZ, 4
+    a.cell = coffee.PRISM  # no tensor-core prism kernel at P4
+    assert lib.coffee_assemble_host(ctypes.byref(a), 4, None) == -2

@@ -57,3 +57,25 @@ def test_host_pipeline_empty_and_more_chunks_than_cells():
     torch.cuda.synchronize()
     ref = oracle.assemble(HELMHOLTZ, 2, TRI, mesh.coords, mesh.cell2vert[:5], None, None)
     assert rel_err_per_cell(got.numpy(), ref) < 1e-5
+
+
+def test_host_pipeline_with_pageable_memory_and_validation():
+    """Pageable host tensors take the same path (copies no longer overlap); validate=True
+    reports a bad vertex id found in any chunk."""
+    mesh, coef, c2d, _ = host_inputs(ADVDIFF, TET, 2, seed=5)
+    x, c2v = torch.from_numpy(mesh.coords), torch.from_numpy(mesh.cell2vert)
+    cf, cd = torch.from_numpy(coef), torch.from_numpy(c2d)
+    out = torch.empty((mesh.ncells, 10, 10), dtype=torch.float32)  # pageable
+    got = coffee.assemble_host(ADVDIFF, 2, TET, x, c2v, cf, cd, precision=coffee.TF32X3, out=out, chunks=3,
+                               validate=True)
+    torch.cuda.synchronize()
+    coffee.check_errors()
+    ref = oracle.assemble(ADVDIFF, 2, TET, mesh.coords, mesh.cell2vert, coef, c2d)
+    assert got.data_ptr() == out.data_ptr() and rel_err_per_cell(got.numpy(), ref) < 1e-5
+    bad = c2v.clone()
+    bad[mesh.ncells - 2, 3] = mesh.nverts + 1  # last chunk
+    coffee.assemble_host(ADVDIFF, 2, TET, x, bad, cf, cd, precision=coffee.TF32X3, out=out, chunks=3,
+                         validate=True)
+    with pytest.raises(coffee.CoffeeError) as ei:
+        coffee.check_errors()
+    assert ei.value.status == -4
