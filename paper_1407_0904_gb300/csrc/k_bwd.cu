@@ -52,8 +52,8 @@ __device__ __forceinline__ void adjugate(const T (&J)[D][D], T (&adj)[D][D], T& 
   }
 }
 
-// Local gradient L[0 .. NL): vertex coordinates (v*D + r), then coefficient values in the
-// oracle's cell-local order (eps_v, then b_{v,r}).
+// Local gradient L[0 .. NL): vertex coordinates (v*D + r), then the cell's coefficient values
+// (eps_v for every vertex v, then b_{v,r}).
 // The arithmetic runs in the type of dL/dA (CT = TA): FP64 for FP64 dL/dA, FP32 for FP32
 // dL/dA (vertex differences are still taken in FP64 and rounded). Gradients are accumulated
 // into FP64 arrays.
