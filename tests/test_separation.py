@@ -42,3 +42,22 @@ def test_bench_uses_the_oracle_only_in_its_cpu_legs():
     top_imports = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
     assert not any(getattr(n, "module", None) == "oracle" or any(a.name == "oracle" for a in n.names)
                    for n in top_imports)
+
+
+def test_missing_library_fails_loudly_without_a_fallback(tmp_path):
+    """With libcoffee.so absent every call raises; nothing falls back to another implementation."""
+    import subprocess
+    import sys
+    code = ("import paper_1407_0904_gb300.binding as b\n"
+            "b.LIB_PATH = %r\n"
+            "for call in (lambda: b.ndof(1, 2, 1), lambda: b.supported(1, 3, 1, 2),\n"
+            "             lambda: b.reference_tensor(0, 1, 0)):\n"
+            "    try:\n"
+            "        call()\n"
+            "    except RuntimeError as e:\n"
+            "        assert 'not built' in str(e)\n"
+            "    else:\n"
+            "        raise SystemExit('no error')\n"
+            "print('raised')\n" % str(tmp_path / "libcoffee.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "raised", r.stdout + r.stderr
