@@ -184,14 +184,15 @@ typedef struct {
  * the combinations whose operands fit in shared memory. Host-only. */
 int coffee_supported(int form, int degree, int cell, int precision);
 
-/* Local assembly with a chosen precision. FP64 runs the plain FP64 kernel; the
+/* Local assembly (section 2, Listings 1-2) with a chosen precision. FP64 runs the plain FP64 kernel; the
  * other precisions run the tcgen05 tensor-core contraction with geometry fused into
  * its producer warps (FP32 geometry, FP64 for ill-conditioned cells).
  * Returns COFFEE_ERR_UNSUPPORTED for combinations without a kernel. */
 int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream);
 
-/* Local assembly of data held in HOST memory (the same kernels as coffee_assemble_ex, with
- * the copies around them). a->coords, a->cell2vert, a->coef, a->cell2dof and a->out are HOST
+/* Local assembly (section 2) of data held in HOST memory, where the paper's CPU framework
+ * keeps the mesh and the element matrices (section 4): the same kernels as coffee_assemble_ex,
+ * with the copies around them. a->coords, a->cell2vert, a->coef, a->cell2dof and a->out are HOST
  * pointers with the layouts of coffee_assemble; out is [ncells][ndof][ndof] (BURGERS_RESIDUAL:
  * [ncells][ndof]), double for FP64 and float otherwise. a->nverts, and a->ncoefnodes for the
  * forms with a coefficient, must be > 0: they size the copies.
