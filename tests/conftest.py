@@ -12,6 +12,13 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (GB300) and libcoffee.so")
 
 
+def pytest_sessionstart(session):
+    """Build libcoffee.so in-tree if it is missing or older than its sources (a no-op otherwise),
+    so that the suite always runs against the library of the sources it tests."""
+    from paper_1407_0904_gb300 import _build
+    _build.build()
+
+
 def pytest_collection_modifyitems(config, items):
     try:
         import torch
