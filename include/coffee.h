@@ -266,6 +266,13 @@ int coffee_batch_plan_costs(const coffee_assemble_args* groups, int ngroups, int
                             void** plan);
 int coffee_batch_launch(void* plan, coffee_stream_t stream);
 void coffee_batch_free(void* plan);
+/* The split both planners use (host-only, no CUDA call): `items` work items with costs
+ * cost[i] >= 0 (finite) go to `grid` CTAs in contiguous ranges; CTA b takes items
+ * [ranges[b], ranges[b+1]), with ranges[0] = 0, ranges[grid] = items, and the cut after CTA b
+ * placed at the first item where the running cost reaches (b+1)/grid of the total.
+ *   cost host [items]; ranges host [grid+1], out. COFFEE_ERR_INVALID_ARG for items < 0,
+ *   grid < 1, NULL pointers or a negative or non-finite cost. */
+int coffee_batch_split(const double* cost, int64_t items, int grid, int64_t* ranges);
 
 /* ---- Global assembly: the consumer of local assembly ----
  * Local assembly yields each cell's contribution to the global linear system (section 2);

@@ -439,6 +439,18 @@ def assemble_backward_noalloc(form, degree, cell, coords, cell2vert, dout, coef=
     return d_coords, (d_coef if form == ADVDIFF else None)
 
 
+def batch_split(costs, grid):
+    """The CTA split of a mixed batch (coffee_batch_split, host-only): ranges [grid+1] int64,
+    CTA b taking work items [ranges[b], ranges[b+1]) of about equal total cost."""
+    c = np.ascontiguousarray(costs, dtype=np.float64)
+    r = np.zeros(int(grid) + 1, dtype=np.int64) if int(grid) >= 1 else np.zeros(1, dtype=np.int64)
+    L = lib()
+    L.coffee_batch_split.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+    _check(L.coffee_batch_split(c.ctypes.data_as(ctypes.c_void_p), c.size, int(grid),
+                                r.ctypes.data_as(ctypes.c_void_p)))
+    return r
+
+
 class BatchPlan:
     """Several (form, degree, cell) groups assembled by one persistent launch.
 

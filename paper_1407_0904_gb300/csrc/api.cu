@@ -558,6 +558,21 @@ struct BatchPlanImpl {
 }  // namespace
 
 namespace {
+// Contiguous ranges of about equal cost: CTA b takes items [ranges[b], ranges[b+1]), cut after
+// the first item at which the running cost reaches b/grid of the total.
+void split_by_cost(const double* cost, int64_t items, int grid, int64_t* ranges) {
+  double total = 0.0;
+  for (int64_t i = 0; i < items; ++i) total += cost[i];
+  for (int b = 0; b <= grid; ++b) ranges[b] = items;
+  ranges[0] = 0;
+  double acc = 0.0;
+  int b = 1;
+  for (int64_t i = 0; i < items && b < grid; ++i) {
+    acc += cost[i];
+    if (acc >= total * b / grid) ranges[b++] = i + 1;
+  }
+}
+
 // Plan shared by both entry points: tile_cost (per group, one full 128-cell tile) when given,
 // else bytes written + item_overhead per 128-output slice.
 int batch_plan_impl(const coffee_assemble_args* groups, int ngroups, int grid, double item_overhead,
@@ -629,18 +644,8 @@ int batch_plan_impl(const coffee_assemble_args* groups, int ngroups, int grid, d
   if (smem == 0) return fail(COFFEE_ERR_UNSUPPORTED, "batch operands do not fit in shared memory");
   if (grid <= 0) grid = c->num_sms;
   grid = (int)std::min<int64_t>(grid, items);
-  // contiguous ranges of about equal cost
-  double total = 0.0;
-  for (double x : cost) total += x;
-  std::vector<int64_t> ranges(grid + 1, items);
-  ranges[0] = 0;
-  double acc = 0.0;
-  int b = 1;
-  for (int64_t i = 0; i < items && b < grid; ++i) {
-    acc += cost[i];
-    if (acc >= total * b / grid) ranges[b++] = i + 1;
-  }
-  for (; b < grid; ++b) ranges[b] = items;
+  std::vector<int64_t> ranges(grid + 1);
+  split_by_cost(cost.data(), items, grid, ranges.data());
   auto* P = new BatchPlanImpl();
   cudaGetDevice(&P->device);
   cudaError_t e = cudaMalloc(&P->d_groups, sizeof(BatchGroup) * ngroups);
@@ -682,6 +687,16 @@ int coffee_batch_plan_costs(const coffee_assemble_args* groups, int ngroups, int
     if (!(tile_cost[i] > 0.0) || !std::isfinite(tile_cost[i]))
       return fail(COFFEE_ERR_INVALID_ARG, "tile_cost must be positive and finite");
   return batch_plan_impl(groups, ngroups, grid, -1.0, tile_cost, plan);
+}
+
+int coffee_batch_split(const double* cost, int64_t items, int grid, int64_t* ranges) {
+  if (items < 0 || grid < 1) return fail(COFFEE_ERR_INVALID_ARG, "need items >= 0 and grid >= 1");
+  if (!ranges || (items > 0 && !cost)) return fail(COFFEE_ERR_INVALID_ARG, "cost and ranges must be non-NULL");
+  for (int64_t i = 0; i < items; ++i)
+    if (!(cost[i] >= 0.0) || !std::isfinite(cost[i]))
+      return fail(COFFEE_ERR_INVALID_ARG, "costs must be finite and >= 0");
+  split_by_cost(cost, items, grid, ranges);
+  return COFFEE_OK;
 }
 
 int coffee_batch_launch(void* plan, coffee_stream_t stream) {

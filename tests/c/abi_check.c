@@ -26,7 +26,8 @@ static const entry_fn entry_points[] = {
     (entry_fn)coffee_assemble_host, (entry_fn)coffee_host_pool_trim,
     (entry_fn)coffee_assemble_backward, (entry_fn)coffee_assemble_backward_noalloc,
     (entry_fn)coffee_batch_plan, (entry_fn)coffee_batch_plan_costs, (entry_fn)coffee_batch_launch,
-    (entry_fn)coffee_batch_free, (entry_fn)coffee_sparsity, (entry_fn)coffee_csr_map,
+    (entry_fn)coffee_batch_free, (entry_fn)coffee_batch_split, (entry_fn)coffee_sparsity,
+    (entry_fn)coffee_csr_map,
     (entry_fn)coffee_assemble_csr, (entry_fn)coffee_csr_supported, (entry_fn)coffee_check_errors,
     (entry_fn)coffee_last_error, (entry_fn)coffee_peak_fp64, (entry_fn)coffee_peak_mma,
     (entry_fn)coffee_diag_wait_timeout};

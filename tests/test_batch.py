@@ -144,3 +144,4 @@ def test_batch_validation_reports_a_bad_index_and_leaves_the_rest_intact():
     keep = torch.ones(outs[gi].shape[0], dtype=torch.bool, device=DEV)
     keep[3] = False
     assert torch.equal(outs[gi][keep], clean[gi][keep])
+
