@@ -536,6 +536,23 @@ int coffee_check_errors(coffee_stream_t stream) {
 
 const char* coffee_last_error(void) { return g_last_error.c_str(); }
 
+int coffee_table_image(int form, int degree, int cell, int precision, uint8_t* img, int64_t* nbytes,
+                       int64_t* meta) {
+  if (!nbytes) return fail(COFFEE_ERR_INVALID_ARG, "nbytes is NULL");
+  if (precision == PREC_FP64 || !coffee_supported(form, degree, cell, precision))
+    return fail(COFFEE_ERR_UNSUPPORTED, "no tensor-core kernel for this form/degree/cell/precision");
+  std::vector<uint8_t> h;
+  TcTable m{};
+  build_tc_image(form, degree, cell, precision, h, m);
+  *nbytes = (int64_t)h.size();
+  if (meta) {
+    const int64_t v[8] = {m.mtiles, m.kbytes, m.kelems, m.K, m.parts, m.aexact, m.ksteps_off, m.scale_off};
+    std::memcpy(meta, v, sizeof v);
+  }
+  if (img) std::memcpy(img, h.data(), h.size());
+  return COFFEE_OK;
+}
+
 int coffee_diag_wait_timeout(coffee_stream_t stream) {
   DeviceCache* c = nullptr;
   {

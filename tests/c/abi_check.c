@@ -30,7 +30,7 @@ static const entry_fn entry_points[] = {
     (entry_fn)coffee_csr_map,
     (entry_fn)coffee_assemble_csr, (entry_fn)coffee_csr_supported, (entry_fn)coffee_check_errors,
     (entry_fn)coffee_last_error, (entry_fn)coffee_peak_fp64, (entry_fn)coffee_peak_mma,
-    (entry_fn)coffee_diag_wait_timeout};
+    (entry_fn)coffee_diag_wait_timeout, (entry_fn)coffee_table_image};
 
 int main(void) {
   for (size_t i = 0; i < sizeof entry_points / sizeof entry_points[0]; ++i) CHECK(entry_points[i] != NULL);

@@ -1,0 +1,126 @@
+"""The tensor-core operand images (host-side set-up of the contraction) decoded on the CPU from
+the canonical no-swizzle K-major layout as include/coffee_diag.h defines it: every image holds
+the reference tensor T^T (rows = element-matrix entries, columns = K) to the accuracy of its
+precision split, zero padding elsewhere, and the Burgers images use exact integer columns where
+the paper's tensors allow them. No GPU needed."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import paper_1407_0904_gb300 as coffee
+
+TRI, TET = coffee.TRIANGLE, coffee.TETRAHEDRON
+SPLIT = {coffee.TF32X3: True, coffee.BF16X3: True, coffee.TF32: False, coffee.BF16: False}
+TF32 = {coffee.TF32X3: True, coffee.TF32: True, coffee.BF16X3: False, coffee.BF16: False}
+
+
+def image(form, k, cell, prec):
+    L = coffee.lib()
+    L.coffee_table_image.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p] * 3
+    n = ctypes.c_int64()
+    meta = (ctypes.c_int64 * 8)()
+    rc = L.coffee_table_image(form, k, cell, prec, None, ctypes.byref(n), meta)
+    if rc == -2:
+        return None
+    assert rc == 0, L.coffee_last_error()
+    img = np.zeros(n.value, dtype=np.uint8)
+    assert L.coffee_table_image(form, k, cell, prec, img.ctypes.data, ctypes.byref(n), None) == 0
+    return img, list(meta)
+
+
+def decode(part, kbytes, tf32):
+    """One 128-row part -> float32 [128, kbytes / elem] from its canonical layout."""
+    r = np.arange(128)[:, None]
+    kb = np.arange(kbytes)[None, :]
+    off = (r // 8) * 8 * kbytes + (kb // 16) * 128 + (r % 8) * 16 + kb % 16
+    raw = np.ascontiguousarray(part[off])                      # logical (row, byte) order
+    if tf32:
+        bits = raw.view(np.uint32)
+        assert np.all(bits & 0x1FFF == 0)                      # tf32: 10 stored mantissa bits
+        return bits.view(np.float32)
+    return (raw.view(np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+def operand(img, meta, tf32, aparts):
+    mtiles, kbytes, parts = meta[0], meta[1], meta[4]
+    tile = 128 * kbytes
+    hi, lo = [], []
+    for m in range(mtiles):
+        base = m * aparts * tile
+        hi.append(decode(img[base:base + tile], kbytes, tf32))
+        lo.append(decode(img[base + tile:base + 2 * tile], kbytes, tf32) if aparts == 2
+                  else np.zeros_like(hi[-1]))
+    return np.vstack(hi).astype(np.float64), np.vstack(lo).astype(np.float64)
+
+
+CASES = [(f, c, k, p) for f in (coffee.MASS, coffee.HELMHOLTZ, coffee.ADVDIFF) for c in (TRI, TET)
+         for k in (1, 2, 3, 4) for p in (coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16)]
+
+
+@pytest.mark.parametrize("form,cell,k,prec", CASES)
+def test_simplex_image_holds_the_reference_tensor(form, cell, k, prec):
+    got = image(form, k, cell, prec)
+    if got is None:
+        pytest.skip("no tensor-core kernel for this combination")
+    img, meta = got
+    mtiles, kbytes, kelems, K, parts = meta[:5]
+    tf32 = TF32[prec]
+    T = coffee.reference_tensor(form, k, cell)                 # [K, N]
+    N = T.shape[1]
+    assert K == T.shape[0] and mtiles == math.ceil(N / 128) and parts == (2 if SPLIT[prec] else 1)
+    assert kelems * (4 if tf32 else 2) == kbytes and kbytes % 32 == 0 and kelems >= K
+    assert len(img) == mtiles * parts * 128 * kbytes
+    hi, lo = operand(img, meta, tf32, parts)
+    ref = np.zeros_like(hi)
+    ref[:N, :K] = T.T
+    # padding rows and columns are zero
+    assert not hi[N:].any() and not hi[:, K:].any() and not lo[N:].any() and not lo[:, K:].any()
+    u = 2.0 ** -11 if tf32 else 2.0 ** -8                      # unit roundoff: 11 or 8 significant bits
+    bound = (u * u * 1.01 if parts == 2 else u) * np.abs(ref) + 1e-300
+    assert np.all(np.abs(hi + lo - ref) <= bound)
+    assert np.all(np.abs(hi - ref) <= u * np.abs(ref) + 1e-300)
+
+
+@pytest.mark.parametrize("cell,k", [(TRI, 1), (TRI, 2), (TRI, 3), (TRI, 4), (TET, 1), (TET, 2)])
+@pytest.mark.parametrize("prec", [coffee.TF32X3, coffee.BF16X3])
+def test_burgers_image_exact_integer_columns(cell, k, prec):
+    """P1-P2 on triangles and tetrahedra: every A column is an integer vector times a float scale
+    (one part, two MMA passes); triangles P3-P4 keep the split image. The columns are T1, then the
+    T2 and T3 rows of coffee_reference_tensor(BURGERS_JAC) after the off-diagonal K-steps."""
+    got = image(coffee.BURGERS_JAC, k, cell, prec)
+    if got is None:
+        pytest.skip("no tensor-core kernel for this combination")
+    img, meta = got
+    mtiles, kbytes, kelems, K, parts, aexact, ksteps_off, scale_off = meta
+    tf32 = TF32[prec]
+    assert aexact == (1 if k <= 2 else 0) and parts == 2
+    T = coffee.reference_tensor(coffee.BURGERS_JAC, k, cell)
+    d = 2 + cell
+    ns = coffee.nnodes(cell, k)
+    nb = ns * ns
+    K1, P = ns * d, d * (d + 1) // 2
+    KA1 = ksteps_off * (8 if tf32 else 16)
+    assert KA1 >= K1 and K == KA1 + K1 + P == T.shape[0] + (KA1 - K1)
+    hi, lo = operand(img, meta, tf32, 1 if aexact else 2)
+    A = hi + lo
+    if aexact:
+        ints = hi
+        assert np.all(ints == np.round(ints)) and not lo.any()
+        odd = np.abs(ints).astype(np.int64)
+        while np.any((odd > 0) & (odd % 2 == 0)):
+            odd = np.where((odd > 0) & (odd % 2 == 0), odd // 2, odd)
+        assert odd.max() < (2048 if tf32 else 256)
+        scales = np.frombuffer(img[scale_off:scale_off + 4 * kelems].tobytes(), dtype=np.float32)
+        assert np.all(np.isfinite(scales)) and np.all(scales > 0)
+        A = ints * scales[None, :].astype(np.float64)
+    trow = [kk if kk < K1 else ns * d + kk - KA1 if KA1 <= kk < KA1 + K1
+            else 2 * ns * d + kk - KA1 - K1 if KA1 + K1 <= kk < KA1 + K1 + P else -1 for kk in range(kelems)]
+    for kk, tr in enumerate(trow):
+        col = np.zeros(mtiles * 128)
+        if tr >= 0:
+            col[:nb] = T[tr]
+        scale = max(np.abs(col).max(), 1e-300)
+        tol = 2.0 ** -23 if aexact else ((2.0 ** -22) if tf32 else 2.0 ** -16) * 1.01
+        assert np.abs(A[:, kk] - col).max() <= tol * scale, (kk, tr)
