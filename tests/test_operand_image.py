@@ -124,3 +124,64 @@ def test_burgers_image_exact_integer_columns(cell, k, prec):
         scale = max(np.abs(col).max(), 1e-300)
         tol = 2.0 ** -23 if aexact else ((2.0 ** -22) if tf32 else 2.0 ** -16) * 1.01
         assert np.abs(A[:, kk] - col).max() <= tol * scale, (kk, tr)
+
+
+@pytest.mark.parametrize("form", [coffee.MASS, coffee.HELMHOLTZ, coffee.ADVDIFF])
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("prec", [coffee.TF32X3, coffee.BF16X3])
+def test_prism_image_holds_the_per_point_tensors_of_the_oracles_basis(form, k, prec):
+    """Prisms: K-chunks of 64 bytes per row (all 128-output slices, hi then lo, per chunk), then
+    the rule's points and weights as float4. The rule is the oracle's (as a set of points), and
+    column q*KQ + c holds, at point q, phi_i phi_j (MASS, HELMHOLTZ c = 0), the symmetric
+    derivative pairs (HELMHOLTZ c = 1..6, ADVDIFF c = 0..5) and phi_i d_a phi_j (ADVDIFF
+    c = 6..8), evaluated here with the oracle's own prism basis: an independent check of the
+    GPU side's prism tabulation and of the streamed layout."""
+    import oracle
+    img, meta = image(form, k, coffee.PRISM, prec)
+    mtiles, kbytes, kelems, K, parts, _, KQ, _ = meta
+    tf32 = TF32[prec]
+    kc = kbytes // (4 if tf32 else 2)
+    nkc = kelems // kc
+    n = oracle.prism_ndof(k)
+    N, Q = n * n, (k + 2) ** 3
+    assert KQ == {coffee.MASS: 1, coffee.HELMHOLTZ: 7, coffee.ADVDIFF: 9}[form] and K == Q * KQ
+    assert mtiles == math.ceil(N / 128) and parts == 2 and nkc == math.ceil(K / kc)
+    tb = 128 * kbytes
+    a_chunk = mtiles * parts * tb
+    assert len(img) == nkc * a_chunk + 16 * Q
+    cols = []
+    for c in range(nkc):
+        rows = []
+        for m in range(mtiles):
+            base = c * a_chunk + m * parts * tb
+            rows.append(decode(img[base:base + tb], kbytes, tf32).astype(np.float64)
+                        + decode(img[base + tb:base + 2 * tb], kbytes, tf32))
+        cols.append(np.vstack(rows))
+    A = np.hstack(cols)                                        # [mtiles*128, nkc*kc]
+    assert not A[N:].any() and not A[:, K:].any()
+    table = np.frombuffer(img[nkc * a_chunk:].tobytes(), dtype=np.float32).reshape(Q, 4).astype(np.float64)
+    pts, wts = table[:, :3], table[:, 3]
+    opts, owts = oracle.prism_rule(k)
+    assert len(owts) == Q
+    near = np.argmin(((pts[:, None, :] - opts[None, :, :]) ** 2).sum(-1), axis=1)
+    assert len(np.unique(near)) == Q
+    assert np.abs(pts - opts[near]).max() < 1e-6 and np.abs(wts - owts[near]).max() < 1e-6 * owts.max()
+    phi, dphi = oracle.prism_basis(k, pts)
+    pairs = [(a, b) for a in range(3) for b in range(a, 3)]
+    tol = 1e-5 if tf32 else 5e-5
+    for q in range(Q):
+        want = []
+        if KQ != 9:
+            want.append(np.outer(phi[q], phi[q]))
+        if KQ >= 7:
+            for a, b in pairs:
+                v = np.outer(dphi[q, :, a], dphi[q, :, b])
+                if a != b:
+                    v = v + np.outer(dphi[q, :, b], dphi[q, :, a])
+                want.append(v)
+        if KQ == 9:
+            want += [np.outer(phi[q], dphi[q, :, a]) for a in range(3)]
+        for c, w in enumerate(want):
+            got = A[:N, q * KQ + c]
+            scale = max(np.abs(w).max(), 1e-12)
+            assert np.abs(got - w.ravel()).max() <= tol * scale, (q, c)
