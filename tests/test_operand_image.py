@@ -185,3 +185,19 @@ def test_prism_image_holds_the_per_point_tensors_of_the_oracles_basis(form, k, p
             got = A[:N, q * KQ + c]
             scale = max(np.abs(w).max(), 1e-12)
             assert np.abs(got - w.ravel()).max() <= tol * scale, (q, c)
+
+
+@pytest.mark.parametrize("cell,k", [(TRI, 1), (TRI, 2), (TRI, 3), (TET, 1), (TET, 2)])
+def test_residual_image_is_the_split_burgers_image(cell, k):
+    """The residual kernel contracts the Jacobian's tensors with A split in hi and lo (it takes
+    no exact-integer form), so its image is the three-pass Burgers image."""
+    for prec in (coffee.TF32X3, coffee.BF16X3):
+        got = image(coffee.BURGERS_RESIDUAL, k, cell, prec)
+        if got is None:
+            continue
+        img, meta = got
+        assert meta[5] == 0 and meta[4] == 2
+        jac = image(coffee.BURGERS_JAC, k, cell, prec)
+        assert jac is not None and jac[1][:4] == meta[:4] and jac[1][6] == meta[6]
+        if jac[1][5] == 0:
+            assert np.array_equal(jac[0], img)  # without an exact form the two images coincide
