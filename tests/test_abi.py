@@ -243,3 +243,29 @@ def test_host_buffer_entry_point_rejects_bad_arguments_before_any_cuda_call():
     a.form, a.degree = coffee.HELMHOLTZ, 4
     a.cell = coffee.PRISM  # no tensor-core prism kernel at P4
     assert lib.coffee_assemble_host(ctypes.byref(a), 4, None) == -2
+
+
+def test_size_limits_are_rejected_on_the_host():
+    """The largest inputs the kernels index: more than 2^31 * 128 cells, nnz of 2^32 or more and an
+    unaligned entry map are refused before any CUDA call."""
+    lib = coffee.lib()
+    A = coffee.binding.AssembleArgs
+    a = A()
+    a.form, a.degree, a.cell, a.precision = coffee.HELMHOLTZ, 2, coffee.TETRAHEDRON, coffee.TF32X3
+    a.coords = a.cell2vert = a.out = 16
+    a.nverts = 10
+    a.ncells = (2 ** 31 - 1) * 128 + 1
+    assert lib.coffee_assemble_ex(ctypes.byref(a), None) == -1
+    assert b"ncells" in lib.coffee_last_error()
+    lib.coffee_assemble_csr.argtypes = [ctypes.POINTER(A), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_void_p]
+    a.ncells = 10
+    assert lib.coffee_assemble_csr(ctypes.byref(a), 256, 256, 2 ** 32, None) == -1
+    assert b"nnz" in lib.coffee_last_error()
+    assert lib.coffee_assemble_csr(ctypes.byref(a), 260, 256, 100, None) == -1
+    assert b"aligned" in lib.coffee_last_error()
+    lib.coffee_sparsity.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    nnz = ctypes.c_int64()
+    assert lib.coffee_sparsity(16, 2 ** 31, 4, 10, 16, None, ctypes.byref(nnz), None) == -1
+    assert lib.coffee_sparsity(16, 10, 129, 10, 16, None, ctypes.byref(nnz), None) == -1
