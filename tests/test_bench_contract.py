@@ -34,3 +34,21 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_other_ranks_exit_quietly():
     assert run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_algorithmic_bytes_per_cell_of_the_headline_and_burgers_workloads():
+    """Roofline numerators: every input read once plus the output written once. Helmholtz P3 on the
+    64^3 x 6 Kuhn mesh: 16 B of cell2vert, 24 nverts/ncells B of coordinates and 1600 B of element
+    matrix = 1620.2 B per cell; Burgers P2 on 2^20 tets adds cell2dof (40 B) and u."""
+    sys.path.insert(0, ROOT)
+    import bench
+    wl = bench.WORKLOADS[bench.HEADLINE]
+    mesh, coef, c2d = wl.build(None)
+    b = bench.alg_bytes_per_cell(wl, mesh, c2d, coef, 20, 4)
+    assert abs(b - (16 + 24 * 65 ** 3 / (64 ** 3 * 6) + 1600)) < 1e-9 and abs(b - 1620.2) < 0.05
+    wl = bench.WORKLOADS["burgers-p2-tet"]
+    mesh, coef, c2d = wl.build(None)
+    nn = coef.size // 3
+    b = bench.alg_bytes_per_cell(wl, mesh, c2d, coef, 30, 4)
+    want = 16 + 24 * mesh.nverts / mesh.ncells + 3600 + 40 + 24 * nn / mesh.ncells
+    assert abs(b - want) < 1e-9 and abs(b - 3693) < 1.0
