@@ -61,3 +61,21 @@ def test_missing_library_fails_loudly_without_a_fallback(tmp_path):
             "print('raised')\n" % str(tmp_path / "libcoffee.so"))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == "raised", r.stdout + r.stderr
+
+
+def test_only_tests_smoke_build_and_the_benchmark_cpu_legs_import_the_oracle():
+    pat = re.compile(r"^\s*(import\s+oracle|from\s+oracle\b)", re.M)
+    users = set()
+    for p in sources(ROOT, (".py",)):
+        rel = os.path.relpath(p, ROOT)
+        if rel.startswith(("tests" + os.sep, "oracle" + os.sep, "_work" + os.sep, "gpurun_out" + os.sep,
+                           "baseline" + os.sep)):
+            continue
+        if pat.search(open(p).read()):
+            users.add(rel)
+    assert users <= {"__graft_entry__.py", "bench.py"}, users
+    tree = ast.parse(open(os.path.join(ROOT, "__graft_entry__.py")).read())
+    for fn in [n for n in tree.body if isinstance(n, ast.FunctionDef)]:
+        imports = [a.name for n in ast.walk(fn) if isinstance(n, ast.Import) for a in n.names]
+        if "oracle" in imports:
+            assert fn.name in {"build", "smoke"}, fn.name
