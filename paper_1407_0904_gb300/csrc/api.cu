@@ -248,7 +248,7 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
   p.N = ndof * ndof;
   p.mtiles = meta.mtiles;
   p.kbytes = meta.kbytes;
-  p.parts = meta.parts;
+  p.tparts = meta.tparts;
   p.ksteps_off = meta.ksteps_off;
   p.aexact = meta.aexact;
   p.scale_off = meta.scale_off;
@@ -546,7 +546,7 @@ int coffee_table_image(int form, int degree, int cell, int precision, uint8_t* i
   build_tc_image(form, degree, cell, precision, h, m);
   *nbytes = (int64_t)h.size();
   if (meta) {
-    const int64_t v[8] = {m.mtiles, m.kbytes, m.kelems, m.K, m.parts, m.aexact, m.ksteps_off, m.scale_off};
+    const int64_t v[8] = {m.mtiles, m.kbytes, m.kelems, m.K, m.tparts, m.aexact, m.ksteps_off, m.scale_off};
     std::memcpy(meta, v, sizeof v);
   }
   if (img) std::memcpy(img, h.data(), h.size());
@@ -613,7 +613,7 @@ int batch_plan_impl(const coffee_assemble_args* groups, int ngroups, int grid, d
   if (rc != COFFEE_OK) return rc;
   std::vector<BatchGroup> hg(ngroups);
   std::vector<double> cost;  // per work item
-  int kbytes_max = 32, parts = 1;
+  int kbytes_max = 32;
   int64_t items = 0;
   for (int i = 0; i < ngroups; ++i) {
     const coffee_assemble_args* a = &groups[i];
@@ -636,7 +636,7 @@ int batch_plan_impl(const coffee_assemble_args* groups, int ngroups, int grid, d
     g.p.N = ns * ns;
     g.p.mtiles = meta.mtiles;
     g.p.kbytes = meta.kbytes;
-    g.p.parts = meta.parts;
+    g.p.tparts = meta.tparts;
     g.p.precision = prec;
     g.p.validate = (a->flags & COFFEE_FLAG_VALIDATE) ? 1 : 0;
     g.p.nu = a->nu;
@@ -646,7 +646,6 @@ int batch_plan_impl(const coffee_assemble_args* groups, int ngroups, int grid, d
     g.degree = a->degree;
     g.lanes = g.p.N <= 32 ? 1 : 0;
     kbytes_max = std::max(kbytes_max, meta.kbytes);
-    parts = meta.parts;
     const int64_t nt = (a->ncells + 127) / 128;
     for (int64_t t = 0; t < nt; ++t) {
       const int64_t cells = std::min<int64_t>(128, a->ncells - t * 128);
@@ -657,7 +656,7 @@ int batch_plan_impl(const coffee_assemble_args* groups, int ngroups, int grid, d
   }
   if (items == 0) return fail(COFFEE_ERR_INVALID_ARG, "all groups are empty");
   int nstages = 0;
-  const int smem = batch_smem(kbytes_max, parts, &nstages);
+  const int smem = batch_smem(kbytes_max, prec, &nstages);
   if (smem == 0) return fail(COFFEE_ERR_UNSUPPORTED, "batch operands do not fit in shared memory");
   if (grid <= 0) grid = c->num_sms;
   grid = (int)std::min<int64_t>(grid, items);

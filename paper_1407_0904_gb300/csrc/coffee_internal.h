@@ -18,6 +18,14 @@ enum { FORM_MASS = 0, FORM_HELMHOLTZ = 1, FORM_ADVDIFF = 2, FORM_BURGERS = 3, FO
 inline int table_form(int form) { return form == FORM_BURGERS_RES ? FORM_BURGERS : form; }
 inline bool burgers_like(int form) { return form == FORM_BURGERS || form == FORM_BURGERS_RES; }
 enum { PREC_FP64 = 0, PREC_TF32 = 1, PREC_TF32X3 = 2, PREC_BF16 = 3, PREC_BF16X3 = 4 };
+// Parts of the tensor-core operands per precision (see PrecTraits in tc_common.cuh): the
+// reference tensor T and the per-cell factors G are each held as a sum of this many tf32/bf16 values.
+COFFEE_HD constexpr int prec_tparts(int prec) {
+  return prec == PREC_TF32 ? 1 : prec == PREC_BF16X3 ? 3 : 2;
+}
+COFFEE_HD constexpr int prec_gparts(int prec) {
+  return prec == PREC_TF32X3 ? 2 : prec == PREC_BF16X3 ? 3 : 1;
+}
 
 // Device error word bits
 enum : unsigned { ERR_INDEX = 1u, ERR_TIMEOUT = 2u, ERR_CAPACITY = 4u };
@@ -111,15 +119,16 @@ int launch_ordered_sum(const int32_t* idx, int64_t ncells, int width, int64_t nn
 
 // ---- tcgen05 tensor-core contraction (k_tc.cu) ----
 // Operand image of the reference tensor for the tensor cores: for each M-tile of
-// 128 output rows, the hi part then (split precisions) the lo part, each
-// 128 rows x kbytes bytes in the canonical no-swizzle K-major core-matrix layout.
+// 128 output rows, the tparts parts of T^T (the first the round-to-nearest of T, each next
+// one of what the previous left), each 128 rows x kbytes bytes in the canonical no-swizzle
+// K-major core-matrix layout.
 struct TcTable {
   const uint8_t* image;  // device
   int mtiles;            // ceil(N / 128) (per block for Burgers)
   int kbytes;            // bytes per operand row (multiple of 32)
   int kelems;            // padded K (elements)
   int K;                 // true K
-  int parts;             // 1 (single pass) or 2 (hi, lo)
+  int tparts;            // parts of T held per M-tile (1, 2 or 3; 1 when aexact)
   int ksteps_off;        // Burgers: K-steps of the off-diagonal component blocks
   int64_t tile_bytes;    // bytes of one part of one M-tile = 128 * kbytes
   int aexact;            // 1: every A column is an integer vector times a scale, so A is held
@@ -137,7 +146,7 @@ struct TcParams {
   unsigned* err;
   int64_t ncells, nverts, ncoefnodes;
   int ns, N;             // outputs per cell
-  int mtiles, kbytes, parts;
+  int mtiles, kbytes, tparts;  // tparts: TcTable::tparts
   int ksteps_off;        // Burgers: K-steps of the off-diagonal component blocks
   unsigned tune;         // TUNE_* knobs
   int subw;              // cells per TMEM accumulator (outputs-on-lanes orientation)
@@ -173,12 +182,12 @@ struct BatchLaunch {
   int grid, smem, nstages, kbytes_max, precision;
   unsigned* err;
 };
-int batch_smem(int kbytes_max, int parts, int* nstages);
+int batch_smem(int kbytes_max, int precision, int* nstages);
 // diagnostic bounded wait that runs out (k_peaks.cu)
 int launch_diag_wait(unsigned* err, void* stream);
 int batch_prepare(int precision, int smem);
 int batch_launch(const BatchLaunch& L, void* stream);
-int stream_one_supported(int form, int kbytes, int parts);
+int stream_one_supported(int form, int kbytes, int precision);
 int launch_stream_one(const BatchGroup& g, int num_sms, void* stream);
 
 // ---- global assembly (k_csr.cu, k_tc_csr.cu) ----

@@ -75,8 +75,7 @@ struct GroupCursor {
 };
 
 template <int PREC, int FORM, int D>
-__device__ __forceinline__ void produce_row(const BatchGroup& g, int64_t e, bool live, uint8_t* hi, uint8_t* lo,
-                                            int row) {
+__device__ __forceinline__ void produce_row(const BatchGroup& g, int64_t e, bool live, uint8_t* base, int row) {
   using PT = PrecTraits<PREC>;
   constexpr int KSTEP = PT::tf32 ? 8 : 16;
   constexpr int KP = round_up(Form<FORM, D>::K, KSTEP);
@@ -90,20 +89,22 @@ __device__ __forceinline__ void produce_row(const BatchGroup& g, int64_t e, bool
 #pragma unroll
     for (int k = 0; k < KP; ++k) G[k] = 0.f;
   }
-  store_operand_row<PREC, KP>(hi, lo, row, G, g.p.kbytes);
+  store_operand_row<PREC, KP>(base, BM * g.p.kbytes, row, G, g.p.kbytes);
 }
 
 template <int PREC>
 __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups, int ngroups, int64_t it0,
                                            int64_t it1, int nstages, int kbytes_max, unsigned* err) {
   using PT = PrecTraits<PREC>;
-  constexpr int PARTS = PT::split ? 2 : 1;
+  constexpr int TPARTS = PT::TPARTS, GPARTS = PT::GPARTS;
+  using PS = Passes<PREC>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int slot_bytes = PARTS * BM * kbytes_max;  // one A slot or one B stage
+  const int slot_bytes = TPARTS * BM * kbytes_max;   // one A slot (T^T parts of one M-tile)
+  const int stage_bytes = GPARTS * BN * kbytes_max;  // one B stage (factor parts of one tile)
   uint8_t* sA = smem;
   uint8_t* sB = smem + ASLOTS * slot_bytes;
-  BatchBars* bars = reinterpret_cast<BatchBars*>(sB + nstages * slot_bytes);
+  BatchBars* bars = reinterpret_cast<BatchBars*>(sB + nstages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -151,15 +152,14 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
       if (!mbar_wait(smem_u32(&bars->empty[s]), (use & 1u) ^ 1u, err)) break;
       const int64_t e = (it - g.item0) * BN + row;
       const bool live = e < g.p.ncells;
-      uint8_t* hi = sB + (size_t)s * slot_bytes;
-      uint8_t* lo = hi + BM * g.p.kbytes;
+      uint8_t* b = sB + (size_t)s * stage_bytes;
       switch (g.form * 2 + g.cell) {
-        case FORM_MASS * 2 + CELL_TRI: produce_row<PREC, FORM_MASS, 2>(g, e, live, hi, lo, row); break;
-        case FORM_MASS * 2 + CELL_TET: produce_row<PREC, FORM_MASS, 3>(g, e, live, hi, lo, row); break;
-        case FORM_HELMHOLTZ * 2 + CELL_TRI: produce_row<PREC, FORM_HELMHOLTZ, 2>(g, e, live, hi, lo, row); break;
-        case FORM_HELMHOLTZ * 2 + CELL_TET: produce_row<PREC, FORM_HELMHOLTZ, 3>(g, e, live, hi, lo, row); break;
-        case FORM_ADVDIFF * 2 + CELL_TRI: produce_row<PREC, FORM_ADVDIFF, 2>(g, e, live, hi, lo, row); break;
-        default: produce_row<PREC, FORM_ADVDIFF, 3>(g, e, live, hi, lo, row); break;
+        case FORM_MASS * 2 + CELL_TRI: produce_row<PREC, FORM_MASS, 2>(g, e, live, b, row); break;
+        case FORM_MASS * 2 + CELL_TET: produce_row<PREC, FORM_MASS, 3>(g, e, live, b, row); break;
+        case FORM_HELMHOLTZ * 2 + CELL_TRI: produce_row<PREC, FORM_HELMHOLTZ, 2>(g, e, live, b, row); break;
+        case FORM_HELMHOLTZ * 2 + CELL_TET: produce_row<PREC, FORM_HELMHOLTZ, 3>(g, e, live, b, row); break;
+        case FORM_ADVDIFF * 2 + CELL_TRI: produce_row<PREC, FORM_ADVDIFF, 2>(g, e, live, b, row); break;
+        default: produce_row<PREC, FORM_ADVDIFF, 3>(g, e, live, b, row); break;
       }
       fence_proxy_async();
       mbar_arrive(smem_u32(&bars->full[s]));
@@ -188,11 +188,11 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
             continue;
           }
           tag[j] = gi * 64 + m;
-          mbar_arrive_expect_tx(bar, part_bytes * PARTS);
-          const uint8_t* src = g.p.image + (size_t)m * PARTS * part_bytes;
+          mbar_arrive_expect_tx(bar, part_bytes * TPARTS);
+          const uint8_t* src = g.p.image + (size_t)m * TPARTS * part_bytes;
           const uint32_t dst = smem_u32(sA + (size_t)j * slot_bytes);
 #pragma unroll
-          for (int q = 0; q < PARTS; ++q) bulk_g2s(dst + q * part_bytes, src + (size_t)q * part_bytes, part_bytes, bar);
+          for (int q = 0; q < TPARTS; ++q) bulk_g2s(dst + q * part_bytes, src + (size_t)q * part_bytes, part_bytes, bar);
         }
       }
       // every copy this thread started has landed before shared memory is released (phases
@@ -220,7 +220,7 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
         stage_of(k / PROD_GROUPS, k % PROD_GROUPS, nstages / PROD_GROUPS, s, use);
         if (!mbar_wait(smem_u32(&bars->full[s]), use & 1u, err)) break;
         tc_fence_after();
-        const uint32_t bstage = b0 + (uint32_t)(s * slot_bytes);
+        const uint32_t bstage = b0 + (uint32_t)(s * stage_bytes);
         for (int m = 0; m < g.p.mtiles; ++m, ++rc, ++ma) {
           const uint32_t j = ma % ASLOTS, around = ma / ASLOTS;
           if (!mbar_wait(smem_u32(&bars->afull[j]), around & 1u, err)) { ok = false; break; }
@@ -229,21 +229,18 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
           tc_fence_after();
           const uint32_t d = tmem + slot * BN;
           const uint32_t atile = a0 + j * (uint32_t)slot_bytes;
-          // outputs on lanes: A = T^T slice, B = G stage; cells on lanes: A = G, B = T^T
-          const uint32_t xo = lanes ? bstage : atile, xc = lanes ? atile : bstage;
           uint32_t acc = 0;
           for (int ks = 0; ks < ksteps; ++ks) {
             const uint32_t ko = (uint32_t)ks * 256u;
-            if constexpr (PT::split) {
-              // small terms first: T_hi G_lo, T_lo G_hi, then T_hi G_hi
-              const uint32_t ahl = lanes ? xo + part : xo, bhl = lanes ? xc : xc + part;
-              mma<PT::tf32>(d, make_desc(ahl + ko, sbo), make_desc(bhl + ko, sbo), idesc, acc);
+#pragma unroll
+            for (int i = 0; i < PS::N; ++i) {
+              // part t of T^T and part g of G, smallest products first; outputs on lanes:
+              // A = T^T slice, B = G stage; cells on lanes: A = G, B = T^T
+              const uint32_t tt = atile + (uint32_t)PS::t(i) * part + ko;
+              const uint32_t gg = bstage + (uint32_t)PS::g(i) * part + ko;
+              mma<PT::tf32>(d, make_desc(lanes ? gg : tt, sbo), make_desc(lanes ? tt : gg, sbo), idesc, acc);
               acc = 1;
-              const uint32_t alh = lanes ? xo : xo + part, blh = lanes ? xc + part : xc;
-              mma<PT::tf32>(d, make_desc(alh + ko, sbo), make_desc(blh + ko, sbo), idesc, 1);
             }
-            mma<PT::tf32>(d, make_desc(xo + ko, sbo), make_desc(xc + ko, sbo), idesc, acc);
-            acc = 1;
           }
           tc_commit(smem_u32(&bars->tfull[slot]));
           tc_commit(smem_u32(&bars->aempty[j]));
@@ -379,14 +376,14 @@ cudaError_t launch_t(const BatchLaunch& L, cudaStream_t s) {
 
 }  // namespace
 
-int batch_smem(int kbytes_max, int parts, int* nstages) {
-  const int slot = parts * BM * kbytes_max;
+int batch_smem(int kbytes_max, int precision, int* nstages) {
+  const int slot = prec_tparts(precision) * BM * kbytes_max, stage = prec_gparts(precision) * BN * kbytes_max;
   const int fixed = ASLOTS * slot + (int)sizeof(BatchBars) + 1024 + 64;
   int s = MAX_STAGES;  // even: the stages are split between the two producer groups
-  while (s >= 2 && fixed + s * slot > SMEM_LIMIT) s -= 2;
+  while (s >= 2 && fixed + s * stage > SMEM_LIMIT) s -= 2;
   if (s < 2) return 0;
   *nstages = s;
-  const int smem = fixed + s * slot;
+  const int smem = fixed + s * stage;
   return smem < SMEM_ONE_CTA ? SMEM_ONE_CTA : smem;
 }
 
@@ -402,15 +399,15 @@ int batch_prepare(int precision, int smem) {
 
 // Single group with its T^T operand streamed per M-tile (used when it does not fit in
 // shared memory for the resident-operand kernel).
-int stream_one_supported(int form, int kbytes, int parts) {
+int stream_one_supported(int form, int kbytes, int precision) {
   int nst = 0;
-  return form != FORM_BURGERS && batch_smem(kbytes, parts, &nst) > 0;
+  return form != FORM_BURGERS && batch_smem(kbytes, precision, &nst) > 0;
 }
 
 int launch_stream_one(const BatchGroup& g, int num_sms, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int nstages = 0;
-  const int smem = batch_smem(g.p.kbytes, g.p.parts, &nstages);
+  const int smem = batch_smem(g.p.kbytes, g.p.precision, &nstages);
   if (smem == 0) return (int)cudaErrorInvalidValue;
   cudaError_t e = (cudaError_t)batch_prepare(g.p.precision, smem);
   if (e != cudaSuccess) return (int)e;

@@ -7,7 +7,7 @@
 // degree-1 prism fields eps, b given at the six vertices). The contraction
 // over K = Q*KQ (189 at P1, 448 at P2) is too deep to keep either operand resident, so both are
 // streamed through shared memory in K-chunks of 64 bytes per row (16 tf32 / 32 bf16 columns):
-//   loader warp 13      one bulk copy per chunk of T^T (all 128-output slices, hi and lo),
+//   loader warp 13      one bulk copy per chunk of T^T (all 128-output slices, all parts),
 //                       completion counted on the stage's mbarrier (transaction bytes);
 //   producer warps 4-11 two threads per cell, each forming half of the chunk's columns of G_e
 //                       (geometry per point in FP32, J from per-cell bilinear coefficients),
@@ -63,16 +63,17 @@ __device__ __forceinline__ void prism_bulk_g2s(uint32_t dst, const void* src, ui
 template <int PREC, int KQ, bool CSR>
 __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParams p, int nstages) {
   using PT = PrecTraits<PREC>;
-  constexpr int PARTS = PT::split ? 2 : 1;
+  constexpr int TPARTS = PT::TPARTS, GPARTS = PT::GPARTS;
+  using PS = Passes<PREC>;
   constexpr int KC = PT::tf32 ? 16 : 32;  // K columns per chunk
   constexpr int TB = BM * PCB;            // bytes of one 128-row part of one chunk
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int MT = p.mtiles, NKC = p.nkc, Q = p.ns, N = p.N;
   const int SG = MT < PSG ? MT : PSG, NG = (MT + SG - 1) / SG;  // slices per group, groups
-  const int a_full = MT * PARTS * TB;            // T^T chunk in the image (all slices)
-  const int a_chunk = SG * PARTS * TB;           // T^T part of a stage (one group)
-  const int stage_bytes = a_chunk + PARTS * TB;  // + the G part
+  const int a_full = MT * TPARTS * TB;            // T^T chunk in the image (all slices)
+  const int a_chunk = SG * TPARTS * TB;           // T^T part of a stage (one group)
+  const int stage_bytes = a_chunk + GPARTS * TB;  // + the G parts
   PBars* bars = reinterpret_cast<PBars*>(smem + nstages * stage_bytes);
   float4* qsm = reinterpret_cast<float4*>(reinterpret_cast<uint8_t*>(bars) + 256);  // points (s,t,z,w) [Q]
 
@@ -229,41 +230,16 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
             if (f == i) v = gf[i];
           return v;
         };
-        uint8_t* b = smem + (size_t)s * stage_bytes + a_chunk;  // G part of the stage
-        // this thread's half of the chunk: 32 bytes of the row (two 16-byte stores per part)
-        if constexpr (PT::tf32) {
+        uint8_t* b = smem + (size_t)s * stage_bytes + a_chunk;  // G parts of the stage
+        // this thread's half of the chunk: 32 bytes of the row (two 16-byte units per part)
+        constexpr int PER = PT::tf32 ? 4 : 8;  // columns per 16-byte unit
 #pragma unroll
-          for (int cc = 0; cc < 2; ++cc) {
-            const int c16 = half * 2 + cc;  // 16-byte unit of the 64-byte row
-            uint32_t h[4], l[4];
+        for (int cc = 0; cc < 2; ++cc) {
+          const int c16 = half * 2 + cc;  // 16-byte unit of the 64-byte row
+          float x[PER];
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-              const float x = factor(c16 * 4 + qq);
-              h[qq] = tf32_rna(x);
-              l[qq] = tf32_rna(x - __uint_as_float(h[qq]));
-            }
-            const uint32_t off = canon_off(row, c16 * 16, PCB);
-            *reinterpret_cast<uint4*>(b + off) = make_uint4(h[0], h[1], h[2], h[3]);
-            if constexpr (PT::split) *reinterpret_cast<uint4*>(b + TB + off) = make_uint4(l[0], l[1], l[2], l[3]);
-          }
-        } else {
-#pragma unroll
-          for (int cc = 0; cc < 2; ++cc) {
-            const int c16 = half * 2 + cc;
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-              const float x0 = factor(c16 * 8 + 2 * qq), x1 = factor(c16 * 8 + 2 * qq + 1);
-              const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-              const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-              const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-              h[qq] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-              l[qq] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-            }
-            const uint32_t off = canon_off(row, c16 * 16, PCB);
-            *reinterpret_cast<uint4*>(b + off) = make_uint4(h[0], h[1], h[2], h[3]);
-            if constexpr (PT::split) *reinterpret_cast<uint4*>(b + TB + off) = make_uint4(l[0], l[1], l[2], l[3]);
-          }
+          for (int qq = 0; qq < PER; ++qq) x[qq] = factor(c16 * PER + qq);
+          store_unit<PT::tf32, GPARTS>(b + canon_off(row, c16 * 16, PCB), TB, x);
         }
         fence_proxy_async();
         mbar_arrive(smem_u32(&bars->full[s]));
@@ -278,14 +254,14 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
       for (int gi = 0; gi < NG && ok; ++gi) {
         const int m0 = gi * SG, mt = MT - m0 < SG ? MT - m0 : SG;  // the group's slices
-        const uint32_t bytes = (uint32_t)(mt * PARTS * TB);
+        const uint32_t bytes = (uint32_t)(mt * TPARTS * TB);
         for (int kc = 0; kc < NKC; ++kc, ++c) {
           const int s = (int)(c % nstages);
           if (!mbar_wait(smem_u32(&bars->empty[s]), ((c / nstages) & 1u) ^ 1u, p.err)) { ok = false; break; }
           const uint32_t bar = smem_u32(&bars->full[s]);
           prism_expect_tx(bar, bytes);
           prism_bulk_g2s(smem_u32(smem + (size_t)s * stage_bytes),
-                         p.image + (size_t)kc * a_full + (size_t)m0 * PARTS * TB, bytes, bar);
+                         p.image + (size_t)kc * a_full + (size_t)m0 * TPARTS * TB, bytes, bar);
         }
       }
       // every issued copy is consumed by the MMA thread's wait on its stage (or the kernel timed out)
@@ -316,17 +292,17 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
           const uint32_t g = st + (uint32_t)a_chunk;
           for (int m = 0; m < mt; ++m) {
             const uint32_t d = tmem + ((rc + m) % RING) * BN;
-            const uint32_t a = st + (uint32_t)(m * PARTS * TB);
+            const uint32_t a = st + (uint32_t)(m * TPARTS * TB);
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
               const uint32_t ko = (uint32_t)ks * 256u;
               uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-              if constexpr (PT::split) {
-                mma<PT::tf32>(d, make_desc(a + ko, sbo), make_desc(g + TB + ko, sbo), idesc, acc);
+#pragma unroll
+              for (int i = 0; i < PS::N; ++i) {  // products of parts, smallest first
+                mma<PT::tf32>(d, make_desc(a + (uint32_t)(PS::t(i) * TB) + ko, sbo),
+                              make_desc(g + (uint32_t)(PS::g(i) * TB) + ko, sbo), idesc, acc);
                 acc = 1;
-                mma<PT::tf32>(d, make_desc(a + TB + ko, sbo), make_desc(g + ko, sbo), idesc, 1);
               }
-              mma<PT::tf32>(d, make_desc(a + ko, sbo), make_desc(g + ko, sbo), idesc, acc);
             }
           }
           tc_commit(smem_u32(&bars->empty[s]));
@@ -416,7 +392,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
 }
 
 struct PGeom {
-  int n, N, mtiles, KQ, Q, K, nkc, parts, kc, elem;
+  int n, N, mtiles, KQ, Q, K, nkc, tparts, gparts, kc, elem;
   int a_chunk;  // bytes of one chunk of T^T in the image (all slices)
   int stage;    // bytes of one shared-memory stage (one slice group of T^T + the G part)
 };
@@ -434,10 +410,11 @@ bool pgeom(int form, int degree, int prec, PGeom& g) {
   g.elem = tf32 ? 4 : 2;
   g.kc = PCB / g.elem;
   g.nkc = (g.K + g.kc - 1) / g.kc;
-  g.parts = (prec == PREC_TF32X3 || prec == PREC_BF16X3) ? 2 : 1;
-  g.a_chunk = g.mtiles * g.parts * BM * PCB;
+  g.tparts = prec_tparts(prec);
+  g.gparts = prec_gparts(prec);
+  g.a_chunk = g.mtiles * g.tparts * BM * PCB;
   const int sg = g.mtiles < PSG ? g.mtiles : PSG;
-  g.stage = (sg + 1) * g.parts * BM * PCB;
+  g.stage = (sg * g.tparts + g.gparts) * BM * PCB;
   return true;
 }
 
@@ -504,20 +481,8 @@ void build_prism_tc_image(int form, int degree, int prec, std::vector<uint8_t>& 
         for (int j = 0; j < g.kc; ++j) {
           const int k = kc * g.kc + j;
           const double x = (o < g.N && k < g.K) ? T[(size_t)k * g.N + o] : 0.0;
-          const uint32_t off = canon_off(r, j * g.elem, PCB);
-          uint8_t* hi = img.data() + (size_t)kc * g.a_chunk + (size_t)(m * g.parts) * tb;
-          uint8_t* lo = hi + tb;
-          if (tf32) {
-            const uint32_t h = host_tf32_rna((float)x);
-            const uint32_t l = host_tf32_rna((float)(x - (double)host_f(h)));
-            std::memcpy(hi + off, &h, 4);
-            if (g.parts == 2) std::memcpy(lo + off, &l, 4);
-          } else {
-            const uint16_t h = host_bf16_rn((float)x);
-            const uint16_t l = host_bf16_rn((float)(x - (double)host_bf16_f(h)));
-            std::memcpy(hi + off, &h, 2);
-            if (g.parts == 2) std::memcpy(lo + off, &l, 2);
-          }
+          host_store_parts(img.data() + (size_t)kc * g.a_chunk + (size_t)(m * g.tparts) * tb, tb,
+                           canon_off(r, j * g.elem, PCB), x, tf32, g.tparts);
         }
       }
   float* qp = reinterpret_cast<float*>(img.data() + (size_t)g.nkc * g.a_chunk);
@@ -532,7 +497,7 @@ void build_prism_tc_image(int form, int degree, int prec, std::vector<uint8_t>& 
   meta.kbytes = PCB;
   meta.kelems = g.nkc * g.kc;
   meta.K = g.K;
-  meta.parts = g.parts;
+  meta.tparts = g.tparts;
   meta.ksteps_off = g.KQ;
   meta.tile_bytes = (int64_t)tb;
 }

@@ -11,12 +11,14 @@
 // Work decomposition (one persistent CTA per SM, cells tiled by 128):
 //   producer warps 4..11  (two groups on alternate tiles) gather each cell's vertices (and coefficient dofs),
 //                         compute J, det, adj in FP32 (FP64 when the cell is badly
-//                         conditioned) and the factors G_e, split them into
-//                         tensor-core operands (tf32 or bf16, hi/lo for the split
-//                         precisions) and store them as the B operand (cells x K,
+//                         conditioned) and the factors G_e (stiffness in the edge basis
+//                         c_ij = |det J| grad(lambda_i).grad(lambda_j)), split them into
+//                         tensor-core operands (tf32 or bf16, one to three parts per
+//                         precision) and store them as the B operand (cells x K,
 //                         K-major) of a shared-memory stage;
 //   MMA warp 12           one thread issues tcgen05.mma: D[o][cell] += T^T[o][k] G[cell][k]
-//                         for every 128-row slice of the outputs into TMEM accumulators;
+//                         for every 128-row slice of the outputs into TMEM accumulators,
+//                         one MMA per product of parts the precision keeps (Passes);
 //   epilogue warps 0..3   tcgen05.ld the accumulator and store it: 128-byte warp stores
 //                         of 32 outputs of one cell (outputs on the TMEM lanes), or
 //                         16-byte stores of a thread's own row (cells on the lanes, for
@@ -75,7 +77,44 @@ int tc_supported(int form, int degree, int cell, int precision) {
   Geom g;
   if (degree < 1 || degree > 4 || !geom_of(form, degree, cell, precision, g)) return 0;
   if (stages_for(g) > 0) return 1;
-  return stream_one_supported(form, g.kbytes, g.parts);
+  return stream_one_supported(form, g.kbytes, precision);
+}
+
+// The stiffness reference tensors re-expressed for the edge factors of cell_factors: rows
+// r0 .. r0+P-1 of T hold the pairs (a <= b) of reference directions and become the edges
+// (i < j) of the simplex. With H_ab = c_{a+1,b+1} (a != b) and H_aa = -sum_{j != a+1} c_{a+1,j},
+// sum_{a<=b} H_ab T_ab = sum_a c_{0,a+1} (-T_aa) + sum_{a<b} c_{a+1,b+1} (T_ab - T_aa - T_bb).
+void to_edge_basis(std::vector<double>& T, int N, int r0, int d) {
+  const int P = npairs(d);
+  auto pr = [&](int a, int b) {  // row of the pair (a, b), a <= b
+    for (int p = 0; p < P; ++p) {
+      int x, y;
+      pair_index(d, p, x, y);
+      if (x == a && y == b) return r0 + p;
+    }
+    return -1;
+  };
+  std::vector<double> E((size_t)P * N);
+  int e = 0;
+  for (int i = 0; i <= d; ++i)
+    for (int j = i + 1; j <= d; ++j, ++e)
+      for (int o = 0; o < N; ++o) {
+        double v;
+        if (i == 0) v = -T[(size_t)pr(j - 1, j - 1) * N + o];
+        else
+          v = T[(size_t)pr(i - 1, j - 1) * N + o] - T[(size_t)pr(i - 1, i - 1) * N + o] -
+              T[(size_t)pr(j - 1, j - 1) * N + o];
+        E[(size_t)e * N + o] = v;
+      }
+  std::copy(E.begin(), E.end(), T.begin() + (size_t)r0 * N);
+}
+
+void tc_reference_tensor(int form, int degree, int cell, std::vector<double>& T) {
+  reference_tensor(form, degree, cell, T);
+  const int d = cell == CELL_TRI ? 2 : 3, P = npairs(d), ns = nnodes(cell, degree), N = ns * ns;
+  if (form == FORM_HELMHOLTZ) to_edge_basis(T, N, 1, d);
+  if (form == FORM_ADVDIFF)
+    for (int v = 0; v <= d; ++v) to_edge_basis(T, N, v * P, d);
 }
 
 void build_tc_image(int form, int degree, int cell, int prec, std::vector<uint8_t>& img, TcTable& meta) {
@@ -87,34 +126,21 @@ void build_tc_image(int form, int degree, int cell, int prec, std::vector<uint8_
     build_burgers_image(degree, cell, prec, form == FORM_BURGERS, img, meta);
     return;
   }
-  Geom g;
+  Geom g{};
   geom_of(form, degree, cell, prec, g);
   std::vector<double> T;
-  reference_tensor(form, degree, cell, T);
+  tc_reference_tensor(form, degree, cell, T);
   const bool tf32 = prec == PREC_TF32 || prec == PREC_TF32X3;
   const int elem = tf32 ? 4 : 2;
   const int64_t tile = (int64_t)BM * g.kbytes;
-  img.assign((size_t)(g.mtiles * g.parts * tile), 0);
+  img.assign((size_t)(g.mtiles * g.tparts * tile), 0);
   for (int m = 0; m < g.mtiles; ++m)
     for (int r = 0; r < BM; ++r) {
       const int o = m * BM + r;
       for (int k = 0; k < g.kelems; ++k) {
         const double x = (o < g.N && k < g.K) ? T[(size_t)k * g.N + o] : 0.0;
-        const float xf = (float)x;
-        const uint32_t off = canon_off(r, k * elem, g.kbytes);
-        uint8_t* hi = img.data() + (size_t)(m * g.parts) * tile;
-        uint8_t* lo = hi + tile;
-        if (tf32) {
-          const uint32_t h = host_tf32_rna(xf);
-          const uint32_t l = host_tf32_rna((float)(x - (double)host_f(h)));
-          std::memcpy(hi + off, &h, 4);
-          if (g.parts == 2) std::memcpy(lo + off, &l, 4);
-        } else {
-          const uint16_t h = host_bf16_rn(xf);
-          const uint16_t l = host_bf16_rn((float)(x - (double)host_bf16_f(h)));
-          std::memcpy(hi + off, &h, 2);
-          if (g.parts == 2) std::memcpy(lo + off, &l, 2);
-        }
+        host_store_parts(img.data() + (size_t)(m * g.tparts) * tile, (size_t)tile, canon_off(r, k * elem, g.kbytes), x,
+                         tf32, g.tparts);
       }
     }
   meta = TcTable{};
@@ -122,7 +148,7 @@ void build_tc_image(int form, int degree, int cell, int prec, std::vector<uint8_
   meta.kbytes = g.kbytes;
   meta.kelems = g.kelems;
   meta.K = g.K;
-  meta.parts = g.parts;
+  meta.tparts = g.tparts;
   meta.tile_bytes = tile;
 }
 
@@ -133,7 +159,8 @@ int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Geom g{};
   g.kbytes = p.kbytes;
-  g.parts = p.parts;
+  g.tparts = p.tparts;
+  g.gparts = prec_gparts(p.precision);
   g.mtiles = p.mtiles;
   g.N = p.N;
   // cells on the lanes only pays for tiny element matrices (measured: P1 tets gain, P2 loses)
@@ -153,13 +180,13 @@ int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, 
     bg.p = p;
     bg.form = form;
     bg.cell = cell;
-    if (!stream_one_supported(form, p.kbytes, p.parts)) {
+    if (!stream_one_supported(form, p.kbytes, p.precision)) {
       why = "operands do not fit in shared memory";
       return (int)cudaErrorInvalidValue;
     }
     return launch_stream_one(bg, num_sms, stream);
   }
-  int smem = g.mtiles * g.parts * BM * g.kbytes + nst * g.parts * BN * g.kbytes +
+  int smem = g.mtiles * g.tparts * BM * g.kbytes + nst * g.gparts * BN * g.kbytes +
              (int)sizeof(Barriers) + 1024 + 64;
   if (smem < SMEM_ONE_CTA) smem = SMEM_ONE_CTA;
   const bool tri = cell == CELL_TRI;

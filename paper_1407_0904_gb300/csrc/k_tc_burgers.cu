@@ -16,7 +16,8 @@
 // Exact A (AX): where every column k of A is an integer vector n_k times a scale c_k with
 // integers the operand type holds exactly (tf32: odd part < 2^11, bf16: < 2^8), A is stored
 // once as the integers and the producers multiply factor k by c_k. The split precisions then
-// need two passes (A B_hi + A B_lo) instead of three, and A takes half the shared memory.
+// need one pass per part of the factors (Passes<PREC, true>) instead of one per product of
+// parts, and A takes one part of shared memory.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -34,8 +35,9 @@ template <int D, int NS, int PREC, bool AX>
 __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, int nstages) {
   using S = BurgersShape<D, NS, PREC>;
   using PT = PrecTraits<PREC>;
-  constexpr int NV = D + 1, P = S::P, KA1 = S::KA1, KD = S::KD, PARTS = S::PARTS;
-  constexpr int APARTS = AX ? 1 : PARTS;  // parts of the resident A operand
+  constexpr int NV = D + 1, P = S::P, KA1 = S::KA1, KD = S::KD, GPARTS = S::GPARTS;
+  constexpr int APARTS = AX ? 1 : PT::TPARTS;  // parts of the resident A operand
+  using PS = Passes<PREC, AX>;
   static_assert(KD * 4 <= SCALE_BYTES, "column scales exceed their shared-memory slot");
   constexpr int NB = D * D;
   constexpr uint32_t IDESC = make_idesc(PT::tf32 ? 2 : 1, BM, BN);
@@ -48,7 +50,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
   constexpr int SPART = BN * S::CWB;  // bytes of one part of a chunk stage
   uint8_t* sA = smem;
   uint8_t* sB = smem + a_bytes;
-  Barriers* bars = reinterpret_cast<Barriers*>(sB + nstages * PARTS * SPART);
+  Barriers* bars = reinterpret_cast<Barriers*>(sB + nstages * GPARTS * SPART);
   float* sc = reinterpret_cast<float*>(bars + 1);  // AX: scale of every A column
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -172,8 +174,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
           uint32_t use;
           stage_of(li++, grp, spg, s, use);
           if (!mbar_wait(smem_u32(&bars->empty[s]), (use & 1u) ^ 1u, p.err)) return ok = false;
-          uint8_t* hi = sB + (size_t)s * PARTS * SPART;
-          store_chunk_fn<PREC, S::CW, S::CWB>(hi, hi + SPART, row, kblk - ch * S::CW,
+          store_chunk_fn<PREC, S::CW, S::CWB>(sB + (size_t)s * GPARTS * SPART, SPART, row, kblk - ch * S::CW,
                                       [&](int l) { return factor(ch * S::CW + l); });
           fence_proxy_async();
           mbar_arrive(smem_u32(&bars->full[s]));
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
             if (!mbar_wait(smem_u32(&bars->full[s]), use & 1u, p.err)) { ok = false; break; }
             tc_fence_after();
             const int ksteps = (kblk - ch * S::CW < S::CW ? kblk - ch * S::CW : S::CW) / S::KSTEP;
-            const uint32_t bstage = b0 + (uint32_t)(s * PARTS * SPART);
+            const uint32_t bstage = b0 + (uint32_t)(s * GPARTS * SPART);
             for (int m = 0; m < S::MT; ++m) {
               const uint32_t d = tmem + ((rc + m) % RING) * BN;
               // K-chunk ch of A: byte column ch * CWB of the row, core matrices 128 bytes apart
@@ -218,15 +219,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
               uint32_t acc = ch > 0 ? 1u : 0u;
               for (int ks = 0; ks < ksteps; ++ks) {
                 const uint32_t ko = (uint32_t)ks * 256u;
-                if constexpr (PT::split) {
-                  mma<PT::tf32>(d, make_desc(atile + ko, sbo_a), make_desc(bstage + SPART + ko, sbo_b), IDESC, acc);
+#pragma unroll
+                for (int i = 0; i < PS::N; ++i) {  // products of parts, smallest first
+                  mma<PT::tf32>(d, make_desc(atile + (uint32_t)(PS::t(i) * tile_bytes) + ko, sbo_a),
+                                make_desc(bstage + (uint32_t)(PS::g(i) * SPART) + ko, sbo_b), IDESC, acc);
                   acc = 1;
-                  if constexpr (!AX)
-                    mma<PT::tf32>(d, make_desc(atile + tile_bytes + ko, sbo_a), make_desc(bstage + ko, sbo_b), IDESC,
-                                  1);
                 }
-                mma<PT::tf32>(d, make_desc(atile + ko, sbo_a), make_desc(bstage + ko, sbo_b), IDESC, acc);
-                acc = 1;
               }
             }
             tc_commit(smem_u32(&bars->empty[s]));
@@ -368,7 +366,7 @@ cudaError_t launch_bp(const TcParams& p, int num_sms, cudaStream_t s, int nst, i
 int burgers_tc_supported(int degree, int cell, int precision) {
   BGeom g;
   if (!bgeom(degree, cell, precision, g)) return 0;
-  return cstages(g) > 0 ? 1 : 0;  // A in hi/lo parts: the larger of the two layouts
+  return cstages(g) > 0 ? 1 : 0;  // A in the precision's parts: the larger of the two layouts
 }
 
 namespace {
@@ -433,7 +431,7 @@ void build_burgers_image(int degree, int cell, int prec, bool exact_ok, std::vec
     exact = integer_column(col, tf32, sc, ints[k]);
     scales[k] = (float)sc;
   }
-  const int aparts = exact ? 1 : g.parts;
+  const int aparts = exact ? 1 : g.aparts;
   const int64_t a_bytes = (int64_t)g.mtiles * aparts * tile;
   img.assign((size_t)(a_bytes + (exact ? g.KD * 4 : 0)), 0);
   for (int m = 0; m < g.mtiles; ++m)
@@ -443,19 +441,7 @@ void build_burgers_image(int degree, int cell, int prec, bool exact_ok, std::vec
         const int tr = trow_of(k);
         const double x = (o >= nb || tr < 0) ? 0.0 : exact ? ints[k][o] : T[(size_t)tr * nb + o];
         const uint32_t off = canon_off(r, k * g.elem, g.kbytes);
-        uint8_t* hi = img.data() + (size_t)(m * aparts) * tile;
-        uint8_t* lo = hi + tile;
-        if (tf32) {
-          const uint32_t h = host_tf32_rna((float)x);
-          const uint32_t l = host_tf32_rna((float)(x - (double)host_f(h)));
-          std::memcpy(hi + off, &h, 4);
-          if (aparts == 2) std::memcpy(lo + off, &l, 4);
-        } else {
-          const uint16_t h = host_bf16_rn((float)x);
-          const uint16_t l = host_bf16_rn((float)(x - (double)host_bf16_f(h)));
-          std::memcpy(hi + off, &h, 2);
-          if (aparts == 2) std::memcpy(lo + off, &l, 2);
-        }
+        host_store_parts(img.data() + (size_t)(m * aparts) * tile, (size_t)tile, off, x, tf32, aparts);
       }
     }
   if (exact) std::memcpy(img.data() + a_bytes, scales.data(), (size_t)g.KD * 4);
@@ -464,7 +450,7 @@ void build_burgers_image(int degree, int cell, int prec, bool exact_ok, std::vec
   meta.kbytes = g.kbytes;
   meta.kelems = g.KD;
   meta.K = g.KA1 + g.K1 + P;
-  meta.parts = g.parts;
+  meta.tparts = aparts;
   meta.ksteps_off = g.KA1 / g.kstep;
   meta.tile_bytes = tile;
   meta.aexact = exact ? 1 : 0;
@@ -476,8 +462,8 @@ int launch_burgers_tc(int cell, const TcParams& p, int num_sms, void* stream, st
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   BGeom g{};
   g.mtiles = p.mtiles;
-  g.parts = p.parts;
-  g.aparts = p.aexact ? 1 : p.parts;
+  g.gparts = prec_gparts(p.precision);
+  g.aparts = p.tparts;
   g.sbytes = p.aexact ? SCALE_BYTES : 0;
   g.kbytes = p.kbytes;
   const int nst = cstages(g);
@@ -485,7 +471,7 @@ int launch_burgers_tc(int cell, const TcParams& p, int num_sms, void* stream, st
     why = "operands do not fit in shared memory";
     return (int)cudaErrorInvalidValue;
   }
-  int smem = g.mtiles * g.aparts * BM * g.kbytes + nst * g.parts * BN * g.kbytes + (int)sizeof(Barriers) + g.sbytes +
+  int smem = g.mtiles * g.aparts * BM * g.kbytes + nst * g.gparts * BN * g.kbytes + (int)sizeof(Barriers) + g.sbytes +
              1024 + 64;
   if (smem < SMEM_ONE_CTA) smem = SMEM_ONE_CTA;
   if (cell == CELL_TRI) {

@@ -36,7 +36,7 @@ struct BurgersShape {
   static constexpr int KD = round_up(KA1 + K1 + P, KSTEP);   // diagonal K
   static constexpr int NBLK = NS * NS;
   static constexpr int MT = (NBLK + BM - 1) / BM;
-  static constexpr int PARTS = PT::split ? 2 : 1;
+  static constexpr int GPARTS = PT::GPARTS;                  // parts of the factor operand
   // Jacobian kernel: the B operand of a block is staged in K-chunks of CWB bytes per row. A
   // chunk is the whole block row: splitting it (more, smaller stages) was measured slower,
   // every extra hand-off between producers and the MMA costing more than it overlaps.
@@ -47,43 +47,20 @@ struct BurgersShape {
   static constexpr int NCHT = D * NCH_D + (D * D - D) * NCH_O;  // chunks per tile
 };
 
-// One operand row (one cell): columns C0..NCOLS-1 whose k-th value is f(k), converted and
-// stored 16 bytes at a time like store_operand_row; the values are formed as they are
-// stored, so no K-long array is held in registers. C0 is a multiple of 8 elements.
+// One operand row (one cell): columns C0..NCOLS-1 whose k-th value is f(k), split into the
+// precision's factor parts (part q at base + q * part_bytes) and stored 16 bytes at a time like
+// store_operand_row; the values are formed as they are stored, so no K-long array is held in
+// registers. C0 is a multiple of 8 elements.
 template <int PREC, int NCOLS, class F, int C0 = 0>
-__device__ __forceinline__ void store_operand_fn(uint8_t* hi, uint8_t* lo, int r, int kbytes, F f) {
+__device__ __forceinline__ void store_operand_fn(uint8_t* base, int part_bytes, int r, int kbytes, F f) {
   using PT = PrecTraits<PREC>;
-  if constexpr (PT::tf32) {
+  constexpr int PER = PT::tf32 ? 4 : 8;  // columns per 16-byte unit
 #pragma unroll
-    for (int c = C0 / 4; c < NCOLS / 4; ++c) {
-      uint32_t h[4], l[4];
+  for (int c = C0 / PER; c < NCOLS / PER; ++c) {
+    float x[PER];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float x = f(c * 4 + q);
-        h[q] = tf32_rna(x);
-        l[q] = tf32_rna(x - __uint_as_float(h[q]));
-      }
-      const uint32_t off = canon_off(r, c * 16, kbytes);
-      *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-      if constexpr (PT::split) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-    }
-  } else {
-#pragma unroll
-    for (int c = C0 / 8; c < NCOLS / 8; ++c) {
-      uint32_t h[4], l[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float x0 = f(c * 8 + 2 * q), x1 = f(c * 8 + 2 * q + 1);
-        __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-        __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-        __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-        h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-      }
-      const uint32_t off = canon_off(r, c * 16, kbytes);
-      *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-      if constexpr (PT::split) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-    }
+    for (int q = 0; q < PER; ++q) x[q] = f(c * PER + q);
+    store_unit<PT::tf32, PT::GPARTS>(base + canon_off(r, c * 16, kbytes), part_bytes, x);
   }
 }
 
@@ -91,34 +68,16 @@ __device__ __forceinline__ void store_operand_fn(uint8_t* hi, uint8_t* lo, int r
 // multiple of 4 tf32 / 8 bf16 columns; constant after unrolling) and are stored 16 bytes at a
 // time in the canonical layout of a CWB-byte row; columns past ncols are not written.
 template <int PREC, int CW, int CWB, class F>
-__device__ __forceinline__ void store_chunk_fn(uint8_t* hi, uint8_t* lo, int r, int ncols, F f) {
+__device__ __forceinline__ void store_chunk_fn(uint8_t* base, int part_bytes, int r, int ncols, F f) {
   using PT = PrecTraits<PREC>;
-  constexpr int PER = PT::tf32 ? 4 : 8;  // columns per 16-byte store
+  constexpr int PER = PT::tf32 ? 4 : 8;  // columns per 16-byte unit
 #pragma unroll
   for (int c = 0; c < CW / PER; ++c) {
     if (c * PER >= ncols) break;
-    uint32_t h[4], l[4];
-    if constexpr (PT::tf32) {
+    float x[PER];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float x = f(c * 4 + q);
-        h[q] = tf32_rna(x);
-        l[q] = tf32_rna(x - __uint_as_float(h[q]));
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float x0 = f(c * 8 + 2 * q), x1 = f(c * 8 + 2 * q + 1);
-        __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-        __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-        __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-        h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-      }
-    }
-    const uint32_t off = canon_off(r, c * 16, CWB);
-    *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    if constexpr (PT::split) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    for (int q = 0; q < PER; ++q) x[q] = f(c * PER + q);
+    store_unit<PT::tf32, PT::GPARTS>(base + canon_off(r, c * 16, CWB), part_bytes, x);
   }
 }
 
@@ -126,7 +85,8 @@ constexpr int SMEM_LIMIT = 227 * 1024;
 constexpr int SMEM_ONE_CTA = 120 * 1024;
 
 struct BGeom {
-  int ns, K1, KA1, KD, kstep, elem, parts, mtiles, kbytes;
+  int ns, K1, KA1, KD, kstep, elem, mtiles, kbytes;
+  int gparts;  // parts of the factor operand
   int aparts;  // parts of the resident A operand (1 when A is held exactly)
   int sbytes;  // shared-memory bytes of the A column scales (0 unless A is exact)
 };
@@ -144,27 +104,27 @@ bool bgeom(int degree, int cell, int prec, BGeom& g) {
   g.K1 = g.ns * d;
   g.KA1 = (g.K1 + g.kstep - 1) / g.kstep * g.kstep;
   g.KD = (g.KA1 + g.K1 + P + g.kstep - 1) / g.kstep * g.kstep;
-  g.parts = (prec == PREC_TF32X3 || prec == PREC_BF16X3) ? 2 : 1;
+  g.gparts = prec_gparts(prec);
   g.mtiles = (g.ns * g.ns + BM - 1) / BM;
   g.kbytes = g.KD * g.elem;
-  g.aparts = g.parts;
+  g.aparts = prec_tparts(prec);
   g.sbytes = 0;
   return true;
 }
 
 int bstages(const BGeom& g) {
   const int a = g.mtiles * g.aparts * BM * g.kbytes;
-  const int b = g.parts * BN * g.kbytes;
+  const int b = g.gparts * BN * g.kbytes;
   const int fixed = a + (int)sizeof(Barriers) + g.sbytes + 1024 + 64;
   int s = MAX_STAGES;  // even: the stages are split between the two producer groups
   while (s >= 2 && fixed + s * b > SMEM_LIMIT) s -= 2;
   return s >= 2 ? s : 0;
 }
 
-// Stages of the Jacobian kernel: PARTS x BN x CWB bytes each (CWB = kbytes), an even count.
+// Stages of the Jacobian kernel: GPARTS x BN x CWB bytes each (CWB = kbytes), an even count.
 int cstages(const BGeom& g) {
   const int a = g.mtiles * g.aparts * BM * g.kbytes;
-  const int b = g.parts * BN * g.kbytes;
+  const int b = g.gparts * BN * g.kbytes;
   const int fixed = a + (int)sizeof(Barriers) + g.sbytes + 1024 + 64;
   int s = MAX_STAGES;
   while (s >= 2 && fixed + s * b > SMEM_LIMIT) s -= 2;

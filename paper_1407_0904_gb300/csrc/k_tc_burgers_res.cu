@@ -29,7 +29,9 @@ template <int D, int NS, int PREC>
 __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p, int nstages) {
   using S = BurgersShape<D, NS, PREC>;
   using PT = PrecTraits<PREC>;
-  constexpr int NV = D + 1, P = S::P, KA1 = S::KA1, KD = S::KD, PARTS = S::PARTS, KSTEP = S::KSTEP;
+  constexpr int NV = D + 1, P = S::P, KA1 = S::KA1, KD = S::KD, KSTEP = S::KSTEP;
+  constexpr int TPARTS = PT::TPARTS, GPARTS = PT::GPARTS;
+  using PS = Passes<PREC>;
   constexpr int NPAD = round_up(S::NBLK, 16);     // MMA N (outputs), <= 256
   static_assert(NPAD <= 256, "residual kernel: at most 256 outputs per cell");
   constexpr int SLOTW = S::MT == 1 ? 128 : 256;   // TMEM columns per accumulator
@@ -40,10 +42,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int kbytes = p.kbytes;  // = KD * ELEM
   const int tile_bytes = BM * kbytes;
-  const int a_bytes = S::MT * PARTS * tile_bytes;
+  const int a_bytes = S::MT * TPARTS * tile_bytes;
   uint8_t* sA = smem;
   uint8_t* sB = smem + a_bytes;
-  Barriers* bars = reinterpret_cast<Barriers*>(sB + nstages * PARTS * tile_bytes);
+  Barriers* bars = reinterpret_cast<Barriers*>(sB + nstages * GPARTS * tile_bytes);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (p.ncells + BN - 1) / BN;
@@ -151,8 +153,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
         if (k < KA1 + S::K1 + P) return H[k - KA1 - S::K1];
         return 0.f;
       };
-      uint8_t* hi = sB + (size_t)s * PARTS * tile_bytes;
-      store_operand_fn<PREC, KD, decltype(factor), KA1>(hi, hi + tile_bytes, row, kbytes, factor);
+      store_operand_fn<PREC, KD, decltype(factor), KA1>(sB + (size_t)s * GPARTS * tile_bytes, tile_bytes, row, kbytes,
+                                                        factor);
       fence_proxy_async();
       mbar_arrive(smem_u32(&bars->full[s]));
     }
@@ -173,23 +175,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
         const uint32_t slot = rc % NSLOT, round = rc / NSLOT;
         if (!mbar_wait(smem_u32(&bars->tempty[slot]), (round & 1u) ^ 1u, p.err)) break;
         tc_fence_after();
-        const uint32_t g = b0 + (uint32_t)(s * PARTS * tile_bytes);  // A: cells x K
+        const uint32_t g = b0 + (uint32_t)(s * GPARTS * tile_bytes);  // A: cells x K
 #pragma unroll
         for (int m = 0; m < S::MT; ++m) {
           const int nm = (NPAD - m * 128) < 128 ? NPAD - m * 128 : 128;
           const uint32_t idesc = make_idesc(PT::tf32 ? 2 : 1, BM, nm);
-          const uint32_t tt = a0 + (uint32_t)(m * PARTS * tile_bytes);  // B: outputs x K
+          const uint32_t tt = a0 + (uint32_t)(m * TPARTS * tile_bytes);  // B: outputs x K
           const uint32_t d = tmem + slot * SLOTW + m * 128;
           uint32_t acc = 0;
           for (int ks = KA1 / KSTEP; ks < KD / KSTEP; ++ks) {
             const uint32_t ko = (uint32_t)ks * 256u;
-            if constexpr (PT::split) {
-              mma<PT::tf32>(d, make_desc(g + tile_bytes + ko, sbo), make_desc(tt + ko, sbo), idesc, acc);
+#pragma unroll
+            for (int i = 0; i < PS::N; ++i) {  // products of parts, smallest first
+              mma<PT::tf32>(d, make_desc(g + (uint32_t)(PS::g(i) * tile_bytes) + ko, sbo),
+                            make_desc(tt + (uint32_t)(PS::t(i) * tile_bytes) + ko, sbo), idesc, acc);
               acc = 1;
-              mma<PT::tf32>(d, make_desc(g + ko, sbo), make_desc(tt + tile_bytes + ko, sbo), idesc, 1);
             }
-            mma<PT::tf32>(d, make_desc(g + ko, sbo), make_desc(tt + ko, sbo), idesc, acc);
-            acc = 1;
           }
         }
         tc_commit(smem_u32(&bars->tfull[slot]));
@@ -306,8 +307,8 @@ int launch_burgers_res_tc(int cell, const TcParams& p, int num_sms, void* stream
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   BGeom g{};
   g.mtiles = p.mtiles;
-  g.parts = p.parts;
-  g.aparts = p.parts;
+  g.gparts = prec_gparts(p.precision);
+  g.aparts = p.tparts;
   g.kbytes = p.kbytes;
   int nst = bstages(g);
   if (nst == 0) {
@@ -315,7 +316,7 @@ int launch_burgers_res_tc(int cell, const TcParams& p, int num_sms, void* stream
     return (int)cudaErrorInvalidValue;
   }
   if (nst > 2 && (p.tune & TUNE_TWO_STAGES)) nst = 2;
-  int smem = g.mtiles * g.parts * BM * g.kbytes + nst * g.parts * BN * g.kbytes + (int)sizeof(Barriers) + 1024 + 64;
+  int smem = g.mtiles * g.aparts * BM * g.kbytes + nst * g.gparts * BN * g.kbytes + (int)sizeof(Barriers) + 1024 + 64;
   if (smem < SMEM_ONE_CTA) smem = SMEM_ONE_CTA;
   if (cell == CELL_TRI) {
     switch (p.ns) {

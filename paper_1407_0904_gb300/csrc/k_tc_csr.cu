@@ -52,7 +52,8 @@ int launch_tc_csr(int form, int cell, const TcParams& p, int num_sms, void* stre
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Geom g{};
   g.kbytes = p.kbytes;
-  g.parts = p.parts;
+  g.tparts = p.tparts;
+  g.gparts = prec_gparts(p.precision);
   g.mtiles = p.mtiles;
   g.N = p.N;
   int nst = stages_for(g, CSR_SMEM);
@@ -64,7 +65,7 @@ int launch_tc_csr(int form, int cell, const TcParams& p, int num_sms, void* stre
   TcParams q = p;
   q.subw = (p.tune & TUNE_SUB32) ? 32 : (p.tune & TUNE_SUB64) ? 64 : (p.tune & TUNE_SUB128) ? 128
                                                                                              : (p.mtiles > 4 ? 64 : 128);
-  int smem = g.mtiles * g.parts * BM * g.kbytes + nst * g.parts * BN * g.kbytes + (int)sizeof(Barriers) + 1024 + 64 +
+  int smem = g.mtiles * g.tparts * BM * g.kbytes + nst * g.gparts * BN * g.kbytes + (int)sizeof(Barriers) + 1024 + 64 +
              CSR_SMEM;
   if (smem < SMEM_ONE_CTA) smem = SMEM_ONE_CTA;
   const bool tri = cell == CELL_TRI;

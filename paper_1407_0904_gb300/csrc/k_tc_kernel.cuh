@@ -47,17 +47,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
   using PT = PrecTraits<PREC>;
   constexpr int KSTEP = PT::tf32 ? 8 : 16;  // K elements per MMA (32 bytes)
   constexpr int KP = round_up(Form<FORM, D>::K, KSTEP);
-  constexpr int PARTS = PT::split ? 2 : 1;
+  constexpr int TPARTS = PT::TPARTS, GPARTS = PT::GPARTS;
+  using PS = Passes<PREC>;
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int kbytes = p.kbytes;
   const int tile_bytes = BM * kbytes;  // one part of one operand tile (A: 128 outputs, B: 128 cells)
-  const int a_bytes = p.mtiles * PARTS * tile_bytes;
+  const int a_bytes = p.mtiles * TPARTS * tile_bytes;
   const int N = p.N;
   uint8_t* sA = smem;
   uint8_t* sB = smem + a_bytes;
-  Barriers* bars = reinterpret_cast<Barriers*>(sB + nstages * PARTS * tile_bytes);
+  Barriers* bars = reinterpret_cast<Barriers*>(sB + nstages * GPARTS * tile_bytes);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (p.ncells + BN - 1) / BN;
@@ -128,8 +129,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
 #pragma unroll
         for (int k = 0; k < KP; ++k) G[k] = 0.f;
       }
-      uint8_t* hi = sB + (size_t)s * PARTS * tile_bytes;
-      store_operand_row<PREC, KP>(hi, hi + tile_bytes, row, G, kbytes);
+      store_operand_row<PREC, KP>(sB + (size_t)s * GPARTS * tile_bytes, tile_bytes, row, G, kbytes);
       fence_proxy_async();
       mbar_arrive(smem_u32(&bars->full[s]));
     }
@@ -152,30 +152,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
         stage_of(tl / PROD_GROUPS, (int)(tl % PROD_GROUPS), spg, s, use);
         if (!mbar_wait(smem_u32(&bars->full[s]), use & 1u, p.err)) break;
         tc_fence_after();
-        const uint32_t bstage = b0 + (uint32_t)(s * PARTS * tile_bytes);
+        const uint32_t bstage = b0 + (uint32_t)(s * GPARTS * tile_bytes);
         for (int j = 0; j < BN / W && ok; ++j)
         for (int m = 0; m < p.mtiles; ++m, ++rc) {
           const uint32_t slot = rc % nslot, round = rc / nslot;
           if (!mbar_wait(smem_u32(&bars->tempty[slot]), (round & 1u) ^ 1u, p.err)) { ok = false; break; }
           tc_fence_after();
           const uint32_t d = tmem + slot * W;
-          const uint32_t atile = a0 + (uint32_t)(m * PARTS * tile_bytes);
+          const uint32_t atile = a0 + (uint32_t)(m * TPARTS * tile_bytes);
           const uint32_t bsub = bstage + (uint32_t)(j * W * kbytes);  // cells j*W.. of the stage
-          // outputs on lanes: A = T^T slice, B = G stage; cells on lanes: A = G, B = T^T
-          const uint32_t xo = LANES ? bstage : atile, xc = LANES ? atile : bsub;
           uint32_t acc = 0;
           for (int ks = 0; ks < ksteps; ++ks) {
             const uint32_t ko = (uint32_t)ks * 256u;
-            if constexpr (PT::split) {
-              // small terms first: T_hi G_lo, T_lo G_hi, then T_hi G_hi
-              const uint32_t ahl = LANES ? xo + tile_bytes : xo, bhl = LANES ? xc : xc + tile_bytes;
-              mma<PT::tf32>(d, make_desc(ahl + ko, sbo), make_desc(bhl + ko, sbo), idesc, acc);
+#pragma unroll
+            for (int i = 0; i < PS::N; ++i) {
+              // part t of T^T and part g of G; outputs on lanes: A = T^T slice, B = G stage;
+              // cells on lanes: A = G, B = T^T
+              const uint32_t tt = atile + (uint32_t)(PS::t(i) * tile_bytes) + ko;
+              const uint32_t gg = (LANES ? bstage : bsub) + (uint32_t)(PS::g(i) * tile_bytes) + ko;
+              mma<PT::tf32>(d, make_desc(LANES ? gg : tt, sbo), make_desc(LANES ? tt : gg, sbo), idesc, acc);
               acc = 1;
-              const uint32_t alh = LANES ? xo : xo + tile_bytes, blh = LANES ? xc + tile_bytes : xc;
-              mma<PT::tf32>(d, make_desc(alh + ko, sbo), make_desc(blh + ko, sbo), idesc, 1);
             }
-            mma<PT::tf32>(d, make_desc(xo + ko, sbo), make_desc(xc + ko, sbo), idesc, acc);
-            acc = 1;
           }
           tc_commit(smem_u32(&bars->tfull[slot]));
         }
@@ -384,7 +381,7 @@ constexpr int SMEM_LIMIT = 227 * 1024;
 constexpr int SMEM_ONE_CTA = 120 * 1024;  // requesting more keeps one CTA (and one TMEM owner) per SM
 
 struct Geom {
-  int K, kelems, kbytes, parts, mtiles, N;
+  int K, kelems, kbytes, tparts, gparts, mtiles, N;
 };
 
 // Cells-on-lanes orientation: the element matrix fits one 128-output slice
@@ -398,7 +395,8 @@ bool geom_of(int form, int degree, int cell, int prec, Geom& g) {
   g.K = form_K(form, degree, cell);
   g.kelems = (g.K + kstep - 1) / kstep * kstep;
   g.kbytes = g.kelems * elem;
-  g.parts = (prec == PREC_TF32X3 || prec == PREC_BF16X3) ? 2 : 1;
+  g.tparts = prec_tparts(prec);
+  g.gparts = prec_gparts(prec);
   const int ns = nnodes(cell, degree);
   g.N = ns * ns;
   g.mtiles = (g.N + BM - 1) / BM;
@@ -406,8 +404,8 @@ bool geom_of(int form, int degree, int cell, int prec, Geom& g) {
 }
 
 int stages_for(const Geom& g, int extra = 0) {
-  const int a = g.mtiles * g.parts * BM * g.kbytes;
-  const int b = g.parts * BN * g.kbytes;
+  const int a = g.mtiles * g.tparts * BM * g.kbytes;
+  const int b = g.gparts * BN * g.kbytes;
   const int fixed = a + (int)sizeof(Barriers) + 1024 + 64;
   int s = MAX_STAGES;  // even: the stages are split between the two producer groups
   while (s >= 2 && fixed + extra + s * b > SMEM_LIMIT) s -= 2;

@@ -1,5 +1,5 @@
 // Shared building blocks of the tcgen05 kernels: PTX wrappers (mbarrier, tcgen05,
-// descriptors), operand splitting into tf32/bf16 hi/lo parts, the canonical no-swizzle
+// descriptors), operand splitting into tf32/bf16 parts, the canonical no-swizzle
 // K-major shared-memory layout, and the FP32 cell geometry with its FP64 fallback.
 #pragma once
 #include <cuda_runtime.h>
@@ -155,60 +155,104 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   return r;
 }
 
+// How each precision represents the two operands of the contraction A_e = sum_k G_e[k] T[k]:
+// the reference tensor T in TPARTS parts and the per-cell factors G in GPARTS parts of the
+// operand type (tf32 or bf16), every part the round-to-nearest of what the previous parts left.
+//   TF32    T 1, G 1: one pass.
+//   TF32X3  T 2, G 2 (hi + lo, 22 bits each): the three products of order <= 1.
+//   BF16    T 2, G 1: T held to 16 bits, so only G's single rounding (2^-8) remains.
+//   BF16X3  T 3, G 3 (24 bits each, the full float): the six products of order <= 2.
 template <int PREC>
-struct PrecTraits;
-template <>
-struct PrecTraits<PREC_TF32> { static constexpr bool tf32 = true, split = false; };
-template <>
-struct PrecTraits<PREC_TF32X3> { static constexpr bool tf32 = true, split = true; };
-template <>
-struct PrecTraits<PREC_BF16> { static constexpr bool tf32 = false, split = false; };
-template <>
-struct PrecTraits<PREC_BF16X3> { static constexpr bool tf32 = false, split = true; };
+struct PrecTraits {
+  static constexpr bool tf32 = PREC == PREC_TF32 || PREC == PREC_TF32X3;
+  static constexpr int TPARTS = prec_tparts(PREC), GPARTS = prec_gparts(PREC);
+};
+
+// The MMA passes of a precision, (part of T, part of G), smallest products first so that the
+// accumulator is small while they are added. TEXACT: T is held exactly in one part (integer
+// columns), so only G's parts are passed.
+template <int PREC, bool TEXACT = false>
+struct Passes {
+  static constexpr int N = TEXACT ? prec_gparts(PREC)
+                                  : (PREC == PREC_TF32 ? 1 : PREC == PREC_TF32X3 ? 3 : PREC == PREC_BF16 ? 2 : 6);
+  __host__ __device__ static constexpr int t(int i) {
+    if (TEXACT) return 0;
+    if (PREC == PREC_TF32X3) return i == 1 ? 1 : 0;                      // (0,1) (1,0) (0,0)
+    if (PREC == PREC_BF16) return i == 0 ? 1 : 0;                        // (1,0) (0,0)
+    if (PREC == PREC_BF16X3) return i == 0 ? 1 : i == 2 ? 2 : i == 4 ? 1 : 0;  // (1,1) (0,2) (2,0) (0,1) (1,0) (0,0)
+    return 0;
+  }
+  __host__ __device__ static constexpr int g(int i) {
+    if (TEXACT) return N - 1 - i;
+    if (PREC == PREC_TF32X3) return i == 0 ? 1 : 0;
+    if (PREC == PREC_BF16X3) return i == 0 ? 1 : i == 1 ? 2 : i == 3 ? 1 : 0;
+    return 0;
+  }
+};
+
+// x as NP parts of the operand type (tf32: 32-bit patterns with the low 13 bits clear; bf16:
+// 16-bit patterns), each the round-to-nearest of the remainder the previous parts left; the
+// remainders are exact in FP32.
+template <bool TF32, int NP>
+__device__ __forceinline__ void split_bits(float x, uint32_t (&b)[NP]) {
+  float r = x;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    if constexpr (TF32) {
+      b[q] = tf32_rna(r);
+      r -= __uint_as_float(b[q]);
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(r);
+      b[q] = (uint32_t)__bfloat16_as_ushort(h);
+      r -= __bfloat162float(h);
+    }
+  }
+}
+
+// One 16-byte unit of each of the NP parts of an operand row from its values x[0..3] (tf32) or
+// x[0..7] (bf16), stored at dst + q * part_bytes.
+template <bool TF32, int NP>
+__device__ __forceinline__ void store_unit(uint8_t* dst, int part_bytes, const float* x) {
+  uint32_t w[NP][4];
+  if constexpr (TF32) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      uint32_t b[NP];
+      split_bits<true, NP>(x[c], b);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) w[q][c] = b[q];
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      uint32_t b0[NP], b1[NP];
+      split_bits<false, NP>(x[2 * c], b0);
+      split_bits<false, NP>(x[2 * c + 1], b1);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) w[q][c] = b0[q] | (b1[q] << 16);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+    *reinterpret_cast<uint4*>(dst + (size_t)q * part_bytes) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+}
 
 // Byte offset of (row r, byte kb) in a canonical K-major operand with kbytes per row.
 __host__ __device__ __forceinline__ uint32_t canon_off(int r, int kb, int kbytes) {
   return (uint32_t)((r >> 3) * (8 * kbytes) + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15));
 }
 
-// Store the row of factors G[0..KP) for cell row r into the hi (and lo) B operand parts.
-// Only the first NCOLS columns (a multiple of the 16-byte chunk) are written.
+// Store the row of factors G[0..KP) for cell row r into the GPARTS parts of the B operand
+// (part q at base + q * part_bytes). Only the first NCOLS columns (a multiple of the 16-byte
+// unit) are written.
 template <int PREC, int KP, int NCOLS = KP>
-__device__ __forceinline__ void store_operand_row(uint8_t* hi, uint8_t* lo, int r, const float (&G)[KP],
+__device__ __forceinline__ void store_operand_row(uint8_t* base, int part_bytes, int r, const float (&G)[KP],
                                                   int kbytes) {
   using PT = PrecTraits<PREC>;
-  if constexpr (PT::tf32) {
+  constexpr int PER = PT::tf32 ? 4 : 8;  // columns per 16-byte unit
 #pragma unroll
-    for (int c = 0; c < NCOLS / 4; ++c) {
-      uint32_t h[4], l[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float x = G[c * 4 + q];
-        h[q] = tf32_rna(x);
-        l[q] = tf32_rna(x - __uint_as_float(h[q]));
-      }
-      const uint32_t off = canon_off(r, c * 16, kbytes);
-      *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-      if constexpr (PT::split) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < NCOLS / 8; ++c) {
-      uint32_t h[4], l[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float x0 = G[c * 8 + 2 * q], x1 = G[c * 8 + 2 * q + 1];
-        __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-        __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-        __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-        h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-      }
-      const uint32_t off = canon_off(r, c * 16, kbytes);
-      *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-      if constexpr (PT::split) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-    }
-  }
+  for (int c = 0; c < NCOLS / PER; ++c)
+    store_unit<PT::tf32, PT::GPARTS>(base + canon_off(r, c * 16, kbytes), part_bytes, &G[c * PER]);
 }
 
 __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -298,6 +342,39 @@ struct Form {
   static constexpr int K = FORM == FORM_MASS ? 1 : FORM == FORM_HELMHOLTZ ? 1 + P : (D + 1) * P + (D + 1) * D;
 };
 
+// Stiffness factors in the edge basis: c_ij = |det J| grad(lambda_i).grad(lambda_j) for the
+// vertex pairs i < j of the simplex, ordered (0,1), (0,2), .., (0,d), (1,2), .., (d-1,d).
+// With grad(lambda_{a+1}) = row a of K = adj / det and grad(lambda_0) = -sum_a grad(lambda_{a+1}),
+// c_ij = g_i.g_j / |det| for g_{a+1} = adj[a], g_0 = -sum_a adj[a]. Because the barycentric
+// gradients sum to zero these d(d+1)/2 numbers carry exactly the information of |det| K K^T
+// (the host re-expresses the stiffness reference tensors for them), and on shape-regular cells
+// they share one sign (no obtuse dihedral angle), so sum_k G_k T_k cancels far less than in the
+// pairs of reference directions: the rounding of the factors to the operand type costs less.
+template <int D>
+__device__ __forceinline__ void edge_factors(const float (&adj)[D][D], float inv, float (&c)[D * (D + 1) / 2]) {
+  float g[D + 1][D];
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      g[a + 1][r] = adj[a][r];
+      s += adj[a][r];
+    }
+    g[0][r] = -s;
+  }
+  int q = 0;
+#pragma unroll
+  for (int i = 0; i < D + 1; ++i)
+#pragma unroll
+    for (int j = i + 1; j < D + 1; ++j) {
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < D; ++r) s = fmaf(g[i][r], g[j][r], s);
+      c[q++] = s * inv;
+    }
+}
+
 // Per-cell factors G[0..KP) (zero padded) for MASS / HELMHOLTZ / ADVDIFF.
 // The cell's index rows (cell2vert, and cell2dof for ADVDIFF); loaded one tile ahead by
 // the producers so that their DRAM latency overlaps the previous cell's work.
@@ -346,26 +423,14 @@ __device__ __forceinline__ void cell_factors_ids(const TcParams& p, const CellId
     for (int r = 0; r < D; ++r) X[v][r] = __ldg(p.coords + (int64_t)vid[v] * D + r);
   float adj[D][D], Dm, sg;
   cell_geometry<D>(X, adj, Dm, sg);
-  const float inv = 1.0f / Dm;
-  float H[P];
-  {
-    int q = 0;
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-      for (int b = a; b < D; ++b) {
-        float s = 0.f;
-#pragma unroll
-        for (int r = 0; r < D; ++r) s = fmaf(adj[a][r], adj[b][r], s);
-        H[q++] = s * inv;
-      }
-  }
+  float C[P];  // edge factors
+  if constexpr (FORM != FORM_MASS) edge_factors<D>(adj, 1.0f / Dm, C);
   if constexpr (FORM == FORM_MASS) {
     G[0] = Dm;
   } else if constexpr (FORM == FORM_HELMHOLTZ) {
     G[0] = Dm;
 #pragma unroll
-    for (int q = 0; q < P; ++q) G[1 + q] = H[q];
+    for (int q = 0; q < P; ++q) G[1 + q] = C[q];
   } else {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -375,7 +440,7 @@ __device__ __forceinline__ void cell_factors_ids(const TcParams& p, const CellId
 #pragma unroll
       for (int r = 0; r < D; ++r) bv[r] = (float)__ldg(cv + 1 + r);
 #pragma unroll
-      for (int q = 0; q < P; ++q) G[v * P + q] = eps * H[q];
+      for (int q = 0; q < P; ++q) G[v * P + q] = eps * C[q];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         float s = 0.f;
@@ -422,6 +487,32 @@ inline uint16_t host_bf16_rn(float x) {
   return (uint16_t)(u >> 16);
 }
 inline float host_bf16_f(uint16_t h) { return host_f((uint32_t)h << 16); }
+// x as np parts of the operand type (tf32 patterns, or bf16 patterns in the low 16 bits), each
+// the round-to-nearest of the remainder left by the previous parts (remainders in FP64).
+inline void host_split(double x, bool tf32, int np, uint32_t* b) {
+  double r = x;
+  for (int q = 0; q < np; ++q) {
+    if (tf32) {
+      b[q] = host_tf32_rna((float)r);
+      r -= (double)host_f(b[q]);
+    } else {
+      b[q] = host_bf16_rn((float)r);
+      r -= (double)host_bf16_f((uint16_t)b[q]);
+    }
+  }
+}
+// Store the np parts of x at byte offset off of parts base, base + part_bytes, ..
+inline void host_store_parts(uint8_t* base, size_t part_bytes, uint32_t off, double x, bool tf32, int np) {
+  uint32_t b[4];
+  host_split(x, tf32, np, b);
+  for (int q = 0; q < np; ++q) {
+    if (tf32) std::memcpy(base + q * part_bytes + off, &b[q], 4);
+    else {
+      const uint16_t h = (uint16_t)b[q];
+      std::memcpy(base + q * part_bytes + off, &h, 2);
+    }
+  }
+}
 
 
 }  // namespace tc

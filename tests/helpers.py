@@ -6,6 +6,11 @@ from paper_1407_0904_gb300 import meshgen
 
 TRI, TET = 0, 1
 MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC = 0, 1, 2, 3
+FP64, TF32, TF32X3, BF16, BF16X3 = 0, 1, 2, 3, 4
+
+# Parity bounds of every precision, per cell: max_ij |A - A_oracle| / max_ij |A_oracle|.
+# FP64 1e-12; the split precisions TF32X3 and BF16X3 1e-5; single-pass TF32 and BF16 1e-2.
+TOL = {FP64: 1e-12, TF32X3: 1e-5, BF16X3: 1e-5, TF32: 1e-2, BF16: 1e-2}
 
 
 def small_mesh(cell, n=None, seed=1):

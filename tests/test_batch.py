@@ -55,7 +55,7 @@ def check_groups(dev, groups, outs, prec, tol, sample=None):
         assert rel_err_per_cell(got, ref) < tol, spec
 
 
-@pytest.mark.parametrize("prec,tol", [(coffee.TF32X3, 1e-5), (coffee.BF16X3, 1e-4)])
+@pytest.mark.parametrize("prec,tol", [(coffee.TF32X3, 1e-5), (coffee.BF16X3, 1e-5)])
 def test_small_mixed_batch(prec, tol):
     tri = meshgen.tri_mesh(40, perturb=0.2, seed=4)
     tet = meshgen.tet_mesh(8, perturb=0.15, seed=5)

@@ -17,11 +17,11 @@ import torch
 import oracle
 import paper_1407_0904_gb300 as coffee
 from paper_1407_0904_gb300 import meshgen
-from tests.helpers import TRI, TET, MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC, coefficients, to_device
+from tests.helpers import TRI, TET, MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC, TOL, coefficients, to_device
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
-EPS = {coffee.FP64: 1e-12, coffee.TF32X3: 1e-5, coffee.BF16X3: 1e-4, coffee.TF32: 1e-2, coffee.BF16: 2e-2}
+EPS = TOL
 
 
 def ragged_mesh(cell, seed):

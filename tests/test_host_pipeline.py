@@ -10,7 +10,7 @@ import torch
 import oracle
 import paper_1407_0904_gb300 as coffee
 from paper_1407_0904_gb300 import meshgen
-from tests.helpers import TRI, TET, MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC, coefficients, rel_err_per_cell
+from tests.helpers import TRI, TET, MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC, TOL, coefficients, rel_err_per_cell
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -44,7 +44,7 @@ def test_host_pipeline_equals_one_device_launch_and_matches_oracle(form, cell, k
     else:
         ref = oracle.assemble(form, k, cell, mesh.coords, mesh.cell2vert, coef, c2d)
         err = rel_err_per_cell(got.numpy(), ref)
-    assert err < (1e-12 if prec == coffee.FP64 else 1e-4 if prec == coffee.BF16X3 else 1e-5), err
+    assert err < TOL[prec], err
 
 
 def test_host_pipeline_empty_and_more_chunks_than_cells():

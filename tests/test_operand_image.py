@@ -1,8 +1,10 @@
 """The tensor-core operand images (host-side set-up of the contraction) decoded on the CPU from
 the canonical no-swizzle K-major layout as include/coffee_diag.h defines it: every image holds
 the reference tensor T^T (rows = element-matrix entries, columns = K) to the accuracy of its
-precision split, zero padding elsewhere, and the Burgers images use exact integer columns where
-the paper's tensors allow them. No GPU needed."""
+precision split (TF32 one part, TF32X3 and BF16 two, BF16X3 three), zero padding elsewhere;
+the stiffness columns of HELMHOLTZ and ADVDIFF are re-expressed for the edge factors
+c_ij = |det J| grad(lambda_i).grad(lambda_j), and the Burgers images use exact integer columns
+where the paper's tensors allow them. No GPU needed."""
 import ctypes
 import math
 
@@ -12,7 +14,7 @@ import pytest
 import paper_1407_0904_gb300 as coffee
 
 TRI, TET = coffee.TRIANGLE, coffee.TETRAHEDRON
-SPLIT = {coffee.TF32X3: True, coffee.BF16X3: True, coffee.TF32: False, coffee.BF16: False}
+TPARTS = {coffee.TF32: 1, coffee.TF32X3: 2, coffee.BF16: 2, coffee.BF16X3: 3}
 TF32 = {coffee.TF32X3: True, coffee.TF32: True, coffee.BF16X3: False, coffee.BF16: False}
 
 
@@ -44,15 +46,35 @@ def decode(part, kbytes, tf32):
 
 
 def operand(img, meta, tf32, aparts):
-    mtiles, kbytes, parts = meta[0], meta[1], meta[4]
+    """(first part, sum of the remaining parts) of the A operand, each [mtiles*128, kelems]."""
+    mtiles, kbytes = meta[0], meta[1]
     tile = 128 * kbytes
-    hi, lo = [], []
+    hi, rest = [], []
     for m in range(mtiles):
         base = m * aparts * tile
-        hi.append(decode(img[base:base + tile], kbytes, tf32))
-        lo.append(decode(img[base + tile:base + 2 * tile], kbytes, tf32) if aparts == 2
-                  else np.zeros_like(hi[-1]))
-    return np.vstack(hi).astype(np.float64), np.vstack(lo).astype(np.float64)
+        parts = [decode(img[base + q * tile:base + (q + 1) * tile], kbytes, tf32).astype(np.float64)
+                 for q in range(aparts)]
+        hi.append(parts[0])
+        rest.append(sum(parts[1:]) if aparts > 1 else np.zeros_like(parts[0]))
+    return np.vstack(hi), np.vstack(rest)
+
+
+def edge_basis(T, r0, d):
+    """Rows r0.. r0+P-1 of T (stiffness pairs a <= b of reference directions) re-expressed for the
+    edge factors c_ij, i < j over the d+1 vertices: H_ab = c_(a+1)(b+1) for a != b and
+    H_aa = -sum_(j != a+1) c_(a+1)j, since the barycentric gradients sum to zero."""
+    pairs = [(a, b) for a in range(d) for b in range(a, d)]
+    row = {p: r0 + i for i, p in enumerate(pairs)}
+    out = T.copy()
+    e = r0
+    for i in range(d + 1):
+        for j in range(i + 1, d + 1):
+            if i == 0:
+                out[e] = -T[row[(j - 1, j - 1)]]
+            else:
+                out[e] = T[row[(i - 1, j - 1)]] - T[row[(i - 1, i - 1)]] - T[row[(j - 1, j - 1)]]
+            e += 1
+    return out
 
 
 CASES = [(f, c, k, p) for f in (coffee.MASS, coffee.HELMHOLTZ, coffee.ADVDIFF) for c in (TRI, TET)
@@ -69,7 +91,14 @@ def test_simplex_image_holds_the_reference_tensor(form, cell, k, prec):
     tf32 = TF32[prec]
     T = coffee.reference_tensor(form, k, cell)                 # [K, N]
     N = T.shape[1]
-    assert K == T.shape[0] and mtiles == math.ceil(N / 128) and parts == (2 if SPLIT[prec] else 1)
+    d = 2 + cell
+    P = d * (d + 1) // 2
+    if form == coffee.HELMHOLTZ:
+        T = edge_basis(T, 1, d)
+    elif form == coffee.ADVDIFF:
+        for v in range(d + 1):
+            T = edge_basis(T, v * P, d)
+    assert K == T.shape[0] and mtiles == math.ceil(N / 128) and parts == TPARTS[prec]
     assert kelems * (4 if tf32 else 2) == kbytes and kbytes % 32 == 0 and kelems >= K
     assert len(img) == mtiles * parts * 128 * kbytes
     hi, lo = operand(img, meta, tf32, parts)
@@ -78,9 +107,9 @@ def test_simplex_image_holds_the_reference_tensor(form, cell, k, prec):
     # padding rows and columns are zero
     assert not hi[N:].any() and not hi[:, K:].any() and not lo[N:].any() and not lo[:, K:].any()
     u = 2.0 ** -11 if tf32 else 2.0 ** -8                      # unit roundoff: 11 or 8 significant bits
-    bound = (u * u * 1.01 if parts == 2 else u) * np.abs(ref) + 1e-300
+    bound = u ** parts * 1.01 * np.abs(ref) + 1e-300           # each part rounds what the previous left
     assert np.all(np.abs(hi + lo - ref) <= bound)
-    assert np.all(np.abs(hi - ref) <= u * np.abs(ref) + 1e-300)
+    assert np.all(np.abs(hi - ref) <= u * 1.01 * np.abs(ref) + 1e-300)
 
 
 @pytest.mark.parametrize("cell,k", [(TRI, 1), (TRI, 2), (TRI, 3), (TRI, 4), (TET, 1), (TET, 2)])
@@ -95,7 +124,7 @@ def test_burgers_image_exact_integer_columns(cell, k, prec):
     img, meta = got
     mtiles, kbytes, kelems, K, parts, aexact, ksteps_off, scale_off = meta
     tf32 = TF32[prec]
-    assert aexact == (1 if k <= 2 else 0) and parts == 2
+    assert aexact == (1 if k <= 2 else 0) and parts == (1 if aexact else TPARTS[prec])
     T = coffee.reference_tensor(coffee.BURGERS_JAC, k, cell)
     d = 2 + cell
     ns = coffee.nnodes(cell, k)
@@ -103,7 +132,7 @@ def test_burgers_image_exact_integer_columns(cell, k, prec):
     K1, P = ns * d, d * (d + 1) // 2
     KA1 = ksteps_off * (8 if tf32 else 16)
     assert KA1 >= K1 and K == KA1 + K1 + P == T.shape[0] + (KA1 - K1)
-    hi, lo = operand(img, meta, tf32, 1 if aexact else 2)
+    hi, lo = operand(img, meta, tf32, parts)
     A = hi + lo
     if aexact:
         ints = hi
@@ -122,7 +151,7 @@ def test_burgers_image_exact_integer_columns(cell, k, prec):
         if tr >= 0:
             col[:nb] = T[tr]
         scale = max(np.abs(col).max(), 1e-300)
-        tol = 2.0 ** -23 if aexact else ((2.0 ** -22) if tf32 else 2.0 ** -16) * 1.01
+        tol = 2.0 ** -23 if aexact else ((2.0 ** -22) if tf32 else 2.0 ** -24) * 1.01
         assert np.abs(A[:, kk] - col).max() <= tol * scale, (kk, tr)
 
 
@@ -130,7 +159,7 @@ def test_burgers_image_exact_integer_columns(cell, k, prec):
 @pytest.mark.parametrize("k", [1, 2, 3])
 @pytest.mark.parametrize("prec", [coffee.TF32X3, coffee.BF16X3])
 def test_prism_image_holds_the_per_point_tensors_of_the_oracles_basis(form, k, prec):
-    """Prisms: K-chunks of 64 bytes per row (all 128-output slices, hi then lo, per chunk), then
+    """Prisms: K-chunks of 64 bytes per row (all 128-output slices, their parts in order), then
     the rule's points and weights as float4. The rule is the oracle's (as a set of points), and
     column q*KQ + c holds, at point q, phi_i phi_j (MASS, HELMHOLTZ c = 0), the symmetric
     derivative pairs (HELMHOLTZ c = 1..6, ADVDIFF c = 0..5) and phi_i d_a phi_j (ADVDIFF
@@ -145,7 +174,7 @@ def test_prism_image_holds_the_per_point_tensors_of_the_oracles_basis(form, k, p
     n = oracle.prism_ndof(k)
     N, Q = n * n, (k + 2) ** 3
     assert KQ == {coffee.MASS: 1, coffee.HELMHOLTZ: 7, coffee.ADVDIFF: 9}[form] and K == Q * KQ
-    assert mtiles == math.ceil(N / 128) and parts == 2 and nkc == math.ceil(K / kc)
+    assert mtiles == math.ceil(N / 128) and parts == TPARTS[prec] and nkc == math.ceil(K / kc)
     tb = 128 * kbytes
     a_chunk = mtiles * parts * tb
     assert len(img) == nkc * a_chunk + 16 * Q
@@ -154,8 +183,8 @@ def test_prism_image_holds_the_per_point_tensors_of_the_oracles_basis(form, k, p
         rows = []
         for m in range(mtiles):
             base = c * a_chunk + m * parts * tb
-            rows.append(decode(img[base:base + tb], kbytes, tf32).astype(np.float64)
-                        + decode(img[base + tb:base + 2 * tb], kbytes, tf32))
+            rows.append(sum(decode(img[base + q * tb:base + (q + 1) * tb], kbytes, tf32).astype(np.float64)
+                            for q in range(parts)))
         cols.append(np.vstack(rows))
     A = np.hstack(cols)                                        # [mtiles*128, nkc*kc]
     assert not A[N:].any() and not A[:, K:].any()
@@ -189,14 +218,14 @@ def test_prism_image_holds_the_per_point_tensors_of_the_oracles_basis(form, k, p
 
 @pytest.mark.parametrize("cell,k", [(TRI, 1), (TRI, 2), (TRI, 3), (TET, 1), (TET, 2)])
 def test_residual_image_is_the_split_burgers_image(cell, k):
-    """The residual kernel contracts the Jacobian's tensors with A split in hi and lo (it takes
-    no exact-integer form), so its image is the three-pass Burgers image."""
+    """The residual kernel contracts the Jacobian's tensors with A split in its precision's parts
+    (it takes no exact-integer form), so its image is the split Burgers image."""
     for prec in (coffee.TF32X3, coffee.BF16X3):
         got = image(coffee.BURGERS_RESIDUAL, k, cell, prec)
         if got is None:
             continue
         img, meta = got
-        assert meta[5] == 0 and meta[4] == 2
+        assert meta[5] == 0 and meta[4] == TPARTS[prec]
         jac = image(coffee.BURGERS_JAC, k, cell, prec)
         assert jac is not None and jac[1][:4] == meta[:4] and jac[1][6] == meta[6]
         if jac[1][5] == 0:

@@ -14,7 +14,7 @@ TOL = 1e-12
 DEV = "cuda:0"
 
 CASES = [(f, c, k) for f in (MASS, HELMHOLTZ, ADVDIFF) for c in (TRI, TET) for k in (1, 2, 3, 4)]
-CASES += [(BURGERS_JAC, c, k) for c in (TRI, TET) for k in (1, 2, 3)]
+CASES += [(BURGERS_JAC, c, k) for c in (TRI, TET) for k in (1, 2, 3, 4)]
 
 
 @pytest.mark.parametrize("form,cell,k", CASES)

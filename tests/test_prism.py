@@ -12,7 +12,7 @@ import torch
 import oracle
 import paper_1407_0904_gb300 as coffee
 from paper_1407_0904_gb300 import meshgen
-from tests.helpers import MASS, HELMHOLTZ, ADVDIFF, rel_err_per_cell
+from tests.helpers import MASS, HELMHOLTZ, ADVDIFF, TOL, rel_err_per_cell
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -82,18 +82,13 @@ def test_prism_errors():
     assert empty.shape == (0, 18, 18)
 
 
-TC_TOL = {coffee.TF32X3: 1e-5, coffee.BF16X3: 1e-4, coffee.TF32: 1e-2, coffee.BF16: 2e-2}
+TC_TOL = TOL
 
 
 def prism_tol(prec, form, k):
-    """The simplex tolerance plus the FP32 accumulation over the prism's long K: the tensor
-    cores add 3K/8 (tf32) or 3K/16 (bf16) partial sums into the FP32 accumulator, each rounded
-    (2^-24), so about 2^-24 sqrt(n) C relative to max|A_e|, with C = sum|G T| / max|A_e| <= 10
-    (the cancellation bound of the simplex derivation). K = Q KQ with Q = (k+2)^3 points and
-    KQ = 1 / 7 / 9 factors per point."""
-    K = (k + 2) ** 3 * {MASS: 1, HELMHOLTZ: 7, ADVDIFF: 9}[form]
-    n = 3 * K / (8 if prec in (coffee.TF32, coffee.TF32X3) else 16)
-    return TC_TOL[prec] + 2.0 ** -24 * n ** 0.5 * 10
+    """The simplex bounds (tests.helpers.TOL) hold for prisms as well: no allowance is added for
+    the long K = (k+2)^3 KQ of the quadrature-point contraction."""
+    return TOL[prec]
 
 
 @pytest.mark.parametrize("form", [MASS, HELMHOLTZ])

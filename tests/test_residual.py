@@ -2,12 +2,15 @@
 
 The residual R(u) = int (u.grad u).v + nu grad u : grad v is quadratic in u; the oracle
 evaluates it by quadrature (pinned in test_oracle_pins against exact rational integrals).
-Error metric: max |R - R_oracle| over all entries divided by max |R_oracle| over the mesh
-(entries of single cells can cancel to nearly zero, so a per-cell ratio is reported, not
-bounded). Tolerances follow the element-matrix tests: the tensor-core path forms
-C[i][s] (one contraction against the Jacobian's T2|T3 tensors, error eps_prec relative to
-sum_k |G_k T_k|) and then R = C u in FP32 with ns-term sums: FP64 1e-12, TF32X3 1e-5,
-BF16X3 1e-4, TF32 1e-2, BF16 2e-2.
+Error metrics, both bounded by the element-matrix tolerances (tests.helpers.TOL):
+  per cell: max_i |R_e - R_oracle,e| / max_i (|J_e| |u_e|)_i, where J_e is the oracle's Burgers
+    Jacobian of the cell and u_e its component-blocked dofs. R = (J_c / 2 + J_nu) u is a sum of
+    products that cancel (with u ~ N(0,1) single entries, even whole cells, of R can be nearly
+    zero), so the un-cancelled magnitude |J_e| |u_e| of the same products is the cell's scale;
+    a cell whose error is large against its own terms fails, wherever |R| itself is small.
+  global: max |R - R_oracle| over all entries divided by max |R_oracle| over the mesh.
+The plain per-cell ratio max_i |dR| / max_i |R_oracle| is printed (maximum and median) and, for
+FP64 and the split precisions, bounded as well.
 """
 import numpy as np
 import pytest
@@ -16,12 +19,11 @@ import torch
 import oracle
 import paper_1407_0904_gb300 as coffee
 from paper_1407_0904_gb300 import meshgen
-from tests.helpers import TRI, TET, to_device
+from tests.helpers import TRI, TET, BURGERS_JAC, TOL, to_device
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 RES = coffee.BURGERS_RESIDUAL
-TOL = {coffee.FP64: 1e-12, coffee.TF32X3: 1e-5, coffee.BF16X3: 1e-4, coffee.TF32: 1e-2, coffee.BF16: 2e-2}
 
 
 def ragged_mesh(cell, seed):
@@ -34,7 +36,16 @@ def errors(got, ref):
     got = np.asarray(got, dtype=np.float64).reshape(ref.shape)
     glob = float(np.abs(got - ref).max() / np.abs(ref).max())
     per = np.abs(got - ref).max(axis=1) / np.maximum(np.abs(ref).max(axis=1), 1e-300)
-    return glob, float(np.median(per))
+    return glob, float(np.median(per)), float(per.max())
+
+
+def cell_errors(got, ref, k, cell, coords, c2v, u, c2d):
+    """Per cell: max_i |dR_i| / max_i (|J| |u|)_i with the oracle's Jacobian J of the cell."""
+    got = np.asarray(got, dtype=np.float64).reshape(ref.shape)
+    J = oracle.assemble(BURGERS_JAC, k, cell, coords, c2v, u.ravel(), c2d, threads=0)
+    ub = np.transpose(u[c2d], (0, 2, 1)).reshape(len(c2v), -1)  # component-blocked
+    scale = np.einsum("eij,ej->ei", np.abs(J), np.abs(ub)).max(axis=1)
+    return float((np.abs(got - ref).max(axis=1) / np.maximum(scale, 1e-300)).max())
 
 
 CASES = [(c, k, p) for c in (TRI, TET) for k in (1, 2, 3, 4)
@@ -53,10 +64,14 @@ def test_residual_matches_oracle(cell, k, prec):
     coffee.check_errors()
     n = coffee.ndof(RES, k, cell)
     assert tuple(out.shape) == (mesh.ncells, n)
-    glob, med = errors(out.cpu().numpy(), ref)
-    print("residual %s P%d %s: %.3e (median per cell %.3e)" % ("tri" if cell == TRI else "tet", k,
-                                                                coffee.PRECISION_NAMES[prec], glob, med))
-    assert glob < TOL[prec]
+    got = out.cpu().numpy()
+    glob, med, worst = errors(got, ref)
+    per = cell_errors(got, ref, k, cell, mesh.coords, mesh.cell2vert, u, c2d)
+    print("residual %s P%d %s: per cell %.3e, global %.3e (max_i|dR|/max_i|R| per cell: median %.3e, max %.3e)"
+          % ("tri" if cell == TRI else "tet", k, coffee.PRECISION_NAMES[prec], per, glob, med, worst))
+    assert per < TOL[prec] and glob < TOL[prec]
+    if prec in (coffee.FP64, coffee.TF32X3, coffee.BF16X3):
+        assert worst < TOL[prec]  # the split precisions meet the bound against max|R| of each cell too
 
 
 def test_residual_is_the_jacobian_applied_to_u_minus_the_convective_half():
@@ -101,5 +116,6 @@ def test_config3_residual_2pow20_sampled():
     sel = np.sort(np.random.default_rng(3).choice(mesh.ncells, 2048, replace=False))
     ref = oracle.burgers_residual(2, TET, mesh.coords, mesh.cell2vert[sel], u, c2d[sel])
     got = out[torch.from_numpy(sel).to(DEV)].cpu().numpy()
-    glob, _ = errors(got, ref)
-    assert glob < TOL[coffee.TF32X3]
+    glob, _, _ = errors(got, ref)
+    per = cell_errors(got, ref, 2, TET, mesh.coords, mesh.cell2vert[sel], u, c2d[sel])
+    assert per < TOL[coffee.TF32X3] and glob < TOL[coffee.TF32X3]
