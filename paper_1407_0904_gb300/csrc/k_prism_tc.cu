@@ -2,11 +2,17 @@
 //
 // A prism's map is not affine, so the Jacobian is evaluated at every quadrature point and the
 // element matrix is a quadrature sum: A_e[o] = sum_{q,f} G_e[q][f] T[q*KQ+f][o] with
-// G_e[q] = w_q |det J_q| (1, (K_q K_q^T)_ab), KQ = 1 (mass) or 7 (Helmholtz), or
-// G_e[q] = w_q |det J_q| (eps_q (K_q K_q^T)_ab, (K_q b_q)_a), KQ = 9 (advection-diffusion with
-// degree-1 prism fields eps, b given at the six vertices). The contraction
-// over K = Q*KQ (189 at P1, 448 at P2) is too deep to keep either operand resident, so both are
-// streamed through shared memory in K-chunks of 64 bytes per row (16 tf32 / 32 bf16 columns):
+// G_e[q] = w_q g(x_q), g = |det J| (1, (K K^T)_ab), KQ = 1 (mass) or 7 (Helmholtz), or
+// g = |det J| (eps (K K^T)_ab, (K b)_a), KQ = 9 (advection-diffusion with degree-1 prism fields
+// eps, b given at the six vertices). The contraction over K = Q*KQ (189 at P1, 875 at P3)
+// accumulates hundreds of MMAs into one FP32 accumulator, and every addition into it is
+// rounded relative to the running sum. So the sum is split about the cell's factors at the
+// centre of the reference prism, g_c = g(1/3, 1/3, 1/2):
+//   A_e = sum_{q,f} w_q (g_f(x_q) - g_c,f) T[q*KQ+f] + sum_f g_c,f Tbar[f],  Tbar[f] = sum_q w_q T[q*KQ+f],
+// the per-point chunks first (deviations only: the running sum stays small; zero for an affine
+// cell) and the centre chunk (KQ columns against the weight-summed tensors) last. Both
+// operands are streamed through shared memory in K-chunks of 64 bytes per row (16 tf32 / 32
+// bf16 columns):
 //   loader warp 13      one bulk copy per chunk of T^T (all 128-output slices, all parts),
 //                       completion counted on the stage's mbarrier (transaction bytes);
 //   producer warps 4-11 two threads per cell, each forming half of the chunk's columns of G_e
@@ -52,6 +58,62 @@ __device__ __forceinline__ void prism_bulk_g2s(uint32_t dst, const void* src, ui
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
+}
+
+// Factors of one quadrature point pq = (s, t, z, w) of a prism (see the kernel comment): J from
+// the per-cell bilinear coefficients (d/ds = A + z B, d/dt = C + z D, d/dz = E + s F + t G), and
+// for advection-diffusion eps and b from the six vertex values CF. Every factor is linear in w.
+template <int KQ>
+__device__ __forceinline__ void prism_point_factors(const float4 pq, const float (&JA)[3], const float (&JB)[3],
+                                                    const float (&JC)[3], const float (&JD)[3], const float (&JE)[3],
+                                                    const float (&JF)[3], const float (&JG)[3],
+                                                    const float (&CF)[6][4], float (&gf)[9]) {
+  float J[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    J[r][0] = fmaf(pq.z, JB[r], JA[r]);
+    J[r][1] = fmaf(pq.z, JD[r], JC[r]);
+    J[r][2] = fmaf(pq.x, JF[r], fmaf(pq.y, JG[r], JE[r]));
+  }
+  const float adj[3][3] = {{J[1][1] * J[2][2] - J[1][2] * J[2][1], J[0][2] * J[2][1] - J[0][1] * J[2][2],
+                            J[0][1] * J[1][2] - J[0][2] * J[1][1]},
+                           {J[1][2] * J[2][0] - J[1][0] * J[2][2], J[0][0] * J[2][2] - J[0][2] * J[2][0],
+                            J[0][2] * J[1][0] - J[0][0] * J[1][2]},
+                           {J[1][0] * J[2][1] - J[1][1] * J[2][0], J[0][1] * J[2][0] - J[0][0] * J[2][1],
+                            J[0][0] * J[1][1] - J[0][1] * J[1][0]}};
+  const float det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+  const float adet = fabsf(det);
+  float wi = pq.w / adet;
+  constexpr int P0 = KQ == 9 ? 0 : 1;  // first pair factor
+  if constexpr (KQ == 9) {
+    // eps and b at the point from the vertex values (degree-1 prism functions)
+    const float lam[3] = {1.f - pq.x - pq.y, pq.x, pq.y};
+    float eps = 0.f, bq[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int v = 0; v < 6; ++v) {
+      const float Nv = v < 3 ? lam[v] * (1.f - pq.z) : lam[v - 3] * pq.z;
+      eps = fmaf(Nv, CF[v][0], eps);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) bq[r] = fmaf(Nv, CF[v][1 + r], bq[r]);
+    }
+    const float sw = det < 0.f ? -pq.w : pq.w;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gf[6 + a] = sw * (adj[a][0] * bq[0] + adj[a][1] * bq[1] + adj[a][2] * bq[2]);
+    wi *= eps;
+  } else {
+    gf[0] = pq.w * adet;
+  }
+  if constexpr (KQ > 1) {
+#pragma unroll
+    for (int a = 0, pp = P0; a < 3; ++a)
+#pragma unroll
+      for (int b = a; b < 3; ++b, ++pp) {
+        float acc = 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) acc = fmaf(adj[a][r], adj[b][r], acc);
+        gf[pp] = wi * acc;
+      }
+  }
 }
 
 // p.N outputs, p.mtiles slices, p.nkc chunks, p.ksteps_off = KQ, p.ns = Q; the image holds the
@@ -120,7 +182,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
       // J(s,t,z) is bilinear: columns d/ds = A + z B, d/dt = C + z D, d/dz = E + s F + t G with
       // vertex differences taken in FP64 before rounding to FP32
       float JA[3], JB[3], JC[3], JD[3], JE[3], JF[3], JG[3];
-      float CF[6][4];  // advection-diffusion: (eps, b) at the six vertices
+      float CF[6][4] = {};  // advection-diffusion: (eps, b) at the six vertices
       if (live) {
         bool bad = false;
         double Xd[6][3];
@@ -164,71 +226,45 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
           JG[r] = (float)(h2 - h0);
         }
       }
+      // the cell's factors at the centre of the reference prism (weight 1): the per-point chunks
+      // carry only the deviations w_q (g(x_q) - g(centre)), the last chunk the centre factors
+      // against the weight-summed tensors
+      float gbar[9] = {};
+      if (live) prism_point_factors<KQ>(make_float4(1.f / 3.f, 1.f / 3.f, 0.5f, 1.f), JA, JB, JC, JD, JE, JF, JG, CF, gbar);
       for (int gi = 0; gi < NG && ok; ++gi) {
-      int gq = -1;      // point whose factors are cached
+      int gq = -1;       // point whose factors are cached
       float gf[9] = {};  // the point's factors (see the kernel comment)
+      float wq = 0.f;    // and its weight
       for (int kc = 0; kc < NKC; ++kc, ++c) {
         const int s = (int)(c % nstages);
         if (!mbar_wait(smem_u32(&bars->empty[s]), ((c / nstages) & 1u) ^ 1u, p.err)) { ok = false; break; }
+        const bool centre = kc == NKC - 1;
         auto factor = [&](int kcol) -> float {
+          if (!live) return 0.f;
+          if (centre) {
+            float v = 0.f;
+#pragma unroll
+            for (int i = 0; i < KQ; ++i)
+              if (kcol == i) v = gbar[i];
+            return v;
+          }
           const int k = kc * KC + kcol;
           const int q = k / KQ, f = k - (k / KQ) * KQ;
-          if (!live || q >= Q) return 0.f;
+          if (q >= Q) return 0.f;
           if (q != gq) {
             gq = q;
             const float4 pq = qsm[q];  // (s, t, z, w)
-            float J[3][3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-              J[r][0] = fmaf(pq.z, JB[r], JA[r]);
-              J[r][1] = fmaf(pq.z, JD[r], JC[r]);
-              J[r][2] = fmaf(pq.x, JF[r], fmaf(pq.y, JG[r], JE[r]));
-            }
-            const float adj[3][3] = {{J[1][1] * J[2][2] - J[1][2] * J[2][1], J[0][2] * J[2][1] - J[0][1] * J[2][2],
-                                      J[0][1] * J[1][2] - J[0][2] * J[1][1]},
-                                     {J[1][2] * J[2][0] - J[1][0] * J[2][2], J[0][0] * J[2][2] - J[0][2] * J[2][0],
-                                      J[0][2] * J[1][0] - J[0][0] * J[1][2]},
-                                     {J[1][0] * J[2][1] - J[1][1] * J[2][0], J[0][1] * J[2][0] - J[0][0] * J[2][1],
-                                      J[0][0] * J[1][1] - J[0][1] * J[1][0]}};
-            const float det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
-            const float adet = fabsf(det);
-            float wi = pq.w / adet;
-            constexpr int P0 = KQ == 9 ? 0 : 1;  // first pair factor
-            if constexpr (KQ == 9) {
-              // eps and b at the point from the vertex values (degree-1 prism functions)
-              const float lam[3] = {1.f - pq.x - pq.y, pq.x, pq.y};
-              float eps = 0.f, bq[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-              for (int v = 0; v < 6; ++v) {
-                const float Nv = v < 3 ? lam[v] * (1.f - pq.z) : lam[v - 3] * pq.z;
-                eps = fmaf(Nv, CF[v][0], eps);
-#pragma unroll
-                for (int r = 0; r < 3; ++r) bq[r] = fmaf(Nv, CF[v][1 + r], bq[r]);
-              }
-              const float sw = det < 0.f ? -pq.w : pq.w;
-#pragma unroll
-              for (int a = 0; a < 3; ++a) gf[6 + a] = sw * (adj[a][0] * bq[0] + adj[a][1] * bq[1] + adj[a][2] * bq[2]);
-              wi *= eps;
-            } else {
-              gf[0] = pq.w * adet;
-            }
-            if constexpr (KQ > 1) {
-#pragma unroll
-              for (int a = 0, pp = P0; a < 3; ++a)
-#pragma unroll
-                for (int b = a; b < 3; ++b, ++pp) {
-                  float acc = 0.f;
-#pragma unroll
-                  for (int r = 0; r < 3; ++r) acc = fmaf(adj[a][r], adj[b][r], acc);
-                  gf[pp] = wi * acc;
-                }
-            }
+            wq = pq.w;
+            prism_point_factors<KQ>(pq, JA, JB, JC, JD, JE, JF, JG, CF, gf);
           }
-          float v = gf[0];
+          float v = gf[0], r = gbar[0];
 #pragma unroll
           for (int i = 1; i < KQ; ++i)
-            if (f == i) v = gf[i];
-          return v;
+            if (f == i) {
+              v = gf[i];
+              r = gbar[i];
+            }
+          return fmaf(-wq, r, v);
         };
         uint8_t* b = smem + (size_t)s * stage_bytes + a_chunk;  // G parts of the stage
         // this thread's half of the chunk: 32 bytes of the row (two 16-byte units per part)
@@ -409,7 +445,7 @@ bool pgeom(int form, int degree, int prec, PGeom& g) {
   g.K = g.Q * g.KQ;
   g.elem = tf32 ? 4 : 2;
   g.kc = PCB / g.elem;
-  g.nkc = (g.K + g.kc - 1) / g.kc;
+  g.nkc = (g.K + g.kc - 1) / g.kc + 1;  // the per-point chunks and the centre chunk
   g.tparts = prec_tparts(prec);
   g.gparts = prec_gparts(prec);
   g.a_chunk = g.mtiles * g.tparts * BM * PCB;
@@ -465,12 +501,17 @@ int prism_tc_supported(int form, int degree, int precision) {
   return pgeom(form, degree, precision, g) && pstages(g) > 0 ? 1 : 0;
 }
 
-// T^T chunks [chunk][slice][part][128 rows x 64 B canonical], then the points (s,t,z,w) [Q]
+// T^T chunks [chunk][slice][part][128 rows x 64 B canonical], then the points (s,t,z,w) [Q].
+// The last chunk holds the weight-summed tensors sum_q w_q T[q*KQ+f] in its first KQ columns.
 void build_prism_tc_image(int form, int degree, int prec, std::vector<uint8_t>& img, TcTable& meta) {
-  PGeom g;
+  PGeom g{};
   pgeom(form, degree, prec, g);
   std::vector<double> T, pts, wts;
   prism_tensor(form, degree, T, pts, wts);
+  std::vector<double> Tbar((size_t)g.KQ * g.N, 0.0);
+  for (int q = 0; q < g.Q; ++q)
+    for (int f = 0; f < g.KQ; ++f)
+      for (int o = 0; o < g.N; ++o) Tbar[(size_t)f * g.N + o] += wts[q] * T[((size_t)q * g.KQ + f) * g.N + o];
   const bool tf32 = g.elem == 4;
   const size_t tb = (size_t)BM * PCB;
   img.assign((size_t)g.nkc * g.a_chunk + (size_t)g.Q * 16, 0);
@@ -480,7 +521,11 @@ void build_prism_tc_image(int form, int degree, int prec, std::vector<uint8_t>& 
         const int o = m * BM + r;
         for (int j = 0; j < g.kc; ++j) {
           const int k = kc * g.kc + j;
-          const double x = (o < g.N && k < g.K) ? T[(size_t)k * g.N + o] : 0.0;
+          double x = 0.0;
+          if (o < g.N) {
+            if (kc == g.nkc - 1) x = j < g.KQ ? Tbar[(size_t)j * g.N + o] : 0.0;
+            else if (k < g.K) x = T[(size_t)k * g.N + o];
+          }
           host_store_parts(img.data() + (size_t)kc * g.a_chunk + (size_t)(m * g.tparts) * tb, tb,
                            canon_off(r, j * g.elem, PCB), x, tf32, g.tparts);
         }

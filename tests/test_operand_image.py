@@ -164,7 +164,9 @@ def test_prism_image_holds_the_per_point_tensors_of_the_oracles_basis(form, k, p
     column q*KQ + c holds, at point q, phi_i phi_j (MASS, HELMHOLTZ c = 0), the symmetric
     derivative pairs (HELMHOLTZ c = 1..6, ADVDIFF c = 0..5) and phi_i d_a phi_j (ADVDIFF
     c = 6..8), evaluated here with the oracle's own prism basis: an independent check of the
-    GPU side's prism tabulation and of the streamed layout."""
+    GPU side's prism tabulation and of the streamed layout. The last chunk holds the
+    weight-summed tensors sum_q w_q T[q*KQ+c] in its first KQ columns (the centre factors'
+    contraction)."""
     import oracle
     img, meta = image(form, k, coffee.PRISM, prec)
     mtiles, kbytes, kelems, K, parts, _, KQ, _ = meta
@@ -174,7 +176,7 @@ def test_prism_image_holds_the_per_point_tensors_of_the_oracles_basis(form, k, p
     n = oracle.prism_ndof(k)
     N, Q = n * n, (k + 2) ** 3
     assert KQ == {coffee.MASS: 1, coffee.HELMHOLTZ: 7, coffee.ADVDIFF: 9}[form] and K == Q * KQ
-    assert mtiles == math.ceil(N / 128) and parts == TPARTS[prec] and nkc == math.ceil(K / kc)
+    assert mtiles == math.ceil(N / 128) and parts == TPARTS[prec] and nkc == math.ceil(K / kc) + 1
     tb = 128 * kbytes
     a_chunk = mtiles * parts * tb
     assert len(img) == nkc * a_chunk + 16 * Q
@@ -186,8 +188,9 @@ def test_prism_image_holds_the_per_point_tensors_of_the_oracles_basis(form, k, p
             rows.append(sum(decode(img[base + q * tb:base + (q + 1) * tb], kbytes, tf32).astype(np.float64)
                             for q in range(parts)))
         cols.append(np.vstack(rows))
-    A = np.hstack(cols)                                        # [mtiles*128, nkc*kc]
-    assert not A[N:].any() and not A[:, K:].any()
+    A = np.hstack(cols[:-1])                                   # [mtiles*128, (nkc-1)*kc]
+    Abar = cols[-1]
+    assert not A[N:].any() and not A[:, K:].any() and not Abar[N:].any() and not Abar[:, KQ:].any()
     table = np.frombuffer(img[nkc * a_chunk:].tobytes(), dtype=np.float32).reshape(Q, 4).astype(np.float64)
     pts, wts = table[:, :3], table[:, 3]
     opts, owts = oracle.prism_rule(k)
@@ -198,6 +201,7 @@ def test_prism_image_holds_the_per_point_tensors_of_the_oracles_basis(form, k, p
     phi, dphi = oracle.prism_basis(k, pts)
     pairs = [(a, b) for a in range(3) for b in range(a, 3)]
     tol = 1e-5 if tf32 else 5e-5
+    wsum = [0.0] * KQ
     for q in range(Q):
         want = []
         if KQ != 9:
@@ -214,6 +218,9 @@ def test_prism_image_holds_the_per_point_tensors_of_the_oracles_basis(form, k, p
             got = A[:N, q * KQ + c]
             scale = max(np.abs(w).max(), 1e-12)
             assert np.abs(got - w.ravel()).max() <= tol * scale, (q, c)
+            wsum[c] = wsum[c] + owts[near[q]] * w.ravel()
+    for c in range(KQ):
+        assert np.abs(Abar[:N, c] - wsum[c]).max() <= tol * np.abs(wsum[c]).max(), c
 
 
 @pytest.mark.parametrize("cell,k", [(TRI, 1), (TRI, 2), (TRI, 3), (TET, 1), (TET, 2)])
