@@ -120,6 +120,10 @@ typedef enum {
 /* cells on the TMEM lanes (M = 128 cells, N = entries) for element matrices of up to 128
  * entries; by default only up to 32 entries */
 #define COFFEE_FLAG_CELL_LANES 64u
+/* with the outputs on the TMEM lanes, gather whole rows of 8 or 32 consecutive cells in shared
+ * memory and write each group with one bulk copy, instead of warp stores of 32 entries of one
+ * cell (the default) */
+#define COFFEE_FLAG_STAGED_STORE 256u
 
 /* Number of rows of the element matrix (or length of the element vector): (k+1)(k+2)/2
  * (triangle), (k+1)(k+2)(k+3)/6 (tetrahedron) or (k+1)^2(k+2)/2 (prism), times d for

@@ -22,6 +22,7 @@ FLAG_SUBTILE_64 = 8     # tuning knob: 64 cells per TMEM accumulator
 FLAG_SUBTILE_32 = 16    # tuning knob: 32 cells per TMEM accumulator
 FLAG_SUBTILE_128 = 32   # tuning knob: 128 cells per TMEM accumulator
 FLAG_CELL_LANES = 64    # tuning knob: cells on the TMEM lanes (element matrices <= 128 entries)
+FLAG_STAGED_STORE = 256  # tuning knob: rows staged in shared memory, written by bulk copies
 
 FORM_NAMES = {MASS: "mass", HELMHOLTZ: "helmholtz", ADVDIFF: "advdiff", BURGERS_JAC: "burgers_jac",
               BURGERS_RESIDUAL: "burgers_residual"}

@@ -257,7 +257,8 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
            ((a->flags & COFFEE_FLAG_SUBTILE_64) ? TUNE_SUB64 : 0u) |
            ((a->flags & COFFEE_FLAG_SUBTILE_32) ? TUNE_SUB32 : 0u) |
            ((a->flags & COFFEE_FLAG_SUBTILE_128) ? TUNE_SUB128 : 0u) |
-           ((a->flags & COFFEE_FLAG_CELL_LANES) ? TUNE_CELL_LANES : 0u);
+           ((a->flags & COFFEE_FLAG_CELL_LANES) ? TUNE_CELL_LANES : 0u) |
+           ((a->flags & COFFEE_FLAG_STAGED_STORE) ? TUNE_STAGED_STORE : 0u);
   p.precision = a->precision;
   p.validate = validate ? 1 : 0;
   p.nu = a->nu;

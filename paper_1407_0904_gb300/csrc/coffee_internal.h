@@ -31,7 +31,7 @@ COFFEE_HD constexpr int prec_gparts(int prec) {
 enum : unsigned { ERR_INDEX = 1u, ERR_TIMEOUT = 2u, ERR_CAPACITY = 4u };
 // Tuning knobs of the tensor-core kernels (from coffee_assemble_args.flags)
 enum : unsigned { TUNE_OUTPUT_LANES = 1u, TUNE_TWO_STAGES = 2u, TUNE_SUB64 = 4u, TUNE_SUB32 = 8u, TUNE_SUB128 = 16u,
-                  TUNE_CELL_LANES = 32u };
+                  TUNE_CELL_LANES = 32u, TUNE_STAGED_STORE = 128u };
 
 // ---- host tabulation (tabulate.cpp) ----
 int nnodes(int cell, int k);
@@ -150,6 +150,8 @@ struct TcParams {
   int ksteps_off;        // Burgers: K-steps of the off-diagonal component blocks
   unsigned tune;         // TUNE_* knobs
   int subw;              // cells per TMEM accumulator (outputs-on-lanes orientation)
+  int stage_cells;       // staged epilogue: rows per bulk copy (0: direct stores)
+  int stage_bufs;        // staged epilogue: buffers of stage_cells rows (2 to 4)
   int precision;
   int validate;
   double nu;
@@ -160,6 +162,10 @@ struct TcParams {
   int64_t scale_off;     // TcTable::scale_off
 };
 int tc_supported(int form, int degree, int cell, int precision);
+// staged epilogue (k_tc_staged.cu): its sub-tile width, rows per bulk copy and the bytes of one
+// buffer of those rows for p (0 when p cannot take it), and the launch
+int staged_plan(const TcParams& p, int& subw, int& cells, int& buf_bytes);
+int launch_tc_staged(int form, int cell, const TcParams& q, int num_sms, void* stream, int nst, int smem);
 int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
 // Burgers-Jacobian tensor-core kernel (k_tc_burgers.cu)
 int burgers_tc_supported(int degree, int cell, int precision);

@@ -186,6 +186,30 @@ int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, 
     }
     return launch_stream_one(bg, num_sms, stream);
   }
+  // staged epilogue (a tuning knob): rows of consecutive cells through shared memory and bulk
+  // copies; direct warp stores otherwise
+  if (!lanes && (p.tune & TUNE_STAGED_STORE)) {
+    int w = 0, ch = 0, buf = 0;
+    if (staged_plan(p, w, ch, buf)) {
+      // as many row buffers as fit beside two operand stages (up to four), then the stages
+      const int pad = round_up((int)sizeof(Barriers), 128) - (int)sizeof(Barriers);
+      int nb = STAGE_BUFS;
+      while (nb > 2 && stages_for(g, nb * buf + pad) < 2) --nb;
+      const int extra = nb * buf + pad;
+      int nss = stages_for(g, extra);
+      if (nss > 2 && (p.tune & TUNE_TWO_STAGES)) nss = 2;
+      if (nss > 0) {
+        TcParams r = q;
+        r.subw = w;
+        r.stage_cells = ch;
+        r.stage_bufs = nb;
+        int smem = g.mtiles * g.tparts * BM * g.kbytes + nss * g.gparts * BN * g.kbytes + (int)sizeof(Barriers) +
+                   extra + 1024 + 64;
+        if (smem < SMEM_ONE_CTA) smem = SMEM_ONE_CTA;
+        return launch_tc_staged(form, cell, r, num_sms, stream, nss, smem);
+      }
+    }
+  }
   int smem = g.mtiles * g.tparts * BM * g.kbytes + nst * g.gparts * BN * g.kbytes +
              (int)sizeof(Barriers) + 1024 + 64;
   if (smem < SMEM_ONE_CTA) smem = SMEM_ONE_CTA;

@@ -20,6 +20,21 @@ constexpr int CSR_STAGES = 2;
 constexpr int CSR_STAGE_BYTES = BN * 32 * 4;
 constexpr int CSR_BAR_BYTES = 128;
 constexpr int CSR_SMEM = CSR_BAR_BYTES + EPI_WARPS * CSR_STAGES * CSR_STAGE_BYTES + 128;  // barriers, ring, slack
+// Staged epilogue: at most STAGE_BUFS buffers of SCH rows (p.stage_bufs, as many as shared
+// memory holds: several bulk copies in flight); the most 128-output slices of one element matrix
+constexpr int STAGE_BUFS = 4;
+constexpr int STAGE_MAXM = 10;  // P4 tetrahedra: 1225 outputs
+template <int SCH>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&v)[SCH]) {
+  static_assert(SCH == 8 || SCH == 32, "staged epilogue: 8 or 32 cells per chunk");
+  if constexpr (SCH == 32) {
+    tmem_ld32(taddr, v);
+  } else {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+  }
+}
 
 __device__ __forceinline__ void csr_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -42,7 +57,15 @@ __device__ __forceinline__ void csr_bulk_g2s(uint32_t dst, const void* src, uint
 // CSR (outputs on lanes only): global assembly. Instead of being stored, every entry is
 //         added into the CSR value array p.out at the position p.map[cell][o]; the element
 //         matrices never reach memory.
-template <int FORM, int D, int PREC, bool LANES, bool CSR = false>
+// SCH > 0, staged (outputs on lanes only): the rows of SCH consecutive cells are gathered from
+//         all of a sub-tile's accumulators into a shared-memory buffer in the output layout and
+//         written with one bulk copy (16-byte aligned: 4 rows of N floats are a multiple of 16
+//         bytes). Used where rows do not start on 32-byte sectors (P4 tetrahedra: 4900-byte
+//         rows), which direct warp stores split. A TMEM load round trip costs hundreds of
+//         cycles, so each wait covers SCH columns of up to STAGE_SG slices (about 40 registers),
+//         and the loop is kept compact (rolled over slice groups): unrolling it over every
+//         slice was measured to thrash the instruction cache. Two buffers alternate.
+template <int FORM, int D, int PREC, bool LANES, bool CSR = false, int SCH = 0>
 __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, int nstages) {
   using PT = PrecTraits<PREC>;
   constexpr int KSTEP = PT::tf32 ? 8 : 16;  // K elements per MMA (32 bytes)
@@ -75,6 +98,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
       mbar_init(smem_u32(&bars->tempty[r]), EPI_WARPS);
     }
     mbar_init(smem_u32(&bars->done), 1);
+    if constexpr (SCH > 0) mbar_init(smem_u32(&bars->epi), EPI_WARPS);
     if constexpr (CSR) {
       uint64_t* ring = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(bars) + round_up((int)sizeof(Barriers), 128));
       for (int i = 0; i < EPI_WARPS * CSR_STAGES; ++i) mbar_init(smem_u32(ring + i), 1);
@@ -226,6 +250,75 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));
     }
+  } else if constexpr (SCH > 0) {
+    // ---------------- epilogue, rows staged in shared memory and bulk-copied ----------------
+    constexpr int SG = SCH >= 32 ? 1 : 5;  // slices per TMEM wait
+    const int q = warp;  // TMEM lane quadrant
+    const int W = p.subw, nslot = 512 / W, MT = p.mtiles;
+    float* stage0 = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + round_up((int)sizeof(Barriers), 128));
+    uint32_t rc = 0, chunk = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int j = 0; j < BN / W && ok; ++j, rc += MT) {
+        // every slice of the sub-tile (MT consecutive slots) before any row is staged
+        for (int m = 0; m < MT && ok; ++m)
+          if (!mbar_wait(smem_u32(&bars->tfull[(rc + m) % nslot]), ((rc + m) / nslot) & 1u, p.err)) ok = false;
+        if (!ok) break;
+        tc_fence_after();
+        for (int c0 = 0; c0 < W; c0 += SCH) {
+          const int64_t cbase = t * BN + j * W + c0;
+          const int64_t rem = p.ncells - cbase;
+          const int ncol = rem <= 0 ? 0 : (rem < SCH ? (int)rem : SCH);
+          if (ncol == 0) break;  // uniform over the epilogue warps
+          float* sbuf = stage0 + (size_t)(chunk % (uint32_t)p.stage_bufs) * SCH * N;
+#pragma unroll 1
+          for (int m0 = 0; m0 < MT; m0 += SG) {
+            uint32_t v[SG][SCH];
+#pragma unroll
+            for (int g = 0; g < SG; ++g)
+              if (m0 + g < MT && (m0 + g) * BM + q * 32 < N)  // warp-uniform
+                tmem_ld_cols<SCH>(tmem + ((uint32_t)(q * 32) << 16) + ((rc + m0 + g) % nslot) * W + c0, v[g]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int g = 0; g < SG; ++g) {
+              const int o = (m0 + g) * BM + q * 32 + lane;
+              if (m0 + g < MT && o < N) {
+                float* dst = sbuf + o;
+#pragma unroll
+                for (int cc = 0; cc < SCH; ++cc)
+                  if (cc < ncol) dst[cc * N] = __uint_as_float(v[g][cc]);
+              }
+            }
+          }
+          fence_proxy_async();  // the rows reach the bulk copy's (async) view of shared memory
+          __syncwarp();
+          // the buffer written next was last read by the copy of chunk + 1 - stage_bufs
+          if (threadIdx.x == 0) {
+            if (p.stage_bufs >= 4) bulk_wait_read<2>();
+            else if (p.stage_bufs == 3) bulk_wait_read<1>();
+            else bulk_wait_read<0>();
+          }
+          // every warp's rows are in the buffer (a bounded wait, unlike bar.sync, so that a warp
+          // leaving on a timeout cannot strand the others)
+          if (lane == 0) mbar_arrive(smem_u32(&bars->epi));
+          if (!mbar_wait(smem_u32(&bars->epi), chunk & 1u, p.err)) { ok = false; break; }
+          const int full = ncol & ~3;  // whole groups of 4 rows: a multiple of 16 bytes
+          if (threadIdx.x == 0 && full > 0) {
+            bulk_s2g(p.out + cbase * N, smem_u32(sbuf), (uint32_t)(full * N * 4));
+            bulk_commit();
+          }
+          for (int i = threadIdx.x; i < (ncol - full) * N; i += EPI_WARPS * 32)  // ragged last rows
+            p.out[(cbase + full) * N + i] = sbuf[full * N + i];
+          ++chunk;
+        }
+        if (!ok) break;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0)
+          for (int m = 0; m < MT; ++m) mbar_arrive(smem_u32(&bars->tempty[(rc + m) % nslot]));
+      }
+    }
+    if (threadIdx.x == 0) bulk_wait_all();  // shared memory stays valid until every copy has read it
   } else if constexpr (!CSR) {
     // ---------------- epilogue, direct 128-byte stores ----------------
     const int q = warp;  // TMEM lane quadrant

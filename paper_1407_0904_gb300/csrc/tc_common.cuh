@@ -139,6 +139,17 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 // wait until at most one bulk group of this thread still reads its shared-memory source
 __device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// 32 lanes x 4 consecutive columns of 32-bit data -> 4 registers per thread
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(taddr));
+}
+// wait until at most N bulk groups of this thread still read their shared-memory source
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
 // 32 lanes x 16 consecutive columns of 32-bit data -> 16 registers per thread
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
@@ -465,6 +476,7 @@ struct alignas(8) Barriers {
   uint64_t tfull[MAX_SLOTS];
   uint64_t tempty[MAX_SLOTS];
   uint64_t done;
+  uint64_t epi;  // staged epilogue: the epilogue warps' own barrier (one phase per bulk copy)
   uint32_t tmem_base;
 };
 

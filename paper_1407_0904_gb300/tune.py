@@ -13,6 +13,8 @@ Knobs (all give bit-identical results; only speed changes):
   FLAG_CELL_LANES     cells on the TMEM lanes for matrices of up to 128 entries
   FLAG_SUBTILE_128/64/32  cells per TMEM accumulator with outputs on the lanes (MMA N)
   FLAG_TWO_STAGES     at most two operand stages
+  FLAG_STAGED_STORE   rows of consecutive cells gathered in shared memory, one bulk copy each
+                      (tried where rows do not start on 32-byte sectors)
 
   python -m paper_1407_0904_gb300.tune [--ncells N] [--out PATH]
   python -m paper_1407_0904_gb300.tune --study    # cost model vs the tuned choices (no GPU)
@@ -72,6 +74,8 @@ def candidates(coffee, n_outputs):
          F.FLAG_SUBTILE_64 | F.FLAG_TWO_STAGES]
     if n_outputs <= 128:
         c += [F.FLAG_OUTPUT_LANES, F.FLAG_CELL_LANES, F.FLAG_CELL_LANES | F.FLAG_TWO_STAGES]
+    if (n_outputs * 4) % 32:  # rows not on 32-byte sectors: rows staged for bulk copies
+        c += [F.FLAG_OUTPUT_LANES | F.FLAG_STAGED_STORE, F.FLAG_OUTPUT_LANES | F.FLAG_STAGED_STORE | F.FLAG_TWO_STAGES]
     return sorted(set(c))
 
 

@@ -168,7 +168,33 @@ def test_tuning_knobs_give_identical_results(form, cell, k):
                       coffee.FLAG_OUTPUT_LANES | coffee.FLAG_TWO_STAGES,
                       coffee.FLAG_OUTPUT_LANES | coffee.FLAG_SUBTILE_64,
                       coffee.FLAG_OUTPUT_LANES | coffee.FLAG_SUBTILE_32,
-                      coffee.FLAG_SUBTILE_128, coffee.FLAG_CELL_LANES)]
+                      coffee.FLAG_SUBTILE_128, coffee.FLAG_CELL_LANES,
+                      coffee.FLAG_OUTPUT_LANES | coffee.FLAG_STAGED_STORE,
+                      coffee.FLAG_OUTPUT_LANES | coffee.FLAG_STAGED_STORE | coffee.FLAG_SUBTILE_32,
+                      coffee.FLAG_OUTPUT_LANES | coffee.FLAG_STAGED_STORE | coffee.FLAG_TWO_STAGES)]
     torch.cuda.synchronize()
     for o in outs[1:]:
         assert torch.equal(o, outs[0])
+
+
+@pytest.mark.parametrize("k,ncells", [(4, 1), (4, 3), (4, 5), (4, 127), (4, 130), (4, 1000), (2, 131), (2, 1000),
+                                      (3, 133)])
+@pytest.mark.parametrize("prec", [coffee.TF32X3, coffee.BF16X3])
+def test_staged_rows_ragged_tails(k, ncells, prec):
+    """Staged epilogue (rows of 8 or 32 consecutive cells gathered in shared memory, whole groups
+    of four rows written by one bulk copy, the ragged last rows by plain stores): equal to the
+    direct warp stores bit for bit, within the bound of the oracle, and nothing written past the
+    last cell, for cell counts that end mid-group, mid-tile and mid-sub-tile."""
+    mesh = meshgen.tet_mesh(6, perturb=0.15, seed=70 + k, ncells=ncells)
+    x, c2v, _, _ = to_device(mesh, None, None, DEV)
+    n = coffee.ndof(HELMHOLTZ, k, TET)
+    outs = []
+    for t in (coffee.FLAG_OUTPUT_LANES, coffee.FLAG_OUTPUT_LANES | coffee.FLAG_STAGED_STORE):
+        buf = torch.full((ncells + 5, n, n), 7.0, dtype=torch.float32, device=DEV)
+        coffee.assemble(HELMHOLTZ, k, TET, x, c2v, precision=prec, out=buf[:ncells], tune=t)
+        torch.cuda.synchronize()
+        assert torch.all(buf[ncells:] == 7.0)
+        outs.append(buf[:ncells])
+    assert torch.equal(outs[0], outs[1])
+    ref = oracle_ref(HELMHOLTZ, k, TET, mesh, None, None)
+    assert rel_err_per_cell(outs[1].cpu().numpy(), ref) < TOL[prec]
