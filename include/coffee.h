@@ -246,7 +246,11 @@ int coffee_assemble_backward(const coffee_assemble_args* a, const void* dout,
  *           before any stream capture.
  *   sharing: every call on a device uses the same array and leaves its contents behind;
  *           each call clears what must start at zero. Calls that overlap on the GPU
- *           (other streams, other host threads) race on the array: serialise them. */
+ *           (other streams, other host threads) race on the array: serialise them.
+ *   errors: device-side index errors set an error word in the same array; it keeps them
+ *           until coffee_check_errors reads it (with the library's own word) and clears it.
+ *           The reference tensor is copied into the array only when the previous call on the
+ *           device used another (form, degree, cell). */
 int coffee_assemble_backward_noalloc(const coffee_assemble_args* a, const void* dout,
                                      double* d_coords, double* d_coef, coffee_stream_t stream);
 

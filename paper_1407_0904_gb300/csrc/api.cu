@@ -530,6 +530,10 @@ int coffee_check_errors(coffee_stream_t stream) {
     e = cudaMemset(c->err, 0, sizeof(unsigned));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(error word)");
   }
+  unsigned wn = 0;  // the allocation-free adjoint keeps its own word in its static scratch
+  int rc = noalloc_error_word(&wn);
+  if (rc != COFFEE_OK) return rc;
+  w |= wn;
   if (w & ERR_TIMEOUT) return fail(COFFEE_ERR_TIMEOUT, "a device wait gave up (bounded spin)");
   if (w & ERR_INDEX) return fail(COFFEE_ERR_DEVICE_INDEX, "out-of-range index in cell2vert/cell2dof");
   return COFFEE_OK;

@@ -51,6 +51,8 @@ void prism_tensor(int form, int k, std::vector<double>& T, std::vector<double>& 
 
 // ---- error reporting (api.cu) ----
 int fail(int status, const std::string& msg);
+// the allocation-free adjoint's own error word on the current device, read and cleared (noalloc.cu)
+int noalloc_error_word(unsigned* w);
 
 // ---- FP64 plain kernel (k_fp64.cu) ----
 struct Fp64Params {

@@ -14,7 +14,7 @@
 // NOALLOC_MAX_CELLS cells and NOALLOC_MAX_NODES vertices / coefficient nodes:
 //   per-cell contributions [cells][28] double | FP64 reference tensor [36*1225] double |
 //   node counts, cursors [nodes] int32 | segment offsets [nodes+1] int64 |
-//   segment slots [cells*4] int64 | error word.
+//   segment slots [cells*4] int64 | error word (read and cleared by coffee_check_errors).
 #include <cuda_runtime.h>
 #include <cstring>
 #include <map>
@@ -56,6 +56,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 std::mutex g_na_mu;
 std::map<int, unsigned char*> g_na_addr;                               // device -> scratch address
 std::map<std::tuple<int, int, int>, std::vector<double>> g_na_tables;  // host copies of T
+std::map<int, std::tuple<int, int, int>> g_na_resident;                // device -> T held in its scratch
 
 int scratch_address(unsigned char** out) {
   int dev = 0;
@@ -74,6 +75,23 @@ int scratch_address(unsigned char** out) {
 }
 
 }  // namespace
+
+// The error word of the no-alloc scratch on the current device (0 when the entry point never
+// ran there), read after the caller's synchronisation and cleared when set.
+int noalloc_error_word(unsigned* w) {
+  *w = 0;
+  std::lock_guard<std::mutex> lock(g_na_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return COFFEE_OK;
+  auto it = g_na_addr.find(dev);
+  if (it == g_na_addr.end()) return COFFEE_OK;
+  unsigned* err = reinterpret_cast<unsigned*>(it->second + O_ERR);
+  cudaError_t e = cudaMemcpy(w, err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && *w) e = cudaMemset(err, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return fail(COFFEE_ERR_CUDA, std::string("no-alloc error word: ") + cudaGetErrorString(e));
+  return COFFEE_OK;
+}
+
 }  // namespace coffee
 
 using namespace coffee;
@@ -124,9 +142,21 @@ extern "C" int coffee_assemble_backward_noalloc(const coffee_assemble_args* a, c
     return fail(COFFEE_ERR_UNSUPPORTED, "no-alloc adjoint: reference tensor larger than its scratch region");
   cudaStream_t s = stream;
   double* dT = reinterpret_cast<double*>(base + O_T);
+  // the error word starts at zero (static device memory) and keeps its bits until
+  // coffee_check_errors reads and clears it, like the library's own error word
   unsigned* err = reinterpret_cast<unsigned*>(base + O_ERR);
-  cudaError_t e = cudaMemcpyAsync(dT, T.data(), T.size() * sizeof(double), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(unsigned), s);
+  // T is uploaded only when another (form, degree, cell) was last held in this device's
+  // scratch: calls are serialised by the caller, so a table left by the previous call is in place
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) {
+    auto res = g_na_resident.find(dev);
+    if (res == g_na_resident.end() || res->second != key) {
+      g_na_resident.erase(dev);
+      e = cudaMemcpyAsync(dT, T.data(), T.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) g_na_resident[dev] = key;
+    }
+  }
   if (e != cudaSuccess) return fail(COFFEE_ERR_CUDA, std::string("no-alloc adjoint: ") + cudaGetErrorString(e));
 
   const int d = a->cell == CELL_TRI ? 2 : 3;

@@ -17,7 +17,7 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-CASES = [(f, c, k) for f in (MASS, HELMHOLTZ, ADVDIFF) for c in (TRI, TET) for k in (1, 2, 3)]
+CASES = [(f, c, k) for f in (MASS, HELMHOLTZ, ADVDIFF) for c in (TRI, TET) for k in (1, 2, 3, 4)]
 
 
 @pytest.mark.parametrize("form,cell,k", CASES)
