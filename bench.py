@@ -456,13 +456,14 @@ def run_ours(args):
                     "peak_source": "FP64 FMA loop measured on this GPU (coffee_peak_fp64)", "flops_per_cell": flops,
                     "kernel_ms": launch_ms, "hbm_gbs": achieved}
         else:
-            # tensor pipe: executed MMA flops (K padded to the 64-byte chunk, outputs to 128-row
-            # slices, three passes for the split precisions) against the tf32/bf16 dense peak
+            # tensor pipe: executed MMA flops (K padded to the 64-byte chunk plus the centre
+            # chunk, outputs to 128-row slices, one pass per product of operand parts the
+            # precision keeps) against the tf32/bf16 dense peak
             tf32 = prec in (coffee.TF32, coffee.TF32X3)
             kc = 16 if tf32 else 32
-            kpad = -(-K // kc) * kc
+            kpad = -(-K // kc) * kc + kc
             npad = -(-(ndof * ndof) // 128) * 128
-            passes = 3 if prec in (coffee.TF32X3, coffee.BF16X3) else 1
+            passes = {coffee.TF32: 1, coffee.TF32X3: 3, coffee.BF16: 2, coffee.BF16X3: 6}[prec]
             executed = 2.0 * kpad * npad * passes
             if tf32:
                 peak_t = device_peaks(coffee)["tf32_tflops"]

@@ -173,6 +173,11 @@ int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, 
 int burgers_tc_supported(int degree, int cell, int precision);
 void build_burgers_image(int degree, int cell, int prec, bool exact_ok, std::vector<uint8_t>& img, TcTable& meta);
 int launch_burgers_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
+// Burgers Jacobian with both operands streamed in K-chunks (k_tc_burgers_stream.cu): tetrahedra
+// P3-P4 and triangles P4, where the resident-operand kernel does not fit
+int burgers_stream_supported(int degree, int cell, int precision);
+void build_burgers_stream_image(int degree, int cell, int prec, std::vector<uint8_t>& img, TcTable& meta);
+int launch_burgers_stream_tc(int cell, int degree, const TcParams& p, int num_sms, void* stream, std::string& why);
 // Burgers-residual (element vector) tensor-core kernel (k_tc_burgers_res.cu)
 int burgers_res_tc_supported(int degree, int cell, int precision);
 int launch_burgers_res_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why);

@@ -363,10 +363,23 @@ cudaError_t launch_bp(const TcParams& p, int num_sms, cudaStream_t s, int nst, i
 
 }  // namespace
 
-int burgers_tc_supported(int degree, int cell, int precision) {
+namespace {
+// The resident-operand kernel takes the shape (A in the precision's parts: the larger of its two
+// layouts); otherwise the streamed kernel (k_tc_burgers_stream.cu) does.
+bool burgers_resident(int degree, int cell, int precision) {
   BGeom g;
-  if (!bgeom(degree, cell, precision, g)) return 0;
-  return cstages(g) > 0 ? 1 : 0;  // A in the precision's parts: the larger of the two layouts
+  return bgeom(degree, cell, precision, g) && cstages(g) > 0;
+}
+int degree_of(int cell, int ns) {
+  for (int k = 1; k <= 4; ++k)
+    if (nnodes(cell, k) == ns) return k;
+  return 0;
+}
+}  // namespace
+
+int burgers_tc_supported(int degree, int cell, int precision) {
+  if (burgers_resident(degree, cell, precision)) return 1;
+  return burgers_stream_supported(degree, cell, precision);
 }
 
 namespace {
@@ -403,6 +416,10 @@ bool integer_column(const std::vector<double>& x, bool tf32, double& scale, std:
 }  // namespace
 
 void build_burgers_image(int degree, int cell, int prec, bool exact_ok, std::vector<uint8_t>& img, TcTable& meta) {
+  if (exact_ok && !burgers_resident(degree, cell, prec)) {  // the Jacobian on the streamed kernel
+    build_burgers_stream_image(degree, cell, prec, img, meta);
+    return;
+  }
   BGeom g;
   bgeom(degree, cell, prec, g);
   std::vector<double> T;
@@ -459,6 +476,8 @@ void build_burgers_image(int degree, int cell, int prec, bool exact_ok, std::vec
 
 int launch_burgers_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why) {
   if (p.ncells == 0) return (int)cudaSuccess;
+  const int degree = degree_of(cell, p.ns);
+  if (!burgers_resident(degree, cell, p.precision)) return launch_burgers_stream_tc(cell, degree, p, num_sms, stream, why);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   BGeom g{};
   g.mtiles = p.mtiles;

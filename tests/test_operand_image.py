@@ -112,12 +112,13 @@ def test_simplex_image_holds_the_reference_tensor(form, cell, k, prec):
     assert np.all(np.abs(hi - ref) <= u * 1.01 * np.abs(ref) + 1e-300)
 
 
-@pytest.mark.parametrize("cell,k", [(TRI, 1), (TRI, 2), (TRI, 3), (TRI, 4), (TET, 1), (TET, 2)])
+@pytest.mark.parametrize("cell,k", [(TRI, 1), (TRI, 2), (TRI, 3), (TET, 1), (TET, 2)])
 @pytest.mark.parametrize("prec", [coffee.TF32X3, coffee.BF16X3])
 def test_burgers_image_exact_integer_columns(cell, k, prec):
     """P1-P2 on triangles and tetrahedra: every A column is an integer vector times a float scale
-    (one part, two MMA passes); triangles P3-P4 keep the split image. The columns are T1, then the
-    T2 and T3 rows of coffee_reference_tensor(BURGERS_JAC) after the off-diagonal K-steps."""
+    (one part, one MMA pass per part of the factors); triangles P3 keep the split image. The
+    columns are T1, then the T2 and T3 rows of coffee_reference_tensor(BURGERS_JAC) after the
+    off-diagonal K-steps."""
     got = image(coffee.BURGERS_JAC, k, cell, prec)
     if got is None:
         pytest.skip("no tensor-core kernel for this combination")
@@ -237,3 +238,50 @@ def test_residual_image_is_the_split_burgers_image(cell, k):
         assert jac is not None and jac[1][:4] == meta[:4] and jac[1][6] == meta[6]
         if jac[1][5] == 0:
             assert np.array_equal(jac[0], img)  # without an exact form the two images coincide
+
+
+@pytest.mark.parametrize("cell,k", [(TET, 3), (TET, 4), (TRI, 4)])
+@pytest.mark.parametrize("prec", [coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16])
+def test_burgers_streamed_image_chunks(cell, k, prec):
+    """Shapes whose operands do not fit in shared memory (tetrahedra P3-P4, triangles P4 in the
+    split precisions) take the streamed layout: per 128-entry slice m and K-chunk of 64 bytes per
+    row, the precision's parts of [T1 | T2 | T3]^T, [m][chunk][part][128 x 64 B]. Decoded here,
+    column kc*CK + j of slice m is the reference-tensor row of that K-column, to the split's
+    accuracy, and zero in the padding."""
+    got = image(coffee.BURGERS_JAC, k, cell, prec)
+    if got is None:
+        pytest.skip("no tensor-core kernel for this combination")
+    img, meta = got
+    mtiles, kbytes, kelems, K, parts, aexact, nca, _ = meta
+    if kbytes != 64:
+        pytest.skip("resident layout for this precision")
+    tf32 = TF32[prec]
+    d, ns = 2 + cell, coffee.nnodes(cell, k)
+    nb, K1, P = ns * ns, ns * d, d * (d + 1) // 2
+    ck = 16 if tf32 else 32
+    KA1 = nca * ck
+    ncd = kelems // ck
+    assert aexact == 0 and parts == TPARTS[prec] and mtiles == math.ceil(nb / 128)
+    assert KA1 == math.ceil(K1 / ck) * ck and kelems == math.ceil((KA1 + K1 + P) / ck) * ck
+    tb = 128 * 64
+    assert len(img) == mtiles * ncd * parts * tb
+    T = coffee.reference_tensor(coffee.BURGERS_JAC, k, cell)
+    u = 2.0 ** -11 if tf32 else 2.0 ** -8
+    for m in range(mtiles):
+        cols = []
+        for kc in range(ncd):
+            base = (m * ncd + kc) * parts * tb
+            cols.append(sum(decode(img[base + q * tb:base + (q + 1) * tb], 64, tf32).astype(np.float64)
+                            for q in range(parts)))
+        A = np.hstack(cols)                                    # [128, ncd * ck]
+        rows = slice(m * 128, min(nb, (m + 1) * 128))
+        nr = rows.stop - rows.start
+        assert not A[nr:].any()
+        for kk in range(kelems):
+            tr = (kk if kk < K1 else ns * d + kk - KA1 if KA1 <= kk < KA1 + K1
+                  else 2 * ns * d + kk - KA1 - K1 if KA1 + K1 <= kk < KA1 + K1 + P else -1)
+            if tr < 0:
+                assert not A[:, kk].any(), kk
+                continue
+            want = T[tr, rows]
+            assert np.all(np.abs(A[:nr, kk] - want) <= u ** parts * 1.01 * np.abs(want) + 1e-300), (m, kk)
