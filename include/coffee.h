@@ -82,10 +82,16 @@ typedef enum {
   COFFEE_BURGERS_RESIDUAL = 4 /* element vectors, see below */
 } coffee_form;
 
-/* Arithmetic of the contraction.  FP64: CUDA-core FP64, double output.
- * TF32 / BF16: one tensor-core pass (FP32 accumulate, float output).
- * TF32X3 / BF16X3: operands split x = hi + lo, products hi*hi + hi*lo + lo*hi
- * accumulated in FP32 on the tensor cores, float output. */
+/* Arithmetic of the contraction A_e = sum_k G_e[k] T[k] (per-cell factors G, reference
+ * tensors T), accumulated in FP32 on the tensor cores, float output; FP64: CUDA-core FP64,
+ * double output. Each operand is held as a sum of parts of the operand type, each part the
+ * round-to-nearest of what the previous ones left:
+ *   TF32:   T and G one tf32 part each, one product;
+ *   TF32X3: T and G two tf32 parts each, the three products hi*hi + hi*lo + lo*hi;
+ *   BF16:   T two bf16 parts, G one, two products;
+ *   BF16X3: T and G three bf16 parts each, the six products of order <= 2.
+ * Parity bounds (max |A - A_exact| / max |A_exact| per cell): 1e-5 for TF32X3 and BF16X3,
+ * 1e-2 for TF32 and BF16. */
 typedef enum {
   COFFEE_FP64 = 0,
   COFFEE_TF32 = 1,
@@ -181,7 +187,18 @@ typedef struct {
   void* out;                 /* device [ncells][ndof][ndof], double or float */
   int64_t ncells;
   unsigned flags;            /* COFFEE_FLAG_* */
+  /* optional, device [nverts][d][2] float: every coordinate as hi = (float)x and
+   * lo = (float)(x - hi), as coffee_split_coords writes them, or NULL. The tensor-core kernels on
+   * triangles and tetrahedra then take the vertex differences of the Jacobian in FP32
+   * ((hi1 - hi0) + (lo1 - lo0)) instead of FP64; coords must still be given (badly conditioned
+   * cells are recomputed from it in FP64). Ignored by the FP64 kernels and by prisms. */
+  const float* coords_split;
 } coffee_assemble_args;
+
+/* Every coordinate x[i], i < n (n = nverts * d), as the float pair (hi, lo) = ((float)x,
+ * (float)(x - hi)) in split[2i], split[2i+1]: the coords_split input of coffee_assemble_args.
+ * Device pointers, asynchronous on stream; n == 0 returns COFFEE_OK. */
+int coffee_split_coords(const double* coords, int64_t n, float* split, coffee_stream_t stream);
 
 /* 1 if coffee_assemble_ex has a kernel for (form, degree, cell, precision), else 0.
  * FP64 covers every form, degree 1..4, both cells; the tensor-core precisions cover
@@ -200,6 +217,8 @@ int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream);
  * pointers with the layouts of coffee_assemble; out is [ncells][ndof][ndof] (BURGERS_RESIDUAL:
  * [ncells][ndof]), double for FP64 and float otherwise. a->nverts, and a->ncoefnodes for the
  * forms with a coefficient, must be > 0: they size the copies.
+ * a->coords_split is ignored: for the tensor-core precisions on triangles and tetrahedra the
+ * coordinates are split into (hi, lo) float pairs on the device after their copy.
  * The coordinates and coefficients are copied to the device once; the cells are assembled in
  * `chunks` launches (chunk boundaries on 128-cell tiles), each chunk's inputs copied in and its
  * results copied back on a second, library-owned stream while the next chunk computes.

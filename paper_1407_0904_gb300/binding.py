@@ -49,6 +49,7 @@ class AssembleArgs(ctypes.Structure):
         ("cell2dof", ctypes.c_void_p),
         ("out", ctypes.c_void_p), ("ncells", ctypes.c_int64),
         ("flags", ctypes.c_uint),
+        ("coords_split", ctypes.c_void_p),
     ]
 
 
@@ -68,6 +69,7 @@ def lib():
         L.coffee_assemble_backward.argtypes = [ctypes.POINTER(AssembleArgs), P, P, P, I, P]
         L.coffee_check_errors.argtypes = [P]
         L.coffee_supported.argtypes = [I, I, I, I]
+        L.coffee_split_coords.argtypes = [P, L64, P, P]
         L.coffee_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
@@ -222,8 +224,24 @@ def check_shapes(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None
         raise ValueError("coef must be [ncoefnodes, %d]" % row)
 
 
+def split_coords(coords, out=None, stream=None):
+    """coffee_split_coords: every coordinate as the float pair (hi, lo) = ((float)x, (float)(x - hi)),
+    a float32 tensor [nverts, d, 2] on the device: the coords_split input of assemble, with which
+    the tensor-core kernels take the Jacobian's vertex differences in FP32."""
+    coords = _dev(coords, torch.float64, "coords")
+    if out is None:
+        out = torch.empty(tuple(coords.shape) + (2,), dtype=torch.float32, device=coords.device)
+    else:
+        _dev(out, torch.float32, "out")
+        if out.numel() != 2 * coords.numel():
+            raise ValueError("out must hold 2 floats per coordinate")
+    _check(lib().coffee_split_coords(_ptr(coords), ctypes.c_int64(coords.numel()), _ptr(out),
+                                     _stream_handle(stream)))
+    return out
+
+
 def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
-              out=None, nu=0.01, validate=False, ncoefnodes=None, tune=0, alloc_out=True):
+              out=None, nu=0.01, validate=False, ncoefnodes=None, tune=0, alloc_out=True, coords_split=None):
     coords = _dev(coords, torch.float64, "coords")
     cell2vert = _dev(cell2vert, torch.int32, "cell2vert")
     coef = _dev(coef, torch.float64, "coef")
@@ -251,19 +269,25 @@ def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, p
     a.cell2dof = _ptr(cell2dof)
     a.out, a.ncells = _ptr(out), ncells
     a.flags = (FLAG_VALIDATE if validate else 0) | int(tune)
+    if coords_split is not None:
+        _dev(coords_split, torch.float32, "coords_split")
+        if coords_split.numel() != 2 * coords.numel():
+            raise ValueError("coords_split must hold 2 floats per coordinate (split_coords)")
+    a.coords_split = _ptr(coords_split)
     return a, out
 
 
 def assemble(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
-             out=None, nu=0.01, validate=False, stream=None, tune=None):
+             out=None, nu=0.01, validate=False, stream=None, tune=None, coords_split=None):
     """Element matrices [ncells, ndof, ndof] (float64 for FP64, float32 otherwise) on the device.
 
     tune: FLAG_OUTPUT_LANES / FLAG_TWO_STAGES knobs; None uses the autotuner's choice for
-    this (form, degree, cell, precision) when one is cached, else the library default."""
+    this (form, degree, cell, precision) when one is cached, else the library default.
+    coords_split: the (hi, lo) float pairs of coords (split_coords), optional."""
     if tune is None:
         tune = _tuned_flags(form, degree, cell, precision)
     a, out = make_args(form, degree, cell, coords, cell2vert, coef, cell2dof, precision, out, nu,
-                       validate, tune=tune)
+                       validate, tune=tune, coords_split=coords_split)
     _check(lib().coffee_assemble_ex(ctypes.byref(a), _stream_handle(stream)))
     return out
 
@@ -456,7 +480,8 @@ class BatchPlan:
     """Several (form, degree, cell) groups assembled by one persistent launch.
 
     groups: list of dicts with keys form, degree, cell, coords, cell2vert and optionally
-    coef, cell2dof, out. All groups use `precision` (a tensor-core precision).
+    coef, cell2dof, out, coords_split (split_coords of coords). All groups use `precision`
+    (a tensor-core precision).
     launch() only enqueues one kernel on the current stream (CUDA-graph capturable).
 
     Work is split over the CTAs by cost. costs="measured" (default) takes each group's time
@@ -480,10 +505,11 @@ class BatchPlan:
         for i, g in enumerate(groups):
             a, out = make_args(g["form"], g["degree"], g["cell"], g["coords"], g["cell2vert"],
                                g.get("coef"), g.get("cell2dof"), precision, g.get("out"),
-                               g.get("nu", 0.01), validate)
+                               g.get("nu", 0.01), validate, coords_split=g.get("coords_split"))
             arr[i] = a
             self.outputs.append(out)
-            self._keep.append((g["coords"], g["cell2vert"], g.get("coef"), g.get("cell2dof"), out))
+            self._keep.append((g["coords"], g["cell2vert"], g.get("coef"), g.get("cell2dof"), out,
+                               g.get("coords_split")))
         if item_overhead is None or item_overhead < 0:
             try:
                 from . import tune as _tune

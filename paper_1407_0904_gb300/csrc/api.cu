@@ -15,6 +15,15 @@
 
 namespace coffee {
 
+// every coordinate as (hi, lo) = ((float)x, (float)(x - hi)): the coords_split input
+__global__ void k_split_coords(const double* __restrict__ x, int64_t n, float2* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const float hi = (float)v;
+    out[i] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+
 static thread_local std::string g_last_error;
 
 int fail(int status, const std::string& msg) {
@@ -239,6 +248,7 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
   p.coef = a->coef;
   p.c2d = a->cell2dof;
   p.image = meta.image;
+  p.xs = a->coords_split;
   p.out = static_cast<float*>(a->out);
   p.err = c->err;
   p.ncells = a->ncells;
@@ -327,6 +337,23 @@ int coffee_supported(int form, int degree, int cell, int precision) {
            (precision == PREC_FP64 || prism_tc_supported(form, degree, precision));
   if (precision == PREC_FP64) return 1;
   return tc_supported(form, degree, cell, precision);
+}
+
+int coffee_split_coords(const double* coords, int64_t n, float* split, coffee_stream_t stream) {
+  if (n < 0) return fail(COFFEE_ERR_INVALID_ARG, "split_coords: n < 0");
+  if (n == 0) return COFFEE_OK;
+  if (!coords || !split) return fail(COFFEE_ERR_INVALID_ARG, "split_coords: coords and split must be non-NULL");
+  DeviceCache* c = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    int rc = device_cache(&c);
+    if (rc != COFFEE_OK) return rc;
+  }
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8);
+  k_split_coords<<<(unsigned)blocks, 256, 0, stream>>>(coords, n, reinterpret_cast<float2*>(split));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "launch(split_coords)");
+  return COFFEE_OK;
 }
 
 int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream) {
@@ -643,6 +670,7 @@ int batch_plan_impl(const coffee_assemble_args* groups, int ngroups, int grid, d
     g.p.kbytes = meta.kbytes;
     g.p.tparts = meta.tparts;
     g.p.precision = prec;
+    g.p.xs = a->coords_split;
     g.p.validate = (a->flags & COFFEE_FLAG_VALIDATE) ? 1 : 0;
     g.p.nu = a->nu;
     g.item0 = items;

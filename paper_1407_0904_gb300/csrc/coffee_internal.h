@@ -140,6 +140,7 @@ struct TcTable {
 
 struct TcParams {
   const double* coords;
+  const float* xs;       // optional: every coordinate as (hi, lo) floats, [nverts][d][2]
   const int32_t* c2v;
   const double* coef;
   const int32_t* c2d;

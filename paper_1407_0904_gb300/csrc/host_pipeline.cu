@@ -1,5 +1,7 @@
 // Local assembly of host-resident data (coffee_assemble_host): the copies around
-// coffee_assemble_ex. Coordinates and coefficients go to the device once; the cells are
+// coffee_assemble_ex. Coordinates and coefficients go to the device once (for the tensor-core
+// precisions on simplices the coordinates are then split into (hi, lo) float pairs on the
+// device, coffee_split_coords); the cells are
 // assembled in chunks, each chunk's index rows copied in on the caller's stream before its
 // launch and its element matrices copied back on a library-owned stream while the next
 // chunk computes. Staging memory comes from a library-owned stream-ordered pool.
@@ -93,9 +95,12 @@ int coffee_assemble_host(const coffee_assemble_args* a, int chunks, coffee_strea
   const size_t b_coef = has_coef ? (size_t)a->ncoefnodes * coef_row * sizeof(double) : 0;
   const size_t b_c2v = (size_t)nc * nv * sizeof(int32_t), b_c2d = (size_t)nc * w * sizeof(int32_t);
   const size_t b_out = (size_t)nc * row_out;
+  // tensor-core kernels on simplices take the vertex differences from (hi, lo) float pairs
+  const bool split = a->precision != PREC_FP64 && a->cell != CELL_PRISM;
+  const size_t b_split = split ? (size_t)a->nverts * d * 2 * sizeof(float) : 0;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t o_coef = al(b_coords), o_c2v = o_coef + al(b_coef), o_c2d = o_c2v + al(b_c2v),
-               o_out = o_c2d + al(b_c2d), total = o_out + al(b_out);
+               o_out = o_c2d + al(b_c2d), o_split = o_out + al(b_out), total = o_split + al(b_split);
 
   HostRes* r = nullptr;
   int rc = host_res(&r);
@@ -113,11 +118,13 @@ int coffee_assemble_host(const coffee_assemble_args* a, int chunks, coffee_strea
   int32_t* d_c2v = reinterpret_cast<int32_t*>(ws + o_c2v);
   int32_t* d_c2d = has_coef ? reinterpret_cast<int32_t*>(ws + o_c2d) : nullptr;
   uint8_t* d_out = ws + o_out;
+  float* d_split = split ? reinterpret_cast<float*>(ws + o_split) : nullptr;
   uint8_t* h_out = static_cast<uint8_t*>(a->out);
 
   e = cudaMemcpyAsync(d_coords, a->coords, b_coords, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && has_coef) e = cudaMemcpyAsync(d_coef, a->coef, b_coef, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) rc = cuda_err(e, "cudaMemcpyAsync(coordinates, coefficients)");
+  if (rc == COFFEE_OK && split) rc = coffee_split_coords(d_coords, a->nverts * d, d_split, s);
 
   // chunks of whole 128-cell tiles, so every chunk's output starts 512-byte aligned
   int64_t per = (nc + chunks - 1) / chunks;
@@ -135,6 +142,7 @@ int coffee_assemble_host(const coffee_assemble_args* a, int chunks, coffee_strea
     }
     coffee_assemble_args b = *a;
     b.coords = d_coords;
+    b.coords_split = d_split;
     b.coef = d_coef;
     b.cell2vert = d_c2v + lo * nv;
     b.cell2dof = has_coef ? d_c2d + lo * w : nullptr;

@@ -145,13 +145,8 @@ __global__ void __launch_bounds__(S_THREADS, 1) k_burgers_stream_tc(const TcPara
           atomicOr(p.err, ERR_INDEX);
           live = false;
         } else {
-          double X[NV][D];
-#pragma unroll
-          for (int v = 0; v < NV; ++v)
-#pragma unroll
-            for (int r = 0; r < D; ++r) X[v][r] = __ldg(p.coords + (int64_t)vid[v] * D + r);
           float adj[D][D], Dm, sg;
-          cell_geometry<D>(X, adj, Dm, sg);
+          cell_geometry_ids<D>(p, vid, adj, Dm, sg);
           const float inv = 1.0f / Dm;
 #pragma unroll
           for (int a = 0; a < D; ++a)

@@ -276,17 +276,10 @@ __device__ __forceinline__ float minor2(float a, float d, float b, float c) {
   return f + e;
 }
 
-// Geometry in FP32 from FP64 vertex differences; falls back to FP64 for badly
-// conditioned cells. Produces adj (K = adj/det), |det| and sign(det).
+// Adjugate (K = adj/det) and determinant in FP32 from the FP32 Jacobian; false when the cell is
+// badly conditioned (Frobenius condition number above KAPPA_FP64).
 template <int D>
-__device__ __forceinline__ void cell_geometry(const double (&X)[D + 1][D], float (&adj)[D][D], float& Dm,
-                                              float& sg) {
-  float J[D][D];
-#pragma unroll
-  for (int r = 0; r < D; ++r)
-#pragma unroll
-    for (int c = 0; c < D; ++c) J[r][c] = (float)(X[c + 1][r] - X[0][r]);
-  float det;
+__device__ __forceinline__ bool geometry_f32(const float (&J)[D][D], float (&adj)[D][D], float& det) {
   if constexpr (D == 2) {
     det = minor2(J[0][0], J[1][1], J[0][1], J[1][0]);
     adj[0][0] = J[1][1]; adj[0][1] = -J[0][1];
@@ -313,33 +306,82 @@ __device__ __forceinline__ void cell_geometry(const double (&X)[D + 1][D], float
       na = fmaf(adj[r][c], adj[r][c], na);
     }
   // kappa_F^2 = |J|_F^2 |adj|_F^2 / det^2
-  const bool bad = !(nj * na <= KAPPA_FP64 * KAPPA_FP64 * det * det);
-  if (bad) {
-    double Jd[D][D], A[D][D], dd;
+  return nj * na <= KAPPA_FP64 * KAPPA_FP64 * det * det;
+}
+
+// The same in FP64 from the FP64 vertex coordinates, rounded to FP32 at the end.
+template <int D>
+__device__ __forceinline__ void geometry_f64(const double (&X)[D + 1][D], float (&adj)[D][D], float& det) {
+  double Jd[D][D], A[D][D], dd;
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) Jd[r][c] = X[c + 1][r] - X[0][r];
+  if constexpr (D == 2) {
+    dd = Jd[0][0] * Jd[1][1] - Jd[0][1] * Jd[1][0];
+    A[0][0] = Jd[1][1]; A[0][1] = -Jd[0][1]; A[1][0] = -Jd[1][0]; A[1][1] = Jd[0][0];
+  } else {
+    A[0][0] = Jd[1][1] * Jd[2][2] - Jd[1][2] * Jd[2][1];
+    A[1][0] = Jd[1][2] * Jd[2][0] - Jd[1][0] * Jd[2][2];
+    A[2][0] = Jd[1][0] * Jd[2][1] - Jd[1][1] * Jd[2][0];
+    A[0][1] = Jd[0][2] * Jd[2][1] - Jd[0][1] * Jd[2][2];
+    A[1][1] = Jd[0][0] * Jd[2][2] - Jd[0][2] * Jd[2][0];
+    A[2][1] = Jd[0][1] * Jd[2][0] - Jd[0][0] * Jd[2][1];
+    A[0][2] = Jd[0][1] * Jd[1][2] - Jd[0][2] * Jd[1][1];
+    A[1][2] = Jd[0][2] * Jd[1][0] - Jd[0][0] * Jd[1][2];
+    A[2][2] = Jd[0][0] * Jd[1][1] - Jd[0][1] * Jd[1][0];
+    dd = Jd[0][0] * A[0][0] + Jd[0][1] * A[1][0] + Jd[0][2] * A[2][0];
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int r = 0; r < D; ++r) adj[a][r] = (float)A[a][r];
+  det = (float)dd;
+}
+
+// Geometry of the cell with vertex ids vid: adj (K = adj/det), |det| and sign(det). The Jacobian
+// J[r][c] = x_{c+1}[r] - x_0[r] is taken in FP32 from the caller's (hi, lo) float pairs of the
+// coordinates when it passed them ((hi1 - hi0) + (lo1 - lo0): the hi difference is exact or
+// rounded once, the lo one is 2^-24 smaller, so J carries about two FP32 roundings, no FP64
+// work), else as the FP64 difference rounded to FP32; badly conditioned cells are recomputed in
+// FP64 from the FP64 coordinates.
+template <int D>
+__device__ __forceinline__ void cell_geometry_ids(const TcParams& p, const int (&vid)[D + 1], float (&adj)[D][D],
+                                                  float& Dm, float& sg) {
+  float J[D][D], det;
+  bool good;
+  if (p.xs != nullptr) {
+    const float2* xs = reinterpret_cast<const float2*>(p.xs);
+    float2 x[D + 1][D];
+#pragma unroll
+    for (int v = 0; v < D + 1; ++v)
+#pragma unroll
+      for (int r = 0; r < D; ++r) x[v][r] = __ldg(xs + (int64_t)vid[v] * D + r);
 #pragma unroll
     for (int r = 0; r < D; ++r)
 #pragma unroll
-      for (int c = 0; c < D; ++c) Jd[r][c] = X[c + 1][r] - X[0][r];
-    if constexpr (D == 2) {
-      dd = Jd[0][0] * Jd[1][1] - Jd[0][1] * Jd[1][0];
-      A[0][0] = Jd[1][1]; A[0][1] = -Jd[0][1]; A[1][0] = -Jd[1][0]; A[1][1] = Jd[0][0];
-    } else {
-      A[0][0] = Jd[1][1] * Jd[2][2] - Jd[1][2] * Jd[2][1];
-      A[1][0] = Jd[1][2] * Jd[2][0] - Jd[1][0] * Jd[2][2];
-      A[2][0] = Jd[1][0] * Jd[2][1] - Jd[1][1] * Jd[2][0];
-      A[0][1] = Jd[0][2] * Jd[2][1] - Jd[0][1] * Jd[2][2];
-      A[1][1] = Jd[0][0] * Jd[2][2] - Jd[0][2] * Jd[2][0];
-      A[2][1] = Jd[0][1] * Jd[2][0] - Jd[0][0] * Jd[2][1];
-      A[0][2] = Jd[0][1] * Jd[1][2] - Jd[0][2] * Jd[1][1];
-      A[1][2] = Jd[0][2] * Jd[1][0] - Jd[0][0] * Jd[1][2];
-      A[2][2] = Jd[0][0] * Jd[1][1] - Jd[0][1] * Jd[1][0];
-      dd = Jd[0][0] * A[0][0] + Jd[0][1] * A[1][0] + Jd[0][2] * A[2][0];
+      for (int c = 0; c < D; ++c) J[r][c] = (x[c + 1][r].x - x[0][r].x) + (x[c + 1][r].y - x[0][r].y);
+    good = geometry_f32<D>(J, adj, det);
+    if (!good) {
+      double X[D + 1][D];
+#pragma unroll
+      for (int v = 0; v < D + 1; ++v)
+#pragma unroll
+        for (int r = 0; r < D; ++r) X[v][r] = __ldg(p.coords + (int64_t)vid[v] * D + r);
+      geometry_f64<D>(X, adj, det);
     }
+  } else {
+    double X[D + 1][D];
 #pragma unroll
-    for (int a = 0; a < D; ++a)
+    for (int v = 0; v < D + 1; ++v)
 #pragma unroll
-      for (int r = 0; r < D; ++r) adj[a][r] = (float)A[a][r];
-    det = (float)dd;
+      for (int r = 0; r < D; ++r) X[v][r] = __ldg(p.coords + (int64_t)vid[v] * D + r);
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) J[r][c] = (float)(X[c + 1][r] - X[0][r]);
+    good = geometry_f32<D>(J, adj, det);
+    if (!good) geometry_f64<D>(X, adj, det);
   }
   Dm = fabsf(det);
   sg = det < 0.f ? -1.f : 1.f;
@@ -427,13 +469,8 @@ __device__ __forceinline__ void cell_factors_ids(const TcParams& p, const CellId
     }
   }
   if (bad) return;
-  double X[NV][D];
-#pragma unroll
-  for (int v = 0; v < NV; ++v)
-#pragma unroll
-    for (int r = 0; r < D; ++r) X[v][r] = __ldg(p.coords + (int64_t)vid[v] * D + r);
   float adj[D][D], Dm, sg;
-  cell_geometry<D>(X, adj, Dm, sg);
+  cell_geometry_ids<D>(p, vid, adj, Dm, sg);
   float C[P];  // edge factors
   if constexpr (FORM != FORM_MASS) edge_factors<D>(adj, 1.0f / Dm, C);
   if constexpr (FORM == FORM_MASS) {

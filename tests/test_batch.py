@@ -13,19 +13,20 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-def make_batch(tri, tet, seed=4):
+def make_batch(tri, tet, seed=4, split=False):
     dev = {}
     for m in (tri, tet):
         coef, c2d, _ = meshgen.advdiff_coefficients(m, seed=seed)
         dev[m.cell] = dict(mesh=m, coords=torch.from_numpy(m.coords).to(DEV),
                            c2v=torch.from_numpy(m.cell2vert).to(DEV), coef_np=coef, c2d_np=c2d,
                            coef=torch.from_numpy(coef).to(DEV), c2d=torch.from_numpy(c2d).to(DEV))
+        dev[m.cell]["xs"] = coffee.split_coords(dev[m.cell]["coords"]) if split else None
     groups = []
     for spec in meshgen.batch_groups(tri, tet, seed=seed):
         d = dev[spec["cell"]]
         sl = slice(spec["start"], spec["start"] + spec["count"])
         g = dict(form=spec["form"], degree=spec["degree"], cell=spec["cell"], coords=d["coords"],
-                 cell2vert=d["c2v"][sl].contiguous(), spec=spec)
+                 cell2vert=d["c2v"][sl].contiguous(), spec=spec, coords_split=d["xs"])
         if spec["form"] == ADVDIFF:
             g["coef"] = d["coef"]
             g["cell2dof"] = d["c2d"][sl].contiguous()
@@ -39,7 +40,8 @@ def check_groups(dev, groups, outs, prec, tol, sample=None):
         if spec["count"] == 0:
             continue
         single = coffee.assemble(g["form"], g["degree"], g["cell"], g["coords"], g["cell2vert"],
-                                 g.get("coef"), g.get("cell2dof"), precision=prec)
+                                 g.get("coef"), g.get("cell2dof"), precision=prec,
+                                 coords_split=g.get("coords_split"))
         assert torch.equal(out, single), spec
         d = dev[g["cell"]]
         m = d["mesh"]
@@ -55,11 +57,14 @@ def check_groups(dev, groups, outs, prec, tol, sample=None):
         assert rel_err_per_cell(got, ref) < tol, spec
 
 
+@pytest.mark.parametrize("split", [False, True])
 @pytest.mark.parametrize("prec,tol", [(coffee.TF32X3, 1e-5), (coffee.BF16X3, 1e-5)])
-def test_small_mixed_batch(prec, tol):
+def test_small_mixed_batch(prec, tol, split):
+    """Every group equal bit for bit to its single-group launch and within the bound of the oracle,
+    with FP64 coordinates or with their (hi, lo) float pairs."""
     tri = meshgen.tri_mesh(40, perturb=0.2, seed=4)
     tet = meshgen.tet_mesh(8, perturb=0.15, seed=5)
-    dev, groups = make_batch(tri, tet)
+    dev, groups = make_batch(tri, tet, split=split)
     plan = coffee.BatchPlan(groups, precision=prec, validate=True)
     outs = plan.launch()
     coffee.check_errors()

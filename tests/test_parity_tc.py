@@ -198,3 +198,61 @@ def test_staged_rows_ragged_tails(k, ncells, prec):
     assert torch.equal(outs[0], outs[1])
     ref = oracle_ref(HELMHOLTZ, k, TET, mesh, None, None)
     assert rel_err_per_cell(outs[1].cpu().numpy(), ref) < TOL[prec]
+
+
+def test_split_coords_are_hi_lo_float_pairs():
+    """coffee_split_coords: hi is the float rounding of x and lo the float rounding of x - hi, so
+    hi + lo holds x to about 2^-48 of |x|."""
+    mesh = meshgen.tet_mesh(5, perturb=0.15, seed=80)
+    x, _, _, _ = to_device(mesh, None, None, DEV)
+    s = coffee.split_coords(x).double().cpu().numpy()
+    assert s.shape == mesh.coords.shape + (2,)
+    np.testing.assert_array_equal(s[..., 0], mesh.coords.astype(np.float32).astype(np.float64))
+    lo = (mesh.coords - s[..., 0]).astype(np.float32).astype(np.float64)
+    np.testing.assert_array_equal(s[..., 1], lo)
+    assert np.abs(s[..., 0] + s[..., 1] - mesh.coords).max() <= 2.0 ** -48 * np.abs(mesh.coords).max()
+
+
+SPLIT_CASES = [(f, c, k, p) for f in (MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC) for c in (TRI, TET)
+               for k in (1, 2, 4) for p in (coffee.TF32X3, coffee.BF16X3, coffee.BF16)]
+
+
+@pytest.mark.parametrize("form,cell,k,prec", SPLIT_CASES)
+def test_split_coordinates_match_oracle(form, cell, k, prec):
+    """The Jacobian's vertex differences taken in FP32 from the (hi, lo) float pairs of the
+    coordinates: same bounds against the oracle as the FP64 differences."""
+    if not coffee.supported(form, k, cell, prec):
+        pytest.skip("combination not built")
+    mesh = ragged_mesh(cell, seed=90 + k)
+    coef, c2d = coefficients(form, mesh, k, seed=9)
+    ref = oracle_ref(form, k, cell, mesh, coef, c2d)
+    x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    xs = coffee.split_coords(x)
+    out = coffee.assemble(form, k, cell, x, c2v, cf, cd, precision=prec, validate=True, coords_split=xs)
+    coffee.check_errors()
+    err = rel_err_per_cell(out.cpu().numpy(), ref)
+    print("split coords %s %s P%d %s: %.3e" % (coffee.FORM_NAMES[form], "tri" if cell == TRI else "tet", k,
+                                               coffee.PRECISION_NAMES[prec], err))
+    assert err < TOL[prec]
+
+
+def test_split_coordinates_sliver_cells_and_full_size():
+    """Badly conditioned cells fall back to FP64 from the FP64 coordinates with the split given too;
+    the 1,572,864-tet Helmholtz P1 and P2 meshes with split coordinates, sampled against the oracle."""
+    rng = np.random.default_rng(5)
+    X = np.concatenate([meshgen.sliver_tet(rng, flat) for flat in (1e-1, 1e-2, 1e-3, 1e-4)])
+    c2v = np.arange(16, dtype=np.int32).reshape(4, 4)
+    sl = meshgen.Mesh(TET, X, c2v, None, (1, 1, 1))
+    ref = oracle_ref(HELMHOLTZ, 2, TET, sl, None, None)
+    x, cv, _, _ = to_device(sl, None, None, DEV)
+    out = coffee.assemble(HELMHOLTZ, 2, TET, x, cv, precision=coffee.TF32X3, coords_split=coffee.split_coords(x))
+    assert rel_err_per_cell(out.cpu().numpy(), ref) < 1e-5
+    mesh = meshgen.tet_mesh(64, perturb=0.15, seed=2)
+    x, c2v, _, _ = to_device(mesh, None, None, DEV)
+    xs = coffee.split_coords(x)
+    sel = np.concatenate([np.random.default_rng(11).choice(mesh.ncells, size=1000, replace=False),
+                          [0, mesh.ncells - 1]])
+    for k in (1, 2):
+        out = coffee.assemble(HELMHOLTZ, k, TET, x, c2v, precision=coffee.TF32X3, coords_split=xs)
+        ref = oracle_ref(HELMHOLTZ, k, TET, mesh, None, None, sel=sel)
+        assert rel_err_per_cell(out[torch.from_numpy(sel).to(DEV)].cpu().numpy(), ref) < 1e-5
