@@ -84,8 +84,16 @@ def _kuhn2pow20(mg, nx):
     return mg.tet_mesh(64, 64, 43, perturb=0.15, seed=3, ncells=2 ** 20)
 
 
+def _kuhn32(mg, nx):
+    return mg.tet_mesh(nx or 32, perturb=0.15, seed=3)
+
+
 def _prism48(mg, nx):
     return mg.prism_mesh(nx or 48, nx or 48, perturb=0.15, seed=6)
+
+
+def _prism24(mg, nx):
+    return mg.prism_mesh(nx or 24, nx or 24, perturb=0.15, seed=6)
 
 
 def _tri64(mg, nx):
@@ -107,6 +115,10 @@ WORKLOADS["advdiff-p2-tet"] = Workload("advdiff-p2-tet", ADVDIFF, 2, TETRAHEDRON
 WORKLOADS["burgers-p2-tet"] = Workload("burgers-p2-tet", BURGERS_JAC, 2, TETRAHEDRON,
                                        "Kuhn 64x64x43 truncated to 2^20 tets, perturbed 0.15h (seed 3), "
                                        "vector P2 u~N(0,1), nu=0.01", _kuhn2pow20)
+for _k in (3, 4):
+    WORKLOADS["burgers-p%d-tet" % _k] = Workload(
+        "burgers-p%d-tet" % _k, BURGERS_JAC, _k, TETRAHEDRON,
+        "32^3x6 = 196,608 Kuhn tets perturbed 0.15h (seed 3), vector P%d u~N(0,1), nu=0.01" % _k, _kuhn32)
 WORKLOADS["burgers-residual-p2-tet"] = Workload("burgers-residual-p2-tet", BURGERS_RESIDUAL, 2, TETRAHEDRON,
                                                 "Kuhn 64x64x43 truncated to 2^20 tets, perturbed 0.15h (seed 3), "
                                                 "vector P2 u~N(0,1), nu=0.01; element vectors", _kuhn2pow20)
@@ -116,6 +128,9 @@ WORKLOADS["helmholtz-p2-prism"] = Workload("helmholtz-p2-prism", HELMHOLTZ, 2, P
 WORKLOADS["helmholtz-p3-prism"] = Workload("helmholtz-p3-prism", HELMHOLTZ, 3, PRISM,
                                            "unit cube, 48x48 two-triangle columns x 48 layers = 221,184 "
                                            "twisted prisms perturbed 0.15h (seed 6)", _prism48)
+WORKLOADS["helmholtz-p4-prism"] = Workload("helmholtz-p4-prism", HELMHOLTZ, 4, PRISM,
+                                           "unit cube, 24x24 two-triangle columns x 24 layers = 27,648 "
+                                           "twisted prisms perturbed 0.15h (seed 6)", _prism24)
 WORKLOADS["advdiff-p2-prism"] = Workload("advdiff-p2-prism", ADVDIFF, 2, PRISM,
                                          "unit cube, 48x48 two-triangle columns x 48 layers = 221,184 "
                                          "twisted prisms perturbed 0.15h (seed 6), eps~U[0.5,1.5], "

@@ -434,7 +434,7 @@ struct PGeom {
 };
 
 bool pgeom(int form, int degree, int prec, PGeom& g) {
-  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF) || degree < 1 || degree > 3) return false;
+  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF) || degree < 1 || degree > 4) return false;
   if (prec == PREC_FP64 || prec < 0 || prec > PREC_BF16X3) return false;
   const bool tf32 = prec == PREC_TF32 || prec == PREC_TF32X3;
   g.n = prism_nnodes(degree);

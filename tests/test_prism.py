@@ -55,8 +55,6 @@ def test_prism_global_assembly_fp64(k):
 def test_prism_errors():
     mesh = meshgen.prism_mesh(3, 2, seed=1)
     x, c2v = to_dev(mesh)
-    with pytest.raises(coffee.CoffeeError):  # tensor-core prisms stop at P3
-        coffee.assemble(HELMHOLTZ, 4, PRISM, x, c2v, precision=coffee.TF32X3)
     with pytest.raises(coffee.CoffeeError):  # prisms cover MASS, HELMHOLTZ and ADVDIFF
         coffee.assemble(coffee.BURGERS_JAC, 1, PRISM, x, c2v, torch.zeros(64 * 3, dtype=torch.float64, device=DEV),
                         c2v, precision=coffee.FP64)
@@ -92,11 +90,11 @@ def prism_tol(prec, form, k):
 
 
 @pytest.mark.parametrize("form", [MASS, HELMHOLTZ])
-@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
 @pytest.mark.parametrize("prec", [coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16])
 def test_prism_tensor_cores_match_oracle(form, k, prec):
     """K-chunked streamed contraction on the tensor cores (972 cells: 7 tiles + a ragged one;
-    P3's 13 output slices run in groups of at most three)."""
+    P3's 13 and P4's 44 output slices run in groups of at most three)."""
     mesh = meshgen.prism_mesh(9, 6, perturb=0.15, seed=30 + k)
     ref = oracle.prism_assemble(form, k, mesh.coords, mesh.cell2vert)
     x, c2v = to_dev(mesh)
@@ -142,7 +140,7 @@ def test_prism_advdiff_fp64_matches_oracle(k, n, nz):
     assert err < 1e-12
 
 
-@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
 @pytest.mark.parametrize("prec", [coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16])
 def test_prism_advdiff_tensor_cores_match_oracle(k, prec):
     """K = 9 Q factors per cell (six diffusion pairs, three advection factors): 972 cells."""
