@@ -68,7 +68,7 @@ typedef struct CUstream_st* coffee_stream_t;
  * of a fixed rule: n = k+2 Gauss-Legendre points per direction on [0,1], the triangle factor
  * collapsed by (s,t) -> (s, t(1-s)) with weight w_s w_t (1-s). Prisms support MASS, HELMHOLTZ
  * and ADVDIFF (eps and b given per vertex through cell2dof [ncells][6], evaluated at each point
- * with the degree-1 prism functions): FP64 for P1-P4 and the tensor-core precisions for P1-P3
+ * with the degree-1 prism functions): FP64 and the tensor-core precisions for P1-P4
  * (the contraction over all quadrature points is streamed through shared memory in K-chunks,
  * at most three 128-output slices at a time),
  * both through coffee_assemble_ex and coffee_assemble_csr. */

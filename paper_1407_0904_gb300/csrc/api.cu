@@ -160,7 +160,7 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
   const bool validate = (a->flags & COFFEE_FLAG_VALIDATE) != 0;
   if (a->cell == CELL_PRISM && a->precision != PREC_FP64) {
     if (!prism_tc_supported(a->form, a->degree, a->precision))
-      return fail(COFFEE_ERR_UNSUPPORTED, "tensor-core prisms: MASS, HELMHOLTZ and ADVDIFF, P1-P3");
+      return fail(COFFEE_ERR_UNSUPPORTED, "tensor-core prisms: MASS, HELMHOLTZ and ADVDIFF, P1-P4");
     TcTable meta{};
     if ((rc = tc_table(*c, a->form, a->degree, a->cell, a->precision, &meta)) != COFFEE_OK) return rc;
     TcParams p{};

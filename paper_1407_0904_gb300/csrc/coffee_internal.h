@@ -90,7 +90,7 @@ struct PrismParams {
   int64_t nnz;
 };
 int launch_prism(int form, const PrismParams& p, int num_sms, void* stream);
-// tensor-core prisms (k_prism_tc.cu): K-chunked streamed contraction, MASS/HELMHOLTZ/ADVDIFF P1-P3
+// tensor-core prisms (k_prism_tc.cu): K-chunked streamed contraction, MASS/HELMHOLTZ/ADVDIFF P1-P4
 struct TcParams;
 struct TcTable;
 int prism_tc_supported(int form, int degree, int precision);

@@ -77,7 +77,7 @@ int main(void) {
 
   /* support queries */
   CHECK(coffee_supported(COFFEE_HELMHOLTZ, 3, COFFEE_TETRAHEDRON, COFFEE_TF32X3) == 1);
-  CHECK(coffee_supported(COFFEE_HELMHOLTZ, 4, COFFEE_PRISM, COFFEE_TF32X3) == 0);
+  CHECK(coffee_supported(COFFEE_HELMHOLTZ, 4, COFFEE_PRISM, COFFEE_TF32X3) == 1);
   CHECK(coffee_csr_supported(COFFEE_BURGERS_RESIDUAL, 2, COFFEE_TETRAHEDRON, COFFEE_FP64) == 0);
 
   /* argument errors are reported on the host, before any CUDA call */

@@ -161,7 +161,7 @@ def test_burgers_reference_tensor_on_reference_cell_matches_oracle(cell, k):
 
 
 def test_support_queries_cover_prisms():
-    """Host-only queries: prisms take MASS, HELMHOLTZ and ADVDIFF (FP64 P1-P4, tensor cores P1-P3),
+    """Host-only queries: prisms take MASS, HELMHOLTZ and ADVDIFF (FP64 and tensor cores P1-P4),
     locally and fused into CSR; the Burgers forms are simplex-only."""
     P = coffee.PRISM
     for form in (coffee.MASS, coffee.HELMHOLTZ, coffee.ADVDIFF):
@@ -169,8 +169,8 @@ def test_support_queries_cover_prisms():
             assert coffee.supported(form, k, P, coffee.FP64)
             assert coffee.csr_supported(form, k, P, coffee.FP64)
             for prec in (coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16):
-                assert bool(coffee.supported(form, k, P, prec)) == (k <= 3)
-                assert bool(coffee.csr_supported(form, k, P, prec)) == (k <= 3)
+                assert coffee.supported(form, k, P, prec)
+                assert coffee.csr_supported(form, k, P, prec)
     for form in (coffee.BURGERS_JAC, coffee.BURGERS_RESIDUAL):
         for prec in (coffee.FP64, coffee.TF32X3):
             assert not coffee.supported(form, 1, P, prec)
@@ -240,8 +240,10 @@ def test_host_buffer_entry_point_rejects_bad_arguments_before_any_cuda_call():
     a.form, a.nverts = coffee.ADVDIFF, 20
     assert lib.coffee_assemble_host(ctypes.byref(a), 4, None) == -1
     assert b"coef" in lib.coffee_last_error()
-    a.form, a.degree = coffee.HELMHOLTZ, 4
-    a.cell = coffee.PRISM  # no tensor-core prism kernel at P4
+    a.form, a.degree, a.cell = coffee.BURGERS_JAC, 4, coffee.TETRAHEDRON
+    a.coef = a.cell2dof = 16
+    a.ncoefnodes = 20
+    a.precision = coffee.BF16X3  # the Burgers Jacobian on tet P4 has no BF16X3 kernel
     assert lib.coffee_assemble_host(ctypes.byref(a), 4, None) == -2
 
 

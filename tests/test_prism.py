@@ -171,7 +171,7 @@ def test_prism_advdiff_global_assembly():
 
 
 @pytest.mark.parametrize("form", [MASS, HELMHOLTZ, ADVDIFF])
-@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
 def test_prism_global_assembly_tensor_cores(form, k):
     """The tensor-core prism kernel adding its entries straight into the CSR values (972 cells,
     a ragged last tile), against the oracle's element matrices scattered on the host."""
