@@ -168,6 +168,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-kernel comparison")
+    ap.add_argument("--no-coef-f32", action="store_true",
+                    help="tensor-core kernels convert the FP64 coefficients per cell instead of reading the "
+                         "float copy that each step rounds once per node")
     ap.add_argument("--nx", type=int, default=None, help="smaller mesh (cells per axis) for profiling")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -378,8 +381,16 @@ def run_ours(args):
     out = torch.empty(oshape, dtype=odt, device=dev)
     stream = torch.cuda.current_stream()
 
+    # forms with coefficients: each step rounds them to floats once per node (coffee_round_coef,
+    # inside the timed step), and the tensor-core kernel reads that copy
+    cf32 = (torch.empty(coef.shape, dtype=torch.float32, device=dev)
+            if coef is not None and prec != coffee.FP64 and not args.no_coef_f32 else None)
+
     def step(precision, o):
-        coffee.assemble(form, degree, cell, coords, c2v, coef, c2d, precision=precision, out=o)
+        if cf32 is not None and precision != coffee.FP64:
+            coffee.round_coef(coef, out=cf32)
+        coffee.assemble(form, degree, cell, coords, c2v, coef, c2d, precision=precision, out=o,
+                        coef_f32=cf32 if precision != coffee.FP64 else None)
 
     # one checked launch before timing (parity against the oracle is the test suite's job)
     step(prec, out)
@@ -455,6 +466,8 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "alg_bytes_per_cell": per_cell, "kernel_ms": launch_ms}
+    if cf32 is not None:
+        roof["kernel_ms_spans"] = "coffee_round_coef and the assembly kernel (one step)"
     if prec == coffee.FP64:
         roof["note"] = ("FP64 kernel: bound by the FP64 ALU (%.2f TFLOP/s measured by coffee_peak_fp64); "
                         "HBM fraction for context" % device_peaks(coffee)["fp64_tflops"])
@@ -543,10 +556,14 @@ def run_ours(args):
                            "ncells": ncells, "degree": degree, "ndof": ndof,
                            "precision": args.precision, "out_dtype": str(odt).replace("torch.", ""),
                            "l2": l2_note(ncells * out_entries(wl, ndof) * out_bytes),
-                           "parallelism": "replicas" if world > 1 else "single"},
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "coefficients": (None if coef is None else
+                                            "rounded to float once per node each step (coffee_round_coef, "
+                                            "timed with the assembly)" if cf32 is not None else
+                                            "FP64, converted per cell in the kernel")},
                 "roofline": roof, "fp64_kernel": fp64,
                 "tc_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
-                "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": args.steps,
+                "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": args.steps * (2 if cf32 is not None else 1),
                 "clocks": clocks, "kernel_sha": sha, "device_peaks": device_peaks(coffee),
                 "graph_replay": graph}
         print(json.dumps(line), flush=True)

@@ -193,12 +193,25 @@ typedef struct {
    * ((hi1 - hi0) + (lo1 - lo0)) instead of FP64; coords must still be given (badly conditioned
    * cells are recomputed from it in FP64). Ignored by the FP64 kernels and by prisms. */
   const float* coords_split;
+  /* optional, device, the layout and length of coef in float: every coefficient rounded to
+   * nearest ((float)coef[i]), as coffee_round_coef writes it, or NULL. The tensor-core kernels
+   * take the coefficients in FP32 either way; given the float copy they read it (half the bytes)
+   * instead of converting each coefficient once per cell that uses it, which on this GPU runs on
+   * the FP64 pipe. Results are bit for bit those without it. coef must still be given (the FP64
+   * kernels read it; every pointer check applies). */
+  const float* coef_f32;
 } coffee_assemble_args;
 
 /* Every coordinate x[i], i < n (n = nverts * d), as the float pair (hi, lo) = ((float)x,
  * (float)(x - hi)) in split[2i], split[2i+1]: the coords_split input of coffee_assemble_args.
  * Device pointers, asynchronous on stream; n == 0 returns COFFEE_OK. */
 int coffee_split_coords(const double* coords, int64_t n, float* split, coffee_stream_t stream);
+
+/* Every coefficient coef[i], i < n (n = ncoefnodes * components), rounded to the nearest float:
+ * out[i] = (float)coef[i], the coef_f32 input of coffee_assemble_args. One conversion per
+ * coefficient node instead of one per cell that reads it (a vertex of a tetrahedral mesh is
+ * shared by about 24 cells). Device pointers, asynchronous on stream; n == 0 returns COFFEE_OK. */
+int coffee_round_coef(const double* coef, int64_t n, float* out, coffee_stream_t stream);
 
 /* 1 if coffee_assemble_ex has a kernel for (form, degree, cell, precision), else 0.
  * FP64 covers every form, degree 1..4, both cells; the tensor-core precisions cover
@@ -217,8 +230,9 @@ int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream);
  * pointers with the layouts of coffee_assemble; out is [ncells][ndof][ndof] (BURGERS_RESIDUAL:
  * [ncells][ndof]), double for FP64 and float otherwise. a->nverts, and a->ncoefnodes for the
  * forms with a coefficient, must be > 0: they size the copies.
- * a->coords_split is ignored: for the tensor-core precisions on triangles and tetrahedra the
- * coordinates are split into (hi, lo) float pairs on the device after their copy.
+ * a->coords_split and a->coef_f32 are ignored: for the tensor-core precisions on triangles and
+ * tetrahedra the coordinates are split into (hi, lo) float pairs on the device after their copy,
+ * and for every tensor-core precision the coefficients are rounded to floats there.
  * The coordinates and coefficients are copied to the device once; the cells are assembled in
  * `chunks` launches (chunk boundaries on 128-cell tiles), each chunk's inputs copied in and its
  * results copied back on a second, library-owned stream while the next chunk computes.

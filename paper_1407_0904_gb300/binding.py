@@ -50,6 +50,7 @@ class AssembleArgs(ctypes.Structure):
         ("out", ctypes.c_void_p), ("ncells", ctypes.c_int64),
         ("flags", ctypes.c_uint),
         ("coords_split", ctypes.c_void_p),
+        ("coef_f32", ctypes.c_void_p),
     ]
 
 
@@ -70,6 +71,7 @@ def lib():
         L.coffee_check_errors.argtypes = [P]
         L.coffee_supported.argtypes = [I, I, I, I]
         L.coffee_split_coords.argtypes = [P, L64, P, P]
+        L.coffee_round_coef.argtypes = [P, L64, P, P]
         L.coffee_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
@@ -240,8 +242,25 @@ def split_coords(coords, out=None, stream=None):
     return out
 
 
+def round_coef(coef, out=None, stream=None):
+    """coffee_round_coef: every coefficient rounded to the nearest float, a float32 tensor of coef's
+    shape on the device: the coef_f32 input of assemble, read by the tensor-core kernels instead
+    of converting each coefficient once per cell that uses it (same results bit for bit)."""
+    coef = _dev(coef, torch.float64, "coef")
+    if out is None:
+        out = torch.empty(tuple(coef.shape), dtype=torch.float32, device=coef.device)
+    else:
+        _dev(out, torch.float32, "out")
+        if out.numel() != coef.numel():
+            raise ValueError("out must hold one float per coefficient")
+    _check(lib().coffee_round_coef(_ptr(coef), ctypes.c_int64(coef.numel()), _ptr(out),
+                                   _stream_handle(stream)))
+    return out
+
+
 def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
-              out=None, nu=0.01, validate=False, ncoefnodes=None, tune=0, alloc_out=True, coords_split=None):
+              out=None, nu=0.01, validate=False, ncoefnodes=None, tune=0, alloc_out=True, coords_split=None,
+              coef_f32=None):
     coords = _dev(coords, torch.float64, "coords")
     cell2vert = _dev(cell2vert, torch.int32, "cell2vert")
     coef = _dev(coef, torch.float64, "coef")
@@ -274,20 +293,26 @@ def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, p
         if coords_split.numel() != 2 * coords.numel():
             raise ValueError("coords_split must hold 2 floats per coordinate (split_coords)")
     a.coords_split = _ptr(coords_split)
+    if coef_f32 is not None:
+        _dev(coef_f32, torch.float32, "coef_f32")
+        if coef is None or coef_f32.numel() != coef.numel():
+            raise ValueError("coef_f32 must hold one float per coefficient of coef (round_coef)")
+    a.coef_f32 = _ptr(coef_f32)
     return a, out
 
 
 def assemble(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
-             out=None, nu=0.01, validate=False, stream=None, tune=None, coords_split=None):
+             out=None, nu=0.01, validate=False, stream=None, tune=None, coords_split=None, coef_f32=None):
     """Element matrices [ncells, ndof, ndof] (float64 for FP64, float32 otherwise) on the device.
 
     tune: FLAG_OUTPUT_LANES / FLAG_TWO_STAGES knobs; None uses the autotuner's choice for
     this (form, degree, cell, precision) when one is cached, else the library default.
-    coords_split: the (hi, lo) float pairs of coords (split_coords), optional."""
+    coords_split: the (hi, lo) float pairs of coords (split_coords), optional.
+    coef_f32: coef rounded to floats (round_coef), optional."""
     if tune is None:
         tune = _tuned_flags(form, degree, cell, precision)
     a, out = make_args(form, degree, cell, coords, cell2vert, coef, cell2dof, precision, out, nu,
-                       validate, tune=tune, coords_split=coords_split)
+                       validate, tune=tune, coords_split=coords_split, coef_f32=coef_f32)
     _check(lib().coffee_assemble_ex(ctypes.byref(a), _stream_handle(stream)))
     return out
 
@@ -480,7 +505,8 @@ class BatchPlan:
     """Several (form, degree, cell) groups assembled by one persistent launch.
 
     groups: list of dicts with keys form, degree, cell, coords, cell2vert and optionally
-    coef, cell2dof, out, coords_split (split_coords of coords). All groups use `precision`
+    coef, cell2dof, out, coords_split (split_coords of coords), coef_f32 (round_coef of coef).
+    All groups use `precision`
     (a tensor-core precision).
     launch() only enqueues one kernel on the current stream (CUDA-graph capturable).
 
@@ -505,11 +531,12 @@ class BatchPlan:
         for i, g in enumerate(groups):
             a, out = make_args(g["form"], g["degree"], g["cell"], g["coords"], g["cell2vert"],
                                g.get("coef"), g.get("cell2dof"), precision, g.get("out"),
-                               g.get("nu", 0.01), validate, coords_split=g.get("coords_split"))
+                               g.get("nu", 0.01), validate, coords_split=g.get("coords_split"),
+                               coef_f32=g.get("coef_f32"))
             arr[i] = a
             self.outputs.append(out)
             self._keep.append((g["coords"], g["cell2vert"], g.get("coef"), g.get("cell2dof"), out,
-                               g.get("coords_split")))
+                               g.get("coords_split"), g.get("coef_f32")))
         if item_overhead is None or item_overhead < 0:
             try:
                 from . import tune as _tune

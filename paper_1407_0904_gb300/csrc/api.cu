@@ -24,6 +24,23 @@ __global__ void k_split_coords(const double* __restrict__ x, int64_t n, float2* 
   }
 }
 
+// every coefficient rounded to the nearest float: the coef_f32 input
+__global__ void k_round_coef(const double* __restrict__ x, int64_t n, float* __restrict__ out) {
+  const int64_t n2 = n / 2;  // pairs, when both pointers allow 16- and 8-byte accesses
+  const bool vec = ((reinterpret_cast<uintptr_t>(x) & 15u) == 0) && ((reinterpret_cast<uintptr_t>(out) & 7u) == 0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (vec) {
+    for (int64_t i = i0; i < n2; i += stride) {
+      const double2 v = __ldcs(reinterpret_cast<const double2*>(x) + i);
+      reinterpret_cast<float2*>(out)[i] = make_float2((float)v.x, (float)v.y);
+    }
+    if (i0 == 0 && (n & 1)) out[n - 1] = (float)x[n - 1];
+  } else {
+    for (int64_t i = i0; i < n; i += stride) out[i] = (float)x[i];
+  }
+}
+
 static thread_local std::string g_last_error;
 
 int fail(int status, const std::string& msg) {
@@ -167,6 +184,7 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
     p.coords = a->coords;
     p.c2v = a->cell2vert;
     p.coef = a->coef;
+    p.cf = a->coef_f32;
     p.c2d = a->cell2dof;
     p.ncoefnodes = a->ncoefnodes;
     p.image = meta.image;
@@ -249,6 +267,7 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
   p.c2d = a->cell2dof;
   p.image = meta.image;
   p.xs = a->coords_split;
+  p.cf = a->coef_f32;
   p.out = static_cast<float*>(a->out);
   p.err = c->err;
   p.ncells = a->ncells;
@@ -337,6 +356,23 @@ int coffee_supported(int form, int degree, int cell, int precision) {
            (precision == PREC_FP64 || prism_tc_supported(form, degree, precision));
   if (precision == PREC_FP64) return 1;
   return tc_supported(form, degree, cell, precision);
+}
+
+int coffee_round_coef(const double* coef, int64_t n, float* out, coffee_stream_t stream) {
+  if (n < 0) return fail(COFFEE_ERR_INVALID_ARG, "round_coef: n < 0");
+  if (n == 0) return COFFEE_OK;
+  if (!coef || !out) return fail(COFFEE_ERR_INVALID_ARG, "round_coef: coef and out must be non-NULL");
+  DeviceCache* c = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    int rc = device_cache(&c);
+    if (rc != COFFEE_OK) return rc;
+  }
+  const int64_t blocks = std::min<int64_t>((n / 2 + 255) / 256 + 1, (int64_t)c->num_sms * 8);
+  k_round_coef<<<(unsigned)blocks, 256, 0, stream>>>(coef, n, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "launch(round_coef)");
+  return COFFEE_OK;
 }
 
 int coffee_split_coords(const double* coords, int64_t n, float* split, coffee_stream_t stream) {
@@ -671,6 +707,7 @@ int batch_plan_impl(const coffee_assemble_args* groups, int ngroups, int grid, d
     g.p.tparts = meta.tparts;
     g.p.precision = prec;
     g.p.xs = a->coords_split;
+    g.p.cf = a->coef_f32;
     g.p.validate = (a->flags & COFFEE_FLAG_VALIDATE) ? 1 : 0;
     g.p.nu = a->nu;
     g.item0 = items;

@@ -143,6 +143,7 @@ struct TcParams {
   const float* xs;       // optional: every coordinate as (hi, lo) floats, [nverts][d][2]
   const int32_t* c2v;
   const double* coef;
+  const float* cf;       // optional: coef rounded to float, same layout
   const int32_t* c2d;
   const uint8_t* image;  // TcTable image
   float* out;

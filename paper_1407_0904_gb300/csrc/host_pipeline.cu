@@ -98,9 +98,13 @@ int coffee_assemble_host(const coffee_assemble_args* a, int chunks, coffee_strea
   // tensor-core kernels on simplices take the vertex differences from (hi, lo) float pairs
   const bool split = a->precision != PREC_FP64 && a->cell != CELL_PRISM;
   const size_t b_split = split ? (size_t)a->nverts * d * 2 * sizeof(float) : 0;
+  // and every tensor-core kernel takes the coefficients as floats, rounded once per node
+  const bool round = a->precision != PREC_FP64 && has_coef;
+  const size_t b_cf = round ? (size_t)a->ncoefnodes * coef_row * sizeof(float) : 0;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t o_coef = al(b_coords), o_c2v = o_coef + al(b_coef), o_c2d = o_c2v + al(b_c2v),
-               o_out = o_c2d + al(b_c2d), o_split = o_out + al(b_out), total = o_split + al(b_split);
+               o_out = o_c2d + al(b_c2d), o_split = o_out + al(b_out), o_cf = o_split + al(b_split),
+               total = o_cf + al(b_cf);
 
   HostRes* r = nullptr;
   int rc = host_res(&r);
@@ -119,12 +123,14 @@ int coffee_assemble_host(const coffee_assemble_args* a, int chunks, coffee_strea
   int32_t* d_c2d = has_coef ? reinterpret_cast<int32_t*>(ws + o_c2d) : nullptr;
   uint8_t* d_out = ws + o_out;
   float* d_split = split ? reinterpret_cast<float*>(ws + o_split) : nullptr;
+  float* d_cf = round ? reinterpret_cast<float*>(ws + o_cf) : nullptr;
   uint8_t* h_out = static_cast<uint8_t*>(a->out);
 
   e = cudaMemcpyAsync(d_coords, a->coords, b_coords, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && has_coef) e = cudaMemcpyAsync(d_coef, a->coef, b_coef, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) rc = cuda_err(e, "cudaMemcpyAsync(coordinates, coefficients)");
   if (rc == COFFEE_OK && split) rc = coffee_split_coords(d_coords, a->nverts * d, d_split, s);
+  if (rc == COFFEE_OK && round) rc = coffee_round_coef(d_coef, a->ncoefnodes * (int64_t)coef_row, d_cf, s);
 
   // chunks of whole 128-cell tiles, so every chunk's output starts 512-byte aligned
   int64_t per = (nc + chunks - 1) / chunks;
@@ -144,6 +150,7 @@ int coffee_assemble_host(const coffee_assemble_args* a, int chunks, coffee_strea
     b.coords = d_coords;
     b.coords_split = d_split;
     b.coef = d_coef;
+    b.coef_f32 = d_cf;
     b.cell2vert = d_c2v + lo * nv;
     b.cell2dof = has_coef ? d_c2d + lo * w : nullptr;
     b.out = d_out + (size_t)lo * row_out;

@@ -197,16 +197,16 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_assemble_prism_tc(const TcParam
           for (int r = 0; r < 3; ++r) Xd[v][r] = __ldg(p.coords + (int64_t)vid * 3 + r);
         }
         if constexpr (KQ == 9) {
+          int cid[6];
 #pragma unroll
           for (int v = 0; v < 6; ++v) {
-            int cid = __ldg(p.c2d + e * 6 + v);
-            if (p.validate && (cid < 0 || cid >= p.ncoefnodes)) {
+            cid[v] = __ldg(p.c2d + e * 6 + v);
+            if (p.validate && (cid[v] < 0 || cid[v] >= p.ncoefnodes)) {
               bad = true;
-              cid = 0;
+              cid[v] = 0;
             }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) CF[v][r] = (float)__ldg(p.coef + (int64_t)cid * 4 + r);
           }
+          coef_rows<6, 4>(p, cid, CF);
         }
         if (bad) {
           if (half == 0) atomicOr(p.err, ERR_INDEX);

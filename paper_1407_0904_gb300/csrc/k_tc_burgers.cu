@@ -137,10 +137,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
               for (int r = 0; r < D; ++r) s = fmaf(adj[a][r], adj[b][r], s);
               H[q++] = (float)p.nu * s * inv;
             }
-#pragma unroll
-          for (int r = 0; r < NS; ++r)
-#pragma unroll
-            for (int c = 0; c < D; ++c) u[r][c] = (float)__ldg(p.coef + (int64_t)did[r] * D + c);
+          coef_rows<NS, D>(p, did, u);
         }
       }
       // blocks and chunks as compile-time indices, so u[.][ci] and P[.][cj] stay in registers

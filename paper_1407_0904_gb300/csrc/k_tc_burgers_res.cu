@@ -129,10 +129,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
               for (int r = 0; r < D; ++r) acc = fmaf(adj[a][r], adj[b][r], acc);
               H[q++] = (float)p.nu * acc * inv;
             }
-#pragma unroll
-          for (int r = 0; r < NS; ++r)
-#pragma unroll
-            for (int c = 0; c < D; ++c) u[r][c] = (float)__ldg(p.coef + (int64_t)did[r] * D + c);
+          coef_rows<NS, D>(p, did, u);
         }
       }
       // factors of C: Q[r][a] (T2 columns), nu H (T3 columns); the T1 columns are not used
@@ -205,12 +202,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
       const bool live = cell < p.ncells;
       // the cell's u is gathered before waiting for its accumulator, so the loads overlap the wait
       float u[NS][D];
+      {
+        int id[NS];
+        bool okid[NS];
 #pragma unroll
-      for (int r = 0; r < NS; ++r) {
-        const int id = live ? __ldg(p.c2d + cell * NS + r) : 0;
-        const bool okid = live && id >= 0 && id < p.ncoefnodes;
-#pragma unroll
-        for (int c = 0; c < D; ++c) u[r][c] = okid ? (float)__ldg(p.coef + (int64_t)id * D + c) : 0.f;
+        for (int r = 0; r < NS; ++r) {
+          id[r] = live ? __ldg(p.c2d + cell * NS + r) : 0;
+          okid[r] = live && id[r] >= 0 && id[r] < p.ncoefnodes;
+        }
+        coef_rows<NS, D>(p, id, u, okid);
       }
       if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) break;
       tc_fence_after();

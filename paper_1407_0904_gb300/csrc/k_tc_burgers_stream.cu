@@ -132,15 +132,27 @@ __global__ void __launch_bounds__(S_THREADS, 1) k_burgers_stream_tc(const TcPara
           if (p.validate && (vid[v] < 0 || vid[v] >= p.nverts)) bad = true;
         }
         // u of the cell: this thread gathers nodes r = half, half + 2, ..
-        for (int r = half; r < NS; r += 2) {
-          const int did = __ldg(p.c2d + e * NS + r);
-          if (p.validate && (did < 0 || did >= p.ncoefnodes)) {
-            bad = true;
-            continue;
-          }
+        constexpr int NH = (NS + 1) / 2;
+        int did[NH];
+        bool okr[NH];
 #pragma unroll
-          for (int cc = 0; cc < D; ++cc) ucell[r * D + cc] = (float)__ldg(p.coef + (int64_t)did * D + cc);
+        for (int j = 0; j < NH; ++j) {
+          const int r = half + 2 * j;
+          did[j] = r < NS ? __ldg(p.c2d + e * NS + r) : 0;
+          okr[j] = r < NS;
+          if (okr[j] && p.validate && (did[j] < 0 || did[j] >= p.ncoefnodes)) {
+            bad = true;
+            okr[j] = false;
+          }
         }
+        float uh[NH][D];
+        coef_rows<NH, D>(p, did, uh, okr);
+#pragma unroll
+        for (int j = 0; j < NH; ++j)
+          if (okr[j]) {
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) ucell[(half + 2 * j) * D + cc] = uh[j][cc];
+          }
         if (bad) {
           atomicOr(p.err, ERR_INDEX);
           live = false;

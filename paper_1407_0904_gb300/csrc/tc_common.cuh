@@ -339,6 +339,28 @@ __device__ __forceinline__ void geometry_f64(const double (&X)[D + 1][D], float 
   det = (float)dd;
 }
 
+// Rows of coefficients as the floats the kernels compute with, v[r][c] = coef[ids[r] * W + c]
+// (0 for rows with ok[r] false when ok is given): read from the caller's float copy when given,
+// else converted from the FP64 array (the same rounding). The copy is chosen once for all the
+// rows, so the loads of every row issue back to back; a test per value would hold each load
+// behind the previous one.
+template <int R, int W>
+__device__ __forceinline__ void coef_rows(const TcParams& p, const int (&ids)[R], float (&v)[R][W],
+                                          const bool* ok = nullptr) {
+  if (p.cf != nullptr) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < W; ++c) v[r][c] = (ok == nullptr || ok[r]) ? __ldg(p.cf + (int64_t)ids[r] * W + c) : 0.f;
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < W; ++c)
+        v[r][c] = (ok == nullptr || ok[r]) ? (float)__ldg(p.coef + (int64_t)ids[r] * W + c) : 0.f;
+  }
+}
+
 // Geometry of the cell with vertex ids vid: adj (K = adj/det), |det| and sign(det). The Jacobian
 // J[r][c] = x_{c+1}[r] - x_0[r] is taken in FP32 from the caller's (hi, lo) float pairs of the
 // coordinates when it passed them ((hi1 - hi0) + (lo1 - lo0): the hi difference is exact or
@@ -480,20 +502,17 @@ __device__ __forceinline__ void cell_factors_ids(const TcParams& p, const CellId
 #pragma unroll
     for (int q = 0; q < P; ++q) G[1 + q] = C[q];
   } else {
+    float eb[NV][D + 1];  // (eps, b) row of each vertex's node
+    coef_rows<NV, D + 1>(p, cid, eb);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double* cv = p.coef + (int64_t)cid[v] * (D + 1);  // (eps, b) row of the node
-      const float eps = (float)__ldg(cv);
-      float bv[D];
 #pragma unroll
-      for (int r = 0; r < D; ++r) bv[r] = (float)__ldg(cv + 1 + r);
-#pragma unroll
-      for (int q = 0; q < P; ++q) G[v * P + q] = eps * C[q];
+      for (int q = 0; q < P; ++q) G[v * P + q] = eb[v][0] * C[q];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         float s = 0.f;
 #pragma unroll
-        for (int r = 0; r < D; ++r) s = fmaf(adj[a][r], bv[r], s);
+        for (int r = 0; r < D; ++r) s = fmaf(adj[a][r], eb[v][1 + r], s);
         G[NV * P + v * D + a] = sg * s;
       }
     }

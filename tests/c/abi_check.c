@@ -23,7 +23,7 @@ typedef void (*entry_fn)(void);
 static const entry_fn entry_points[] = {
     (entry_fn)coffee_ndof, (entry_fn)coffee_tabulate, (entry_fn)coffee_reference_tensor,
     (entry_fn)coffee_supported, (entry_fn)coffee_assemble, (entry_fn)coffee_assemble_ex,
-    (entry_fn)coffee_split_coords,
+    (entry_fn)coffee_split_coords, (entry_fn)coffee_round_coef,
     (entry_fn)coffee_assemble_host, (entry_fn)coffee_host_pool_trim,
     (entry_fn)coffee_assemble_backward, (entry_fn)coffee_assemble_backward_noalloc,
     (entry_fn)coffee_batch_plan, (entry_fn)coffee_batch_plan_costs, (entry_fn)coffee_batch_launch,
@@ -91,6 +91,8 @@ int main(void) {
   CHECK(coffee_assemble_ex(&a, NULL) == COFFEE_ERR_INVALID_ARG); /* NULL pointers */
   CHECK(coffee_split_coords(NULL, 0, NULL, NULL) == COFFEE_OK);   /* nothing to split */
   CHECK(coffee_split_coords(NULL, -1, NULL, NULL) == COFFEE_ERR_INVALID_ARG);
+  CHECK(coffee_round_coef(NULL, 0, NULL, NULL) == COFFEE_OK);     /* nothing to round */
+  CHECK(coffee_round_coef(NULL, -1, NULL, NULL) == COFFEE_ERR_INVALID_ARG);
   a.ncells = 0;
   CHECK(coffee_assemble_ex(&a, NULL) == COFFEE_OK); /* empty input: no launch */
   CHECK(coffee_assemble_host(&a, 0, NULL) == COFFEE_ERR_INVALID_ARG);

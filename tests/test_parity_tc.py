@@ -236,6 +236,42 @@ def test_split_coordinates_match_oracle(form, cell, k, prec):
     assert err < TOL[prec]
 
 
+def test_round_coef_is_the_float_rounding():
+    """coffee_round_coef: every coefficient as (float)coef, also for odd lengths and a start that
+    is not 16-byte aligned (the scalar loop)."""
+    rng = np.random.default_rng(81)
+    c = torch.from_numpy(rng.standard_normal(100001) * 10.0 ** rng.integers(-30, 30, 100001)).to(DEV)
+    for v in (c, c[1:]):
+        r = coffee.round_coef(v)
+        assert torch.equal(r, v.float())
+
+
+COEF_CASES = ([(f, c, k, p) for f in (ADVDIFF, BURGERS_JAC, coffee.BURGERS_RESIDUAL) for c in (TRI, TET)
+               for k in (1, 2, 3, 4) for p in (coffee.TF32X3, coffee.BF16)]
+              + [(ADVDIFF, coffee.PRISM, k, coffee.TF32X3) for k in (1, 2, 4)])
+
+
+@pytest.mark.parametrize("form,cell,k,prec", COEF_CASES)
+def test_float_coefficients_give_the_same_bits(form, cell, k, prec):
+    """The coefficients read from their float copy (round_coef) instead of converted in the kernel:
+    every kernel that reads coefficients (advection-diffusion factors, the Burgers Jacobian in its
+    resident and streamed kernels, the residual, prisms) gives the same bits."""
+    if not coffee.supported(form, k, cell, prec):
+        pytest.skip("combination not built")
+    if cell == coffee.PRISM:
+        mesh = meshgen.prism_mesh(6, 4, perturb=0.15, seed=82)
+        coef, c2d, _ = meshgen.advdiff_coefficients(mesh, 84)
+    else:
+        mesh = ragged_mesh(cell, seed=83 + k)
+        coef, c2d = coefficients(BURGERS_JAC if form == coffee.BURGERS_RESIDUAL else form, mesh, k, seed=84)
+    x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    a = coffee.assemble(form, k, cell, x, c2v, cf, cd, precision=prec, validate=True)
+    b = coffee.assemble(form, k, cell, x, c2v, cf, cd, precision=prec, validate=True,
+                        coef_f32=coffee.round_coef(cf))
+    coffee.check_errors()
+    assert torch.equal(a, b)
+
+
 def test_split_coordinates_sliver_cells_and_full_size():
     """Badly conditioned cells fall back to FP64 from the FP64 coordinates with the split given too;
     the 1,572,864-tet Helmholtz P1 and P2 meshes with split coordinates, sampled against the oracle."""
