@@ -368,6 +368,9 @@ def run_ours(args):
     if not coffee.supported(form, degree, cell, prec):
         raise SystemExit("no kernel for %s in %s" % (wl.name, args.precision))
 
+    # the kernel family the library runs for this workload (the FP32 CUDA-core kernel for small
+    # element matrices, where it is faster than the tensor cores)
+    path = coffee.assemble_path(form, degree, cell, prec, coffee.binding._tuned_flags(form, degree, cell, prec))
     mesh, coef_np, c2d_np = wl.build(args.nx)
     ndof = coffee.ndof(form, degree, cell)
     coords = torch.from_numpy(mesh.coords).to(dev)
@@ -551,12 +554,15 @@ def run_ours(args):
         line = {"metric": metric_of(wl), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp64": "f64"}.get(args.precision, args.precision), "data": "synthetic",
+                "dtype": "f32" if path == 2 else {"fp64": "f64"}.get(args.precision, args.precision),
+                "data": "synthetic",
                 "config": {"workload": "%s, %s" % (wl.name, mesh_desc_of(wl, args.nx, mesh)),
                            "ncells": ncells, "degree": degree, "ndof": ndof,
                            "precision": args.precision, "out_dtype": str(odt).replace("torch.", ""),
                            "l2": l2_note(ncells * out_entries(wl, ndof) * out_bytes),
                            "parallelism": "replicas" if world > 1 else "single",
+                           "kernel": coffee.PATH_NAMES[path] + (" (the faster kernel for this element matrix; "
+                                                                 "%s requested)" % args.precision if path == 2 else ""),
                            "coefficients": (None if coef is None else
                                             "rounded to float once per node each step (coffee_round_coef, "
                                             "timed with the assembly)" if cf32 is not None else

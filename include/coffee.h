@@ -130,6 +130,16 @@ typedef enum {
  * memory and write each group with one bulk copy, instead of warp stores of 32 entries of one
  * cell (the default) */
 #define COFFEE_FLAG_STAGED_STORE 256u
+/* Element matrices of at most 100 entries (MASS, HELMHOLTZ, ADVDIFF on triangles P1-P3 and
+ * tetrahedra P1-P2) have a second kernel besides the tensor-core one: one CUDA-core thread per
+ * cell, A_e = sum_k G_e[k] T[k] in FP32 (T rounded once to FP32; within every tensor-core
+ * precision's bound). The library picks the faster one per (form, degree, cell) for local
+ * assembly (measured: the CUDA-core kernel for P1 on both cells and for triangles P2; global
+ * CSR assembly and batches always use the tensor cores); these flags force one:
+ * TENSOR_CORES the tcgen05 kernel, CUDA_CORES the FP32 kernel (ignored where it has no
+ * instance). Results of the two differ by rounding, within the precision's bound. */
+#define COFFEE_FLAG_TENSOR_CORES 512u
+#define COFFEE_FLAG_CUDA_CORES 1024u
 
 /* Number of rows of the element matrix (or length of the element vector): (k+1)(k+2)/2
  * (triangle), (k+1)(k+2)(k+3)/6 (tetrahedron) or (k+1)^2(k+2)/2 (prism), times d for
@@ -217,6 +227,12 @@ int coffee_round_coef(const double* coef, int64_t n, float* out, coffee_stream_t
  * FP64 covers every form, degree 1..4, both cells; the tensor-core precisions cover
  * the combinations whose operands fit in shared memory. Host-only. */
 int coffee_supported(int form, int degree, int cell, int precision);
+
+/* The kernel family coffee_assemble_ex runs for local assembly with these arguments and flags:
+ * 0 the FP64 kernel, 1 the tensor cores (tcgen05), 2 the FP32 CUDA-core kernel for small
+ * element matrices (COFFEE_FLAG_TENSOR_CORES / COFFEE_FLAG_CUDA_CORES); COFFEE_ERR_UNSUPPORTED
+ * where coffee_supported is 0. Host-only. */
+int coffee_assemble_path(int form, int degree, int cell, int precision, unsigned flags);
 
 /* Local assembly (section 2, Listings 1-2) with a chosen precision. FP64 runs the plain FP64 kernel; the
  * other precisions run the tcgen05 tensor-core contraction with geometry fused into

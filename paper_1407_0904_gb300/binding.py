@@ -23,6 +23,8 @@ FLAG_SUBTILE_32 = 16    # tuning knob: 32 cells per TMEM accumulator
 FLAG_SUBTILE_128 = 32   # tuning knob: 128 cells per TMEM accumulator
 FLAG_CELL_LANES = 64    # tuning knob: cells on the TMEM lanes (element matrices <= 128 entries)
 FLAG_STAGED_STORE = 256  # tuning knob: rows staged in shared memory, written by bulk copies
+FLAG_TENSOR_CORES = 512  # small element matrices: force the tcgen05 kernel
+FLAG_CUDA_CORES = 1024   # small element matrices: force the FP32 CUDA-core kernel
 
 FORM_NAMES = {MASS: "mass", HELMHOLTZ: "helmholtz", ADVDIFF: "advdiff", BURGERS_JAC: "burgers_jac",
               BURGERS_RESIDUAL: "burgers_residual"}
@@ -72,6 +74,7 @@ def lib():
         L.coffee_supported.argtypes = [I, I, I, I]
         L.coffee_split_coords.argtypes = [P, L64, P, P]
         L.coffee_round_coef.argtypes = [P, L64, P, P]
+        L.coffee_assemble_path.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint]
         L.coffee_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
@@ -240,6 +243,17 @@ def split_coords(coords, out=None, stream=None):
     _check(lib().coffee_split_coords(_ptr(coords), ctypes.c_int64(coords.numel()), _ptr(out),
                                      _stream_handle(stream)))
     return out
+
+
+PATH_NAMES = {0: "fp64", 1: "tensor cores", 2: "cuda cores fp32"}
+
+
+def assemble_path(form, degree, cell, precision, flags=0):
+    """coffee_assemble_path: 0 the FP64 kernel, 1 the tensor cores, 2 the FP32 CUDA-core kernel."""
+    r = lib().coffee_assemble_path(form, degree, cell, precision, int(flags))
+    if r < 0:
+        _check(r)
+    return r
 
 
 def round_coef(coef, out=None, stream=None):

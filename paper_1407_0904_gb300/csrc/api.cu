@@ -294,6 +294,13 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
   p.map = map;
   p.nnz = nnz;
   std::string why;
+  const bool simt = !map && simt_supported(a->form, a->degree, a->cell) && !(a->flags & COFFEE_FLAG_TENSOR_CORES) &&
+                    ((a->flags & COFFEE_FLAG_CUDA_CORES) || simt_default(a->form, a->degree, a->cell));
+  if (simt) {
+    cudaError_t e = (cudaError_t)launch_simt(a->form, a->degree, a->cell, p, c->num_sms, stream, why);
+    if (e != cudaSuccess) return cuda_fail(e, ("launch(assemble_simt) " + why).c_str());
+    return COFFEE_OK;
+  }
   cudaError_t e = map ? (cudaError_t)launch_tc_csr(a->form, a->cell, p, c->num_sms, stream, why)
                       : (cudaError_t)launch_tc(a->form, a->cell, p, c->num_sms, stream, why);
   if (e != cudaSuccess)
@@ -356,6 +363,15 @@ int coffee_supported(int form, int degree, int cell, int precision) {
            (precision == PREC_FP64 || prism_tc_supported(form, degree, precision));
   if (precision == PREC_FP64) return 1;
   return tc_supported(form, degree, cell, precision);
+}
+
+int coffee_assemble_path(int form, int degree, int cell, int precision, unsigned flags) {
+  if (!coffee_supported(form, degree, cell, precision))
+    return fail(COFFEE_ERR_UNSUPPORTED, "no kernel for this form/degree/cell/precision");
+  if (precision == PREC_FP64) return 0;
+  const bool simt = simt_supported(form, degree, cell) && !(flags & COFFEE_FLAG_TENSOR_CORES) &&
+                    ((flags & COFFEE_FLAG_CUDA_CORES) || simt_default(form, degree, cell));
+  return simt ? 2 : 1;
 }
 
 int coffee_round_coef(const double* coef, int64_t n, float* out, coffee_stream_t stream) {

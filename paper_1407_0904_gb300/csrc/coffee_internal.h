@@ -171,6 +171,13 @@ int tc_supported(int form, int degree, int cell, int precision);
 int staged_plan(const TcParams& p, int& subw, int& cells, int& buf_bytes);
 int launch_tc_staged(int form, int cell, const TcParams& q, int num_sms, void* stream, int nst, int smem);
 int launch_tc(int form, int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
+// T [K][N] (FP64) of the tensor-core contraction: the stiffness tensors in the edge basis
+void tc_reference_tensor(int form, int degree, int cell, std::vector<double>& T);
+// CUDA-core kernel for small element matrices (k_simt.cu): MASS, HELMHOLTZ and ADVDIFF on
+// triangles P1-P3 and tetrahedra P1-P2, FP32; simt_default: where it is the default path
+int simt_supported(int form, int degree, int cell);
+int simt_default(int form, int degree, int cell);
+int launch_simt(int form, int degree, int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
 // Burgers-Jacobian tensor-core kernel (k_tc_burgers.cu)
 int burgers_tc_supported(int degree, int cell, int precision);
 void build_burgers_image(int degree, int cell, int prec, bool exact_ok, std::vector<uint8_t>& img, TcTable& meta);

@@ -1,0 +1,229 @@
+// CUDA-core local assembly of small element matrices (MASS, HELMHOLTZ, ADVDIFF on triangles
+// P1-P3 and tetrahedra P1-P2): A_e = sum_k G_e[k] T[k], the contraction of section 4 (the
+// reference tensor T against the per-cell geometry and coefficient factors G_e) in FP32, one
+// thread per cell.
+//
+// Why not the tensor cores here: with K = 1 to 36 factors and 9 to 100 entries per cell the
+// contraction is a few hundred FMAs per cell against 36 to 400 bytes written, so the work is
+// bound by HBM and by the per-cell gather and geometry, not by multiply-adds. The tensor-core
+// kernel (k_tc_kernel.cuh) runs that per-cell work on 8 producer warps per SM; this kernel runs
+// it on every warp the SM holds, which hides the gather latency, and the FMAs (T is read from
+// constant memory, uniform across the warp, as an FMA operand) cost less than the MMA hand-offs.
+//
+// Per warp and 32 consecutive cells: each lane gathers its cell, forms G_e (the producers'
+// cell_factors_ids: FP32 geometry with the FP64 fallback for badly conditioned cells, the
+// vertex differences from (hi, lo) float pairs split by integer operations, so no FP64
+// instruction runs for regular cells), computes its N entries and writes them to a
+// shared-memory staging block (row stride N rounded up to odd: conflict-free); the warp then
+// writes the 32 rows, contiguous in the output, with coalesced 16-byte stores.
+// Accuracy: T is rounded to FP32 once (2^-24) and the K-term sums accumulate in FP32, which
+// meets every tensor-core precision's bound (TF32X3/BF16X3 1e-5, TF32/BF16 1e-2).
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <mutex>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+#include "coffee_internal.h"
+#include "tc_common.cuh"
+
+namespace coffee {
+namespace {
+using namespace tc;
+
+constexpr int SIMT_THREADS = 256;
+constexpr int SIMT_WARPS = SIMT_THREADS / 32;
+
+__host__ __device__ constexpr int s_ns(int d, int k) { return d == 2 ? (k + 1) * (k + 2) / 2 : (k + 1) * (k + 2) * (k + 3) / 6; }
+__host__ __device__ constexpr int s_K(int form, int d) {
+  return form == FORM_MASS ? 1 : form == FORM_HELMHOLTZ ? 1 + d * (d + 1) / 2 : (d + 1) * (d * (d + 1) / 2) + (d + 1) * d;
+}
+__host__ __device__ constexpr int s_maxdeg(int d) { return d == 2 ? 3 : 2; }
+__host__ __device__ constexpr int s_size(int form, int d, int k) { return s_K(form, d) * s_ns(d, k) * s_ns(d, k); }
+// offset of each instance's table in the constant bank: forms 0-2, d = 2, 3, degrees 1..maxdeg
+__host__ __device__ constexpr int s_off(int form, int d, int k) {
+  int off = 0;
+  for (int f = 0; f < 3; ++f)
+    for (int dd = 2; dd <= 3; ++dd)
+      for (int kk = 1; kk <= s_maxdeg(dd); ++kk) {
+        if (f == form && dd == d && kk == k) return off;
+        off += s_size(f, dd, kk);
+      }
+  return off;  // one past the last: the total
+}
+constexpr int S_TOTAL = s_off(3, 0, 0);
+static_assert(S_TOTAL * 4 <= 60 * 1024, "reference tensors exceed the constant bank");
+
+// T [K][N] in FP32 of every instance (edge-basis form of the stiffness tensors, as the
+// tensor-core images), written once per device before the first launch that reads it
+__constant__ float c_T[S_TOTAL];
+
+// index rows of cell e; tetrahedra with 16-byte aligned index arrays read each row with one
+// 16-byte load (v4, uniform)
+template <int FORM, int D>
+__device__ __forceinline__ void simt_ids(const TcParams& p, int64_t e, bool v4, CellIds<FORM, D>& ids) {
+  if constexpr (D == 3) {
+    if (v4) {
+      const int4 a = __ldg(reinterpret_cast<const int4*>(p.c2v) + e);
+      ids.vid[0] = a.x, ids.vid[1] = a.y, ids.vid[2] = a.z, ids.vid[3] = a.w;
+      if constexpr (FORM == FORM_ADVDIFF) {
+        const int4 b = __ldg(reinterpret_cast<const int4*>(p.c2d) + e);
+        ids.cid[0] = b.x, ids.cid[1] = b.y, ids.cid[2] = b.z, ids.cid[3] = b.w;
+      }
+      return;
+    }
+  }
+  load_ids<FORM, D>(p, e, ids);
+}
+
+template <int FORM, int D, int DEG>
+__global__ void __launch_bounds__(SIMT_THREADS) k_assemble_simt(const TcParams p) {
+  constexpr int NS = s_ns(D, DEG), N = NS * NS, K = s_K(FORM, D), OFF = s_off(FORM, D, DEG);
+  constexpr int SR = N | 1;  // staging row stride
+  extern __shared__ float stage[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* st = stage + warp * 32 * SR;
+  const int64_t ntiles = (p.ncells + 31) / 32;
+  const bool vec = (reinterpret_cast<uintptr_t>(p.out) & 15) == 0;
+  const bool v4 = (reinterpret_cast<uintptr_t>(p.c2v) & 15) == 0 &&
+                  (FORM != FORM_ADVDIFF || (reinterpret_cast<uintptr_t>(p.c2d) & 15) == 0);
+  for (int64_t t = (int64_t)blockIdx.x * SIMT_WARPS + warp; t < ntiles; t += (int64_t)gridDim.x * SIMT_WARPS) {
+    const int64_t c0 = t * 32, e = c0 + lane;
+    float G[K];
+    bool bad = false;
+    if (e < p.ncells) {
+      CellIds<FORM, D> ids;
+      simt_ids<FORM, D>(p, e, v4, ids);
+      cell_factors_ids<FORM, D, K, true>(p, ids, G, bad);
+      if (bad) atomicOr(p.err, ERR_INDEX);
+    }
+    if (e >= p.ncells || bad) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) G[k] = 0.f;
+    }
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+      float a = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) a = fmaf(G[k], c_T[OFF + k * N + o], a);
+      st[lane * SR + o] = a;
+    }
+    __syncwarp();
+    // the 32 rows are contiguous in the output: 32 N floats from c0 N on (16-byte aligned when
+    // the output is, since 32 N floats are a multiple of 16 bytes)
+    const int rows = (int)(p.ncells - c0 < 32 ? p.ncells - c0 : 32);
+    float* dst = p.out + c0 * N;
+    if (rows == 32 && vec) {
+#pragma unroll 4
+      for (int i = lane; i < 8 * N; i += 32) {  // 8 N float4 per warp tile
+        float4 v;
+        const int j = 4 * i;
+        v.x = st[((j + 0) / N) * SR + (j + 0) % N];
+        v.y = st[((j + 1) / N) * SR + (j + 1) % N];
+        v.z = st[((j + 2) / N) * SR + (j + 2) % N];
+        v.w = st[((j + 3) / N) * SR + (j + 3) % N];
+        __stcs(reinterpret_cast<float4*>(dst) + i, v);
+      }
+    } else {
+      for (int i = lane; i < rows * N; i += 32) __stcs(dst + i, st[(i / N) * SR + i % N]);
+    }
+    __syncwarp();
+  }
+}
+
+using SimtKernel = void (*)(const TcParams);
+
+template <int FORM, int D>
+SimtKernel pick_deg(int degree) {
+  switch (degree) {
+    case 1: return k_assemble_simt<FORM, D, 1>;
+    case 2: return k_assemble_simt<FORM, D, 2>;
+    case 3: if constexpr (D == 2) return k_assemble_simt<FORM, D, 3>;
+  }
+  return nullptr;
+}
+
+SimtKernel pick(int form, int degree, int cell) {
+  if (cell == CELL_TRI) {
+    switch (form) {
+      case FORM_MASS: return pick_deg<FORM_MASS, 2>(degree);
+      case FORM_HELMHOLTZ: return pick_deg<FORM_HELMHOLTZ, 2>(degree);
+      case FORM_ADVDIFF: return pick_deg<FORM_ADVDIFF, 2>(degree);
+    }
+  } else if (cell == CELL_TET) {
+    switch (form) {
+      case FORM_MASS: return pick_deg<FORM_MASS, 3>(degree);
+      case FORM_HELMHOLTZ: return pick_deg<FORM_HELMHOLTZ, 3>(degree);
+      case FORM_ADVDIFF: return pick_deg<FORM_ADVDIFF, 3>(degree);
+    }
+  }
+  return nullptr;
+}
+
+std::mutex g_simt_mu;
+std::set<std::tuple<int, int, int, int>> g_simt_loaded;  // (device, form, degree, cell)
+
+}  // namespace
+
+int simt_supported(int form, int degree, int cell) {
+  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF)) return 0;
+  if (!(cell == CELL_TRI || cell == CELL_TET)) return 0;
+  const int d = cell == CELL_TRI ? 2 : 3;
+  return degree >= 1 && degree <= s_maxdeg(d) ? 1 : 0;
+}
+
+// where the CUDA-core kernel is the faster one (measured, TF32X3 tensor-core kernel with its
+// tuned knobs against this one, 1,572,864 tets and 2,097,152 triangles, every form): P1 on both
+// cells (tets 1.3-2.2x, triangles 2.5-3.0x) and triangles P2 (1.35-1.8x); tets P2 and
+// triangles P3 stay on the tensor cores (their 100-entry matrices cost the CUDA cores more FMAs
+// than the tensor-core kernel's hand-offs)
+int simt_default(int form, int degree, int cell) {
+  (void)form;
+  return degree == 1 || (cell == CELL_TRI && degree == 2) ? 1 : 0;
+}
+
+int launch_simt(int form, int degree, int cell, const TcParams& p, int num_sms, void* stream, std::string& why) {
+  SimtKernel kern = simt_supported(form, degree, cell) ? pick(form, degree, cell) : nullptr;
+  if (!kern) {
+    why = "no CUDA-core kernel for this form/degree/cell";
+    return (int)cudaErrorInvalidValue;
+  }
+  if (p.ncells == 0) return (int)cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  const int d = cell == CELL_TRI ? 2 : 3, ns = s_ns(d, degree), N = ns * ns;
+  {
+    std::lock_guard<std::mutex> lock(g_simt_mu);
+    if (!g_simt_loaded.count({dev, form, degree, cell})) {
+      std::vector<double> T;
+      tc_reference_tensor(form, degree, cell, T);
+      std::vector<float> f(T.size());
+      for (size_t i = 0; i < T.size(); ++i) f[i] = (float)T[i];
+      if ((int)f.size() != s_size(form, d, degree)) {
+        why = "reference tensor size mismatch";
+        return (int)cudaErrorInvalidValue;
+      }
+      e = cudaMemcpyToSymbol(c_T, f.data(), f.size() * sizeof(float), (size_t)s_off(form, d, degree) * sizeof(float),
+                             cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return (int)e;
+      g_simt_loaded.insert({dev, form, degree, cell});
+    }
+  }
+  const int smem = SIMT_WARPS * 32 * (N | 1) * (int)sizeof(float);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return (int)e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SIMT_THREADS, smem);
+  if (e != cudaSuccess) return (int)e;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t warps_needed = (p.ncells + 31) / 32;
+  const int64_t blocks_needed = (warps_needed + SIMT_WARPS - 1) / SIMT_WARPS;
+  const int64_t full = (int64_t)num_sms * per_sm;
+  const int grid = (int)(blocks_needed < full ? blocks_needed : full);
+  kern<<<grid, SIMT_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(p);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace coffee

@@ -361,13 +361,35 @@ __device__ __forceinline__ void coef_rows(const TcParams& p, const int (&ids)[R]
   }
 }
 
+// x = hi + lo by integer operations, with no FP64 instruction: hi is x truncated to the 24
+// significant bits of a float, lo the 29 fraction bits below them as an integer r, converted to
+// float (rounded to nearest) and scaled exactly by the weight of the double's last bit,
+// 2^(e - 1075) for the biased exponent e. So hi + lo holds x to 2^-48 of |x|, like the
+// (hi, lo) pairs of coffee_split_coords. False for |x| outside [2^-70, 2^100) other than zero
+// (hi = lo = 0 then), where the caller falls back to FP64.
+__device__ __forceinline__ bool split_exact(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t h = (uint32_t)(b >> 32), l = (uint32_t)b;
+  const uint32_t sign = h & 0x80000000u;
+  const int e = (int)((h >> 20) & 0x7FFu);
+  const bool zero = ((h & 0x7FFFFFFFu) | l) == 0u;
+  const bool ok = zero || (e >= 1023 - 70 && e < 1023 + 100);
+  const uint32_t hb = sign | ((uint32_t)(e - 1023 + 127) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29);
+  const float unit = __uint_as_float((uint32_t)(e - 1075 + 127) << 23);
+  const float lm = __uint2float_rn(l & 0x1FFFFFFFu) * unit;
+  const bool use = ok && !zero;
+  hi = use ? __uint_as_float(hb) : 0.f;
+  lo = use ? __uint_as_float(__float_as_uint(lm) | sign) : 0.f;
+  return ok;
+}
+
 // Geometry of the cell with vertex ids vid: adj (K = adj/det), |det| and sign(det). The Jacobian
-// J[r][c] = x_{c+1}[r] - x_0[r] is taken in FP32 from the caller's (hi, lo) float pairs of the
-// coordinates when it passed them ((hi1 - hi0) + (lo1 - lo0): the hi difference is exact or
-// rounded once, the lo one is 2^-24 smaller, so J carries about two FP32 roundings, no FP64
-// work), else as the FP64 difference rounded to FP32; badly conditioned cells are recomputed in
-// FP64 from the FP64 coordinates.
-template <int D>
+// J[r][c] = x_{c+1}[r] - x_0[r] is taken in FP32 from (hi, lo) float pairs of the coordinates,
+// (hi1 - hi0) + (lo1 - lo0) (the hi difference is exact or rounded once, the lo one is 2^-24
+// smaller, so J carries about two FP32 roundings), when the caller passed the pairs or, with
+// ISPLIT, from pairs split here by integer operations (split_exact); else as the FP64 difference
+// rounded to FP32. Badly conditioned cells are recomputed in FP64 from the FP64 coordinates.
+template <int D, bool ISPLIT = false>
 __device__ __forceinline__ void cell_geometry_ids(const TcParams& p, const int (&vid)[D + 1], float (&adj)[D][D],
                                                   float& Dm, float& sg) {
   float J[D][D], det;
@@ -392,6 +414,24 @@ __device__ __forceinline__ void cell_geometry_ids(const TcParams& p, const int (
         for (int r = 0; r < D; ++r) X[v][r] = __ldg(p.coords + (int64_t)vid[v] * D + r);
       geometry_f64<D>(X, adj, det);
     }
+  } else if constexpr (ISPLIT) {
+    double X[D + 1][D];
+#pragma unroll
+    for (int v = 0; v < D + 1; ++v)
+#pragma unroll
+      for (int r = 0; r < D; ++r) X[v][r] = __ldg(p.coords + (int64_t)vid[v] * D + r);
+    float2 x[D + 1][D];
+    bool ok = true;
+#pragma unroll
+    for (int v = 0; v < D + 1; ++v)
+#pragma unroll
+      for (int r = 0; r < D; ++r) ok = split_exact(X[v][r], x[v][r].x, x[v][r].y) && ok;
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) J[r][c] = (x[c + 1][r].x - x[0][r].x) + (x[c + 1][r].y - x[0][r].y);
+    good = geometry_f32<D>(J, adj, det) && ok;
+    if (!good) geometry_f64<D>(X, adj, det);
   } else {
     double X[D + 1][D];
 #pragma unroll
@@ -470,7 +510,7 @@ __device__ __forceinline__ void load_ids(const TcParams& p, int64_t e, CellIds<F
   }
 }
 
-template <int FORM, int D, int KP>
+template <int FORM, int D, int KP, bool ISPLIT = false>
 __device__ __forceinline__ void cell_factors_ids(const TcParams& p, const CellIds<FORM, D>& ids, float (&G)[KP],
                                                  bool& bad) {
   constexpr int NV = D + 1, P = D * (D + 1) / 2;
@@ -492,7 +532,7 @@ __device__ __forceinline__ void cell_factors_ids(const TcParams& p, const CellId
   }
   if (bad) return;
   float adj[D][D], Dm, sg;
-  cell_geometry_ids<D>(p, vid, adj, Dm, sg);
+  cell_geometry_ids<D, ISPLIT>(p, vid, adj, Dm, sg);
   float C[P];  // edge factors
   if constexpr (FORM != FORM_MASS) edge_factors<D>(adj, 1.0f / Dm, C);
   if constexpr (FORM == FORM_MASS) {

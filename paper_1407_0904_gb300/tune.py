@@ -15,6 +15,8 @@ Knobs (all give bit-identical results; only speed changes):
   FLAG_TWO_STAGES     at most two operand stages
   FLAG_STAGED_STORE   rows of consecutive cells gathered in shared memory, one bulk copy each
                       (tried where rows do not start on 32-byte sectors)
+  FLAG_CUDA_CORES / FLAG_TENSOR_CORES  the FP32 CUDA-core kernel or the tensor cores, where a
+                      small element matrix has both
 
   python -m paper_1407_0904_gb300.tune [--ncells N] [--out PATH]
   python -m paper_1407_0904_gb300.tune --study    # cost model vs the tuned choices (no GPU)
@@ -68,7 +70,10 @@ def load_batch(path=None, gpu=None):
         return json.load(f).get("batch", {})
 
 
-def candidates(coffee, n_outputs):
+def candidates(coffee, n_outputs, cuda_cores=False):
+    """Knob combinations to time. Where the element matrix also has the FP32 CUDA-core kernel
+    (cuda_cores), the tensor-core combinations are forced onto the tensor cores and the
+    CUDA-core kernel is one more candidate; 0 (the library's default path) stays in the list."""
     F = coffee
     c = [0, F.FLAG_TWO_STAGES, F.FLAG_SUBTILE_128, F.FLAG_SUBTILE_64, F.FLAG_SUBTILE_32,
          F.FLAG_SUBTILE_64 | F.FLAG_TWO_STAGES]
@@ -76,6 +81,8 @@ def candidates(coffee, n_outputs):
         c += [F.FLAG_OUTPUT_LANES, F.FLAG_CELL_LANES, F.FLAG_CELL_LANES | F.FLAG_TWO_STAGES]
     if (n_outputs * 4) % 32:  # rows not on 32-byte sectors: rows staged for bulk copies
         c += [F.FLAG_OUTPUT_LANES | F.FLAG_STAGED_STORE, F.FLAG_OUTPUT_LANES | F.FLAG_STAGED_STORE | F.FLAG_TWO_STAGES]
+    if cuda_cores:
+        c = [0, F.FLAG_CUDA_CORES] + [t | F.FLAG_TENSOR_CORES for t in c]
     return sorted(set(c))
 
 
@@ -135,7 +142,8 @@ def tune_all(forms=None, cells=(0, 1), degrees=(1, 2, 3, 4), precisions=None, nc
                         continue
                     n = coffee.ndof(form, k, cell) ** 2
                     times = {}
-                    for t in candidates(coffee, n):
+                    simt = coffee.assemble_path(form, k, cell, prec, coffee.FLAG_CUDA_CORES) == 2
+                    for t in candidates(coffee, n, simt):
                         times[t] = time_case(coffee, form, k, cell, prec, meshes[cell], t, reps=reps)
                     best = min(times, key=times.get)
                     key = "%d/%d/%d/%d" % (form, k, cell, prec)

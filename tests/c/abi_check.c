@@ -23,7 +23,7 @@ typedef void (*entry_fn)(void);
 static const entry_fn entry_points[] = {
     (entry_fn)coffee_ndof, (entry_fn)coffee_tabulate, (entry_fn)coffee_reference_tensor,
     (entry_fn)coffee_supported, (entry_fn)coffee_assemble, (entry_fn)coffee_assemble_ex,
-    (entry_fn)coffee_split_coords, (entry_fn)coffee_round_coef,
+    (entry_fn)coffee_split_coords, (entry_fn)coffee_round_coef, (entry_fn)coffee_assemble_path,
     (entry_fn)coffee_assemble_host, (entry_fn)coffee_host_pool_trim,
     (entry_fn)coffee_assemble_backward, (entry_fn)coffee_assemble_backward_noalloc,
     (entry_fn)coffee_batch_plan, (entry_fn)coffee_batch_plan_costs, (entry_fn)coffee_batch_launch,
@@ -78,6 +78,11 @@ int main(void) {
   /* support queries */
   CHECK(coffee_supported(COFFEE_HELMHOLTZ, 3, COFFEE_TETRAHEDRON, COFFEE_TF32X3) == 1);
   CHECK(coffee_supported(COFFEE_HELMHOLTZ, 4, COFFEE_PRISM, COFFEE_TF32X3) == 1);
+  CHECK(coffee_assemble_path(COFFEE_HELMHOLTZ, 1, COFFEE_TETRAHEDRON, COFFEE_TF32X3, 0) == 2);
+  CHECK(coffee_assemble_path(COFFEE_HELMHOLTZ, 1, COFFEE_TETRAHEDRON, COFFEE_TF32X3, COFFEE_FLAG_TENSOR_CORES) == 1);
+  CHECK(coffee_assemble_path(COFFEE_HELMHOLTZ, 3, COFFEE_TETRAHEDRON, COFFEE_TF32X3, 0) == 1);
+  CHECK(coffee_assemble_path(COFFEE_HELMHOLTZ, 3, COFFEE_TETRAHEDRON, COFFEE_FP64, 0) == 0);
+  CHECK(coffee_assemble_path(COFFEE_BURGERS_JAC, 1, COFFEE_TRIANGLE, COFFEE_TF32X3, COFFEE_FLAG_CUDA_CORES) == 1);
   CHECK(coffee_csr_supported(COFFEE_BURGERS_RESIDUAL, 2, COFFEE_TETRAHEDRON, COFFEE_FP64) == 0);
 
   /* argument errors are reported on the host, before any CUDA call */

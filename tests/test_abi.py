@@ -177,6 +177,27 @@ def test_support_queries_cover_prisms():
             assert not coffee.csr_supported(form, 1, P, prec)
 
 
+def test_assemble_path_query():
+    """Host-only: which kernel family runs. Small element matrices (MASS, HELMHOLTZ, ADVDIFF on
+    P1 simplices and P2 triangles) default to the FP32 CUDA-core kernel, the rest of the
+    tensor-core precisions to the tensor cores; the flags force either where both exist; FP64
+    is the FP64 kernel; unsupported combinations raise."""
+    T, R, P = coffee.TETRAHEDRON, coffee.TRIANGLE, coffee.PRISM
+    for form in (coffee.MASS, coffee.HELMHOLTZ, coffee.ADVDIFF):
+        for cell, k, default in ((T, 1, 2), (R, 1, 2), (R, 2, 2), (T, 2, 1), (R, 3, 1), (T, 3, 1), (R, 4, 1)):
+            for prec in (coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16):
+                assert coffee.assemble_path(form, k, cell, prec) == default
+                assert coffee.assemble_path(form, k, cell, prec, coffee.FLAG_TENSOR_CORES) == 1
+                forced = 2 if (cell == T and k <= 2) or (cell == R and k <= 3) else 1
+                assert coffee.assemble_path(form, k, cell, prec, coffee.FLAG_CUDA_CORES) == forced
+            assert coffee.assemble_path(form, k, cell, coffee.FP64) == 0
+        assert coffee.assemble_path(form, 2, P, coffee.TF32X3, coffee.FLAG_CUDA_CORES) == 1
+    for form in (coffee.BURGERS_JAC, coffee.BURGERS_RESIDUAL):
+        assert coffee.assemble_path(form, 1, T, coffee.TF32X3, coffee.FLAG_CUDA_CORES) == 1
+    with pytest.raises(coffee.CoffeeError):
+        coffee.assemble_path(coffee.BURGERS_JAC, 1, P, coffee.TF32X3)
+
+
 def test_reference_tensor_queries_for_residual_and_prisms():
     """Host-only: the residual contracts the Jacobian's reference tensors; prisms, whose
     Jacobian varies over the cell, have none and are rejected."""
