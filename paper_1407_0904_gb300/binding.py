@@ -349,7 +349,8 @@ def _tuned_flags(form, degree, cell, precision):
     ent = _tune_cache.get("%d/%d/%d/%d" % (form, degree, cell, precision))
     if ent is not None:
         return int(ent.get("flags", 0))
-    return _tune.model_flags(ndof(form, degree, cell) ** 2)
+    return _tune.model_flags(ndof(form, degree, cell) ** 2,
+                             assemble_path(form, degree, cell, precision, FLAG_CUDA_CORES) == 2)
 
 
 def assemble_plain(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, out=None,

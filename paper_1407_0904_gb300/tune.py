@@ -243,9 +243,13 @@ def tune_batch(ncells_per_mesh=2 ** 17, log=print):
     return {"item_overhead": best, "ms": times[best], "candidates": {str(k): round(v, 5) for k, v in times.items()}}
 
 
-def model_flags(n_outputs):
+def model_flags(n_outputs, cuda_cores=False):
     """Knobs chosen without timing, from the number of entries N of the element matrix.
 
+    - Where the element matrix also has the FP32 CUDA-core kernel (cuda_cores): that kernel
+      when N <= 36 (its K-term sums for N entries cost N K FMAs per cell against the
+      tensor-core kernel's fixed hand-offs per 128-cell tile), else the tensor cores with the
+      knobs below.
     - Cells on the TMEM lanes when N <= 64: one thread then writes its cell's whole row
       (<= 256 bytes, at most two 128-byte lines) with 16-byte stores, so rows are completed
       by one thread in order; above that a thread holds too many accumulator columns.
@@ -255,6 +259,10 @@ def model_flags(n_outputs):
     - Otherwise the library default (128 cells per accumulator up to four slices).
     """
     from . import binding as coffee
+    if cuda_cores:
+        if n_outputs <= 36:
+            return coffee.FLAG_CUDA_CORES
+        return model_flags(n_outputs) | coffee.FLAG_TENSOR_CORES
     mtiles = (n_outputs + 127) // 128
     if n_outputs <= 64:
         return coffee.FLAG_CELL_LANES
@@ -274,7 +282,7 @@ def study(entries=None, log=print):
         n = coffee.ndof(form, k, cell) ** 2
         cands = {int(float(c)): t for c, t in ent["candidates"].items()}
         best = min(cands.values())
-        mf = model_flags(n)
+        mf = model_flags(n, coffee.assemble_path(form, k, cell, prec, coffee.FLAG_CUDA_CORES) == 2)
         model_t = cands.get(mf)
         rows.append({"key": key, "form": coffee.FORM_NAMES[form], "degree": k, "cell": "tri" if cell == 0 else "tet",
                      "N": n, "best_flags": int(ent["flags"]), "best_ms": best, "model_flags": mf,

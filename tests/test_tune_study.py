@@ -29,6 +29,12 @@ def test_model_rules(n, flags):
     assert tune.model_flags(n) == flags
 
 
+@pytest.mark.parametrize("n,flags", [(9, coffee.FLAG_CUDA_CORES), (36, coffee.FLAG_CUDA_CORES),
+                                     (100, coffee.FLAG_TENSOR_CORES)])
+def test_model_rules_with_the_cuda_core_kernel(n, flags):
+    assert tune.model_flags(n, cuda_cores=True) == flags
+
+
 def test_batch_costs_prefer_in_batch_tile_times(monkeypatch):
     """BatchPlan's measured costs: the batch kernel's own per-tile time for every group when the
     cache has them, else the single-group kernel's time per 128-cell tile, else None (the plan
