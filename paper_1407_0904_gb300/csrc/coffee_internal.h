@@ -189,6 +189,7 @@ void build_burgers_stream_image(int degree, int cell, int prec, std::vector<uint
 int launch_burgers_stream_tc(int cell, int degree, const TcParams& p, int num_sms, void* stream, std::string& why);
 // Burgers-residual (element vector) tensor-core kernel (k_tc_burgers_res.cu)
 int burgers_res_tc_supported(int degree, int cell, int precision);
+void build_burgers_res_image(int degree, int cell, int prec, std::vector<uint8_t>& img, TcTable& meta);
 int launch_burgers_res_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
 // ---- mixed-batch persistent kernel (k_batch.cu) ----
 struct BatchGroup {

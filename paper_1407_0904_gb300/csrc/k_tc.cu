@@ -122,8 +122,12 @@ void build_tc_image(int form, int degree, int cell, int prec, std::vector<uint8_
     build_prism_tc_image(form, degree, prec, img, meta);
     return;
   }
-  if (burgers_like(form)) {  // the Jacobian takes the exact integer form of A where it exists
-    build_burgers_image(degree, cell, prec, form == FORM_BURGERS, img, meta);
+  if (form == FORM_BURGERS_RES) {  // the T2 and T3 columns only
+    build_burgers_res_image(degree, cell, prec, img, meta);
+    return;
+  }
+  if (form == FORM_BURGERS) {  // the Jacobian takes the exact integer form of A where it exists
+    build_burgers_image(degree, cell, prec, true, img, meta);
     return;
   }
   Geom g{};

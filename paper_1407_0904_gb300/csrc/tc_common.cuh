@@ -571,6 +571,7 @@ struct alignas(8) Barriers {
   uint64_t empty[MAX_STAGES];
   uint64_t tfull[MAX_SLOTS];
   uint64_t tempty[MAX_SLOTS];
+  uint64_t aux[MAX_SLOTS];  // Burgers residual: the u buffer of each accumulator slot written
   uint64_t done;
   uint64_t epi;  // staged epilogue: the epilogue warps' own barrier (one phase per bulk copy)
   uint32_t tmem_base;

@@ -39,9 +39,11 @@ def check_groups(dev, groups, outs, prec, tol, sample=None):
         spec = g["spec"]
         if spec["count"] == 0:
             continue
+        # batches run on the tensor cores: the single-group launch is forced there too (small
+        # element matrices would otherwise take the CUDA-core kernel)
         single = coffee.assemble(g["form"], g["degree"], g["cell"], g["coords"], g["cell2vert"],
                                  g.get("coef"), g.get("cell2dof"), precision=prec,
-                                 coords_split=g.get("coords_split"))
+                                 coords_split=g.get("coords_split"), tune=coffee.FLAG_TENSOR_CORES)
         assert torch.equal(out, single), spec
         d = dev[g["cell"]]
         m = d["mesh"]

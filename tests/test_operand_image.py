@@ -224,20 +224,31 @@ def test_prism_image_holds_the_per_point_tensors_of_the_oracles_basis(form, k, p
         assert np.abs(Abar[:N, c] - wsum[c]).max() <= tol * np.abs(wsum[c]).max(), c
 
 
-@pytest.mark.parametrize("cell,k", [(TRI, 1), (TRI, 2), (TRI, 3), (TET, 1), (TET, 2)])
-def test_residual_image_is_the_split_burgers_image(cell, k):
-    """The residual kernel contracts the Jacobian's tensors with A split in its precision's parts
-    (it takes no exact-integer form), so its image is the split Burgers image."""
-    for prec in (coffee.TF32X3, coffee.BF16X3):
-        got = image(coffee.BURGERS_RESIDUAL, k, cell, prec)
-        if got is None:
-            continue
-        img, meta = got
-        assert meta[5] == 0 and meta[4] == TPARTS[prec]
-        jac = image(coffee.BURGERS_JAC, k, cell, prec)
-        assert jac is not None and jac[1][:4] == meta[:4] and jac[1][6] == meta[6]
-        if jac[1][5] == 0:
-            assert np.array_equal(jac[0], img)  # without an exact form the two images coincide
+@pytest.mark.parametrize("cell,k", [(TRI, 1), (TRI, 2), (TRI, 3), (TRI, 4), (TET, 1), (TET, 2)])
+@pytest.mark.parametrize("prec", [coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16])
+def test_residual_image_holds_t2_and_t3(cell, k, prec):
+    """The residual contracts only the T2 and T3 tensors of the Jacobian: its image holds
+    [T2 | T3]^T (columns = the d ns T2 rows of the Burgers reference tensor, then its P T3 rows),
+    split into the precision's parts of T, zero in the padding rows and columns."""
+    got = image(coffee.BURGERS_RESIDUAL, k, cell, prec)
+    if got is None:
+        pytest.skip("no tensor-core kernel for this combination")
+    img, meta = got
+    mtiles, kbytes, kelems, K, parts, aexact, _, _ = meta
+    d, ns = 2 + cell, coffee.nnodes(cell, k)
+    nb, K1, P = ns * ns, ns * d, d * (d + 1) // 2
+    assert mtiles == (nb + 127) // 128 and aexact == 0 and parts == TPARTS[prec] and K == K1 + P
+    tf32 = TF32[prec]
+    assert kelems * (4 if tf32 else 2) == kbytes and kelems % (8 if tf32 else 16) == 0 and kelems >= K
+    hi, rest = operand(img, meta, tf32, parts)
+    A = hi + rest
+    T = coffee.reference_tensor(coffee.BURGERS_JAC, k, cell).reshape(-1, nb)
+    want = np.zeros((128 * mtiles, kelems))
+    want[:nb, :K] = T[K1:K1 + K].T
+    tol = {coffee.TF32X3: 2.0 ** -21, coffee.BF16X3: 2.0 ** -23, coffee.TF32: 2.0 ** -10,
+           coffee.BF16: 2.0 ** -15}[prec]
+    assert np.all(A[nb:] == 0) and np.all(A[:, K:] == 0)
+    assert np.abs(A - want).max() <= tol * np.abs(T).max()
 
 
 @pytest.mark.parametrize("cell,k", [(TET, 3), (TET, 4), (TRI, 4)])
