@@ -111,11 +111,34 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
     const int pw = warp - PROD_WARP0;
     const int grp = pw >> 2, row = ((pw & 3) << 5) + lane;
     const int spg = nstages / PROD_GROUPS;
+    const int64_t tstep = (int64_t)PROD_GROUPS * gridDim.x;
+    // index rows one tile ahead (the next tile of this group): the coordinate and u gathers of
+    // a tile then wait on one level of loads instead of two
+    int nvid[NV], ndid[NS];
+    {
+      const int64_t e0 = (blockIdx.x + (int64_t)grp * gridDim.x) * BN + row;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) nvid[v] = e0 < p.ncells ? __ldg(p.c2v + e0 * NV + v) : 0;
+#pragma unroll
+      for (int r = 0; r < NS; ++r) ndid[r] = e0 < p.ncells ? __ldg(p.c2d + e0 * NS + r) : 0;
+    }
     int64_t li = 0;
-    for (int64_t t = blockIdx.x + (int64_t)grp * gridDim.x; t < ntiles; t += (int64_t)PROD_GROUPS * gridDim.x, ++li) {
+    for (int64_t t = blockIdx.x + (int64_t)grp * gridDim.x; t < ntiles; t += tstep, ++li) {
       const int64_t e = t * BN + row;
       const int64_t tl = li * PROD_GROUPS + grp;  // the CTA's tile number: its accumulator slot
       const uint32_t slot = (uint32_t)(tl % NSLOT), round = (uint32_t)(tl / NSLOT);
+      int vid[NV], did[NS];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) vid[v] = nvid[v];
+#pragma unroll
+      for (int r = 0; r < NS; ++r) did[r] = ndid[r];
+      {
+        const int64_t en = e + tstep * BN;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) nvid[v] = en < p.ncells ? __ldg(p.c2v + en * NV + v) : 0;
+#pragma unroll
+        for (int r = 0; r < NS; ++r) ndid[r] = en < p.ncells ? __ldg(p.c2d + en * NS + r) : 0;
+      }
       int s;
       uint32_t use;
       stage_of(li, grp, spg, s, use);
@@ -123,19 +146,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
       float u[NS][D], Pm[D][D], H[P];
       bool live = e < p.ncells;
       if (live) {
-        int vid[NV];
         bool bad = false;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          vid[v] = __ldg(p.c2v + e * NV + v);
+        for (int v = 0; v < NV; ++v)
           if (p.validate && (vid[v] < 0 || vid[v] >= p.nverts)) bad = true;
-        }
-        int did[NS];
 #pragma unroll
-        for (int r = 0; r < NS; ++r) {
-          did[r] = __ldg(p.c2d + e * NS + r);
+        for (int r = 0; r < NS; ++r)
           if (p.validate && (did[r] < 0 || did[r] >= p.ncoefnodes)) bad = true;
-        }
         if (bad) {
           atomicOr(p.err, ERR_INDEX);
           live = false;
