@@ -210,6 +210,16 @@ typedef struct {
    * the FP64 pipe. Results are bit for bit those without it. coef must still be given (the FP64
    * kernels read it; every pointer check applies). */
   const float* coef_f32;
+  /* entries between the starts of consecutive element matrices in out: 0 (or ndof*ndof) for the
+   * contiguous layout [ncells][ndof][ndof]; a larger value pads every matrix, e.g. to a multiple
+   * of 32 entries so that each starts on a 128-byte line (element matrices whose size is not a
+   * multiple of 32 entries otherwise start at 4- or 8-byte offsets, and warp stores that straddle
+   * lines run at about half the rate: tetrahedra P4, 1225 entries). The padding is not written.
+   * Local assembly of MASS, HELMHOLTZ and ADVDIFF on triangles and tetrahedra (FP64, tensor-core
+   * and CUDA-core kernels); anything else with a nonzero stride other than ndof*ndof returns
+   * COFFEE_ERR_INVALID_ARG, as does a stride below ndof*ndof. Ignored by the adjoint entry
+   * points. */
+  int64_t out_stride;
 } coffee_assemble_args;
 
 /* Every coordinate x[i], i < n (n = nverts * d), as the float pair (hi, lo) = ((float)x,
@@ -246,6 +256,7 @@ int coffee_assemble_ex(const coffee_assemble_args* a, coffee_stream_t stream);
  * pointers with the layouts of coffee_assemble; out is [ncells][ndof][ndof] (BURGERS_RESIDUAL:
  * [ncells][ndof]), double for FP64 and float otherwise. a->nverts, and a->ncoefnodes for the
  * forms with a coefficient, must be > 0: they size the copies.
+ * a->out_stride must be 0 (contiguous results).
  * a->coords_split and a->coef_f32 are ignored: for the tensor-core precisions on triangles and
  * tetrahedra the coordinates are split into (hi, lo) float pairs on the device after their copy,
  * and for every tensor-core precision the coefficients are rounded to floats there.

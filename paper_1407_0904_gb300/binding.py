@@ -53,6 +53,7 @@ class AssembleArgs(ctypes.Structure):
         ("flags", ctypes.c_uint),
         ("coords_split", ctypes.c_void_p),
         ("coef_f32", ctypes.c_void_p),
+        ("out_stride", ctypes.c_int64),
     ]
 
 
@@ -274,7 +275,7 @@ def round_coef(coef, out=None, stream=None):
 
 def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
               out=None, nu=0.01, validate=False, ncoefnodes=None, tune=0, alloc_out=True, coords_split=None,
-              coef_f32=None):
+              coef_f32=None, out_stride=0):
     coords = _dev(coords, torch.float64, "coords")
     cell2vert = _dev(cell2vert, torch.int32, "cell2vert")
     coef = _dev(coef, torch.float64, "coef")
@@ -285,7 +286,16 @@ def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, p
     n = ndof(form, degree, cell)
     odt = torch.float64 if precision == FP64 else torch.float32
     shape = (ncells, n) if form == BURGERS_RESIDUAL else (ncells, n, n)  # element vectors or matrices
-    if out is None:
+    if out_stride:
+        # padded rows: out is the flat buffer [ncells, out_stride] (see assemble)
+        if out is None:
+            if alloc_out:
+                out = torch.empty((ncells, out_stride), dtype=odt, device=coords.device)
+        else:
+            _dev(out, odt, "out")
+            if ncells and out.numel() < (ncells - 1) * out_stride + int(np.prod(shape[1:])):
+                raise ValueError("out must hold (ncells - 1) * out_stride + %d elements" % int(np.prod(shape[1:])))
+    elif out is None:
         if alloc_out:
             out = torch.empty(shape, dtype=odt, device=coords.device)
     else:
@@ -312,22 +322,32 @@ def make_args(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, p
         if coef is None or coef_f32.numel() != coef.numel():
             raise ValueError("coef_f32 must hold one float per coefficient of coef (round_coef)")
     a.coef_f32 = _ptr(coef_f32)
+    a.out_stride = int(out_stride or 0)
     return a, out
 
 
 def assemble(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None, precision=FP64,
-             out=None, nu=0.01, validate=False, stream=None, tune=None, coords_split=None, coef_f32=None):
+             out=None, nu=0.01, validate=False, stream=None, tune=None, coords_split=None, coef_f32=None,
+             out_stride=None):
     """Element matrices [ncells, ndof, ndof] (float64 for FP64, float32 otherwise) on the device.
 
     tune: FLAG_OUTPUT_LANES / FLAG_TWO_STAGES knobs; None uses the autotuner's choice for
     this (form, degree, cell, precision) when one is cached, else the library default.
     coords_split: the (hi, lo) float pairs of coords (split_coords), optional.
-    coef_f32: coef rounded to floats (round_coef), optional."""
+    coef_f32: coef rounded to floats (round_coef), optional.
+    out_stride: entries between consecutive element matrices (padded rows, e.g. a multiple of 32
+    so that every matrix starts on a 128-byte line); out is then the flat buffer of ncells rows of
+    out_stride entries (allocated when None), and the result is the strided view
+    [ncells, ndof, ndof] of it. The padding is not written."""
     if tune is None:
         tune = _tuned_flags(form, degree, cell, precision)
     a, out = make_args(form, degree, cell, coords, cell2vert, coef, cell2dof, precision, out, nu,
-                       validate, tune=tune, coords_split=coords_split, coef_f32=coef_f32)
+                       validate, tune=tune, coords_split=coords_split, coef_f32=coef_f32,
+                       out_stride=out_stride or 0)
     _check(lib().coffee_assemble_ex(ctypes.byref(a), _stream_handle(stream)))
+    if out_stride:
+        n = ndof(form, degree, cell)
+        return out.as_strided((cell2vert.shape[0], n, n), (int(out_stride), n, 1))
     return out
 
 

@@ -162,6 +162,16 @@ int check_args(const coffee_assemble_args* a) {
   }
   if (a->ncells > (int64_t)INT32_MAX * 128)
     return fail(COFFEE_ERR_INVALID_ARG, "ncells too large");
+  if (a->out_stride != 0) {
+    const int nd = coffee_ndof(a->form, a->degree, a->cell);
+    const int64_t N = a->form == FORM_BURGERS_RES ? nd : (int64_t)nd * nd;
+    if (a->out_stride != N) {
+      if (a->out_stride < N) return fail(COFFEE_ERR_INVALID_ARG, "out_stride is below the element matrix size");
+      if (!(a->form == FORM_MASS || a->form == FORM_HELMHOLTZ || a->form == FORM_ADVDIFF) || a->cell == CELL_PRISM)
+        return fail(COFFEE_ERR_INVALID_ARG,
+                    "out_stride: padded rows for MASS, HELMHOLTZ and ADVDIFF on triangles and tetrahedra only");
+    }
+  }
   return COFFEE_OK;
 }
 
@@ -246,6 +256,7 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
     p.ns = ns;
     p.N = ns * ns;
     p.ndof = ndof;
+    p.ostride = a->out_stride ? a->out_stride : (a->form == FORM_BURGERS_RES ? ndof : (int64_t)ndof * ndof);
     p.nu = a->nu;
     p.validate = validate ? 1 : 0;
     p.map = map;
@@ -275,6 +286,7 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
   p.ncoefnodes = a->ncoefnodes;
   p.ns = ns;
   p.N = ndof * ndof;
+  p.ostride = a->out_stride ? a->out_stride : (a->form == FORM_BURGERS_RES ? ndof : (int64_t)ndof * ndof);
   p.mtiles = meta.mtiles;
   p.kbytes = meta.kbytes;
   p.tparts = meta.tparts;
@@ -718,6 +730,7 @@ int batch_plan_impl(const coffee_assemble_args* groups, int ngroups, int grid, d
     g.p.ncoefnodes = a->ncoefnodes;
     g.p.ns = ns;
     g.p.N = ns * ns;
+    g.p.ostride = ns * ns;  // batches write contiguous rows
     g.p.mtiles = meta.mtiles;
     g.p.kbytes = meta.kbytes;
     g.p.tparts = meta.tparts;

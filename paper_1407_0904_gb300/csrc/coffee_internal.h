@@ -64,6 +64,7 @@ struct Fp64Params {
   void* out;        // double [ncells][ndof][ndof]
   unsigned* err;
   int64_t ncells, nverts, ncoefnodes;
+  int64_t ostride;  // entries between consecutive element matrices (element vectors) in out
   int ns, N, ndof;
   double nu;
   int validate;
@@ -149,6 +150,7 @@ struct TcParams {
   float* out;
   unsigned* err;
   int64_t ncells, nverts, ncoefnodes;
+  int64_t ostride;       // entries between consecutive element matrices in out (N when contiguous)
   int ns, N;             // outputs per cell
   int mtiles, kbytes, tparts;  // tparts: TcTable::tparts
   int ksteps_off;        // Burgers: K-steps of the off-diagonal component blocks

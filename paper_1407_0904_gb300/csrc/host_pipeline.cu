@@ -78,6 +78,7 @@ int coffee_assemble_host(const coffee_assemble_args* a, int chunks, coffee_strea
   if (!a->coords || !a->cell2vert || !a->out)
     return fail(COFFEE_ERR_INVALID_ARG, "coords, cell2vert and out must be non-NULL");
   if (a->nverts <= 0) return fail(COFFEE_ERR_INVALID_ARG, "nverts must be > 0 (it sizes the coordinate copy)");
+  if (a->out_stride != 0) return fail(COFFEE_ERR_INVALID_ARG, "out_stride must be 0 for host buffers");
   const bool has_coef = a->form == FORM_ADVDIFF || burgers_like(a->form);
   if (has_coef && (!a->coef || !a->cell2dof || a->ncoefnodes <= 0))
     return fail(COFFEE_ERR_INVALID_ARG, "this form needs coef, cell2dof and ncoefnodes > 0");

@@ -260,6 +260,7 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
     for (int64_t it = it0; it < it1 && ok; ++it) {
       const BatchGroup& g = groups[cur.at(it)];
       const int N = g.p.N;
+      const int64_t RS = g.p.ostride;  // row stride of the output (N unless padded)
       if (g.lanes) {
         // cells on lanes: thread = cell, its row of N <= 32 outputs from one TMEM load
         const uint32_t slot = rc % RING, round = rc / RING;
@@ -274,8 +275,8 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
           else tmem_ld16(taddr, *reinterpret_cast<uint32_t(*)[16]>(v));
           tmem_wait_ld();
           if (c0 + lane < g.p.ncells) {
-            float* row = g.p.out + (c0 + lane) * N;
-            if ((N & 3) == 0 && (reinterpret_cast<uintptr_t>(g.p.out) & 15) == 0) {
+            float* row = g.p.out + (c0 + lane) * RS;
+            if ((RS & 3) == 0 && (reinterpret_cast<uintptr_t>(g.p.out) & 15) == 0) {
 #pragma unroll
               for (int k4 = 0; k4 < 8; ++k4)
                 if (4 * k4 < N)
@@ -310,13 +311,13 @@ __device__ __forceinline__ void batch_body(const BatchGroup* __restrict__ groups
           tmem_ld32(taddr + 32, v1);
           tmem_wait_ld();
           if (o < N) {
-            float* dst = g.p.out + cbase * N + o;
+            float* dst = g.p.out + cbase * RS + o;
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-              if (j < ncol) __stcs(dst + (int64_t)j * N, __uint_as_float(v0[j]));
+              if (j < ncol) __stcs(dst + (int64_t)j * RS, __uint_as_float(v0[j]));
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-              if (32 + j < ncol) __stcs(dst + (int64_t)(32 + j) * N, __uint_as_float(v1[j]));
+              if (32 + j < ncol) __stcs(dst + (int64_t)(32 + j) * RS, __uint_as_float(v1[j]));
           }
         }
         }

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(128) k_assemble_fp64(const Fp64Params p) {
 #pragma unroll
     for (int r = 0; r < D; ++r) Pm[a][r] = sg * g.adj[a][r];
 
-  double* out = static_cast<double*>(p.out) + (CSR ? 0 : e * (int64_t)p.ndof * p.ndof);
+  double* out = static_cast<double*>(p.out) + (CSR ? 0 : e * p.ostride);
   const int npad = (p.ndof * p.ndof + 3) & ~3;
   auto put = [&](int64_t idx, double v) {
     if constexpr (CSR) {
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(128) k_assemble_fp64(const Fp64Params p) {
     }
     const double* T2 = T + (int64_t)ns * D * nb;
     const double* T3 = T + (int64_t)2 * ns * D * nb;
-    double* outv = static_cast<double*>(p.out) + e * (int64_t)p.ndof;
+    double* outv = static_cast<double*>(p.out) + e * p.ostride;
     for (int i = 0; i < ns; ++i) {
       double R[D];
 #pragma unroll

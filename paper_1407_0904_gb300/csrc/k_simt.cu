@@ -110,11 +110,14 @@ __global__ void __launch_bounds__(SIMT_THREADS) k_assemble_simt(const TcParams p
       st[lane * SR + o] = a;
     }
     __syncwarp();
-    // the 32 rows are contiguous in the output: 32 N floats from c0 N on (16-byte aligned when
-    // the output is, since 32 N floats are a multiple of 16 bytes)
+    // contiguous rows (the default layout): the 32 rows are 32 N floats from c0 N on (16-byte
+    // aligned when the output is, since 32 N floats are a multiple of 16 bytes); padded rows
+    // (a row stride above N): each row's N floats with coalesced scalar stores
     const int rows = (int)(p.ncells - c0 < 32 ? p.ncells - c0 : 32);
-    float* dst = p.out + c0 * N;
-    if (rows == 32 && vec) {
+    float* dst = p.out + c0 * p.ostride;
+    if (p.ostride != N) {
+      for (int i = lane; i < rows * N; i += 32) __stcs(dst + (int64_t)(i / N) * p.ostride + i % N, st[(i / N) * SR + i % N]);
+    } else if (rows == 32 && vec) {
 #pragma unroll 4
       for (int i = lane; i < 8 * N; i += 32) {  // 8 N float4 per warp tile
         float4 v;

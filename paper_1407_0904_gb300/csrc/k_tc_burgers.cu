@@ -96,26 +96,42 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
     const int grp = pw >> 2, row = ((pw & 3) << 5) + lane;
     const int spg = nstages / PROD_GROUPS;
     bool ok = true;
+    // index rows one tile ahead (the next tile of this group): the coordinate and u gathers of
+    // a tile then wait on one level of loads instead of two
+    int nvid[NV], ndid[NS];
+    {
+      const int64_t e0 = (blockIdx.x + (int64_t)grp * gridDim.x) * BN + row;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) nvid[v] = e0 < p.ncells ? __ldg(p.c2v + e0 * NV + v) : 0;
+#pragma unroll
+      for (int r = 0; r < NS; ++r) ndid[r] = e0 < p.ncells ? __ldg(p.c2d + e0 * NS + r) : 0;
+    }
     for (int64_t tl = grp; ok; tl += PROD_GROUPS) {  // local tile number; groups alternate
       const int64_t t = blockIdx.x + tl * gridDim.x;
       if (t >= ntiles) break;
       int64_t li = (tl / PROD_GROUPS) * S::NCHT;  // index among this group's chunks
       const int64_t e = t * BN + row;
+      int vid[NV], did[NS];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) vid[v] = nvid[v];
+#pragma unroll
+      for (int r = 0; r < NS; ++r) did[r] = ndid[r];
+      {
+        const int64_t en = e + (int64_t)PROD_GROUPS * gridDim.x * BN;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) nvid[v] = en < p.ncells ? __ldg(p.c2v + en * NV + v) : 0;
+#pragma unroll
+        for (int r = 0; r < NS; ++r) ndid[r] = en < p.ncells ? __ldg(p.c2d + en * NS + r) : 0;
+      }
       float u[NS][D], Pm[D][D], H[P];
       bool live = e < p.ncells, bad = false;
       if (live) {
-        int vid[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          vid[v] = __ldg(p.c2v + e * NV + v);
+        for (int v = 0; v < NV; ++v)
           if (p.validate && (vid[v] < 0 || vid[v] >= p.nverts)) bad = true;
-        }
-        int did[NS];
 #pragma unroll
-        for (int r = 0; r < NS; ++r) {
-          did[r] = __ldg(p.c2d + e * NS + r);
+        for (int r = 0; r < NS; ++r)
           if (p.validate && (did[r] < 0 || did[r] >= p.ncoefnodes)) bad = true;
-        }
         if (bad) {
           atomicOr(p.err, ERR_INDEX);
           live = false;

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
   } else if constexpr (LANES) {
     // ---------------- epilogue, cells on lanes: each thread writes its cell's row ----------------
     const int q = warp;  // lanes 32q..32q+31 = cells of the tile
-    const bool vec = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(p.out) & 15) == 0;
+    const bool vec = (p.ostride & 3) == 0 && (reinterpret_cast<uintptr_t>(p.out) & 15) == 0;
     uint32_t rc = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++rc) {
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
       if (!mbar_wait(smem_u32(&bars->tfull[slot]), round & 1u, p.err)) { ok = false; break; }
       tc_fence_after();
       const int64_t cell = t * BN + q * 32 + lane;
-      float* row = p.out + cell * N;
+      float* row = p.out + cell * p.ostride;
       if (t * BN + q * 32 < p.ncells) {  // warp-uniform
         for (int c0 = 0; c0 < NP; c0 += 32) {
           uint32_t v[32];
@@ -344,8 +344,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_assemble_tc(const TcParams p, i
             if (cw == 64) tmem_ld32(taddr + 32, v1);
             tmem_wait_ld();
             if (o < N) {
-              float* dst = p.out + cbase * N + o;
-              const int64_t stride = N;
+              float* dst = p.out + cbase * p.ostride + o;
+              const int64_t stride = p.ostride;
               if (ncol == 64) {
 #pragma unroll
                 for (int jj = 0; jj < 32; ++jj) __stcs(dst + jj * stride, __uint_as_float(v0[jj]));

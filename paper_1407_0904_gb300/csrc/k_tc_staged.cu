@@ -39,7 +39,8 @@ cudaError_t launch_staged_prec(const TcParams& p, int num_sms, cudaStream_t s, i
 }  // namespace
 
 int staged_plan(const TcParams& p, int& subw, int& cells, int& buf_bytes) {
-  if (p.mtiles > STAGE_MAXM || (reinterpret_cast<uintptr_t>(p.out) & 15) != 0) return 0;
+  // rows gathered for one bulk copy must be contiguous in the output
+  if (p.mtiles > STAGE_MAXM || (reinterpret_cast<uintptr_t>(p.out) & 15) != 0 || p.ostride != p.N) return 0;
   // cells per accumulator: the explicit knob if every slice of a sub-tile fits the 512 TMEM
   // columns, else the widest that leaves room for two sub-tiles, else for one
   int w = (p.tune & TUNE_SUB32) ? 32 : (p.tune & TUNE_SUB64) ? 64 : (p.tune & TUNE_SUB128) ? 128 : 0;
