@@ -171,6 +171,9 @@ def parse():
     ap.add_argument("--out-stride", type=int, default=0,
                     help="entries between consecutive element matrices (padded rows; 0 = contiguous). "
                          "-1: the matrix size rounded up to 32 entries (128-byte rows)")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "tensor-cores", "cuda-cores"],
+                    help="small element matrices: force the tcgen05 or the FP32 CUDA-core kernel "
+                         "(auto: the library's choice)")
     ap.add_argument("--no-coef-f32", action="store_true",
                     help="tensor-core kernels convert the FP64 coefficients per cell instead of reading the "
                          "float copy that each step rounds once per node")
@@ -373,7 +376,13 @@ def run_ours(args):
 
     # the kernel family the library runs for this workload (the FP32 CUDA-core kernel for small
     # element matrices, where it is faster than the tensor cores)
-    path = coffee.assemble_path(form, degree, cell, prec, coffee.binding._tuned_flags(form, degree, cell, prec))
+    force = {"auto": 0, "tensor-cores": coffee.FLAG_TENSOR_CORES, "cuda-cores": coffee.FLAG_CUDA_CORES}[args.kernel]
+    tune = None
+    if force:
+        tune = force | (coffee.binding._tuned_flags(form, degree, cell, prec)
+                        & ~(coffee.FLAG_TENSOR_CORES | coffee.FLAG_CUDA_CORES))
+    path = coffee.assemble_path(form, degree, cell, prec,
+                                tune if tune is not None else coffee.binding._tuned_flags(form, degree, cell, prec))
     mesh, coef_np, c2d_np = wl.build(args.nx)
     ndof = coffee.ndof(form, degree, cell)
     coords = torch.from_numpy(mesh.coords).to(dev)
@@ -400,7 +409,8 @@ def run_ours(args):
         if cf32 is not None and precision != coffee.FP64:
             coffee.round_coef(coef, out=cf32)
         coffee.assemble(form, degree, cell, coords, c2v, coef, c2d, precision=precision, out=o,
-                        coef_f32=cf32 if precision != coffee.FP64 else None, out_stride=ostride or None)
+                        coef_f32=cf32 if precision != coffee.FP64 else None, out_stride=ostride or None,
+                        tune=tune if precision != coffee.FP64 else None)
 
     # one checked launch before timing (parity against the oracle is the test suite's job)
     step(prec, out)
