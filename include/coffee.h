@@ -140,6 +140,15 @@ typedef enum {
  * instance). Results of the two differ by rounding, within the precision's bound. */
 #define COFFEE_FLAG_TENSOR_CORES 512u
 #define COFFEE_FLAG_CUDA_CORES 1024u
+/* BURGERS_JAC on the tensor cores with component blocks of at most 128 entries (triangles
+ * P1-P3, tetrahedra P1-P2) has two forms: the block form (every component block contracted over
+ * [T1 | T2 | T3]) and the factored form, block(ci, cj) = sum_a P[a][cj] V_a^ci + [ci == cj] C
+ * with V_a^ci = sum_r u[r][ci] T1[r, a] contracted on the tensor cores and P = |det J| K applied
+ * per cell in the epilogue. The factored form is the default for tetrahedra P2 (measured faster
+ * there), the block form elsewhere; these flags force one. Results agree within the precision's
+ * bound. */
+#define COFFEE_FLAG_BURGERS_BLOCKS 2048u
+#define COFFEE_FLAG_BURGERS_FACTORED 4096u
 
 /* Number of rows of the element matrix (or length of the element vector): (k+1)(k+2)/2
  * (triangle), (k+1)(k+2)(k+3)/6 (tetrahedron) or (k+1)^2(k+2)/2 (prism), times d for

@@ -25,6 +25,8 @@ FLAG_CELL_LANES = 64    # tuning knob: cells on the TMEM lanes (element matrices
 FLAG_STAGED_STORE = 256  # tuning knob: rows staged in shared memory, written by bulk copies
 FLAG_TENSOR_CORES = 512  # small element matrices: force the tcgen05 kernel
 FLAG_CUDA_CORES = 1024   # small element matrices: force the FP32 CUDA-core kernel
+FLAG_BURGERS_BLOCKS = 2048    # Burgers Jacobian: the block form (every block over [T1|T2|T3])
+FLAG_BURGERS_FACTORED = 4096  # Burgers Jacobian: the factored form (T1 against u, P in the epilogue)
 
 FORM_NAMES = {MASS: "mass", HELMHOLTZ: "helmholtz", ADVDIFF: "advdiff", BURGERS_JAC: "burgers_jac",
               BURGERS_RESIDUAL: "burgers_residual"}

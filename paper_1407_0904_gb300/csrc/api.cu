@@ -293,13 +293,18 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
   p.ksteps_off = meta.ksteps_off;
   p.aexact = meta.aexact;
   p.scale_off = meta.scale_off;
+  p.aux_off = meta.aux_off;
+  p.aux_vparts = meta.aux_vparts;
+  p.aux_cparts = meta.aux_cparts;
   p.tune = ((a->flags & COFFEE_FLAG_OUTPUT_LANES) ? TUNE_OUTPUT_LANES : 0u) |
            ((a->flags & COFFEE_FLAG_TWO_STAGES) ? TUNE_TWO_STAGES : 0u) |
            ((a->flags & COFFEE_FLAG_SUBTILE_64) ? TUNE_SUB64 : 0u) |
            ((a->flags & COFFEE_FLAG_SUBTILE_32) ? TUNE_SUB32 : 0u) |
            ((a->flags & COFFEE_FLAG_SUBTILE_128) ? TUNE_SUB128 : 0u) |
            ((a->flags & COFFEE_FLAG_CELL_LANES) ? TUNE_CELL_LANES : 0u) |
-           ((a->flags & COFFEE_FLAG_STAGED_STORE) ? TUNE_STAGED_STORE : 0u);
+           ((a->flags & COFFEE_FLAG_STAGED_STORE) ? TUNE_STAGED_STORE : 0u) |
+           ((a->flags & COFFEE_FLAG_BURGERS_BLOCKS) ? TUNE_BURGERS_BLOCKS : 0u) |
+           ((a->flags & COFFEE_FLAG_BURGERS_FACTORED) ? TUNE_BURGERS_FACTORED : 0u);
   p.precision = a->precision;
   p.validate = validate ? 1 : 0;
   p.nu = a->nu;

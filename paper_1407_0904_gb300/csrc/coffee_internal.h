@@ -31,7 +31,8 @@ COFFEE_HD constexpr int prec_gparts(int prec) {
 enum : unsigned { ERR_INDEX = 1u, ERR_TIMEOUT = 2u, ERR_CAPACITY = 4u };
 // Tuning knobs of the tensor-core kernels (from coffee_assemble_args.flags)
 enum : unsigned { TUNE_OUTPUT_LANES = 1u, TUNE_TWO_STAGES = 2u, TUNE_SUB64 = 4u, TUNE_SUB32 = 8u, TUNE_SUB128 = 16u,
-                  TUNE_CELL_LANES = 32u, TUNE_STAGED_STORE = 128u };
+                  TUNE_CELL_LANES = 32u, TUNE_STAGED_STORE = 128u, TUNE_BURGERS_BLOCKS = 256u,
+                  TUNE_BURGERS_FACTORED = 512u };
 
 // ---- host tabulation (tabulate.cpp) ----
 int nnodes(int cell, int k);
@@ -137,6 +138,8 @@ struct TcTable {
   int aexact;            // 1: every A column is an integer vector times a scale, so A is held
                          // exactly in one part and the scales (float [kelems]) follow the tiles
   int64_t scale_off;     // byte offset of those scales in the image
+  int64_t aux_off;       // Burgers Jacobian: offset of the factored-form image (0: none)
+  int aux_vparts, aux_cparts;  // its parts of the T1 and of the T2|T3 operands
 };
 
 struct TcParams {
@@ -166,6 +169,8 @@ struct TcParams {
   int nkc;               // prisms: K-chunks of the streamed contraction
   int aexact;            // TcTable::aexact
   int64_t scale_off;     // TcTable::scale_off
+  int64_t aux_off;       // TcTable::aux_off
+  int aux_vparts, aux_cparts;
 };
 int tc_supported(int form, int degree, int cell, int precision);
 // staged epilogue (k_tc_staged.cu): its sub-tile width, rows per bulk copy and the bytes of one
@@ -192,6 +197,14 @@ int launch_burgers_stream_tc(int cell, int degree, const TcParams& p, int num_sm
 // Burgers-residual (element vector) tensor-core kernel (k_tc_burgers_res.cu)
 int burgers_res_tc_supported(int degree, int cell, int precision);
 void build_burgers_res_image(int degree, int cell, int prec, std::vector<uint8_t>& img, TcTable& meta);
+// integer form of an operand column (k_tc_burgers.cu): x = n * scale with n exact in the type
+bool integer_column(const std::vector<double>& x, bool tf32, double& scale, std::vector<double>& n);
+// Burgers Jacobian in the factored form (k_tc_burgers_fact.cu): element matrices of at most 128
+// entries per component block; the image is appended to the block kernel's (TcTable::aux_off)
+int burgers_fact_supported(int degree, int cell, int precision);
+int burgers_fact_default(int degree, int cell);
+void build_burgers_fact_image(int degree, int cell, int prec, std::vector<uint8_t>& img, int& vparts, int& cparts);
+int launch_burgers_fact_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
 int launch_burgers_res_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
 // ---- mixed-batch persistent kernel (k_batch.cu) ----
 struct BatchGroup {

@@ -390,7 +390,6 @@ int burgers_tc_supported(int degree, int cell, int precision) {
   return burgers_stream_supported(degree, cell, precision);
 }
 
-namespace {
 // Integer form of one A column: x[o] = n[o] * scale for all o, with integers the operand type
 // holds exactly (odd part below 2^11 for tf32, 2^8 for bf16). The smallest multiplier N of
 // x / max|x| that lands every entry on an integer (to 1e-9) is taken; the reconstruction
@@ -421,7 +420,6 @@ bool integer_column(const std::vector<double>& x, bool tf32, double& scale, std:
   }
   return false;
 }
-}  // namespace
 
 void build_burgers_image(int degree, int cell, int prec, bool exact_ok, std::vector<uint8_t>& img, TcTable& meta) {
   if (exact_ok && !burgers_resident(degree, cell, prec)) {  // the Jacobian on the streamed kernel
@@ -480,11 +478,27 @@ void build_burgers_image(int degree, int cell, int prec, bool exact_ok, std::vec
   meta.tile_bytes = tile;
   meta.aexact = exact ? 1 : 0;
   meta.scale_off = exact ? a_bytes : 0;
+  // the factored-form kernel's operands follow, 1024-byte aligned, where that kernel applies
+  if (exact_ok && burgers_fact_supported(degree, cell, prec)) {
+    std::vector<uint8_t> aux;
+    int vparts = 0, cparts = 0;
+    build_burgers_fact_image(degree, cell, prec, aux, vparts, cparts);
+    const size_t off = (img.size() + 1023) & ~(size_t)1023;
+    img.resize(off + aux.size(), 0);
+    std::memcpy(img.data() + off, aux.data(), aux.size());
+    meta.aux_off = (int64_t)off;
+    meta.aux_vparts = vparts;
+    meta.aux_cparts = cparts;
+  }
 }
 
 int launch_burgers_tc(int cell, const TcParams& p, int num_sms, void* stream, std::string& why) {
   if (p.ncells == 0) return (int)cudaSuccess;
   const int degree = degree_of(cell, p.ns);
+  // the factored form where it is the faster one, or where it is asked for
+  if (p.aux_off != 0 && !(p.tune & TUNE_BURGERS_BLOCKS) &&
+      (burgers_fact_default(degree, cell) || (p.tune & TUNE_BURGERS_FACTORED)))
+    return launch_burgers_fact_tc(cell, p, num_sms, stream, why);
   if (!burgers_resident(degree, cell, p.precision)) return launch_burgers_stream_tc(cell, degree, p, num_sms, stream, why);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   BGeom g{};

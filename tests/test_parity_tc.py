@@ -49,6 +49,47 @@ def test_tc_matches_oracle(form, cell, k, prec):
     assert err < TOL[prec]
 
 
+BURGERS_FORMS = [(c, k, p) for c, ks in ((TRI, (1, 2, 3)), (TET, (1, 2))) for k in ks
+                 for p in (coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16)]
+
+
+@pytest.mark.parametrize("cell,k,prec", BURGERS_FORMS)
+def test_burgers_block_form_when_forced(cell, k, prec):
+    """Component blocks of at most 128 entries have two forms: the block form (every block
+    contracted over [T1 | T2 | T3]) and the factored form (T1 against u, P applied in the
+    epilogue); each forced by its flag meets the bounds against the oracle."""
+    mesh = ragged_mesh(cell, seed=60 + k)
+    coef, c2d = coefficients(BURGERS_JAC, mesh, k, seed=61)
+    ref = oracle_ref(BURGERS_JAC, k, cell, mesh, coef, c2d)
+    x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    blocks = coffee.assemble(BURGERS_JAC, k, cell, x, c2v, cf, cd, precision=prec, validate=True,
+                             tune=coffee.FLAG_BURGERS_BLOCKS)
+    fact = coffee.assemble(BURGERS_JAC, k, cell, x, c2v, cf, cd, precision=prec, validate=True,
+                           tune=coffee.FLAG_BURGERS_FACTORED)
+    coffee.check_errors()
+    eb = rel_err_per_cell(blocks.cpu().numpy(), ref)
+    ef = rel_err_per_cell(fact.cpu().numpy(), ref)
+    print("burgers %s P%d %s: blocks %.3e factored %.3e" % ("tri" if cell == TRI else "tet", k,
+                                                           coffee.PRECISION_NAMES[prec], eb, ef))
+    assert eb < TOL[prec] and ef < TOL[prec]
+
+
+@pytest.mark.parametrize("ncells", [1, 63, 64, 65, 127, 128, 129, 191, 257])
+def test_burgers_factored_tile_edges(ncells):
+    """64-cell tiles in pairs: single tiles, odd tile counts and ragged last tiles; nothing
+    written past the last cell."""
+    mesh = meshgen.tet_mesh(4, perturb=0.15, seed=62, ncells=ncells)
+    coef, c2d = coefficients(BURGERS_JAC, mesh, 2, seed=63)
+    ref = oracle_ref(BURGERS_JAC, 2, TET, mesh, coef, c2d)
+    x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    out = torch.full((ncells + 2, 30, 30), 7.0, dtype=torch.float32, device=DEV)
+    coffee.assemble(BURGERS_JAC, 2, TET, x, c2v, cf, cd, precision=coffee.TF32X3, out=out[:ncells])
+    torch.cuda.synchronize()
+    coffee.check_errors()
+    assert rel_err_per_cell(out[:ncells].cpu().numpy(), ref) < 1e-5
+    assert torch.all(out[ncells:] == 7.0)
+
+
 @pytest.mark.parametrize("ncells", [1, 127, 128, 129, 255, 257])
 def test_tile_edges(ncells):
     mesh = meshgen.tet_mesh(4, perturb=0.15, seed=3, ncells=ncells)
