@@ -671,8 +671,8 @@ def run_special(args):
         plan.launch()
         coffee.check_errors()
         step = plan.launch
-        kernel = "k_batch_tc"
-        launches_per_step = 1
+        kernel = "k_batch_tc + k_simt_batch (small element matrices)" if plan.launches == 2 else "k_batch_tc"
+        launches_per_step = plan.launches
         note = None
     elif args.workload == "global-helmholtz-p3-tet":
         k = 3

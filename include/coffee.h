@@ -323,15 +323,20 @@ int coffee_assemble_backward(const coffee_assemble_args* a, const void* dout,
 int coffee_assemble_backward_noalloc(const coffee_assemble_args* a, const void* dout,
                                      double* d_coords, double* d_coef, coffee_stream_t stream);
 
-/* Mixed batch: several (form, degree, cell) groups assembled by ONE persistent launch
- * (the paper runs one specialised kernel per form, degree and cell shape, sections 4-5).
+/* Mixed batch: several (form, degree, cell) groups assembled by one persistent tensor-core
+ * launch (the paper runs one specialised kernel per form, degree and cell shape, sections 4-5),
+ * plus one launch of the CUDA-core kernel for the groups of small element matrices that run
+ * there by default (P1 simplices and P2 triangles; coffee_assemble_path), unless groups[0].flags
+ * has COFFEE_FLAG_TENSOR_CORES, which keeps every group on the tensor cores.
  * Each group is a coffee_assemble_args (its own inputs, output and cell count); all groups
  * share one tensor-core precision and are MASS, HELMHOLTZ or ADVDIFF. The plan (host)
- * uploads the groups' tables, cuts every group into 128-cell tiles and gives each CTA a
- * contiguous range of tiles of about equal cost (bytes written + item_overhead per
- * 128-output slice). Planning allocates device memory and synchronises; launching only
- * enqueues one kernel, so it can be captured in a CUDA graph. The plan refers to the
- * groups' device buffers, which must stay valid while it is launched.
+ * uploads the groups' tables, cuts every tensor-core group into 128-cell tiles and gives each
+ * CTA a contiguous range of tiles of about equal cost (bytes written + item_overhead per
+ * 128-output slice), and numbers the CUDA-core groups' 32-cell warp tiles across the groups.
+ * Planning allocates device memory and synchronises; launching only enqueues the (at most two)
+ * kernels, so it can be captured in a CUDA graph. The plan refers to the groups' device
+ * buffers, which must stay valid while it is launched. Every group's result equals, bit for
+ * bit, its own coffee_assemble_ex on the same kernel family.
  *   grid <= 0 selects one CTA per SM; item_overhead < 0 selects the default (16384). */
 int coffee_batch_plan(const coffee_assemble_args* groups, int ngroups, int grid, double item_overhead,
                       void** plan);

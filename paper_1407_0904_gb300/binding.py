@@ -539,13 +539,16 @@ def batch_split(costs, grid):
 
 
 class BatchPlan:
-    """Several (form, degree, cell) groups assembled by one persistent launch.
+    """Several (form, degree, cell) groups assembled by one persistent tensor-core launch, plus
+    one CUDA-core launch for the groups of small element matrices that run there by default
+    (P1 simplices, P2 triangles), unless all_tensor_cores.
 
     groups: list of dicts with keys form, degree, cell, coords, cell2vert and optionally
     coef, cell2dof, out, coords_split (split_coords of coords), coef_f32 (round_coef of coef).
     All groups use `precision`
     (a tensor-core precision).
-    launch() only enqueues one kernel on the current stream (CUDA-graph capturable).
+    launch() only enqueues the plan's kernels (`launches` of them) on the current stream
+    (CUDA-graph capturable).
 
     Work is split over the CTAs by cost. costs="measured" (default) takes each group's time
     per 128-cell tile from the autotuner's cache for this GPU (coffee_batch_plan_costs) and
@@ -554,7 +557,7 @@ class BatchPlan:
     model; a list gives one tile cost per group."""
 
     def __init__(self, groups, precision=TF32X3, grid=0, item_overhead=-1.0, validate=False,
-                 costs="measured"):
+                 costs="measured", all_tensor_cores=False):
         L = lib()
         L.coffee_batch_plan.argtypes = [ctypes.POINTER(AssembleArgs), ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]
@@ -569,7 +572,8 @@ class BatchPlan:
             a, out = make_args(g["form"], g["degree"], g["cell"], g["coords"], g["cell2vert"],
                                g.get("coef"), g.get("cell2dof"), precision, g.get("out"),
                                g.get("nu", 0.01), validate, coords_split=g.get("coords_split"),
-                               coef_f32=g.get("coef_f32"))
+                               coef_f32=g.get("coef_f32"),
+                               tune=FLAG_TENSOR_CORES if (all_tensor_cores and i == 0) else 0)
             arr[i] = a
             self.outputs.append(out)
             self._keep.append((g["coords"], g["cell2vert"], g.get("coef"), g.get("cell2dof"), out,
@@ -580,6 +584,9 @@ class BatchPlan:
                 item_overhead = float(_tune.load_batch().get("item_overhead", -1.0))
             except Exception:
                 item_overhead = -1.0
+        simt = [not all_tensor_cores and assemble_path(g["form"], g["degree"], g["cell"], precision) == 2
+                for g in groups]
+        self.launches = int(any(simt)) + int(not all(simt))
         if isinstance(costs, str):
             costs = self.measured_costs(groups, precision) if costs == "measured" else None
         self.costs = costs

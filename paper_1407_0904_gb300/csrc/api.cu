@@ -671,6 +671,10 @@ struct BatchPlanImpl {
   BatchLaunch L{};
   BatchGroup* d_groups = nullptr;
   int64_t* d_ranges = nullptr;
+  SimtGroup* d_sgroups = nullptr;  // the CUDA-core groups
+  int nsg = 0;
+  int64_t stiles = 0;
+  int num_sms = 0;
   int device = 0;
 };
 }  // namespace
@@ -712,16 +716,47 @@ int batch_plan_impl(const coffee_assemble_args* groups, int ngroups, int grid, d
   DeviceCache* c = nullptr;
   int rc = device_cache(&c);
   if (rc != COFFEE_OK) return rc;
-  std::vector<BatchGroup> hg(ngroups);
+  std::vector<BatchGroup> hg;
+  std::vector<SimtGroup> sg;
   std::vector<double> cost;  // per work item
   int kbytes_max = 32;
-  int64_t items = 0;
+  int64_t items = 0, stiles = 0;
+  const bool all_tc = (groups[0].flags & COFFEE_FLAG_TENSOR_CORES) != 0;
   for (int i = 0; i < ngroups; ++i) {
     const coffee_assemble_args* a = &groups[i];
+    const int ns = nnodes(a->cell, a->degree);
+    if (!all_tc && simt_supported(a->form, a->degree, a->cell) && simt_default(a->form, a->degree, a->cell)) {
+      // CUDA-core group: the standalone kernel's parameters, warp tiles numbered on
+      cudaError_t eu = (cudaError_t)simt_upload(a->form, a->degree, a->cell);
+      if (eu != cudaSuccess) return cuda_fail(eu, "coffee_batch_plan (reference tensor)");
+      SimtGroup s{};
+      s.p.coords = a->coords;
+      s.p.c2v = a->cell2vert;
+      s.p.coef = a->coef;
+      s.p.c2d = a->cell2dof;
+      s.p.out = static_cast<float*>(a->out);
+      s.p.err = c->err;
+      s.p.ncells = a->ncells;
+      s.p.nverts = a->nverts;
+      s.p.ncoefnodes = a->ncoefnodes;
+      s.p.ns = ns;
+      s.p.N = ns * ns;
+      s.p.ostride = ns * ns;
+      s.p.precision = prec;
+      s.p.xs = a->coords_split;
+      s.p.cf = a->coef_f32;
+      s.p.validate = (a->flags & COFFEE_FLAG_VALIDATE) ? 1 : 0;
+      s.p.nu = a->nu;
+      s.tile0 = stiles;
+      s.kind = simt_kind(a->form, a->degree, a->cell);
+      stiles += (a->ncells + 31) / 32;
+      sg.push_back(s);
+      continue;
+    }
     TcTable meta{};
     if ((rc = tc_table(*c, a->form, a->degree, a->cell, prec, &meta)) != COFFEE_OK) return rc;
-    const int ns = nnodes(a->cell, a->degree);
-    BatchGroup& g = hg[i];
+    hg.emplace_back();
+    BatchGroup& g = hg.back();
     std::memset(&g, 0, sizeof(g));
     g.p.coords = a->coords;
     g.p.c2v = a->cell2vert;
@@ -758,31 +793,45 @@ int batch_plan_impl(const coffee_assemble_args* groups, int ngroups, int grid, d
     }
     items += nt;
   }
-  if (items == 0) return fail(COFFEE_ERR_INVALID_ARG, "all groups are empty");
-  int nstages = 0;
-  const int smem = batch_smem(kbytes_max, prec, &nstages);
-  if (smem == 0) return fail(COFFEE_ERR_UNSUPPORTED, "batch operands do not fit in shared memory");
+  if (items == 0 && stiles == 0) return fail(COFFEE_ERR_INVALID_ARG, "all groups are empty");
+  const int ntc = (int)hg.size();
+  int nstages = 0, smem = 0;
+  if (items > 0) {
+    smem = batch_smem(kbytes_max, prec, &nstages);
+    if (smem == 0) return fail(COFFEE_ERR_UNSUPPORTED, "batch operands do not fit in shared memory");
+  }
   if (grid <= 0) grid = c->num_sms;
-  grid = (int)std::min<int64_t>(grid, items);
-  std::vector<int64_t> ranges(grid + 1);
-  split_by_cost(cost.data(), items, grid, ranges.data());
+  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, items));
+  std::vector<int64_t> ranges(grid + 1, 0);
+  if (items > 0) split_by_cost(cost.data(), items, grid, ranges.data());
   auto* P = new BatchPlanImpl();
   cudaGetDevice(&P->device);
-  cudaError_t e = cudaMalloc(&P->d_groups, sizeof(BatchGroup) * ngroups);
-  if (e == cudaSuccess) e = cudaMalloc(&P->d_ranges, sizeof(int64_t) * (grid + 1));
-  if (e == cudaSuccess)
-    e = cudaMemcpy(P->d_groups, hg.data(), sizeof(BatchGroup) * ngroups, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(P->d_ranges, ranges.data(), sizeof(int64_t) * (grid + 1), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = (cudaError_t)batch_prepare(prec, smem);
+  cudaError_t e = cudaSuccess;
+  if (ntc > 0) {
+    e = cudaMalloc(&P->d_groups, sizeof(BatchGroup) * ntc);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_ranges, sizeof(int64_t) * (grid + 1));
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_groups, hg.data(), sizeof(BatchGroup) * ntc, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(P->d_ranges, ranges.data(), sizeof(int64_t) * (grid + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = (cudaError_t)batch_prepare(prec, smem);
+  }
+  if (e == cudaSuccess && !sg.empty()) {
+    e = cudaMalloc(&P->d_sgroups, sizeof(SimtGroup) * sg.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(P->d_sgroups, sg.data(), sizeof(SimtGroup) * sg.size(), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     cudaFree(P->d_groups);
     cudaFree(P->d_ranges);
+    cudaFree(P->d_sgroups);
     delete P;
     return cuda_fail(e, "coffee_batch_plan");
   }
+  P->nsg = (int)sg.size();
+  P->stiles = stiles;
+  P->num_sms = c->num_sms;
   P->L.groups = P->d_groups;
-  P->L.ngroups = ngroups;
+  P->L.ngroups = ntc;
   P->L.ranges = P->d_ranges;
   P->L.grid = grid;
   P->L.smem = smem;
@@ -822,8 +871,14 @@ int coffee_batch_split(const double* cost, int64_t items, int grid, int64_t* ran
 int coffee_batch_launch(void* plan, coffee_stream_t stream) {
   if (!plan) return fail(COFFEE_ERR_INVALID_ARG, "plan is NULL");
   auto* P = static_cast<BatchPlanImpl*>(plan);
-  cudaError_t e = (cudaError_t)batch_launch(P->L, stream);
-  if (e != cudaSuccess) return cuda_fail(e, "launch(batch)");
+  if (P->nsg > 0) {
+    cudaError_t e = (cudaError_t)launch_simt_batch(P->d_sgroups, P->nsg, P->stiles, P->num_sms, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch(batch, CUDA cores)");
+  }
+  if (P->L.ngroups > 0) {
+    cudaError_t e = (cudaError_t)batch_launch(P->L, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch(batch)");
+  }
   return COFFEE_OK;
 }
 
@@ -832,6 +887,7 @@ void coffee_batch_free(void* plan) {
   auto* P = static_cast<BatchPlanImpl*>(plan);
   cudaFree(P->d_groups);
   cudaFree(P->d_ranges);
+  cudaFree(P->d_sgroups);
   delete P;
 }
 

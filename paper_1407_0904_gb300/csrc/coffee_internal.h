@@ -185,6 +185,15 @@ void tc_reference_tensor(int form, int degree, int cell, std::vector<double>& T)
 int simt_supported(int form, int degree, int cell);
 int simt_default(int form, int degree, int cell);
 int launch_simt(int form, int degree, int cell, const TcParams& p, int num_sms, void* stream, std::string& why);
+// the CUDA-core share of a mixed batch: groups whose 32-cell warp tiles are numbered from tile0
+struct SimtGroup {
+  TcParams p;
+  int64_t tile0;
+  int kind;  // simt_kind(form, degree, cell)
+};
+int simt_kind(int form, int degree, int cell);
+int simt_upload(int form, int degree, int cell);
+int launch_simt_batch(const SimtGroup* groups, int ngroups, int64_t ntiles, int num_sms, void* stream);
 // Burgers-Jacobian tensor-core kernel (k_tc_burgers.cu)
 int burgers_tc_supported(int degree, int cell, int precision);
 void build_burgers_image(int degree, int cell, int prec, bool exact_ok, std::vector<uint8_t>& img, TcTable& meta);

@@ -77,61 +77,101 @@ __device__ __forceinline__ void simt_ids(const TcParams& p, int64_t e, bool v4, 
   load_ids<FORM, D>(p, e, ids);
 }
 
+// One warp tile: the 32 cells from 32 t on, staged in st (32 rows of SR = N | 1 floats).
 template <int FORM, int D, int DEG>
-__global__ void __launch_bounds__(SIMT_THREADS) k_assemble_simt(const TcParams p) {
+__device__ __forceinline__ void simt_tile(const TcParams& p, int64_t t, int lane, float* st) {
   constexpr int NS = s_ns(D, DEG), N = NS * NS, K = s_K(FORM, D), OFF = s_off(FORM, D, DEG);
   constexpr int SR = N | 1;  // staging row stride
-  extern __shared__ float stage[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* st = stage + warp * 32 * SR;
-  const int64_t ntiles = (p.ncells + 31) / 32;
   const bool vec = (reinterpret_cast<uintptr_t>(p.out) & 15) == 0;
   const bool v4 = (reinterpret_cast<uintptr_t>(p.c2v) & 15) == 0 &&
                   (FORM != FORM_ADVDIFF || (reinterpret_cast<uintptr_t>(p.c2d) & 15) == 0);
-  for (int64_t t = (int64_t)blockIdx.x * SIMT_WARPS + warp; t < ntiles; t += (int64_t)gridDim.x * SIMT_WARPS) {
-    const int64_t c0 = t * 32, e = c0 + lane;
-    float G[K];
-    bool bad = false;
-    if (e < p.ncells) {
-      CellIds<FORM, D> ids;
-      simt_ids<FORM, D>(p, e, v4, ids);
-      cell_factors_ids<FORM, D, K, true>(p, ids, G, bad);
-      if (bad) atomicOr(p.err, ERR_INDEX);
-    }
-    if (e >= p.ncells || bad) {
+  const int64_t c0 = t * 32, e = c0 + lane;
+  float G[K];
+  bool bad = false;
+  if (e < p.ncells) {
+    CellIds<FORM, D> ids;
+    simt_ids<FORM, D>(p, e, v4, ids);
+    cell_factors_ids<FORM, D, K, true>(p, ids, G, bad);
+    if (bad) atomicOr(p.err, ERR_INDEX);
+  }
+  if (e >= p.ncells || bad) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) G[k] = 0.f;
-    }
+    for (int k = 0; k < K; ++k) G[k] = 0.f;
+  }
 #pragma unroll
-    for (int o = 0; o < N; ++o) {
-      float a = 0.f;
+  for (int o = 0; o < N; ++o) {
+    float a = 0.f;
 #pragma unroll
-      for (int k = 0; k < K; ++k) a = fmaf(G[k], c_T[OFF + k * N + o], a);
-      st[lane * SR + o] = a;
-    }
-    __syncwarp();
-    // contiguous rows (the default layout): the 32 rows are 32 N floats from c0 N on (16-byte
-    // aligned when the output is, since 32 N floats are a multiple of 16 bytes); padded rows
-    // (a row stride above N): each row's N floats with coalesced scalar stores
-    const int rows = (int)(p.ncells - c0 < 32 ? p.ncells - c0 : 32);
-    float* dst = p.out + c0 * p.ostride;
-    if (p.ostride != N) {
-      for (int i = lane; i < rows * N; i += 32) __stcs(dst + (int64_t)(i / N) * p.ostride + i % N, st[(i / N) * SR + i % N]);
-    } else if (rows == 32 && vec) {
+    for (int k = 0; k < K; ++k) a = fmaf(G[k], c_T[OFF + k * N + o], a);
+    st[lane * SR + o] = a;
+  }
+  __syncwarp();
+  // contiguous rows (the default layout): the 32 rows are 32 N floats from c0 N on (16-byte
+  // aligned when the output is, since 32 N floats are a multiple of 16 bytes); padded rows
+  // (a row stride above N): each row's N floats with coalesced scalar stores
+  const int rows = (int)(p.ncells - c0 < 32 ? p.ncells - c0 : 32);
+  float* dst = p.out + c0 * p.ostride;
+  if (p.ostride != N) {
+    for (int i = lane; i < rows * N; i += 32) __stcs(dst + (int64_t)(i / N) * p.ostride + i % N, st[(i / N) * SR + i % N]);
+  } else if (rows == 32 && vec) {
 #pragma unroll 4
-      for (int i = lane; i < 8 * N; i += 32) {  // 8 N float4 per warp tile
-        float4 v;
-        const int j = 4 * i;
-        v.x = st[((j + 0) / N) * SR + (j + 0) % N];
-        v.y = st[((j + 1) / N) * SR + (j + 1) % N];
-        v.z = st[((j + 2) / N) * SR + (j + 2) % N];
-        v.w = st[((j + 3) / N) * SR + (j + 3) % N];
-        __stcs(reinterpret_cast<float4*>(dst) + i, v);
-      }
-    } else {
-      for (int i = lane; i < rows * N; i += 32) __stcs(dst + i, st[(i / N) * SR + i % N]);
+    for (int i = lane; i < 8 * N; i += 32) {  // 8 N float4 per warp tile
+      float4 v;
+      const int j = 4 * i;
+      v.x = st[((j + 0) / N) * SR + (j + 0) % N];
+      v.y = st[((j + 1) / N) * SR + (j + 1) % N];
+      v.z = st[((j + 2) / N) * SR + (j + 2) % N];
+      v.w = st[((j + 3) / N) * SR + (j + 3) % N];
+      __stcs(reinterpret_cast<float4*>(dst) + i, v);
     }
-    __syncwarp();
+  } else {
+    for (int i = lane; i < rows * N; i += 32) __stcs(dst + i, st[(i / N) * SR + i % N]);
+  }
+  __syncwarp();
+}
+
+template <int FORM, int D, int DEG>
+__global__ void __launch_bounds__(SIMT_THREADS) k_assemble_simt(const TcParams p) {
+  constexpr int NS = s_ns(D, DEG), N = NS * NS;
+  extern __shared__ float stage[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* st = stage + warp * 32 * (N | 1);
+  const int64_t ntiles = (p.ncells + 31) / 32;
+  for (int64_t t = (int64_t)blockIdx.x * SIMT_WARPS + warp; t < ntiles; t += (int64_t)gridDim.x * SIMT_WARPS)
+    simt_tile<FORM, D, DEG>(p, t, lane, st);
+}
+
+// Several groups in one launch (the CUDA-core share of a mixed batch): warp tiles are numbered
+// across the groups (group g owns tiles tile0 .. of its cells), each warp finds the group of its
+// tile and runs that shape's tile. The shapes are those the CUDA cores take by default.
+constexpr int SB_SR = 37;  // staging stride of the largest of them (triangles P2: 36 entries)
+template <int FORM, int D, int DEG>
+__device__ __forceinline__ void simt_tile_b(const TcParams& p, int64_t t, int lane, float* st) {
+  static_assert((s_ns(D, DEG) * s_ns(D, DEG) | 1) <= SB_SR, "batch staging stride");
+  simt_tile<FORM, D, DEG>(p, t, lane, st);
+}
+__global__ void __launch_bounds__(SIMT_THREADS) k_simt_batch(const SimtGroup* __restrict__ groups, int ngroups,
+                                                           int64_t ntiles) {
+  extern __shared__ float stage[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* st = stage + warp * 32 * SB_SR;
+  for (int64_t t = (int64_t)blockIdx.x * SIMT_WARPS + warp; t < ntiles; t += (int64_t)gridDim.x * SIMT_WARPS) {
+    int g = 0;
+    while (g + 1 < ngroups && groups[g + 1].tile0 <= t) ++g;
+    const SimtGroup& G = groups[g];
+    const int64_t lt = t - G.tile0;
+    switch (G.kind) {
+      case FORM_MASS * 8 + CELL_TRI * 4 + 1: simt_tile_b<FORM_MASS, 2, 1>(G.p, lt, lane, st); break;
+      case FORM_MASS * 8 + CELL_TRI * 4 + 2: simt_tile_b<FORM_MASS, 2, 2>(G.p, lt, lane, st); break;
+      case FORM_MASS * 8 + CELL_TET * 4 + 1: simt_tile_b<FORM_MASS, 3, 1>(G.p, lt, lane, st); break;
+      case FORM_HELMHOLTZ * 8 + CELL_TRI * 4 + 1: simt_tile_b<FORM_HELMHOLTZ, 2, 1>(G.p, lt, lane, st); break;
+      case FORM_HELMHOLTZ * 8 + CELL_TRI * 4 + 2: simt_tile_b<FORM_HELMHOLTZ, 2, 2>(G.p, lt, lane, st); break;
+      case FORM_HELMHOLTZ * 8 + CELL_TET * 4 + 1: simt_tile_b<FORM_HELMHOLTZ, 3, 1>(G.p, lt, lane, st); break;
+      case FORM_ADVDIFF * 8 + CELL_TRI * 4 + 1: simt_tile_b<FORM_ADVDIFF, 2, 1>(G.p, lt, lane, st); break;
+      case FORM_ADVDIFF * 8 + CELL_TRI * 4 + 2: simt_tile_b<FORM_ADVDIFF, 2, 2>(G.p, lt, lane, st); break;
+      case FORM_ADVDIFF * 8 + CELL_TET * 4 + 1: simt_tile_b<FORM_ADVDIFF, 3, 1>(G.p, lt, lane, st); break;
+      default: break;  // the planner assigns only these shapes
+    }
   }
 }
 
@@ -186,6 +226,42 @@ int simt_default(int form, int degree, int cell) {
   return degree == 1 || (cell == CELL_TRI && degree == 2) ? 1 : 0;
 }
 
+// T of (form, degree, cell) in the constant bank of the current device, written once
+int simt_upload(int form, int degree, int cell) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  const int d = cell == CELL_TRI ? 2 : 3;
+  std::lock_guard<std::mutex> lock(g_simt_mu);
+  if (g_simt_loaded.count({dev, form, degree, cell})) return (int)cudaSuccess;
+  std::vector<double> T;
+  tc_reference_tensor(form, degree, cell, T);
+  std::vector<float> f(T.size());
+  for (size_t i = 0; i < T.size(); ++i) f[i] = (float)T[i];
+  if ((int)f.size() != s_size(form, d, degree)) return (int)cudaErrorInvalidValue;
+  e = cudaMemcpyToSymbol(c_T, f.data(), f.size() * sizeof(float), (size_t)s_off(form, d, degree) * sizeof(float),
+                         cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return (int)e;
+  g_simt_loaded.insert({dev, form, degree, cell});
+  return (int)cudaSuccess;
+}
+
+int simt_kind(int form, int degree, int cell) { return form * 8 + cell * 4 + degree; }
+
+int launch_simt_batch(const SimtGroup* groups, int ngroups, int64_t ntiles, int num_sms, void* stream) {
+  if (ntiles == 0) return (int)cudaSuccess;
+  const int smem = SIMT_WARPS * 32 * SB_SR * (int)sizeof(float);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_simt_batch, SIMT_THREADS, smem);
+  if (e != cudaSuccess) return (int)e;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t blocks_needed = (ntiles + SIMT_WARPS - 1) / SIMT_WARPS;
+  const int64_t full = (int64_t)num_sms * per_sm;
+  const int grid = (int)(blocks_needed < full ? blocks_needed : full);
+  k_simt_batch<<<grid, SIMT_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(groups, ngroups, ntiles);
+  return (int)cudaGetLastError();
+}
+
 int launch_simt(int form, int degree, int cell, const TcParams& p, int num_sms, void* stream, std::string& why) {
   SimtKernel kern = simt_supported(form, degree, cell) ? pick(form, degree, cell) : nullptr;
   if (!kern) {
@@ -193,26 +269,11 @@ int launch_simt(int form, int degree, int cell, const TcParams& p, int num_sms, 
     return (int)cudaErrorInvalidValue;
   }
   if (p.ncells == 0) return (int)cudaSuccess;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return (int)e;
+  cudaError_t e = cudaSuccess;
   const int d = cell == CELL_TRI ? 2 : 3, ns = s_ns(d, degree), N = ns * ns;
-  {
-    std::lock_guard<std::mutex> lock(g_simt_mu);
-    if (!g_simt_loaded.count({dev, form, degree, cell})) {
-      std::vector<double> T;
-      tc_reference_tensor(form, degree, cell, T);
-      std::vector<float> f(T.size());
-      for (size_t i = 0; i < T.size(); ++i) f[i] = (float)T[i];
-      if ((int)f.size() != s_size(form, d, degree)) {
-        why = "reference tensor size mismatch";
-        return (int)cudaErrorInvalidValue;
-      }
-      e = cudaMemcpyToSymbol(c_T, f.data(), f.size() * sizeof(float), (size_t)s_off(form, d, degree) * sizeof(float),
-                             cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) return (int)e;
-      g_simt_loaded.insert({dev, form, degree, cell});
-    }
+  if ((e = (cudaError_t)simt_upload(form, degree, cell)) != cudaSuccess) {
+    why = "reference tensor upload";
+    return (int)e;
   }
   const int smem = SIMT_WARPS * 32 * (N | 1) * (int)sizeof(float);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -39,11 +39,13 @@ def check_groups(dev, groups, outs, prec, tol, sample=None):
         spec = g["spec"]
         if spec["count"] == 0:
             continue
-        # batches run on the tensor cores: the single-group launch is forced there too (small
-        # element matrices would otherwise take the CUDA-core kernel)
+        # the batch runs each group on its default kernel family (the CUDA cores for small
+        # element matrices, the tensor cores otherwise): the single-group launch on the same
+        simt = coffee.assemble_path(g["form"], g["degree"], g["cell"], prec) == 2
         single = coffee.assemble(g["form"], g["degree"], g["cell"], g["coords"], g["cell2vert"],
                                  g.get("coef"), g.get("cell2dof"), precision=prec,
-                                 coords_split=g.get("coords_split"), tune=coffee.FLAG_TENSOR_CORES)
+                                 coords_split=g.get("coords_split"),
+                                 tune=coffee.FLAG_CUDA_CORES if simt else coffee.FLAG_TENSOR_CORES)
         assert torch.equal(out, single), spec
         d = dev[g["cell"]]
         m = d["mesh"]
@@ -71,6 +73,26 @@ def test_small_mixed_batch(prec, tol, split):
     outs = plan.launch()
     coffee.check_errors()
     check_groups(dev, groups, outs, prec, tol)
+
+
+def test_batch_all_on_the_tensor_cores():
+    """all_tensor_cores keeps the small-matrix groups in the tensor-core launch: every group then
+    equals its single-group tensor-core launch bit for bit and meets the bound."""
+    tri = meshgen.tri_mesh(24, perturb=0.2, seed=12)
+    tet = meshgen.tet_mesh(6, perturb=0.15, seed=13)
+    dev, groups = make_batch(tri, tet, seed=12)
+    plan = coffee.BatchPlan(groups, precision=coffee.TF32X3, all_tensor_cores=True)
+    assert plan.launches == 1
+    outs = plan.launch()
+    coffee.check_errors()
+    for g, out in zip(groups, outs):
+        if g["spec"]["count"] == 0:
+            continue
+        single = coffee.assemble(g["form"], g["degree"], g["cell"], g["coords"], g["cell2vert"],
+                                 g.get("coef"), g.get("cell2dof"), precision=coffee.TF32X3,
+                                 tune=coffee.FLAG_TENSOR_CORES)
+        assert torch.equal(out, single), g["spec"]
+    assert coffee.BatchPlan(groups, precision=coffee.TF32X3).launches == 2
 
 
 def test_batch_plan_options_do_not_change_results():
