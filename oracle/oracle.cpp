@@ -1,7 +1,7 @@
 // FP64 CPU oracle for finite-element local assembly (COFFEE, arXiv:1407.0904).
 //
 // TEST INFRASTRUCTURE ONLY. This file is the slow, plain reference against which
-// the CUDA path is judged. Only the test suite, the smoke check and the timed CPU
+// the CUDA path is checked. Only the test suite, the smoke check and the timed CPU
 // baseline of the benchmark may load it. It shares no code, table or constant with
 // the CUDA library: its quadrature rule (collapsed Gauss-Legendre with the Duffy
 // Jacobian written out), its Lagrange basis (monomial Vandermonde inversion) and its
