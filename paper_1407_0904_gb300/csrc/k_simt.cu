@@ -98,12 +98,26 @@ __device__ __forceinline__ void simt_tile(const TcParams& p, int64_t t, int lane
 #pragma unroll
     for (int k = 0; k < K; ++k) G[k] = 0.f;
   }
+  if constexpr (FORM == FORM_ADVDIFF) {
 #pragma unroll
-  for (int o = 0; o < N; ++o) {
-    float a = 0.f;
+    for (int o = 0; o < N; ++o) {
+      float a = 0.f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) a = fmaf(G[k], c_T[OFF + k * N + o], a);
-    st[lane * SR + o] = a;
+      for (int k = 0; k < K; ++k) a = fmaf(G[k], c_T[OFF + k * N + o], a);
+      st[lane * SR + o] = a;
+    }
+  } else {
+    // MASS and HELMHOLTZ are symmetric: the upper triangle is formed and mirrored
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+#pragma unroll
+      for (int j = i; j < NS; ++j) {
+        float a = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) a = fmaf(G[k], c_T[OFF + k * N + i * NS + j], a);
+        st[lane * SR + i * NS + j] = a;
+        if (j != i) st[lane * SR + j * NS + i] = a;
+      }
   }
   __syncwarp();
   // contiguous rows (the default layout): the 32 rows are 32 N floats from c0 N on (16-byte
