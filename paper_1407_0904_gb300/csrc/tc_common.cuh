@@ -371,15 +371,18 @@ __device__ __forceinline__ bool split_exact(double x, float& hi, float& lo) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const uint32_t h = (uint32_t)(b >> 32), l = (uint32_t)b;
   const uint32_t sign = h & 0x80000000u;
-  const int e = (int)((h >> 20) & 0x7FFu);
-  const bool zero = ((h & 0x7FFFFFFFu) | l) == 0u;
-  const bool ok = zero || (e >= 1023 - 70 && e < 1023 + 100);
-  const uint32_t hb = sign | ((uint32_t)(e - 1023 + 127) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29);
-  const float unit = __uint_as_float((uint32_t)(e - 1075 + 127) << 23);
+  const uint32_t ef = h & 0x7FF00000u;  // biased exponent e, in place
+  // e == 0: zero (a binary64 subnormal, below 2^-1022, is taken as zero too)
+  const bool zero = ef == 0u;
+  const bool ok = zero || (ef - ((1023u - 70u) << 20)) < (170u << 20);
+  // hi: the exponent field rebiased in place (e - 896 stays within 8 bits in range, so the
+  // field's top three bits are clear), then the 20 + 3 fraction bits shifted into place
+  const uint32_t hb = __funnelshift_l(l, h - (896u << 20), 3) | sign;
+  // lo: the 29 bits below, times 2^(e - 1075) (float exponent field e - 948)
+  const float unit = __uint_as_float((ef << 3) - (948u << 23));
   const float lm = __uint2float_rn(l & 0x1FFFFFFFu) * unit;
-  const bool use = ok && !zero;
-  hi = use ? __uint_as_float(hb) : 0.f;
-  lo = use ? __uint_as_float(__float_as_uint(lm) | sign) : 0.f;
+  hi = (ok && !zero) ? __uint_as_float(hb) : 0.f;
+  lo = (ok && !zero) ? __uint_as_float(__float_as_uint(lm) | sign) : 0.f;
   return ok;
 }
 
