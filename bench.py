@@ -112,6 +112,9 @@ for _k in (1, 2, 3, 4):
 WORKLOADS["advdiff-p2-tet"] = Workload("advdiff-p2-tet", ADVDIFF, 2, TETRAHEDRON,
                                        "Kuhn 64x64x43 truncated to 2^20 tets, perturbed 0.15h (seed 3), "
                                        "eps~U[0.5,1.5], b~U[-1,1]^3 per vertex", _kuhn2pow20)
+WORKLOADS["burgers-p1-tet"] = Workload("burgers-p1-tet", BURGERS_JAC, 1, TETRAHEDRON,
+                                       "Kuhn 64x64x43 truncated to 2^20 tets, perturbed 0.15h (seed 3), "
+                                       "vector P1 u~N(0,1), nu=0.01", _kuhn2pow20)
 WORKLOADS["burgers-p2-tet"] = Workload("burgers-p2-tet", BURGERS_JAC, 2, TETRAHEDRON,
                                        "Kuhn 64x64x43 truncated to 2^20 tets, perturbed 0.15h (seed 3), "
                                        "vector P2 u~N(0,1), nu=0.01", _kuhn2pow20)

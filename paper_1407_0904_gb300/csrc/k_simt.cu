@@ -36,23 +36,29 @@ constexpr int SIMT_THREADS = 256;
 constexpr int SIMT_WARPS = SIMT_THREADS / 32;
 
 __host__ __device__ constexpr int s_ns(int d, int k) { return d == 2 ? (k + 1) * (k + 2) / 2 : (k + 1) * (k + 2) * (k + 3) / 6; }
-__host__ __device__ constexpr int s_K(int form, int d) {
-  return form == FORM_MASS ? 1 : form == FORM_HELMHOLTZ ? 1 + d * (d + 1) / 2 : (d + 1) * (d * (d + 1) / 2) + (d + 1) * d;
+// rows of T: MASS 1, HELMHOLTZ 1 + P (edge factors), ADVDIFF (d+1) P + (d+1) d; the Burgers
+// Jacobian's [T1 | T2 | T3]: 2 ns d + P (of one d x d component block's ns^2 entries)
+__host__ __device__ constexpr int s_K(int form, int d, int k = 1) {
+  return form == FORM_MASS ? 1 : form == FORM_HELMHOLTZ ? 1 + d * (d + 1) / 2
+       : form == FORM_ADVDIFF ? (d + 1) * (d * (d + 1) / 2) + (d + 1) * d
+       : 2 * s_ns(d, k) * d + d * (d + 1) / 2;
 }
-__host__ __device__ constexpr int s_maxdeg(int d) { return d == 2 ? 3 : 2; }
-__host__ __device__ constexpr int s_size(int form, int d, int k) { return s_K(form, d) * s_ns(d, k) * s_ns(d, k); }
-// offset of each instance's table in the constant bank: forms 0-2, d = 2, 3, degrees 1..maxdeg
+// instances: MASS, HELMHOLTZ, ADVDIFF on triangles P1-P3 and tetrahedra P1-P2; the Burgers
+// Jacobian on P1 simplices
+__host__ __device__ constexpr int s_maxdeg(int form, int d) { return form == FORM_BURGERS ? 1 : d == 2 ? 3 : 2; }
+__host__ __device__ constexpr int s_size(int form, int d, int k) { return s_K(form, d, k) * s_ns(d, k) * s_ns(d, k); }
+// offset of each instance's table in the constant bank
 __host__ __device__ constexpr int s_off(int form, int d, int k) {
   int off = 0;
-  for (int f = 0; f < 3; ++f)
+  for (int f = 0; f <= FORM_BURGERS; ++f)
     for (int dd = 2; dd <= 3; ++dd)
-      for (int kk = 1; kk <= s_maxdeg(dd); ++kk) {
+      for (int kk = 1; kk <= s_maxdeg(f, dd); ++kk) {
         if (f == form && dd == d && kk == k) return off;
         off += s_size(f, dd, kk);
       }
   return off;  // one past the last: the total
 }
-constexpr int S_TOTAL = s_off(3, 0, 0);
+constexpr int S_TOTAL = s_off(FORM_BURGERS + 1, 0, 0);
 static_assert(S_TOTAL * 4 <= 60 * 1024, "reference tensors exceed the constant bank");
 
 // T [K][N] in FP32 of every instance (edge-basis form of the stiffness tensors, as the
@@ -144,6 +150,139 @@ __device__ __forceinline__ void simt_tile(const TcParams& p, int64_t t, int lane
   __syncwarp();
 }
 
+// The Burgers Jacobian on P1 simplices (vector P1: d*(d+1) entries per row), one cell per thread,
+// in the factored form of its d x d component blocks of ns^2 entries (ns = d + 1):
+//   block(ci, cj) = sum_a P[a][cj] V_a^ci + [ci == cj] C,   V_a^ci = sum_r u[r][ci] T1[r d + a],
+//   C = sum_{r,a} Q[r][a] T2[r d + a] + sum_p nu H_p T3[p],   Q[r][a] = sum_c u[r][c] P[a][c],
+// with P = |det J| K and T = [T1 | T2 | T3] the Burgers reference tensors (rows r d + a of T1 and
+// T2, then the P pair rows of T3) in constant memory. The cell's matrix goes to the staging block
+// row by row and out with the warp's coalesced stores.
+constexpr int SIMT_BTHREADS = 128;  // the staging block of a tetrahedron is 145 floats per cell
+template <int D>
+__device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, int lane, float* st) {
+  constexpr int NS = D + 1, NV = D + 1, NDOF = D * NS, N = NDOF * NDOF, NB = NS * NS, K1 = NS * D;
+  constexpr int P = D * (D + 1) / 2, OFF = s_off(FORM_BURGERS, D, 1), SR = N | 1;
+  const int64_t c0 = t * 32, e = c0 + lane;
+  float u[NS][D], Pm[D][D], H[P];
+#pragma unroll
+  for (int r = 0; r < NS; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) u[r][c] = 0.f;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) Pm[a][c] = 0.f;
+#pragma unroll
+  for (int q = 0; q < P; ++q) H[q] = 0.f;
+  if (e < p.ncells) {
+    int vid[NV], did[NS];
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      vid[v] = __ldg(p.c2v + e * NV + v);
+      if (p.validate && (vid[v] < 0 || vid[v] >= p.nverts)) bad = true;
+    }
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+      did[r] = __ldg(p.c2d + e * NS + r);
+      if (p.validate && (did[r] < 0 || did[r] >= p.ncoefnodes)) bad = true;
+    }
+    if (bad) {
+      atomicOr(p.err, ERR_INDEX);
+    } else {
+      float adj[D][D], Dm, sg;
+      cell_geometry_ids<D, true>(p, vid, adj, Dm, sg);
+      const float inv = 1.0f / Dm, nu = (float)p.nu;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int c = 0; c < D; ++c) Pm[a][c] = sg * adj[a][c];
+      int q = 0;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = a; b < D; ++b) {
+          float s = 0.f;
+#pragma unroll
+          for (int r = 0; r < D; ++r) s = fmaf(adj[a][r], adj[b][r], s);
+          H[q++] = nu * s * inv;
+        }
+      coef_rows<NS, D>(p, did, u);
+    }
+  }
+  // C, shared by the diagonal blocks
+  float C[NB];
+#pragma unroll
+  for (int o = 0; o < NB; ++o) {
+    float v = 0.f;
+#pragma unroll
+    for (int r = 0; r < NS; ++r)
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float q = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) q = fmaf(u[r][c], Pm[a][c], q);
+        v = fmaf(q, c_T[OFF + (K1 + r * D + a) * NB + o], v);
+      }
+#pragma unroll
+    for (int q = 0; q < P; ++q) v = fmaf(H[q], c_T[OFF + (2 * K1 + q) * NB + o], v);
+    C[o] = v;
+  }
+  float* row = st + lane * SR;
+#pragma unroll
+  for (int ci = 0; ci < D; ++ci) {
+#pragma unroll
+    for (int o = 0; o < NB; ++o) {
+      float V[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float v = 0.f;
+#pragma unroll
+        for (int r = 0; r < NS; ++r) v = fmaf(u[r][ci], c_T[OFF + (r * D + a) * NB + o], v);
+        V[a] = v;
+      }
+      const int i = o / NS, j = o % NS;
+#pragma unroll
+      for (int cj = 0; cj < D; ++cj) {
+        float v = ci == cj ? C[o] : 0.f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) v = fmaf(Pm[a][cj], V[a], v);
+        row[(ci * NS + i) * NDOF + cj * NS + j] = v;
+      }
+    }
+  }
+  __syncwarp();
+  const int rows = (int)(p.ncells - c0 < 32 ? p.ncells - c0 : 32);
+  float* dst = p.out + c0 * N;
+  if (rows == 32 && (reinterpret_cast<uintptr_t>(p.out) & 15) == 0) {
+#pragma unroll 4
+    for (int i = lane; i < 8 * N; i += 32) {
+      float4 v;
+      const int j = 4 * i;
+      v.x = st[((j + 0) / N) * SR + (j + 0) % N];
+      v.y = st[((j + 1) / N) * SR + (j + 1) % N];
+      v.z = st[((j + 2) / N) * SR + (j + 2) % N];
+      v.w = st[((j + 3) / N) * SR + (j + 3) % N];
+      __stcs(reinterpret_cast<float4*>(dst) + i, v);
+    }
+  } else {
+    for (int i = lane; i < rows * N; i += 32) __stcs(dst + i, st[(i / N) * SR + i % N]);
+  }
+  __syncwarp();
+}
+
+template <int D>
+__global__ void __launch_bounds__(SIMT_BTHREADS) k_assemble_simt_burgers(const TcParams p) {
+  constexpr int NDOF = D * (D + 1), N = NDOF * NDOF;
+  extern __shared__ float stage[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* st = stage + warp * 32 * (N | 1);
+  const int64_t ntiles = (p.ncells + 31) / 32;
+  for (int64_t t = (int64_t)blockIdx.x * (SIMT_BTHREADS / 32) + warp; t < ntiles;
+       t += (int64_t)gridDim.x * (SIMT_BTHREADS / 32))
+    simt_tile_burgers<D>(p, t, lane, st);
+}
+
 template <int FORM, int D, int DEG>
 __global__ void __launch_bounds__(SIMT_THREADS) k_assemble_simt(const TcParams p) {
   constexpr int NS = s_ns(D, DEG), N = NS * NS;
@@ -202,6 +341,10 @@ SimtKernel pick_deg(int degree) {
 }
 
 SimtKernel pick(int form, int degree, int cell) {
+  if (form == FORM_BURGERS) {
+    if (degree != 1) return nullptr;
+    return cell == CELL_TRI ? k_assemble_simt_burgers<2> : cell == CELL_TET ? k_assemble_simt_burgers<3> : nullptr;
+  }
   if (cell == CELL_TRI) {
     switch (form) {
       case FORM_MASS: return pick_deg<FORM_MASS, 2>(degree);
@@ -224,10 +367,10 @@ std::set<std::tuple<int, int, int, int>> g_simt_loaded;  // (device, form, degre
 }  // namespace
 
 int simt_supported(int form, int degree, int cell) {
-  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF)) return 0;
+  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF || form == FORM_BURGERS)) return 0;
   if (!(cell == CELL_TRI || cell == CELL_TET)) return 0;
   const int d = cell == CELL_TRI ? 2 : 3;
-  return degree >= 1 && degree <= s_maxdeg(d) ? 1 : 0;
+  return degree >= 1 && degree <= s_maxdeg(form, d) ? 1 : 0;
 }
 
 // where the CUDA-core kernel is the faster one (measured, TF32X3 tensor-core kernel with its
@@ -236,7 +379,7 @@ int simt_supported(int form, int degree, int cell) {
 // triangles P3 stay on the tensor cores (their 100-entry matrices cost the CUDA cores more FMAs
 // than the tensor-core kernel's hand-offs)
 int simt_default(int form, int degree, int cell) {
-  (void)form;
+  if (form == FORM_BURGERS) return degree == 1 ? 1 : 0;
   return degree == 1 || (cell == CELL_TRI && degree == 2) ? 1 : 0;
 }
 
@@ -284,23 +427,25 @@ int launch_simt(int form, int degree, int cell, const TcParams& p, int num_sms, 
   }
   if (p.ncells == 0) return (int)cudaSuccess;
   cudaError_t e = cudaSuccess;
-  const int d = cell == CELL_TRI ? 2 : 3, ns = s_ns(d, degree), N = ns * ns;
+  const int d = cell == CELL_TRI ? 2 : 3, ns = s_ns(d, degree);
+  const int nd = form == FORM_BURGERS ? d * ns : ns, N = nd * nd;
   if ((e = (cudaError_t)simt_upload(form, degree, cell)) != cudaSuccess) {
     why = "reference tensor upload";
     return (int)e;
   }
-  const int smem = SIMT_WARPS * 32 * (N | 1) * (int)sizeof(float);
+  const int threads = form == FORM_BURGERS ? SIMT_BTHREADS : SIMT_THREADS, warps = threads / 32;
+  const int smem = warps * 32 * (N | 1) * (int)sizeof(float);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return (int)e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SIMT_THREADS, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   if (e != cudaSuccess) return (int)e;
   if (per_sm < 1) per_sm = 1;
   const int64_t warps_needed = (p.ncells + 31) / 32;
-  const int64_t blocks_needed = (warps_needed + SIMT_WARPS - 1) / SIMT_WARPS;
+  const int64_t blocks_needed = (warps_needed + warps - 1) / warps;
   const int64_t full = (int64_t)num_sms * per_sm;
   const int grid = (int)(blocks_needed < full ? blocks_needed : full);
-  kern<<<grid, SIMT_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(p);
+  kern<<<grid, threads, smem, static_cast<cudaStream_t>(stream)>>>(p);
   return (int)cudaGetLastError();
 }
 

@@ -179,9 +179,9 @@ def test_support_queries_cover_prisms():
 
 def test_assemble_path_query():
     """Host-only: which kernel family runs. Small element matrices (MASS, HELMHOLTZ, ADVDIFF on
-    P1 simplices and P2 triangles) default to the FP32 CUDA-core kernel, the rest of the
-    tensor-core precisions to the tensor cores; the flags force either where both exist; FP64
-    is the FP64 kernel; unsupported combinations raise."""
+    P1 simplices and P2 triangles, the Burgers Jacobian on P1 simplices) default to the FP32
+    CUDA-core kernel, the rest of the tensor-core precisions to the tensor cores; the flags force
+    either where both exist; FP64 is the FP64 kernel; unsupported combinations raise."""
     T, R, P = coffee.TETRAHEDRON, coffee.TRIANGLE, coffee.PRISM
     for form in (coffee.MASS, coffee.HELMHOLTZ, coffee.ADVDIFF):
         for cell, k, default in ((T, 1, 2), (R, 1, 2), (R, 2, 2), (T, 2, 1), (R, 3, 1), (T, 3, 1), (R, 4, 1)):
@@ -192,8 +192,11 @@ def test_assemble_path_query():
                 assert coffee.assemble_path(form, k, cell, prec, coffee.FLAG_CUDA_CORES) == forced
             assert coffee.assemble_path(form, k, cell, coffee.FP64) == 0
         assert coffee.assemble_path(form, 2, P, coffee.TF32X3, coffee.FLAG_CUDA_CORES) == 1
-    for form in (coffee.BURGERS_JAC, coffee.BURGERS_RESIDUAL):
-        assert coffee.assemble_path(form, 1, T, coffee.TF32X3, coffee.FLAG_CUDA_CORES) == 1
+    for cell in (T, R):  # the Burgers Jacobian: P1 on the CUDA cores, the rest on the tensor cores
+        assert coffee.assemble_path(coffee.BURGERS_JAC, 1, cell, coffee.TF32X3) == 2
+        assert coffee.assemble_path(coffee.BURGERS_JAC, 1, cell, coffee.TF32X3, coffee.FLAG_TENSOR_CORES) == 1
+        assert coffee.assemble_path(coffee.BURGERS_JAC, 2, cell, coffee.TF32X3, coffee.FLAG_CUDA_CORES) == 1
+    assert coffee.assemble_path(coffee.BURGERS_RESIDUAL, 1, T, coffee.TF32X3, coffee.FLAG_CUDA_CORES) == 1
     with pytest.raises(coffee.CoffeeError):
         coffee.assemble_path(coffee.BURGERS_JAC, 1, P, coffee.TF32X3)
 

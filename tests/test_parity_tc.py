@@ -62,10 +62,11 @@ def test_burgers_block_form_when_forced(cell, k, prec):
     coef, c2d = coefficients(BURGERS_JAC, mesh, k, seed=61)
     ref = oracle_ref(BURGERS_JAC, k, cell, mesh, coef, c2d)
     x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    tc = coffee.FLAG_TENSOR_CORES  # P1 would otherwise take the CUDA-core kernel
     blocks = coffee.assemble(BURGERS_JAC, k, cell, x, c2v, cf, cd, precision=prec, validate=True,
-                             tune=coffee.FLAG_BURGERS_BLOCKS)
+                             tune=tc | coffee.FLAG_BURGERS_BLOCKS)
     fact = coffee.assemble(BURGERS_JAC, k, cell, x, c2v, cf, cd, precision=prec, validate=True,
-                           tune=coffee.FLAG_BURGERS_FACTORED)
+                           tune=tc | coffee.FLAG_BURGERS_FACTORED)
     coffee.check_errors()
     eb = rel_err_per_cell(blocks.cpu().numpy(), ref)
     ef = rel_err_per_cell(fact.cpu().numpy(), ref)

@@ -12,8 +12,8 @@ import torch
 
 import paper_1407_0904_gb300 as coffee
 from paper_1407_0904_gb300 import meshgen
-from tests.helpers import (TRI, TET, MASS, HELMHOLTZ, ADVDIFF, TOL, coefficients, rel_err_per_cell,
-                           to_device, oracle_ref)
+from tests.helpers import (TRI, TET, MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC, TOL, coefficients,
+                           rel_err_per_cell, to_device, oracle_ref)
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -42,6 +42,39 @@ def test_cuda_core_kernel_matches_oracle(form, cell, k, prec):
     err = rel_err_per_cell(out.cpu().numpy(), ref)
     print("simt %s %s P%d: %.3e" % (coffee.FORM_NAMES[form], "tri" if cell == TRI else "tet", k, err))
     assert err < 1e-5
+
+
+@pytest.mark.parametrize("cell", [TRI, TET])
+@pytest.mark.parametrize("prec", [coffee.TF32X3, coffee.BF16, coffee.BF16X3])
+def test_burgers_p1_on_the_cuda_cores(cell, prec):
+    """The Burgers Jacobian on P1 simplices (the default path): factored blocks in FP32 against
+    the oracle, within the split precisions' bound whatever precision is asked for; with the
+    float coefficient copy bit for bit the same; a ragged last warp tile."""
+    mesh = mesh_of(cell, seed=70)
+    coef, c2d = coefficients(BURGERS_JAC, mesh, 1, seed=71)
+    ref = oracle_ref(BURGERS_JAC, 1, cell, mesh, coef, c2d)
+    x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    assert coffee.assemble_path(BURGERS_JAC, 1, cell, prec) == 2
+    out = coffee.assemble(BURGERS_JAC, 1, cell, x, c2v, cf, cd, precision=prec, validate=True)
+    coffee.check_errors()
+    err = rel_err_per_cell(out.cpu().numpy(), ref)
+    print("simt burgers %s P1: %.3e" % ("tri" if cell == TRI else "tet", err))
+    assert err < 1e-5
+    out2 = coffee.assemble(BURGERS_JAC, 1, cell, x, c2v, cf, cd, precision=prec, coef_f32=coffee.round_coef(cf))
+    assert torch.equal(out, out2)
+
+
+def test_burgers_p1_flags_a_bad_index():
+    mesh = mesh_of(TET, seed=72)
+    coef, c2d = coefficients(BURGERS_JAC, mesh, 1, seed=73)
+    x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    bad = cd.clone()
+    bad[5, 2] = mesh.nverts * 10
+    out = coffee.assemble(BURGERS_JAC, 1, TET, x, c2v, cf, bad, precision=coffee.TF32X3, validate=True)
+    with pytest.raises(coffee.CoffeeError) as ei:
+        coffee.check_errors()
+    assert ei.value.status == -4
+    assert torch.count_nonzero(out[5]) == 0
 
 
 @pytest.mark.parametrize("form,cell", [(f, c) for f in (MASS, HELMHOLTZ, ADVDIFF) for c in (TRI, TET)])
