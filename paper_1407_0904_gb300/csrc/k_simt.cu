@@ -158,9 +158,10 @@ __device__ __forceinline__ void simt_tile(const TcParams& p, int64_t t, int lane
 // T2, then the P pair rows of T3) in constant memory. The cell's matrix goes to the staging block
 // row by row and out with the warp's coalesced stores.
 constexpr int SIMT_BTHREADS = 128;  // the staging block of a tetrahedron is 145 floats per cell
-template <int D>
+// RES: the residual instead (element vectors, R[(c, i)] = sum_s C[i][s] u[s][c]; C as above).
+template <int D, bool RES = false>
 __device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, int lane, float* st) {
-  constexpr int NS = D + 1, NV = D + 1, NDOF = D * NS, N = NDOF * NDOF, NB = NS * NS, K1 = NS * D;
+  constexpr int NS = D + 1, NV = D + 1, NDOF = D * NS, N = RES ? NDOF : NDOF * NDOF, NB = NS * NS, K1 = NS * D;
   constexpr int P = D * (D + 1) / 2, OFF = s_off(FORM_BURGERS, D, 1), SR = N | 1;
   const int64_t c0 = t * 32, e = c0 + lane;
   float u[NS][D], Pm[D][D], H[P];
@@ -229,8 +230,19 @@ __device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, 
     C[o] = v;
   }
   float* row = st + lane * SR;
+  if constexpr (RES) {
 #pragma unroll
-  for (int ci = 0; ci < D; ++ci) {
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        float v = 0.f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) v = fmaf(C[i * NS + s], u[s][c], v);
+        row[c * NS + i] = v;
+      }
+  }
+#pragma unroll
+  for (int ci = 0; ci < (RES ? 0 : D); ++ci) {
 #pragma unroll
     for (int o = 0; o < NB; ++o) {
       float V[D];
@@ -271,16 +283,16 @@ __device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, 
   __syncwarp();
 }
 
-template <int D>
+template <int D, bool RES>
 __global__ void __launch_bounds__(SIMT_BTHREADS) k_assemble_simt_burgers(const TcParams p) {
-  constexpr int NDOF = D * (D + 1), N = NDOF * NDOF;
+  constexpr int NDOF = D * (D + 1), N = RES ? NDOF : NDOF * NDOF;
   extern __shared__ float stage[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* st = stage + warp * 32 * (N | 1);
   const int64_t ntiles = (p.ncells + 31) / 32;
   for (int64_t t = (int64_t)blockIdx.x * (SIMT_BTHREADS / 32) + warp; t < ntiles;
        t += (int64_t)gridDim.x * (SIMT_BTHREADS / 32))
-    simt_tile_burgers<D>(p, t, lane, st);
+    simt_tile_burgers<D, RES>(p, t, lane, st);
 }
 
 template <int FORM, int D, int DEG>
@@ -341,9 +353,11 @@ SimtKernel pick_deg(int degree) {
 }
 
 SimtKernel pick(int form, int degree, int cell) {
-  if (form == FORM_BURGERS) {
+  if (form == FORM_BURGERS || form == FORM_BURGERS_RES) {
     if (degree != 1) return nullptr;
-    return cell == CELL_TRI ? k_assemble_simt_burgers<2> : cell == CELL_TET ? k_assemble_simt_burgers<3> : nullptr;
+    if (form == FORM_BURGERS_RES)
+      return cell == CELL_TRI ? k_assemble_simt_burgers<2, true> : cell == CELL_TET ? k_assemble_simt_burgers<3, true> : nullptr;
+    return cell == CELL_TRI ? k_assemble_simt_burgers<2, false> : cell == CELL_TET ? k_assemble_simt_burgers<3, false> : nullptr;
   }
   if (cell == CELL_TRI) {
     switch (form) {
@@ -367,10 +381,10 @@ std::set<std::tuple<int, int, int, int>> g_simt_loaded;  // (device, form, degre
 }  // namespace
 
 int simt_supported(int form, int degree, int cell) {
-  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF || form == FORM_BURGERS)) return 0;
+  if (!(form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF || burgers_like(form))) return 0;
   if (!(cell == CELL_TRI || cell == CELL_TET)) return 0;
   const int d = cell == CELL_TRI ? 2 : 3;
-  return degree >= 1 && degree <= s_maxdeg(form, d) ? 1 : 0;
+  return degree >= 1 && degree <= s_maxdeg(burgers_like(form) ? FORM_BURGERS : form, d) ? 1 : 0;
 }
 
 // where the CUDA-core kernel is the faster one (measured, TF32X3 tensor-core kernel with its
@@ -379,7 +393,7 @@ int simt_supported(int form, int degree, int cell) {
 // triangles P3 stay on the tensor cores (their 100-entry matrices cost the CUDA cores more FMAs
 // than the tensor-core kernel's hand-offs)
 int simt_default(int form, int degree, int cell) {
-  if (form == FORM_BURGERS) return degree == 1 ? 1 : 0;
+  if (burgers_like(form)) return degree == 1 ? 1 : 0;
   return degree == 1 || (cell == CELL_TRI && degree == 2) ? 1 : 0;
 }
 
@@ -428,12 +442,13 @@ int launch_simt(int form, int degree, int cell, const TcParams& p, int num_sms, 
   if (p.ncells == 0) return (int)cudaSuccess;
   cudaError_t e = cudaSuccess;
   const int d = cell == CELL_TRI ? 2 : 3, ns = s_ns(d, degree);
-  const int nd = form == FORM_BURGERS ? d * ns : ns, N = nd * nd;
-  if ((e = (cudaError_t)simt_upload(form, degree, cell)) != cudaSuccess) {
+  const int nd = burgers_like(form) ? d * ns : ns, N = form == FORM_BURGERS_RES ? nd : nd * nd;
+  // the residual contracts the Jacobian's tensors: one table for both
+  if ((e = (cudaError_t)simt_upload(burgers_like(form) ? FORM_BURGERS : form, degree, cell)) != cudaSuccess) {
     why = "reference tensor upload";
     return (int)e;
   }
-  const int threads = form == FORM_BURGERS ? SIMT_BTHREADS : SIMT_THREADS, warps = threads / 32;
+  const int threads = burgers_like(form) ? SIMT_BTHREADS : SIMT_THREADS, warps = threads / 32;
   const int smem = warps * 32 * (N | 1) * (int)sizeof(float);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return (int)e;

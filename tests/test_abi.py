@@ -179,7 +179,7 @@ def test_support_queries_cover_prisms():
 
 def test_assemble_path_query():
     """Host-only: which kernel family runs. Small element matrices (MASS, HELMHOLTZ, ADVDIFF on
-    P1 simplices and P2 triangles, the Burgers Jacobian on P1 simplices) default to the FP32
+    P1 simplices and P2 triangles, the Burgers Jacobian and residual on P1 simplices) default to the FP32
     CUDA-core kernel, the rest of the tensor-core precisions to the tensor cores; the flags force
     either where both exist; FP64 is the FP64 kernel; unsupported combinations raise."""
     T, R, P = coffee.TETRAHEDRON, coffee.TRIANGLE, coffee.PRISM
@@ -196,7 +196,8 @@ def test_assemble_path_query():
         assert coffee.assemble_path(coffee.BURGERS_JAC, 1, cell, coffee.TF32X3) == 2
         assert coffee.assemble_path(coffee.BURGERS_JAC, 1, cell, coffee.TF32X3, coffee.FLAG_TENSOR_CORES) == 1
         assert coffee.assemble_path(coffee.BURGERS_JAC, 2, cell, coffee.TF32X3, coffee.FLAG_CUDA_CORES) == 1
-    assert coffee.assemble_path(coffee.BURGERS_RESIDUAL, 1, T, coffee.TF32X3, coffee.FLAG_CUDA_CORES) == 1
+    assert coffee.assemble_path(coffee.BURGERS_RESIDUAL, 1, T, coffee.TF32X3) == 2
+    assert coffee.assemble_path(coffee.BURGERS_RESIDUAL, 2, T, coffee.TF32X3, coffee.FLAG_CUDA_CORES) == 1
     with pytest.raises(coffee.CoffeeError):
         coffee.assemble_path(coffee.BURGERS_JAC, 1, P, coffee.TF32X3)
 

@@ -74,6 +74,25 @@ def test_residual_matches_oracle(cell, k, prec):
         assert worst < TOL[prec]  # the split precisions meet the bound against max|R| of each cell too
 
 
+@pytest.mark.parametrize("cell", [TRI, TET])
+@pytest.mark.parametrize("prec", [coffee.TF32X3, coffee.BF16X3])
+def test_residual_p1_both_kernel_families(cell, prec):
+    """P1 runs on the CUDA cores by default; the tensor-core kernel, forced, meets the same bounds
+    (per cell against the un-cancelled magnitude and globally)."""
+    mesh = ragged_mesh(cell, seed=64)
+    u, c2d, _ = meshgen.burgers_coefficients(mesh, 1, seed=9)
+    ref = oracle.burgers_residual(1, cell, mesh.coords, mesh.cell2vert, u, c2d)
+    x, c2v, cf, cd = to_device(mesh, u.ravel(), c2d, DEV)
+    assert coffee.assemble_path(RES, 1, cell, prec) == 2
+    for tune in (0, coffee.FLAG_TENSOR_CORES):
+        out = coffee.assemble(RES, 1, cell, x, c2v, cf, cd, precision=prec, validate=True, tune=tune)
+        coffee.check_errors()
+        got = out.cpu().numpy()
+        glob, _, worst = errors(got, ref)
+        per = cell_errors(got, ref, 1, cell, mesh.coords, mesh.cell2vert, u, c2d)
+        assert per < TOL[prec] and glob < TOL[prec] and worst < TOL[prec]
+
+
 def test_residual_is_the_jacobian_applied_to_u_minus_the_convective_half():
     """R(u) = J_c(u) u / 2 + J_nu u for the quadratic residual, where J_c is the convective part of
     the Jacobian: so J(u) u - R(u) = N(u, u) (the convective term once more); checked on the GPU
