@@ -130,15 +130,15 @@ typedef enum {
  * memory and write each group with one bulk copy, instead of warp stores of 32 entries of one
  * cell (the default) */
 #define COFFEE_FLAG_STAGED_STORE 256u
-/* Small element matrices (MASS, HELMHOLTZ, ADVDIFF on triangles P1-P3 and tetrahedra P1-P2,
- * the Burgers Jacobian and residual on P1 simplices) have a second kernel besides the
- * tensor-core one: one CUDA-core thread per cell, A_e = sum_k G_e[k] T[k] in FP32 (T rounded
- * once to FP32; within every tensor-core precision's bound). The library picks the faster one
- * per (form, degree, cell) for local assembly (measured: the CUDA-core kernel for P1 on both
- * cells, the Burgers forms included, and for triangles P2; global CSR assembly stays on the
- * tensor cores, batches put the CUDA-core groups in a launch of their own); these flags force
- * one: TENSOR_CORES the tcgen05 kernel, CUDA_CORES the FP32 kernel (ignored where it has no
- * instance). Results of the two differ by rounding, within the precision's bound. */
+/* Small element matrices (MASS, HELMHOLTZ, ADVDIFF on triangles P1-P3 and tetrahedra P1-P2;
+ * the Burgers Jacobian and residual on P1 simplices and P2 triangles) have a second kernel
+ * besides the tensor-core one: one CUDA-core thread per cell, A_e = sum_k G_e[k] T[k] in FP32
+ * (T rounded once to FP32; within every tensor-core precision's bound). The library picks the
+ * faster one per (form, degree, cell) for local assembly (measured: the CUDA-core kernel for P1
+ * on both cells and for triangles P2, the Burgers forms included; global CSR assembly stays on
+ * the tensor cores, batches put the CUDA-core groups in a launch of their own); these flags
+ * force one: TENSOR_CORES the tcgen05 kernel, CUDA_CORES the FP32 kernel (ignored where it has
+ * no instance). Results of the two differ by rounding, within the precision's bound. */
 #define COFFEE_FLAG_TENSOR_CORES 512u
 #define COFFEE_FLAG_CUDA_CORES 1024u
 /* BURGERS_JAC on the tensor cores with component blocks of at most 128 entries (triangles

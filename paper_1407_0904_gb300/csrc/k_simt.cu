@@ -44,8 +44,8 @@ __host__ __device__ constexpr int s_K(int form, int d, int k = 1) {
        : 2 * s_ns(d, k) * d + d * (d + 1) / 2;
 }
 // instances: MASS, HELMHOLTZ, ADVDIFF on triangles P1-P3 and tetrahedra P1-P2; the Burgers
-// Jacobian on P1 simplices
-__host__ __device__ constexpr int s_maxdeg(int form, int d) { return form == FORM_BURGERS ? 1 : d == 2 ? 3 : 2; }
+// Jacobian on triangles P1-P2 and tetrahedra P1
+__host__ __device__ constexpr int s_maxdeg(int form, int d) { return form == FORM_BURGERS ? (d == 2 ? 2 : 1) : d == 2 ? 3 : 2; }
 __host__ __device__ constexpr int s_size(int form, int d, int k) { return s_K(form, d, k) * s_ns(d, k) * s_ns(d, k); }
 // offset of each instance's table in the constant bank
 __host__ __device__ constexpr int s_off(int form, int d, int k) {
@@ -150,8 +150,8 @@ __device__ __forceinline__ void simt_tile(const TcParams& p, int64_t t, int lane
   __syncwarp();
 }
 
-// The Burgers Jacobian on P1 simplices (vector P1: d*(d+1) entries per row), one cell per thread,
-// in the factored form of its d x d component blocks of ns^2 entries (ns = d + 1):
+// The Burgers Jacobian on triangles P1-P2 and tetrahedra P1 (vector Pk: d ns entries per row), one
+// cell per thread, in the factored form of its d x d component blocks of ns^2 entries:
 //   block(ci, cj) = sum_a P[a][cj] V_a^ci + [ci == cj] C,   V_a^ci = sum_r u[r][ci] T1[r d + a],
 //   C = sum_{r,a} Q[r][a] T2[r d + a] + sum_p nu H_p T3[p],   Q[r][a] = sum_c u[r][c] P[a][c],
 // with P = |det J| K and T = [T1 | T2 | T3] the Burgers reference tensors (rows r d + a of T1 and
@@ -159,10 +159,10 @@ __device__ __forceinline__ void simt_tile(const TcParams& p, int64_t t, int lane
 // row by row and out with the warp's coalesced stores.
 constexpr int SIMT_BTHREADS = 128;  // the staging block of a tetrahedron is 145 floats per cell
 // RES: the residual instead (element vectors, R[(c, i)] = sum_s C[i][s] u[s][c]; C as above).
-template <int D, bool RES = false>
+template <int D, int DEG, bool RES = false>
 __device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, int lane, float* st) {
-  constexpr int NS = D + 1, NV = D + 1, NDOF = D * NS, N = RES ? NDOF : NDOF * NDOF, NB = NS * NS, K1 = NS * D;
-  constexpr int P = D * (D + 1) / 2, OFF = s_off(FORM_BURGERS, D, 1), SR = N | 1;
+  constexpr int NS = s_ns(D, DEG), NV = D + 1, NDOF = D * NS, N = RES ? NDOF : NDOF * NDOF, NB = NS * NS;
+  constexpr int K1 = NS * D, P = D * (D + 1) / 2, OFF = s_off(FORM_BURGERS, D, DEG), SR = N | 1;
   const int64_t c0 = t * 32, e = c0 + lane;
   float u[NS][D], Pm[D][D], H[P];
 #pragma unroll
@@ -283,16 +283,16 @@ __device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, 
   __syncwarp();
 }
 
-template <int D, bool RES>
+template <int D, int DEG, bool RES>
 __global__ void __launch_bounds__(SIMT_BTHREADS) k_assemble_simt_burgers(const TcParams p) {
-  constexpr int NDOF = D * (D + 1), N = RES ? NDOF : NDOF * NDOF;
+  constexpr int NDOF = D * s_ns(D, DEG), N = RES ? NDOF : NDOF * NDOF;
   extern __shared__ float stage[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* st = stage + warp * 32 * (N | 1);
   const int64_t ntiles = (p.ncells + 31) / 32;
   for (int64_t t = (int64_t)blockIdx.x * (SIMT_BTHREADS / 32) + warp; t < ntiles;
        t += (int64_t)gridDim.x * (SIMT_BTHREADS / 32))
-    simt_tile_burgers<D, RES>(p, t, lane, st);
+    simt_tile_burgers<D, DEG, RES>(p, t, lane, st);
 }
 
 template <int FORM, int D, int DEG>
@@ -354,10 +354,11 @@ SimtKernel pick_deg(int degree) {
 
 SimtKernel pick(int form, int degree, int cell) {
   if (form == FORM_BURGERS || form == FORM_BURGERS_RES) {
-    if (degree != 1) return nullptr;
-    if (form == FORM_BURGERS_RES)
-      return cell == CELL_TRI ? k_assemble_simt_burgers<2, true> : cell == CELL_TET ? k_assemble_simt_burgers<3, true> : nullptr;
-    return cell == CELL_TRI ? k_assemble_simt_burgers<2, false> : cell == CELL_TET ? k_assemble_simt_burgers<3, false> : nullptr;
+    const bool res = form == FORM_BURGERS_RES;
+    if (cell == CELL_TRI && degree == 1) return res ? k_assemble_simt_burgers<2, 1, true> : k_assemble_simt_burgers<2, 1, false>;
+    if (cell == CELL_TRI && degree == 2) return res ? k_assemble_simt_burgers<2, 2, true> : k_assemble_simt_burgers<2, 2, false>;
+    if (cell == CELL_TET && degree == 1) return res ? k_assemble_simt_burgers<3, 1, true> : k_assemble_simt_burgers<3, 1, false>;
+    return nullptr;
   }
   if (cell == CELL_TRI) {
     switch (form) {
@@ -393,7 +394,9 @@ int simt_supported(int form, int degree, int cell) {
 // triangles P3 stay on the tensor cores (their 100-entry matrices cost the CUDA cores more FMAs
 // than the tensor-core kernel's hand-offs)
 int simt_default(int form, int degree, int cell) {
-  if (burgers_like(form)) return degree == 1 ? 1 : 0;
+  // the Burgers forms: P1 (2^20 tets: Jacobian 0.221 vs 0.662 ms, residual 0.049 vs 0.078) and
+  // triangles P2 (2^21 cells: 0.444 vs 0.520 ms, residual 0.137 vs 0.160)
+  if (burgers_like(form)) return degree == 1 || (cell == CELL_TRI && degree == 2) ? 1 : 0;
   return degree == 1 || (cell == CELL_TRI && degree == 2) ? 1 : 0;
 }
 

@@ -83,7 +83,7 @@ int main(void) {
   CHECK(coffee_assemble_path(COFFEE_HELMHOLTZ, 3, COFFEE_TETRAHEDRON, COFFEE_TF32X3, 0) == 1);
   CHECK(coffee_assemble_path(COFFEE_HELMHOLTZ, 3, COFFEE_TETRAHEDRON, COFFEE_FP64, 0) == 0);
   CHECK(coffee_assemble_path(COFFEE_BURGERS_JAC, 1, COFFEE_TRIANGLE, COFFEE_TF32X3, 0) == 2);
-  CHECK(coffee_assemble_path(COFFEE_BURGERS_JAC, 2, COFFEE_TRIANGLE, COFFEE_TF32X3, COFFEE_FLAG_CUDA_CORES) == 1);
+  CHECK(coffee_assemble_path(COFFEE_BURGERS_JAC, 2, COFFEE_TETRAHEDRON, COFFEE_TF32X3, COFFEE_FLAG_CUDA_CORES) == 1);
   CHECK(coffee_csr_supported(COFFEE_BURGERS_RESIDUAL, 2, COFFEE_TETRAHEDRON, COFFEE_FP64) == 0);
 
   /* argument errors are reported on the host, before any CUDA call */

@@ -192,12 +192,13 @@ def test_assemble_path_query():
                 assert coffee.assemble_path(form, k, cell, prec, coffee.FLAG_CUDA_CORES) == forced
             assert coffee.assemble_path(form, k, cell, coffee.FP64) == 0
         assert coffee.assemble_path(form, 2, P, coffee.TF32X3, coffee.FLAG_CUDA_CORES) == 1
-    for cell in (T, R):  # the Burgers Jacobian: P1 on the CUDA cores, the rest on the tensor cores
-        assert coffee.assemble_path(coffee.BURGERS_JAC, 1, cell, coffee.TF32X3) == 2
-        assert coffee.assemble_path(coffee.BURGERS_JAC, 1, cell, coffee.TF32X3, coffee.FLAG_TENSOR_CORES) == 1
-        assert coffee.assemble_path(coffee.BURGERS_JAC, 2, cell, coffee.TF32X3, coffee.FLAG_CUDA_CORES) == 1
-    assert coffee.assemble_path(coffee.BURGERS_RESIDUAL, 1, T, coffee.TF32X3) == 2
-    assert coffee.assemble_path(coffee.BURGERS_RESIDUAL, 2, T, coffee.TF32X3, coffee.FLAG_CUDA_CORES) == 1
+    # the Burgers forms: P1 and triangles P2 on the CUDA cores, the rest on the tensor cores
+    for form in (coffee.BURGERS_JAC, coffee.BURGERS_RESIDUAL):
+        for cell, k in ((T, 1), (R, 1), (R, 2)):
+            assert coffee.assemble_path(form, k, cell, coffee.TF32X3) == 2
+            assert coffee.assemble_path(form, k, cell, coffee.TF32X3, coffee.FLAG_TENSOR_CORES) == 1
+        assert coffee.assemble_path(form, 2, T, coffee.TF32X3, coffee.FLAG_CUDA_CORES) == 1
+        assert coffee.assemble_path(form, 3, R, coffee.TF32X3) == 1
     with pytest.raises(coffee.CoffeeError):
         coffee.assemble_path(coffee.BURGERS_JAC, 1, P, coffee.TF32X3)
 

@@ -64,6 +64,27 @@ def test_burgers_p1_on_the_cuda_cores(cell, prec):
     assert torch.equal(out, out2)
 
 
+@pytest.mark.parametrize("form", [BURGERS_JAC, coffee.BURGERS_RESIDUAL])
+@pytest.mark.parametrize("prec", [coffee.TF32X3, coffee.BF16])
+def test_burgers_triangles_p2_on_the_cuda_cores(form, prec):
+    """Triangles P2 (the default path there): Jacobian and residual within the split
+    precisions' bound of the oracle."""
+    mesh = mesh_of(TRI, seed=74)
+    coef, c2d = coefficients(BURGERS_JAC, mesh, 2, seed=75)
+    x, c2v, cf, cd = to_device(mesh, coef, c2d, DEV)
+    assert coffee.assemble_path(form, 2, TRI, prec, coffee.FLAG_CUDA_CORES) == 2
+    out = coffee.assemble(form, 2, TRI, x, c2v, cf, cd, precision=prec, validate=True, tune=coffee.FLAG_CUDA_CORES)
+    coffee.check_errors()
+    if form == BURGERS_JAC:
+        ref = oracle_ref(BURGERS_JAC, 2, TRI, mesh, coef, c2d)
+        assert rel_err_per_cell(out.cpu().numpy(), ref) < 1e-5
+    else:
+        import oracle
+        ref = oracle.burgers_residual(2, TRI, mesh.coords, mesh.cell2vert, coef.reshape(-1, 2), c2d)
+        got = out.cpu().numpy()
+        assert np.abs(got - ref).max() < 1e-5 * np.abs(ref).max()
+
+
 def test_burgers_p1_flags_a_bad_index():
     mesh = mesh_of(TET, seed=72)
     coef, c2d = coefficients(BURGERS_JAC, mesh, 1, seed=73)
