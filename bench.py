@@ -180,6 +180,14 @@ def parse():
     ap.add_argument("--no-coef-f32", action="store_true",
                     help="tensor-core kernels convert the FP64 coefficients per cell instead of reading the "
                          "float copy that each step rounds once per node")
+    ap.add_argument("--coords-split", default="auto", choices=["auto", "on", "off"],
+                    help="split the coordinates into float (hi, lo) pairs once per vertex in each step "
+                         "(coffee_split_coords, timed with the assembly) and pass them to the kernel; "
+                         "auto: on for degree 1 (many cells per vertex, little work per cell; measured "
+                         "faster on P1 tetrahedra, even on P1 triangles, slower on the tensor-core P2 kernels)")
+    ap.add_argument("--graph", default="auto", choices=["auto", "on", "off"],
+                    help="replay each timed step as a CUDA graph captured once (auto: when a step launches "
+                         "more than one kernel, so that host time between the launches is not timed)")
     ap.add_argument("--nx", type=int, default=None, help="smaller mesh (cells per axis) for profiling")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -408,20 +416,53 @@ def run_ours(args):
     cf32 = (torch.empty(coef.shape, dtype=torch.float32, device=dev)
             if coef is not None and prec != coffee.FP64 and not args.no_coef_f32 else None)
 
+    # small element matrices: each step also splits every coordinate once per vertex into float
+    # (hi, lo) pairs (coffee_split_coords, inside the timed step), from which the kernel takes the
+    # Jacobian's vertex differences, instead of splitting each vertex once per cell that uses it
+    xsplit = None
+    if (prec != coffee.FP64 and cell != PRISM
+            and (args.coords_split == "on" or (args.coords_split == "auto" and degree == 1))):
+        xsplit = torch.empty(tuple(coords.shape) + (2,), dtype=torch.float32, device=dev)
+    launches_per_step = 1 + (cf32 is not None) + (xsplit is not None)
+
     def step(precision, o):
-        if cf32 is not None and precision != coffee.FP64:
+        fast = precision != coffee.FP64
+        if xsplit is not None and fast:
+            coffee.split_coords(coords, out=xsplit)
+        if cf32 is not None and fast:
             coffee.round_coef(coef, out=cf32)
         coffee.assemble(form, degree, cell, coords, c2v, coef, c2d, precision=precision, out=o,
-                        coef_f32=cf32 if precision != coffee.FP64 else None, out_stride=ostride or None,
-                        tune=tune if precision != coffee.FP64 else None)
+                        coef_f32=cf32 if fast else None, out_stride=ostride or None,
+                        coords_split=xsplit if fast else None, tune=tune if fast else None)
 
     # one checked launch before timing (parity against the oracle is the test suite's job)
     step(prec, out)
     coffee.check_errors()
 
-    def timed(precision, o, steps, warmup):
+    def capture(fn):
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                fn()
+        stream.wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        torch.cuda.synchronize()
+        return g
+
+    # a step of several launches (coordinate split, coefficient rounding, assembly) replays as one
+    # CUDA graph: launched one by one from Python, the host time between them is in the step
+    run = lambda: step(prec, out)
+    step_graph = None
+    if args.graph == "on" or (args.graph == "auto" and launches_per_step > 1):
+        step_graph = capture(run)
+        run = step_graph.replay
+
+    def timed(fn, steps, warmup):
         for _ in range(warmup):
-            step(precision, o)
+            fn()
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -432,7 +473,7 @@ def run_ours(args):
         t0.record(stream)
         for a, b in evs:
             a.record(stream)
-            step(precision, o)
+            fn()
             b.record(stream)
         t1.record(stream)
         torch.cuda.synchronize()
@@ -441,7 +482,7 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.5)  # let nvidia-smi start sampling before the timed region
-    total_ms, launch_ms = timed(prec, out, args.steps, args.warmup)
+    total_ms, launch_ms = timed(run, args.steps, args.warmup)
     clocks = sampler.stop()
     coffee.check_errors()
     total_ms = reduce_over_ranks(total_ms, world, "max", dev)
@@ -489,8 +530,10 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "alg_bytes_per_cell": per_cell, "kernel_ms": launch_ms}
-    if cf32 is not None:
-        roof["kernel_ms_spans"] = "coffee_round_coef and the assembly kernel (one step)"
+    if launches_per_step > 1:
+        roof["kernel_ms_spans"] = " and ".join(
+            ["coffee_split_coords"] * (xsplit is not None) + ["coffee_round_coef"] * (cf32 is not None)
+            + ["the assembly kernel (one step)"])
     if prec == coffee.FP64:
         roof["note"] = ("FP64 kernel: bound by the FP64 ALU (%.2f TFLOP/s measured by coffee_peak_fp64); "
                         "HBM fraction for context" % device_peaks(coffee)["fp64_tflops"])
@@ -532,7 +575,7 @@ def run_ours(args):
     if prec != coffee.FP64 and not args.no_fp64:
         out64 = torch.empty(tuple(out.shape), dtype=torch.float64, device=dev)  # same row layout
         fsteps = max(3, min(args.steps // 20, 100))
-        tms, lms = timed(coffee.FP64, out64, fsteps, 3)
+        tms, lms = timed(lambda: step(coffee.FP64, out64), fsteps, 3)
         fp64 = {"value": ncells * fsteps / (tms / 1e3), "kernel_ms": lms, "steps": fsteps}
         del out64
 
@@ -589,10 +632,15 @@ def run_ours(args):
                            "coefficients": (None if coef is None else
                                             "rounded to float once per node each step (coffee_round_coef, "
                                             "timed with the assembly)" if cf32 is not None else
-                                            "FP64, converted per cell in the kernel")},
+                                            "FP64, converted per cell in the kernel"),
+                           "launch": ("each step replays a CUDA graph of its %d kernels" % launches_per_step
+                                      if step_graph is not None else "each step launched from Python"),
+                           "coordinates": ("split into float (hi, lo) pairs once per vertex each step "
+                                           "(coffee_split_coords, timed with the assembly)" if xsplit is not None
+                                           else "FP64, split per cell in the kernel")},
                 "roofline": roof, "fp64_kernel": fp64,
                 "tc_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
-                "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": args.steps * (2 if cf32 is not None else 1),
+                "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": args.steps * launches_per_step,
                 "clocks": clocks, "kernel_sha": sha, "device_peaks": device_peaks(coffee),
                 "graph_replay": graph}
         print(json.dumps(line), flush=True)

@@ -207,11 +207,13 @@ typedef struct {
   void* out;                 /* device [ncells][ndof][ndof], double or float */
   int64_t ncells;
   unsigned flags;            /* COFFEE_FLAG_* */
-  /* optional, device [nverts][d][2] float: every coordinate as hi = (float)x and
-   * lo = (float)(x - hi), as coffee_split_coords writes them, or NULL. The tensor-core kernels on
+  /* optional, device [nverts][d][2] float: every coordinate x as a float pair (hi, lo) with
+   * hi + lo = x to about 2^-48 |x|, as coffee_split_coords writes them (hi = (float)x and
+   * lo = (float)(x - hi) serve as well), or NULL. The tensor-core and CUDA-core kernels on
    * triangles and tetrahedra then take the vertex differences of the Jacobian in FP32
-   * ((hi1 - hi0) + (lo1 - lo0)) instead of FP64; coords must still be given (badly conditioned
-   * cells are recomputed from it in FP64). Ignored by the FP64 kernels and by prisms. */
+   * ((hi1 - hi0) + (lo1 - lo0)) from the pairs instead of forming them per cell; coords must
+   * still be given (badly conditioned cells are recomputed from it in FP64). Ignored by the FP64
+   * kernels and by prisms. */
   const float* coords_split;
   /* optional, device, the layout and length of coef in float: every coefficient rounded to
    * nearest ((float)coef[i]), as coffee_round_coef writes it, or NULL. The tensor-core kernels
@@ -232,9 +234,13 @@ typedef struct {
   int64_t out_stride;
 } coffee_assemble_args;
 
-/* Every coordinate x[i], i < n (n = nverts * d), as the float pair (hi, lo) = ((float)x,
- * (float)(x - hi)) in split[2i], split[2i+1]: the coords_split input of coffee_assemble_args.
- * Device pointers, asynchronous on stream; n == 0 returns COFFEE_OK. */
+/* Every coordinate x[i], i < n (n = nverts * d), as a float pair (hi, lo) in split[2i],
+ * split[2i+1] with hi + lo = x to 2^-48 |x| (for 2^-100 <= |x| < 2^127, where lo is a normal
+ * float): the coords_split input of coffee_assemble_args.
+ * For 2^-70 <= |x| < 2^100, hi is x truncated to the 24 significant bits of a float (|hi| <= |x|,
+ * same sign) and lo = x - hi rounded to the nearest float; outside that range hi = (float)x and
+ * lo = (float)(x - hi); zero gives (0, 0). Device pointers, both 8-byte aligned (else
+ * COFFEE_ERR_INVALID_ARG), asynchronous on stream; n == 0 returns COFFEE_OK. */
 int coffee_split_coords(const double* coords, int64_t n, float* split, coffee_stream_t stream);
 
 /* Every coefficient coef[i], i < n (n = ncoefnodes * components), rounded to the nearest float:

@@ -233,9 +233,11 @@ def check_shapes(form, degree, cell, coords, cell2vert, coef=None, cell2dof=None
 
 
 def split_coords(coords, out=None, stream=None):
-    """coffee_split_coords: every coordinate as the float pair (hi, lo) = ((float)x, (float)(x - hi)),
-    a float32 tensor [nverts, d, 2] on the device: the coords_split input of assemble, with which
-    the tensor-core kernels take the Jacobian's vertex differences in FP32."""
+    """coffee_split_coords: every coordinate as a float pair (hi, lo) with hi + lo = x to 2^-48 |x|
+    (hi: x truncated to 24 significant bits, lo: the rest rounded to a float; for |x| outside
+    [2^-70, 2^100) hi = (float)x, lo = (float)(x - hi)), a float32 tensor [nverts, d, 2] on the
+    device: the coords_split input of assemble, with which the kernels take the Jacobian's vertex
+    differences in FP32 without splitting each vertex again for every cell that uses it."""
     coords = _dev(coords, torch.float64, "coords")
     if out is None:
         out = torch.empty(tuple(coords.shape) + (2,), dtype=torch.float32, device=coords.device)

@@ -12,15 +12,80 @@
 #include "../../include/coffee.h"
 #include "../../include/coffee_diag.h"
 #include "coffee_internal.h"
+#include "tc_common.cuh"
 
 namespace coffee {
 
-// every coordinate as (hi, lo) = ((float)x, (float)(x - hi)): the coords_split input
+// The two per-node conversion kernels below (coordinates, coefficients) move a few MB each. They
+// convert by integer operations: FP64 instructions, conversions included, issue at 1/16 of a
+// warp per SM cycle on this GPU, which made both kernels FP64-bound (ncu: SM 64% busy, DRAM 10%).
+// The FP64 forms run out of line (a call, so the compiler cannot if-convert them into every
+// thread's path) for the values the integer forms do not cover. With one 16-byte load in flight
+// per thread a full GPU holds about 5 MB of loads at once, so each thread issues UNROLL
+// independent 16-byte loads before it converts and stores any of them.
+constexpr int UNROLL = 4;
+
+__device__ __noinline__ float2 split_pair_f64(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+// x as a float pair (hi, lo) with hi + lo = x to 2^-48 of |x| (lo a normal float:
+// 2^-100 <= |x| < 2^127). In the range split_exact takes (|x| in [2^-70, 2^100)), hi is x
+// truncated to 24 significant bits and lo the rest; outside it hi = (float)x, lo = (float)(x - hi).
+__device__ __forceinline__ float2 split_pair(double v) {
+  float hi, lo;
+  if (!tc::split_exact(v, hi, lo)) return split_pair_f64(v);
+  return make_float2(hi, lo);
+}
+
+__device__ __noinline__ float f32_of_f64(double v) { return (float)v; }
+
+// The float nearest to v, ties to even (IEEE 754 round to nearest): where the result is a normal
+// float (biased exponent e of v in [897, 1150], |v| in [2^-126, 2^128)) the float's exponent is
+// e - 896 and its 23 fraction bits are v's top 23; the 29 bits below decide: above half an ulp,
+// or exactly half with an odd result, add one ulp (a carry moves into the exponent, up to
+// infinity past the largest float, as rounding to nearest gives). Zero, results below 2^-126,
+// infinities and NaN take the conversion instruction.
+__device__ __forceinline__ float f32_rn(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const uint32_t h = (uint32_t)(b >> 32), l = (uint32_t)b;
+  const uint32_t ef = h & 0x7FF00000u;
+  if (ef - (897u << 20) > ((1150u - 897u) << 20)) return f32_of_f64(v);
+  const uint32_t f = __funnelshift_l(l, (h & 0x7FFFFFFFu) - (896u << 20), 3);
+  const uint32_t rem = l & 0x1FFFFFFFu;
+  const uint32_t up = (uint32_t)(rem > 0x10000000u) | ((uint32_t)(rem == 0x10000000u) & f);
+  return __uint_as_float(((f + (up & 1u))) | (h & 0x80000000u));
+}
+
+// every coordinate as its (hi, lo) pair: the coords_split input
 __global__ void k_split_coords(const double* __restrict__ x, int64_t n, float2* __restrict__ out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = x[i];
-    const float hi = (float)v;
-    out[i] = make_float2(hi, (float)(v - (double)hi));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(x) & 15u) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
+  if (vec) {  // pairs of coordinates: 16 bytes in, 16 out
+    const int64_t n2 = n / 2;
+    const double2* x2 = reinterpret_cast<const double2*>(x);
+    float4* o4 = reinterpret_cast<float4*>(out);
+    for (int64_t b = i0; b < n2; b += UNROLL * stride) {
+      double2 v[UNROLL];
+#pragma unroll
+      for (int j = 0; j < UNROLL; ++j) {
+        const int64_t i = b + j * stride;
+        v[j] = i < n2 ? __ldcs(x2 + i) : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < UNROLL; ++j) {
+        const int64_t i = b + j * stride;
+        if (i < n2) {
+          const float2 a = split_pair(v[j].x), c = split_pair(v[j].y);
+          o4[i] = make_float4(a.x, a.y, c.x, c.y);
+        }
+      }
+    }
+    if (i0 == 0 && (n & 1)) out[n - 1] = split_pair(x[n - 1]);
+  } else {
+    for (int64_t i = i0; i < n; i += stride) out[i] = split_pair(x[i]);
   }
 }
 
@@ -31,13 +96,22 @@ __global__ void k_round_coef(const double* __restrict__ x, int64_t n, float* __r
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (vec) {
-    for (int64_t i = i0; i < n2; i += stride) {
-      const double2 v = __ldcs(reinterpret_cast<const double2*>(x) + i);
-      reinterpret_cast<float2*>(out)[i] = make_float2((float)v.x, (float)v.y);
+    for (int64_t b = i0; b < n2; b += UNROLL * stride) {
+      double2 v[UNROLL];
+#pragma unroll
+      for (int j = 0; j < UNROLL; ++j) {
+        const int64_t i = b + j * stride;
+        v[j] = i < n2 ? __ldcs(reinterpret_cast<const double2*>(x) + i) : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < UNROLL; ++j) {
+        const int64_t i = b + j * stride;
+        if (i < n2) reinterpret_cast<float2*>(out)[i] = make_float2(f32_rn(v[j].x), f32_rn(v[j].y));
+      }
     }
-    if (i0 == 0 && (n & 1)) out[n - 1] = (float)x[n - 1];
+    if (i0 == 0 && (n & 1)) out[n - 1] = f32_rn(x[n - 1]);
   } else {
-    for (int64_t i = i0; i < n; i += stride) out[i] = (float)x[i];
+    for (int64_t i = i0; i < n; i += stride) out[i] = f32_rn(x[i]);
   }
 }
 
@@ -412,13 +486,15 @@ int coffee_split_coords(const double* coords, int64_t n, float* split, coffee_st
   if (n < 0) return fail(COFFEE_ERR_INVALID_ARG, "split_coords: n < 0");
   if (n == 0) return COFFEE_OK;
   if (!coords || !split) return fail(COFFEE_ERR_INVALID_ARG, "split_coords: coords and split must be non-NULL");
+  if ((reinterpret_cast<uintptr_t>(coords) & 7u) || (reinterpret_cast<uintptr_t>(split) & 7u))
+    return fail(COFFEE_ERR_INVALID_ARG, "split_coords: coords and split must be 8-byte aligned");
   DeviceCache* c = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
     int rc = device_cache(&c);
     if (rc != COFFEE_OK) return rc;
   }
-  const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8);
+  const int64_t blocks = std::min<int64_t>((n / 2 + 255) / 256 + 1, (int64_t)c->num_sms * 8);
   k_split_coords<<<(unsigned)blocks, 256, 0, stream>>>(coords, n, reinterpret_cast<float2*>(split));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "launch(split_coords)");

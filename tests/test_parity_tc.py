@@ -243,16 +243,38 @@ def test_staged_rows_ragged_tails(k, ncells, prec):
 
 
 def test_split_coords_are_hi_lo_float_pairs():
-    """coffee_split_coords: hi is the float rounding of x and lo the float rounding of x - hi, so
-    hi + lo holds x to about 2^-48 of |x|."""
+    """coffee_split_coords: for 2^-70 <= |x| < 2^100, hi is x with the 29 fraction bits below a
+    float's 24 significant bits cleared and lo the float rounding of x - hi (exact in FP64);
+    outside that range hi = (float)x, lo = (float)(x - hi); either way hi + lo holds x to 2^-48
+    of |x| where lo stays a normal float (2^-100 <= |x| < 2^127)."""
     mesh = meshgen.tet_mesh(5, perturb=0.15, seed=80)
-    x, _, _, _ = to_device(mesh, None, None, DEV)
-    s = coffee.split_coords(x).double().cpu().numpy()
-    assert s.shape == mesh.coords.shape + (2,)
-    np.testing.assert_array_equal(s[..., 0], mesh.coords.astype(np.float32).astype(np.float64))
-    lo = (mesh.coords - s[..., 0]).astype(np.float32).astype(np.float64)
-    np.testing.assert_array_equal(s[..., 1], lo)
-    assert np.abs(s[..., 0] + s[..., 1] - mesh.coords).max() <= 2.0 ** -48 * np.abs(mesh.coords).max()
+    rng = np.random.default_rng(81)
+    extra = np.concatenate([
+        [0.0, -0.0, 1.0, -1.0, 2.0 ** -70, -(2.0 ** -70), 2.0 ** 100 * (1 - 2.0 ** -53), 2.0 ** 100, -(2.0 ** 100),
+         2.0 ** -71, 1e-30, -1e-35, 1e35, 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -25, 1.0 - 2.0 ** -53],
+        rng.standard_normal(64) * 10.0 ** rng.integers(-25, 28, 64)])
+    x64 = np.concatenate([mesh.coords.ravel(), extra])
+    x = torch.from_numpy(x64).to(DEV)
+    s = coffee.split_coords(x).double().cpu().numpy().reshape(-1, 2)
+    assert s.shape == (x64.size, 2)
+    inr = (np.abs(x64) >= 2.0 ** -70) & (np.abs(x64) < 2.0 ** 100)
+    hi_t = (x64.view(np.uint64) & ~np.uint64((1 << 29) - 1)).view(np.float64)
+    hi = np.where(inr, hi_t, x64.astype(np.float32).astype(np.float64))
+    hi[x64 == 0] = 0.0
+    np.testing.assert_array_equal(s[:, 0], hi)
+    np.testing.assert_array_equal(s[:, 1], (x64 - hi).astype(np.float32).astype(np.float64))
+    normal = (np.abs(x64) >= 2.0 ** -100) & (np.abs(x64) < 2.0 ** 127)
+    assert (normal | (x64 == 0)).sum() > x64.size - 8
+    err = np.abs((s[:, 0] - x64) + s[:, 1])  # s0 - x is exact: no rounding in the check itself
+    assert np.all(err[normal] <= 2.0 ** -48 * np.abs(x64[normal]))
+    # odd counts and pointers off the 16-byte boundary take the one-value-per-thread path
+    s1 = coffee.split_coords(x[1:]).double().cpu().numpy().reshape(-1, 2)
+    np.testing.assert_array_equal(s1, s[1:])
+    buf = torch.empty(2 * x64.size + 2, dtype=torch.float32, device=DEV)
+    coffee.split_coords(x, out=buf[2:])
+    np.testing.assert_array_equal(buf[2:].double().cpu().numpy().reshape(-1, 2), s)
+    with pytest.raises(RuntimeError):
+        coffee.split_coords(x, out=buf[1:-1])  # 4-byte offset: not a float pair boundary
 
 
 SPLIT_CASES = [(f, c, k, p) for f in (MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC) for c in (TRI, TET)
@@ -279,13 +301,22 @@ def test_split_coordinates_match_oracle(form, cell, k, prec):
 
 
 def test_round_coef_is_the_float_rounding():
-    """coffee_round_coef: every coefficient as (float)coef, also for odd lengths and a start that
-    is not 16-byte aligned (the scalar loop)."""
+    """coffee_round_coef: every coefficient as (float)coef, bit for bit (ties to even, carries into
+    the exponent, overflow to infinity, results below the normal range, zeros, infinities, NaN),
+    also for odd lengths and a start that is not 16-byte aligned (the scalar loop)."""
     rng = np.random.default_rng(81)
-    c = torch.from_numpy(rng.standard_normal(100001) * 10.0 ** rng.integers(-30, 30, 100001)).to(DEV)
-    for v in (c, c[1:]):
+    u = 2.0 ** -24
+    fmax = float(np.finfo(np.float32).max)
+    edge = np.array([1 + u, 1 + 3 * u, 1 + u + 2.0 ** -52, 1 + u - 2.0 ** -52, 2 - u, 2 - u / 2, 2 - 2 * u,
+                     fmax, fmax * (1 + u / 2), fmax * (1 + u / 2) * (1 - 2.0 ** -52), fmax * (1 + u),
+                     2.0 ** 127 * (2 - 2.0 ** -30), 2.0 ** 128, 1e39, 2.0 ** -126, 2.0 ** -126 * (1 - 2.0 ** -30),
+                     2.0 ** -127, 1e-40, 1e-45, 1e-50, 2.0 ** -1074, 0.0, np.inf, np.nan, 0.1, 1 / 3])
+    edge = np.concatenate([edge, -edge])
+    c = torch.from_numpy(np.concatenate([rng.standard_normal(100001) * 10.0 ** rng.integers(-30, 30, 100001),
+                                         edge])).to(DEV)
+    for v in (c, c[1:], c[2:]):
         r = coffee.round_coef(v)
-        assert torch.equal(r, v.float())
+        assert torch.equal(r.view(torch.int32), v.float().view(torch.int32))
 
 
 COEF_CASES = ([(f, c, k, p) for f in (ADVDIFF, BURGERS_JAC, coffee.BURGERS_RESIDUAL) for c in (TRI, TET)
