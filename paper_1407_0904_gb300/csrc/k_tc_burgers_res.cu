@@ -157,6 +157,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
           atomicOr(p.err, ERR_INDEX);
           live = false;
         } else {
+          // u's loads first: issued before the coordinates' and the geometry, both gathers share
+          // one round trip to memory instead of the second waiting for the geometry
+          coef_rows<NS, D>(p, did, u);
           float adj[D][D], Dm, sg;
           cell_geometry_ids<D>(p, vid, adj, Dm, sg);
           const float inv = 1.0f / Dm;
@@ -174,7 +177,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
               for (int r = 0; r < D; ++r) acc = fmaf(adj[a][r], adj[b][r], acc);
               H[q++] = nu * acc * inv;
             }
-          coef_rows<NS, D>(p, did, u);
         }
       }
       // u for the epilogue, once the slot's previous tile has left it
