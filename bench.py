@@ -183,8 +183,8 @@ def parse():
     ap.add_argument("--coords-split", default="auto", choices=["auto", "on", "off"],
                     help="split the coordinates into float (hi, lo) pairs once per vertex in each step "
                          "(coffee_split_coords, timed with the assembly) and pass them to the kernel; "
-                         "auto: on for degree 1 (many cells per vertex, little work per cell; measured "
-                         "faster on P1 tetrahedra, even on P1 triangles, slower on the tensor-core P2 kernels)")
+                         "auto: on for degree 1 and the residual (many cells per vertex, little work per cell; "
+                         "measured faster there, even on P1 triangles, slower on the tensor-core P2 matrices)")
     ap.add_argument("--graph", default="auto", choices=["auto", "on", "off"],
                     help="replay each timed step as a CUDA graph captured once (auto: when a step launches "
                          "more than one kernel, so that host time between the launches is not timed)")
@@ -421,7 +421,8 @@ def run_ours(args):
     # Jacobian's vertex differences, instead of splitting each vertex once per cell that uses it
     xsplit = None
     if (prec != coffee.FP64 and cell != PRISM
-            and (args.coords_split == "on" or (args.coords_split == "auto" and degree == 1))):
+            and (args.coords_split == "on"
+                 or (args.coords_split == "auto" and (degree == 1 or form == BURGERS_RESIDUAL)))):
         xsplit = torch.empty(tuple(coords.shape) + (2,), dtype=torch.float32, device=dev)
     launches_per_step = 1 + (cf32 is not None) + (xsplit is not None)
 

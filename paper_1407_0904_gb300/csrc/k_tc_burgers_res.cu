@@ -20,6 +20,10 @@
 // third of its time on that gather and waited on the MMA only 4% of the time, so it set the
 // rate.) A slot's buffer is rewritten after the epilogue has released the slot's accumulator,
 // which it does after its last read of u.
+// Each epilogue warp stages its 32 cells' rows (contiguous in the output) in shared memory and
+// writes them with coalesced 16-byte stores: written by each thread as its own 4 d ns-byte row,
+// every store instruction of the warp touched 32 sectors for 256 bytes (measured: without the
+// output stores the kernel ran 20% faster).
 // Pipeline roles and bounded waits are those of k_tc_burgers.cu.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -48,6 +52,8 @@ struct ResShape {
   static constexpr int SLOTW = NPAD <= 128 ? 128 : 256;
   static constexpr int NSLOT = 512 / SLOTW;
   static constexpr int UBYTES = NSLOT * K1 * BM * 4;  // the u ring
+  static constexpr int OSTRIDE = NS * D + 1;            // staged output row (odd: conflict-free)
+  static constexpr int OBYTES = EPI_WARPS * 32 * OSTRIDE * 4;
 };
 
 template <int D, int NS, int PREC>
@@ -69,7 +75,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
   uint8_t* sA = smem;
   uint8_t* sB = smem + a_bytes;
   float* ring = reinterpret_cast<float*>(sB + nstages * GPARTS * tile_bytes);  // [NSLOT][K1][BM]
-  Barriers* bars = reinterpret_cast<Barriers*>(reinterpret_cast<uint8_t*>(ring) + S::UBYTES);
+  float* ostage = ring + S::UBYTES / 4;  // [EPI_WARPS][32][OSTRIDE]
+  Barriers* bars = reinterpret_cast<Barriers*>(reinterpret_cast<uint8_t*>(ostage) + S::OBYTES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (p.ncells + BN - 1) / BN;
@@ -249,6 +256,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
     // ---------------- epilogue: each thread forms and writes its cell's residual ----------------
     const int q = warp;  // lanes 32q..32q+31 = cells of the tile
     const int row = q * 32 + lane;
+    float* ost = ostage + q * 32 * S::OSTRIDE;
+    const bool vec = (reinterpret_cast<uintptr_t>(p.out) & 15u) == 0;
     uint32_t rc = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++rc) {
       const uint32_t slot = rc % NSLOT, round = rc / NSLOT;
@@ -287,16 +296,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_res_tc(const TcParams p
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[slot]));  // accumulator and u buffer free
-      if (live) {
-        float* out = p.out + cell * NDOF;
-        if constexpr (NDOF % 2 == 0) {
+      // the warp's rows, contiguous in the output, through shared memory
+      const int64_t c0 = t * BN + q * 32;
+      if (c0 < p.ncells) {  // warp-uniform
 #pragma unroll
-          for (int x = 0; x < NDOF; x += 2)
-            __stcs(reinterpret_cast<float2*>(out + x), make_float2(R[x / NS][x % NS], R[(x + 1) / NS][(x + 1) % NS]));
-        } else {
+        for (int x = 0; x < NDOF; ++x) ost[lane * S::OSTRIDE + x] = R[x / NS][x % NS];
+        __syncwarp();
+        const int nlive = (int)((p.ncells - c0) < 32 ? (p.ncells - c0) : 32);
+        const int nel = nlive * NDOF;
+        float* out = p.out + c0 * NDOF;
+        const int n4 = vec ? nel / 4 : 0;  // rows of 32 cells start 128 d ns bytes apart
+        for (int f = lane; f < n4; f += 32) {
+          float v[4];
 #pragma unroll
-          for (int x = 0; x < NDOF; ++x) __stcs(out + x, R[x / NS][x % NS]);
+          for (int j = 0; j < 4; ++j) {
+            const int e = 4 * f + j;
+            v[j] = ost[(e / NDOF) * S::OSTRIDE + e % NDOF];
+          }
+          __stcs(reinterpret_cast<float4*>(out) + f, make_float4(v[0], v[1], v[2], v[3]));
         }
+        for (int e = 4 * n4 + lane; e < nel; e += 32) __stcs(out + e, ost[(e / NDOF) * S::OSTRIDE + e % NDOF]);
+        __syncwarp();
       }
     }
   }
@@ -316,8 +336,9 @@ int res_smem(int ns, int d, int prec, int nst) {
   const int kstep = tf32 ? 8 : 16, elem = tf32 ? 4 : 2, P = d * (d + 1) / 2, K1 = ns * d;
   const int kbytes = round_up(K1 + P, kstep) * elem;
   const int npad = round_up(ns * ns, 16), nslot = npad <= 128 ? 4 : 2, mt = (ns * ns + BM - 1) / BM;
+  const int obytes = EPI_WARPS * 32 * (ns * d + 1) * 4;  // ResShape::OBYTES
   return mt * prec_tparts(prec) * BM * kbytes + nst * prec_gparts(prec) * BN * kbytes + nslot * K1 * BM * 4 +
-         (int)sizeof(Barriers) + 1024 + 64;
+         obytes + (int)sizeof(Barriers) + 1024 + 64;
 }
 
 // operand stages (even, one set per producer group) that fit, 0 if none
