@@ -191,6 +191,8 @@ __device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, 
     if (bad) {
       atomicOr(p.err, ERR_INDEX);
     } else {
+      // u's loads first, so that they and the coordinates' share one round trip to memory
+      coef_rows<NS, D>(p, did, u);
       float adj[D][D], Dm, sg;
       cell_geometry_ids<D, true>(p, vid, adj, Dm, sg);
       const float inv = 1.0f / Dm, nu = (float)p.nu;
@@ -208,7 +210,6 @@ __device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, 
           for (int r = 0; r < D; ++r) s = fmaf(adj[a][r], adj[b][r], s);
           H[q++] = nu * s * inv;
         }
-      coef_rows<NS, D>(p, did, u);
     }
   }
   // C, shared by the diagonal blocks

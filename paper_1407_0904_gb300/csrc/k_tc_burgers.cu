@@ -136,6 +136,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
           atomicOr(p.err, ERR_INDEX);
           live = false;
         } else {
+          // u's loads first, so that they and the coordinates' share one round trip to memory
+          coef_rows<NS, D>(p, did, u);
           float adj[D][D], Dm, sg;
           cell_geometry_ids<D>(p, vid, adj, Dm, sg);
           const float inv = 1.0f / Dm;
@@ -153,7 +155,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_tc(const TcParams p, in
               for (int r = 0; r < D; ++r) s = fmaf(adj[a][r], adj[b][r], s);
               H[q++] = (float)p.nu * s * inv;
             }
-          coef_rows<NS, D>(p, did, u);
         }
       }
       // blocks and chunks as compile-time indices, so u[.][ci] and P[.][cj] stay in registers

@@ -204,6 +204,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_fact_tc(const TcParams 
           atomicOr(p.err, ERR_INDEX);
           live = false;
         } else {
+          // u's loads first, so that they and the coordinates' share one round trip to memory
+          coef_rows<NS, D>(p, did, u);
           float adj[D][D], Dm, sg;
           cell_geometry_ids<D>(p, vid, adj, Dm, sg);
           const float inv = 1.0f / Dm;
@@ -221,7 +223,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_burgers_fact_tc(const TcParams 
               for (int r = 0; r < D; ++r) acc = fmaf(adj[a][r], adj[b][r], acc);
               H[q++] = nu * acc * inv;
             }
-          coef_rows<NS, D>(p, did, u);
         }
       }
       uint8_t* st = stages + (size_t)s * S::STAGE;
