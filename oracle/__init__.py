@@ -52,6 +52,8 @@ def _load():
         lib.oracle_prism_rule.argtypes = [I, P, P]
         lib.oracle_prism_basis.argtypes = [I, I, P, P, P]
         lib.oracle_prism_assemble.argtypes = [I, I, P, P, P, P, L, P, I]
+        lib.oracle_prism_burgers_rule.argtypes = [I, P, P]
+        lib.oracle_prism_burgers.argtypes = [I, I, ctypes.c_double, P, P, P, P, L, P, I]
         _lib = lib
     return _lib
 
@@ -260,4 +262,26 @@ def prism_assemble(form, k, coords, c2v, coef=None, c2d=None, threads=0):
     if _load().oracle_prism_assemble(form, k, _p(coords), _p(c2v), _p(coef), _p(c2d), c2v.shape[0], _p(out),
                                      threads) != 0:
         raise ValueError("oracle_prism_assemble failed")
+    return out
+
+
+def prism_burgers_rule(k):
+    """(pts [nq, 3], wts [nq]) of the Burgers prism rule: (3k+3)//2 points per direction."""
+    L = _load()
+    nq = L.oracle_prism_burgers_rule(k, None, None)
+    pts, wts = np.zeros((nq, 3)), np.zeros(nq)
+    L.oracle_prism_burgers_rule(k, _p(pts), _p(wts))
+    return pts, wts
+
+
+def prism_burgers(k, coords, c2v, u, c2d, nu=0.01, residual=False, threads=0):
+    """Vector Burgers on prisms (section 5.2's third shape): the Jacobians [ncells, 3n, 3n] of
+    R[(c,i)] = int (u.grad u_c) phi_i + nu grad u_c . grad phi_i, or with residual=True the
+    residual vectors [ncells, 3n]; u [ncoefnodes, 3] nodal values, c2d [ncells, n]."""
+    coords, c2v, u, c2d = _f64(coords), _i32(c2v), _f64(u), _i32(c2d)
+    N = 3 * prism_ndof(k)
+    out = np.zeros((c2v.shape[0], N) if residual else (c2v.shape[0], N, N))
+    if _load().oracle_prism_burgers(k, 1 if residual else 0, nu, _p(coords), _p(c2v), _p(u), _p(c2d),
+                                    c2v.shape[0], _p(out), threads) != 0:
+        raise ValueError("oracle_prism_burgers failed")
     return out

@@ -617,6 +617,122 @@ void prism_matrix(int form, int k, const Basis& T, const Rule& R, const double* 
   }
 }
 
+// Vector Burgers on prisms (section 5.2 runs Burgers on prisms too). The element matrix is the
+// Jacobian of the residual R[(c,i)] = int (u.grad u_c) phi_i + nu grad u_c . grad phi_i, taken as
+// in cell_matrix's Burgers branch, with the prism's Jacobian, determinant and inverse at every
+// quadrature point. u is the degree-k vector field, u[r][c] at the n prism nodes.
+// Quadrature: the same construction as prism_rule with n = (3k+3)/2 points per direction, since
+// the trilinear term phi_i phi_j d u has degree 3k-1 in the triangle variables (one more under
+// the collapsed map) and 3k in zeta on prisms with planar faces.
+int prism_burgers_points(int k) { return (3 * k + 3) / 2; }
+
+Rule prism_rule_points(int n) {
+  std::vector<double> x, w;
+  gauss_legendre01(n, x, w);
+  Rule R;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int l = 0; l < n; ++l) {
+        R.pts.push_back(x[i]);
+        R.pts.push_back(x[j] * (1.0 - x[i]));
+        R.pts.push_back(x[l]);
+        R.wts.push_back(w[i] * w[j] * (1.0 - x[i]) * w[l]);
+      }
+  R.nq = (int)R.wts.size();
+  return R;
+}
+
+// physical gradients g[i][m] = sum_a K[a][m] dphi_i[a] of the n prism functions at a point, and
+// w |det J| there (K = J^{-1} by the adjugate)
+double prism_point(const double* X, const double* xi, double w, const double* dphi, int n, double* g) {
+  double J[3][3];
+  prism_jacobian(X, xi, J);
+  double adj[3][3];  // adj[a][m] = cofactor(m, a)
+  adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  adj[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  adj[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  adj[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  const double det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+  for (int i = 0; i < n; ++i)
+    for (int m = 0; m < 3; ++m) {
+      double s = 0.0;
+      for (int a = 0; a < 3; ++a) s += adj[a][m] / det * dphi[(size_t)i * 3 + a];
+      g[(size_t)i * 3 + m] = s;
+    }
+  return w * std::fabs(det);
+}
+
+// u(x_q)[a] and grad u(x_q)[a][m] from the nodal values
+void prism_u_at(const double* u, const double* phi, const double* g, int n, double uq[3], double gu[3][3]) {
+  for (int a = 0; a < 3; ++a) {
+    uq[a] = 0.0;
+    for (int m = 0; m < 3; ++m) gu[a][m] = 0.0;
+  }
+  for (int r = 0; r < n; ++r)
+    for (int a = 0; a < 3; ++a) {
+      uq[a] += u[r * 3 + a] * phi[r];
+      for (int m = 0; m < 3; ++m) gu[a][m] += u[r * 3 + a] * g[(size_t)r * 3 + m];
+    }
+}
+
+// element matrix [3n][3n] (component-blocked rows and columns (c, i))
+void prism_burgers_matrix(int k, const Rule& R, const double* phiq, const double* dphiq, const double* X,
+                          const double* u, double nu, double* A) {
+  const int n = prism_ndof(k), N = 3 * n;
+  std::fill(A, A + (size_t)N * N, 0.0);
+  std::vector<double> g((size_t)n * 3);
+  for (int q = 0; q < R.nq; ++q) {
+    const double* ph = phiq + (size_t)q * n;
+    const double Dw = prism_point(X, &R.pts[(size_t)q * 3], R.wts[q], dphiq + (size_t)q * n * 3, n, g.data());
+    double uq[3], gu[3][3];
+    prism_u_at(u, ph, g.data(), n, uq, gu);
+    for (int ci = 0; ci < 3; ++ci)
+      for (int i = 0; i < n; ++i)
+        for (int cj = 0; cj < 3; ++cj)
+          for (int j = 0; j < n; ++j) {
+            // (du.grad u).v + (u.grad du).v + nu grad du : grad v, du = phi_j e_cj, v = phi_i e_ci
+            double s = ph[i] * ph[j] * gu[ci][cj];
+            if (ci == cj) {
+              double ug = 0.0, gg = 0.0;
+              for (int m = 0; m < 3; ++m) {
+                ug += uq[m] * g[(size_t)j * 3 + m];
+                gg += g[(size_t)i * 3 + m] * g[(size_t)j * 3 + m];
+              }
+              s += ph[i] * ug + nu * gg;
+            }
+            A[(size_t)(ci * n + i) * N + cj * n + j] += s * Dw;
+          }
+  }
+}
+
+// element residual [3n]
+void prism_burgers_residual(int k, const Rule& R, const double* phiq, const double* dphiq, const double* X,
+                            const double* u, double nu, double* Rv) {
+  const int n = prism_ndof(k);
+  std::fill(Rv, Rv + 3 * n, 0.0);
+  std::vector<double> g((size_t)n * 3);
+  for (int q = 0; q < R.nq; ++q) {
+    const double* ph = phiq + (size_t)q * n;
+    const double Dw = prism_point(X, &R.pts[(size_t)q * 3], R.wts[q], dphiq + (size_t)q * n * 3, n, g.data());
+    double uq[3], gu[3][3];
+    prism_u_at(u, ph, g.data(), n, uq, gu);
+    for (int c = 0; c < 3; ++c) {
+      double adv = 0.0;
+      for (int m = 0; m < 3; ++m) adv += uq[m] * gu[c][m];
+      for (int i = 0; i < n; ++i) {
+        double visc = 0.0;
+        for (int m = 0; m < 3; ++m) visc += gu[c][m] * g[(size_t)i * 3 + m];
+        Rv[c * n + i] += (adv * ph[i] + nu * visc) * Dw;
+      }
+    }
+  }
+}
+
 void set_threads(int nthreads) {
 #ifdef _OPENMP
   omp_set_num_threads(nthreads > 0 ? nthreads : omp_get_num_procs());
@@ -826,6 +942,43 @@ int oracle_prism_assemble(int form, int degree, const double* coords, const int3
       for (int v = 0; v < 6; ++v)
         for (int r = 0; r < 4; ++r) cf[v * 4 + r] = coef[(int64_t)c2d[e * 6 + v] * 4 + r];
     prism_matrix(form, degree, T, R, phiq.data(), dphiq.data(), X, cf, out + e * (int64_t)n * n);
+  }
+  return 0;
+}
+
+// the Burgers prism rule ((3k+3)/2 points per direction): pts [nq][3], wts [nq]; NULL queries nq
+int oracle_prism_burgers_rule(int degree, double* pts, double* wts) {
+  if (degree < 1 || degree > 4) return -1;
+  Rule R = prism_rule_points(prism_burgers_points(degree));
+  if (pts) std::memcpy(pts, R.pts.data(), R.pts.size() * sizeof(double));
+  if (wts) std::memcpy(wts, R.wts.data(), R.wts.size() * sizeof(double));
+  return R.nq;
+}
+
+// vector Burgers on prisms: u [ncoefnodes][3], cell2dof [ncells][n] (n = prism_ndof(degree));
+// residual 0: Jacobians out [ncells][3n][3n]; residual 1: residual vectors out [ncells][3n]
+int oracle_prism_burgers(int degree, int residual, double nu, const double* coords, const int32_t* c2v,
+                         const double* u, const int32_t* c2d, int64_t ncells, double* out, int nthreads) {
+  if (degree < 1 || degree > 4 || ncells < 0 || !u || !c2d) return -1;
+  Basis T = lagrange(CELL_TRI, degree);
+  Rule R = prism_rule_points(prism_burgers_points(degree));
+  const int n = prism_ndof(degree), N = 3 * n;
+  std::vector<double> phiq((size_t)R.nq * n), dphiq((size_t)R.nq * n * 3);
+  for (int q = 0; q < R.nq; ++q)
+    eval_prism_basis(T, degree, &R.pts[(size_t)q * 3], &phiq[(size_t)q * n], &dphiq[(size_t)q * n * 3]);
+  set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < ncells; ++e) {
+    double X[18];
+    std::vector<double> ue((size_t)n * 3);
+    for (int v = 0; v < 6; ++v)
+      for (int r = 0; r < 3; ++r) X[v * 3 + r] = coords[(int64_t)c2v[e * 6 + v] * 3 + r];
+    for (int r = 0; r < n; ++r)
+      for (int a = 0; a < 3; ++a) ue[(size_t)r * 3 + a] = u[(int64_t)c2d[e * n + r] * 3 + a];
+    if (residual)
+      prism_burgers_residual(degree, R, phiq.data(), dphiq.data(), X, ue.data(), nu, out + e * (int64_t)N);
+    else
+      prism_burgers_matrix(degree, R, phiq.data(), dphiq.data(), X, ue.data(), nu, out + e * (int64_t)N * N);
   }
   return 0;
 }
