@@ -609,6 +609,21 @@ def run_ours(args):
             h2d += h_coef.numel() * 8 + h_c2d.numel() * 4
         e2e = {"value": reduce_over_ranks(ncells * e_steps, world, "sum", dev) / (ems / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())}
+        # the host link on this machine: one device-to-host copy of the step's output bytes into the
+        # same page-locked buffer, the bound of the end-to-end step
+        src = out.reshape(-1)[:h_out.numel()]
+        dst = h_out.reshape(-1)
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        cms = a.elapsed_time(b) / 3
+        e2e["link"] = {"d2h_gbs": e2e["d2h_bytes_per_step"] / (cms / 1e3) / 1e9, "output_copy_ms": cms,
+                       "step_ms": ems / e_steps, "step_over_copy": (ems / e_steps) / cms,
+                       "note": "one device-to-host copy of the output bytes, page-locked, CUDA events"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.nx is None:

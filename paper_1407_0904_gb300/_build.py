@@ -15,7 +15,7 @@ LIB = os.path.join(PKG, "libcoffee.so")
 
 CU_SOURCES = ["api.cu", "k_fp64.cu", "k_tc.cu", "k_tc_staged.cu", "k_tc_burgers.cu", "k_tc_burgers_stream.cu", "k_bwd.cu", "noalloc.cu", "k_batch.cu",
               "k_csr.cu", "k_tc_csr.cu", "k_tc_burgers_res.cu",
-              "k_prism.cu", "k_prism_tc.cu", "k_peaks.cu", "host_pipeline.cu", "k_simt.cu",
+              "k_prism.cu", "k_prism_burgers.cu", "k_prism_tc.cu", "k_peaks.cu", "host_pipeline.cu", "k_simt.cu",
               "k_tc_burgers_fact.cu"]
 CPP_SOURCES = ["tabulate.cpp"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -169,7 +169,11 @@ int fp64_table(DeviceCache& c, int form, int degree, int cell, const double** T)
     return COFFEE_OK;
   }
   std::vector<double> h;
-  if (cell == CELL_PRISM) {
+  if (cell == CELL_PRISM && form == FORM_BURGERS) {
+    // the basis at the Burgers rule's points, then the points and weights
+    int Q = 0;
+    prism_burgers_table(degree, h, Q);
+  } else if (cell == CELL_PRISM) {
     // per-point tensors, then the rule's points and weights (read by the prism kernel)
     std::vector<double> pts, wts;
     prism_tensor(form, degree, h, pts, wts);
@@ -283,6 +287,30 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
     std::string why;
     cudaError_t e = (cudaError_t)launch_prism_tc(a->form, a->degree, p, c->num_sms, stream, why);
     if (e != cudaSuccess) return cuda_fail(e, ("launch(assemble_prism_tc) " + why).c_str());
+    return COFFEE_OK;
+  }
+  if (a->cell == CELL_PRISM && burgers_like(a->form)) {
+    if (map) return fail(COFFEE_ERR_UNSUPPORTED, "global assembly of Burgers on prisms is not built");
+    const double* T = nullptr;
+    if ((rc = fp64_table(*c, a->form, a->degree, a->cell, &T)) != COFFEE_OK) return rc;
+    const int pb = prism_burgers_points(a->degree);
+    PrismParams p{};
+    p.coords = a->coords;
+    p.c2v = a->cell2vert;
+    p.coef = a->coef;
+    p.c2d = a->cell2dof;
+    p.ncoefnodes = a->ncoefnodes;
+    p.T = T;
+    p.out = a->out;
+    p.err = c->err;
+    p.ncells = a->ncells;
+    p.nverts = a->nverts;
+    p.Q = pb * pb * pb;
+    p.N = prism_nnodes(a->degree);
+    p.validate = validate ? 1 : 0;
+    p.nu = a->nu;
+    cudaError_t e = (cudaError_t)launch_prism_burgers(a->form, a->degree, p, c->num_sms, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch(prism_burgers)");
     return COFFEE_OK;
   }
   if (a->cell == CELL_PRISM) {
@@ -450,8 +478,9 @@ int coffee_reference_tensor(int form, int degree, int cell, int* K, int* N, doub
 int coffee_supported(int form, int degree, int cell, int precision) {
   if (!valid_fdc(form, degree, cell) || precision < PREC_FP64 || precision > PREC_BF16X3) return 0;
   if (cell == CELL_PRISM)
-    return (form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF) &&
-           (precision == PREC_FP64 || prism_tc_supported(form, degree, precision));
+    return ((form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF) &&
+            (precision == PREC_FP64 || prism_tc_supported(form, degree, precision))) ||
+           (burgers_like(form) && precision == PREC_FP64);
   if (precision == PREC_FP64) return 1;
   return tc_supported(form, degree, cell, precision);
 }

@@ -49,6 +49,9 @@ int prism_nnodes(int k);
 void prism_rule(int k, std::vector<double>& pts, std::vector<double>& wts);
 void prism_basis(int k, int npts, const double* x, double* phi, double* grads);
 void prism_tensor(int form, int k, std::vector<double>& T, std::vector<double>& pts, std::vector<double>& wts);
+void prism_rule_points(int n, std::vector<double>& pts, std::vector<double>& wts);
+int prism_burgers_points(int k);
+void prism_burgers_table(int k, std::vector<double>& tab, int& Q);
 
 // ---- error reporting (api.cu) ----
 int fail(int status, const std::string& msg);
@@ -90,8 +93,12 @@ struct PrismParams {
   int validate;
   const uint32_t* map;   // global assembly (blocked entry map), else NULL
   int64_t nnz;
+  double nu;             // Burgers viscosity
 };
 int launch_prism(int form, const PrismParams& p, int num_sms, void* stream);
+// vector Burgers on prisms, FP64 (k_prism_burgers.cu): the Jacobian (FORM_BURGERS) or the residual
+// (FORM_BURGERS_RES); p.T holds prism_burgers_table, p.N the nodes n of one component, p.Q points
+int launch_prism_burgers(int form, int degree, const PrismParams& p, int num_sms, void* stream);
 // tensor-core prisms (k_prism_tc.cu): K-chunked streamed contraction, MASS/HELMHOLTZ/ADVDIFF P1-P4
 struct TcParams;
 struct TcTable;

@@ -268,8 +268,7 @@ namespace coffee {
 
 int prism_nnodes(int k) { return (k + 1) * (k + 2) / 2 * (k + 1); }
 
-void prism_rule(int k, std::vector<double>& pts, std::vector<double>& wts) {
-  const int n = k + 2;
+void prism_rule_points(int n, std::vector<double>& pts, std::vector<double>& wts) {
   std::vector<double> g, w;
   gauss_jacobi01(n, 0, g, w);  // alpha = 0: Gauss-Legendre
   pts.clear();
@@ -283,6 +282,8 @@ void prism_rule(int k, std::vector<double>& pts, std::vector<double>& wts) {
         wts.push_back(w[i] * w[j] * (1.0 - g[i]) * w[l]);
       }
 }
+
+void prism_rule(int k, std::vector<double>& pts, std::vector<double>& wts) { prism_rule_points(k + 2, pts, wts); }
 
 void prism_basis(int k, int npts, const double* x, double* phi, double* grads) {
   const int nt = (k + 1) * (k + 2) / 2, n = prism_nnodes(k);
@@ -346,6 +347,28 @@ void prism_tensor(int form, int k, std::vector<double>& T, std::vector<double>& 
           for (int a = 0; a < 3; ++a) T[((size_t)q * KQ + 6 + a) * N + o] = ph[i] * gr[(size_t)j * 3 + a];
       }
   }
+}
+
+// Vector Burgers on prisms: the basis at the points of its rule, (3k+3)/2 Gauss-Legendre points per
+// direction (the trilinear term phi_i phi_j grad u has degree 3k-1 in the triangle variables and
+// 3k in zeta on prisms with planar faces), as tab [Q][n][4] = (phi, d_s phi, d_t phi, d_z phi),
+// then the points [Q][3] and the weights [Q]. The kernel evaluates the quadrature loop directly.
+int prism_burgers_points(int k) { return (3 * k + 3) / 2; }
+
+void prism_burgers_table(int k, std::vector<double>& tab, int& Q) {
+  std::vector<double> pts, wts;
+  prism_rule_points(prism_burgers_points(k), pts, wts);
+  Q = (int)wts.size();
+  const int n = prism_nnodes(k);
+  std::vector<double> phi((size_t)Q * n), g((size_t)Q * n * 3);
+  prism_basis(k, Q, pts.data(), phi.data(), g.data());
+  tab.assign((size_t)Q * n * 4, 0.0);
+  for (size_t i = 0; i < (size_t)Q * n; ++i) {
+    tab[i * 4] = phi[i];
+    for (int a = 0; a < 3; ++a) tab[i * 4 + 1 + a] = g[i * 3 + a];
+  }
+  tab.insert(tab.end(), pts.begin(), pts.end());
+  tab.insert(tab.end(), wts.begin(), wts.end());
 }
 
 }  // namespace coffee

@@ -162,7 +162,7 @@ def test_burgers_reference_tensor_on_reference_cell_matches_oracle(cell, k):
 
 def test_support_queries_cover_prisms():
     """Host-only queries: prisms take MASS, HELMHOLTZ and ADVDIFF (FP64 and tensor cores P1-P4),
-    locally and fused into CSR; the Burgers forms are simplex-only."""
+    locally and fused into CSR; the Burgers Jacobian and residual in FP64, locally only."""
     P = coffee.PRISM
     for form in (coffee.MASS, coffee.HELMHOLTZ, coffee.ADVDIFF):
         for k in range(1, 5):
@@ -172,9 +172,12 @@ def test_support_queries_cover_prisms():
                 assert coffee.supported(form, k, P, prec)
                 assert coffee.csr_supported(form, k, P, prec)
     for form in (coffee.BURGERS_JAC, coffee.BURGERS_RESIDUAL):
-        for prec in (coffee.FP64, coffee.TF32X3):
-            assert not coffee.supported(form, 1, P, prec)
-            assert not coffee.csr_supported(form, 1, P, prec)
+        for k in range(1, 5):
+            assert coffee.supported(form, k, P, coffee.FP64)
+            assert not coffee.csr_supported(form, k, P, coffee.FP64)
+            for prec in (coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16):
+                assert not coffee.supported(form, k, P, prec)
+                assert not coffee.csr_supported(form, k, P, prec)
 
 
 def test_assemble_path_query():
