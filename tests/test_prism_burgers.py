@@ -71,8 +71,8 @@ def test_prism_burgers_checks_and_edges():
     coffee.assemble(coffee.BURGERS_RESIDUAL, 1, PRISM, x, badv, ud, cd, precision=coffee.FP64, validate=True)
     with pytest.raises(coffee.CoffeeError):
         coffee.check_errors()
-    empty = coffee.assemble(coffee.BURGERS_JAC, 2, PRISM, x, c2v[:0].contiguous(), ud, cd[:0].contiguous(),
-                            precision=coffee.FP64)
+    empty = coffee.assemble(coffee.BURGERS_JAC, 2, PRISM, x, c2v[:0].contiguous(), ud,
+                            torch.empty((0, 18), dtype=torch.int32, device=DEV), precision=coffee.FP64)
     assert empty.shape == (0, 54, 54)
     # a ragged count of cells (odd, not a multiple of the warps per block) matches the oracle
     sl = slice(0, 7)
