@@ -138,6 +138,10 @@ WORKLOADS["advdiff-p2-prism"] = Workload("advdiff-p2-prism", ADVDIFF, 2, PRISM,
                                          "unit cube, 48x48 two-triangle columns x 48 layers = 221,184 "
                                          "twisted prisms perturbed 0.15h (seed 6), eps~U[0.5,1.5], "
                                          "b~U[-1,1]^3 per vertex", _prism48)
+WORKLOADS["burgers-p2-prism"] = Workload("burgers-p2-prism", BURGERS_JAC, 2, PRISM,
+                                         "unit cube, 24x24 two-triangle columns x 24 layers = 27,648 "
+                                         "twisted prisms perturbed 0.15h (seed 6), vector P2 u~N(0,1) per "
+                                         "conforming node, nu=0.01; FP64 only (--precision fp64)", _prism24)
 WORKLOADS["helmholtz-p1-tri"] = Workload("helmholtz-p1-tri", HELMHOLTZ, 1, TRIANGLE,
                                          "unit square 64x64x2 triangles perturbed 0.2h (seed 1)", _tri64)
 # the same problem at a size where HBM, not the launch, sets the time (its roofline fraction)
@@ -284,6 +288,9 @@ def kernel_source_sha():
 
 def oracle_cells(wl, mesh, coef, c2d, sel, threads=0):
     import oracle
+    if wl.cell == PRISM and wl.form in (BURGERS_JAC, BURGERS_RESIDUAL):
+        return oracle.prism_burgers(wl.degree, mesh.coords, mesh.cell2vert[sel], coef.reshape(-1, 3), c2d[sel],
+                                    residual=wl.form == BURGERS_RESIDUAL, threads=threads)
     if wl.cell == PRISM:
         extra = (coef, c2d[sel]) if wl.form == ADVDIFF else ()
         return oracle.prism_assemble(wl.form, wl.degree, mesh.coords, mesh.cell2vert[sel], *extra, threads=threads)
@@ -538,7 +545,19 @@ def run_ours(args):
     if prec == coffee.FP64:
         roof["note"] = ("FP64 kernel: bound by the FP64 ALU (%.2f TFLOP/s measured by coffee_peak_fp64); "
                         "HBM fraction for context" % device_peaks(coffee)["fp64_tflops"])
-    if cell == PRISM:
+    if cell == PRISM and form in (BURGERS_JAC, BURGERS_RESIDUAL):
+        # vector Burgers, evaluated point by point: per point the factors (u, grad u, K: about 12
+        # FMAs per node and component set) and, per scalar pair (i, j), 9 FMAs for the component
+        # blocks and 12 for the diagonal terms (residual: 12 per node)
+        Q = ((3 * degree + 3) // 2) ** 3
+        n = ndof // 3
+        fma = Q * (12 * n + 60 + (12 * n if form == BURGERS_RESIDUAL else 21 * n * n))
+        tf = 2.0 * fma * ncells / (launch_ms / 1e3) / 1e12
+        p64 = device_peaks(coffee)["fp64_tflops"]
+        roof = {"bound": "alu", "achieved": tf, "peak": p64, "unit": "TFLOP/s", "frac": tf / p64, "traffic": None,
+                "peak_source": "FP64 FMA loop measured on this GPU (coffee_peak_fp64)",
+                "flops_per_cell": 2.0 * fma, "kernel_ms": launch_ms, "hbm_gbs": achieved}
+    elif cell == PRISM:
         # non-affine cells: the contraction over all quadrature points (K = KQ Q) dominates
         Q = (degree + 2) ** 3
         K = Q * {HELMHOLTZ: 7, ADVDIFF: 9}.get(form, 1)
