@@ -91,6 +91,9 @@ def test_golden_element_sizes_printed_in_paper():
     rows = read_golden("element_sizes.txt")
     assert len(rows) >= 4
     for r in rows:
+        if r[1] == "prism":
+            assert r[0] == "helmholtz" and oracle.prism_ndof(int(r[2])) == int(r[3])
+            continue
         form, cell, k, n = FORMS[r[0]], NAME[r[1]], int(r[2]), int(r[3])
         assert oracle.ndof(form, k, cell) == n
 
