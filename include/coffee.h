@@ -73,9 +73,9 @@ typedef struct CUstream_st* coffee_stream_t;
  * at most three 128-output slices at a time),
  * both through coffee_assemble_ex and coffee_assemble_csr. The Burgers Jacobian and residual on
  * prisms (u per node through cell2dof [ncells][(k+1)^2(k+2)/2], rows and columns blocked by
- * component as on simplices) run in FP64, local assembly only, with their own rule of
- * (3k+3)/2 points per direction (the trilinear term's degree); other precisions and
- * coffee_assemble_csr return COFFEE_ERR_UNSUPPORTED. */
+ * component as on simplices) run in FP64 with their own rule of (3k+3)/2 points per direction
+ * (the trilinear term's degree), the Jacobian also through coffee_assemble_csr; other
+ * precisions return COFFEE_ERR_UNSUPPORTED. */
 typedef enum { COFFEE_TRIANGLE = 0, COFFEE_TETRAHEDRON = 1, COFFEE_PRISM = 2 } coffee_cell;
 
 typedef enum {

@@ -290,7 +290,7 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
     return COFFEE_OK;
   }
   if (a->cell == CELL_PRISM && burgers_like(a->form)) {
-    if (map) return fail(COFFEE_ERR_UNSUPPORTED, "global assembly of Burgers on prisms is not built");
+    if (map && a->form == FORM_BURGERS_RES) return fail(COFFEE_ERR_UNSUPPORTED, "global assembly of element vectors");
     const double* T = nullptr;
     if ((rc = fp64_table(*c, a->form, a->degree, a->cell, &T)) != COFFEE_OK) return rc;
     const int pb = prism_burgers_points(a->degree);
@@ -309,6 +309,8 @@ int assemble_impl(const coffee_assemble_args* a, const uint32_t* map, int64_t nn
     p.N = prism_nnodes(a->degree);
     p.validate = validate ? 1 : 0;
     p.nu = a->nu;
+    p.map = map;
+    p.nnz = nnz;
     cudaError_t e = (cudaError_t)launch_prism_burgers(a->form, a->degree, p, c->num_sms, stream);
     if (e != cudaSuccess) return cuda_fail(e, "launch(prism_burgers)");
     return COFFEE_OK;
@@ -599,8 +601,7 @@ int coffee_csr_supported(int form, int degree, int cell, int precision) {
   if (!valid_fdc(form, degree, cell) || precision < PREC_FP64 || precision > PREC_BF16X3) return 0;
   if (form == FORM_BURGERS_RES) return 0;
   if (cell == CELL_PRISM)
-    return precision == PREC_FP64 ? (form == FORM_MASS || form == FORM_HELMHOLTZ || form == FORM_ADVDIFF)
-                                  : prism_tc_supported(form, degree, precision);
+    return precision == PREC_FP64 ? 1 : prism_tc_supported(form, degree, precision);
   return precision == PREC_FP64 ? 1 : tc_csr_supported(form, degree, cell, precision);
 }
 

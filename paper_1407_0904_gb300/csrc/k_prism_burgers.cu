@@ -16,6 +16,8 @@
 // residual takes a_c = w|det| u.grad u_c and gamma_ca = w|det| nu (K grad u_c)_a and sums
 // a_c phi_i + gamma_c . dphi_i per node i. The rule, the basis and its reference derivatives at
 // the points come from the host's table (prism_burgers_table: (3k+3)/2 points per direction).
+// Global assembly (CSR, the Jacobian): each entry is added into the CSR values at its map
+// position (csr_map_index over the (3n)^2 entries of the cell) instead of being stored.
 #include <cuda_runtime.h>
 #include "coffee_internal.h"
 
@@ -31,7 +33,7 @@ __host__ __device__ constexpr int pb_warp_doubles(int k, bool res, int Q) {
   return Q * pb_factors(res) + 18 + 3 * pb_nodes(k);
 }
 
-template <int DEG, bool RES>
+template <int DEG, bool RES, bool CSR>
 __global__ void __launch_bounds__(PBW * 32) k_prism_burgers(const PrismParams p) {
   constexpr int n = pb_nodes(DEG), N = 3 * n, NF = pb_factors(RES);
   extern __shared__ double pbs[];
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(PBW * 32) k_prism_burgers(const PrismParams p)
     }
     __syncwarp();
     if constexpr (!RES) {
-      double* out = static_cast<double*>(p.out) + e * (int64_t)N * N;
+      double* out = CSR ? nullptr : static_cast<double*>(p.out) + e * (int64_t)N * N;
       for (int o = lane; o < n * n; o += 32) {
         const int i = o / n, j = o - (o / n) * n;
         double acc[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, dg = 0.0;
@@ -165,8 +167,17 @@ __global__ void __launch_bounds__(PBW * 32) k_prism_burgers(const PrismParams p)
 #pragma unroll
         for (int ci = 0; ci < 3; ++ci)
 #pragma unroll
-          for (int cj = 0; cj < 3; ++cj)
-            out[(int64_t)(ci * n + i) * N + cj * n + j] = acc[ci * 3 + cj] + (ci == cj ? dg : 0.0);
+          for (int cj = 0; cj < 3; ++cj) {
+            const int loc = (ci * n + i) * N + cj * n + j;
+            const double v = acc[ci * 3 + cj] + (ci == cj ? dg : 0.0);
+            if constexpr (CSR) {
+              const uint32_t pos = __ldg(p.map + csr_map_index(e, loc, (N * N + 3) & ~3));
+              if (pos < (uint64_t)p.nnz) atomicAdd(static_cast<double*>(p.out) + pos, v);
+              else atomicOr(p.err, ERR_INDEX);
+            } else {
+              out[loc] = v;
+            }
+          }
       }
     } else {
       double* out = static_cast<double*>(p.out) + e * (int64_t)N;
@@ -190,7 +201,7 @@ __global__ void __launch_bounds__(PBW * 32) k_prism_burgers(const PrismParams p)
 
 template <int DEG, bool RES>
 cudaError_t launch_pb(const PrismParams& p, int num_sms, cudaStream_t s) {
-  auto kern = k_prism_burgers<DEG, RES>;
+  auto kern = (!RES && p.map) ? k_prism_burgers<DEG, RES, true> : k_prism_burgers<DEG, RES, false>;
   const size_t smem = (size_t)PBW * pb_warp_doubles(DEG, RES, p.Q) * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

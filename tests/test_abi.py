@@ -162,7 +162,7 @@ def test_burgers_reference_tensor_on_reference_cell_matches_oracle(cell, k):
 
 def test_support_queries_cover_prisms():
     """Host-only queries: prisms take MASS, HELMHOLTZ and ADVDIFF (FP64 and tensor cores P1-P4),
-    locally and fused into CSR; the Burgers Jacobian and residual in FP64, locally only."""
+    locally and fused into CSR; the Burgers Jacobian (locally and into CSR) and residual in FP64."""
     P = coffee.PRISM
     for form in (coffee.MASS, coffee.HELMHOLTZ, coffee.ADVDIFF):
         for k in range(1, 5):
@@ -174,7 +174,7 @@ def test_support_queries_cover_prisms():
     for form in (coffee.BURGERS_JAC, coffee.BURGERS_RESIDUAL):
         for k in range(1, 5):
             assert coffee.supported(form, k, P, coffee.FP64)
-            assert not coffee.csr_supported(form, k, P, coffee.FP64)
+            assert bool(coffee.csr_supported(form, k, P, coffee.FP64)) == (form == coffee.BURGERS_JAC)
             for prec in (coffee.TF32X3, coffee.BF16X3, coffee.TF32, coffee.BF16):
                 assert not coffee.supported(form, k, P, prec)
                 assert not coffee.csr_supported(form, k, P, prec)

@@ -81,3 +81,21 @@ def test_prism_burgers_checks_and_edges():
                           precision=coffee.FP64)
     coffee.check_errors()
     assert rel_err_per_cell(out.cpu().numpy(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_prism_burgers_global_assembly_fp64(k):
+    """The Jacobian added straight into CSR values over a conforming vector dof numbering
+    (component-blocked: global row c * nnodes + node), against the oracle's element matrices
+    scattered by the oracle's own CSR assembly."""
+    mesh = meshgen.prism_mesh(4, 3, perturb=0.15, seed=60 + k)
+    u, c2d, nn = meshgen.burgers_coefficients(mesh, k, seed=61 + k)
+    l2g = np.concatenate([c2d.astype(np.int64) + c * nn for c in range(3)], axis=1).astype(np.int32)
+    A_e = oracle.prism_burgers(k, mesh.coords, mesh.cell2vert, u, c2d)
+    x, c2v, ud, cd = on_device(mesh, u, c2d)
+    M = coffee.CsrMatrix(torch.from_numpy(l2g).to(DEV), 3 * nn)
+    vals = M.assemble(coffee.BURGERS_JAC, k, PRISM, x, c2v, ud, cd, precision=coffee.FP64, validate=True)
+    coffee.check_errors()
+    rp, ci = M.rowptr.cpu().numpy(), M.colidx.cpu().numpy()
+    ref = oracle.csr_assemble(A_e, l2g, rp, ci)
+    np.testing.assert_allclose(vals.cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
