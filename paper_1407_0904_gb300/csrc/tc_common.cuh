@@ -534,6 +534,8 @@ __device__ __forceinline__ void cell_factors_ids(const TcParams& p, const CellId
     }
   }
   if (bad) return;
+  float eb[FORM == FORM_ADVDIFF ? NV : 1][D + 1];  // (eps, b) row of each vertex's node
+  if constexpr (FORM == FORM_ADVDIFF) coef_rows<NV, D + 1>(p, cid, eb);  // issued before the coordinates'
   float adj[D][D], Dm, sg;
   cell_geometry_ids<D, ISPLIT>(p, vid, adj, Dm, sg);
   float C[P];  // edge factors
@@ -545,8 +547,6 @@ __device__ __forceinline__ void cell_factors_ids(const TcParams& p, const CellId
 #pragma unroll
     for (int q = 0; q < P; ++q) G[1 + q] = C[q];
   } else {
-    float eb[NV][D + 1];  // (eps, b) row of each vertex's node
-    coef_rows<NV, D + 1>(p, cid, eb);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
 #pragma unroll
