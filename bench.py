@@ -34,7 +34,9 @@ L2_BYTES = 129 * 2 ** 20
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # tensor-core kernel on the headline workload, keyed by the sha256 prefix of the kernel
 # source it was measured on; reported as null once the source has changed.
-TRAFFIC = {"3996a5005b13b753": 2.4902e9}  # 31.86 MB read + 2.4583 GB written per launch (ncu, one launch, full size)
+# DRAM bytes per launch of the headline kernel (ncu, one launch, full size), by kernel source hash
+TRAFFIC = {"64f9c5da8e0a5bb9": 2.4903e9,   # 31.86 MB read + 2.4584 GB written
+           "3996a5005b13b753": 2.4902e9}   # 31.86 MB read + 2.4583 GB written
 
 MASS, HELMHOLTZ, ADVDIFF, BURGERS_JAC, BURGERS_RESIDUAL = 0, 1, 2, 3, 4
 TRIANGLE, TETRAHEDRON, PRISM = 0, 1, 2
