@@ -155,14 +155,24 @@ __device__ __forceinline__ void simt_tile(const TcParams& p, int64_t t, int lane
 //   block(ci, cj) = sum_a P[a][cj] V_a^ci + [ci == cj] C,   V_a^ci = sum_r u[r][ci] T1[r d + a],
 //   C = sum_{r,a} Q[r][a] T2[r d + a] + sum_p nu H_p T3[p],   Q[r][a] = sum_c u[r][c] P[a][c],
 // with P = |det J| K and T = [T1 | T2 | T3] the Burgers reference tensors (rows r d + a of T1 and
-// T2, then the P pair rows of T3) in constant memory. The cell's matrix goes to the staging block
-// row by row and out with the warp's coalesced stores.
-constexpr int SIMT_BTHREADS = 128;  // the staging block of a tetrahedron is 145 floats per cell
+// T2, then the P pair rows of T3) in constant memory. Each block row ci of the cell's matrix (its
+// ns rows, contiguous in the output) goes to the staging block and out with the warp's coalesced
+// 16-byte stores before the next is formed, so a warp stages ns d ns floats per cell instead of
+// the whole matrix (tetrahedra: 49 instead of 145; shared memory had limited a multiprocessor to
+// 12 warps); rows whose block row is not a multiple of 4 floats (triangles P1) stage the matrix.
+constexpr int SIMT_BTHREADS = 128;
+template <int D, int DEG, bool RES>
+__host__ __device__ constexpr int sb_stride(int ns) {  // staging floats per cell (odd)
+  return RES ? ((D * ns) | 1) : ((ns * D * ns) % 4 == 0 ? ((ns * D * ns) | 1) : ((D * ns * D * ns) | 1));
+}
 // RES: the residual instead (element vectors, R[(c, i)] = sum_s C[i][s] u[s][c]; C as above).
 template <int D, int DEG, bool RES = false>
 __device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, int lane, float* st) {
   constexpr int NS = s_ns(D, DEG), NV = D + 1, NDOF = D * NS, N = RES ? NDOF : NDOF * NDOF, NB = NS * NS;
-  constexpr int K1 = NS * D, P = D * (D + 1) / 2, OFF = s_off(FORM_BURGERS, D, DEG), SR = N | 1;
+  constexpr int K1 = NS * D, P = D * (D + 1) / 2, OFF = s_off(FORM_BURGERS, D, DEG);
+  constexpr int BR = NS * NDOF;                     // floats of one block row of a cell
+  constexpr bool BYROW = !RES && BR % 4 == 0;        // stage and write one block row at a time
+  constexpr int SR = sb_stride<D, DEG, RES>(NS);
   const int64_t c0 = t * 32, e = c0 + lane;
   float u[NS][D], Pm[D][D], H[P];
 #pragma unroll
@@ -213,6 +223,16 @@ __device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, 
     }
   }
   // C, shared by the diagonal blocks
+  float Q[NS][D];  // Q[r][a] = sum_c u[r][c] P[a][c]
+#pragma unroll
+  for (int r = 0; r < NS; ++r)
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      float q = 0.f;
+#pragma unroll
+      for (int c = 0; c < D; ++c) q = fmaf(u[r][c], Pm[a][c], q);
+      Q[r][a] = q;
+    }
   float C[NB];
 #pragma unroll
   for (int o = 0; o < NB; ++o) {
@@ -220,17 +240,13 @@ __device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, 
 #pragma unroll
     for (int r = 0; r < NS; ++r)
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        float q = 0.f;
-#pragma unroll
-        for (int c = 0; c < D; ++c) q = fmaf(u[r][c], Pm[a][c], q);
-        v = fmaf(q, c_T[OFF + (K1 + r * D + a) * NB + o], v);
-      }
+      for (int a = 0; a < D; ++a) v = fmaf(Q[r][a], c_T[OFF + (K1 + r * D + a) * NB + o], v);
 #pragma unroll
     for (int q = 0; q < P; ++q) v = fmaf(H[q], c_T[OFF + (2 * K1 + q) * NB + o], v);
     C[o] = v;
   }
   float* row = st + lane * SR;
+  const int rows = (int)(p.ncells - c0 < 32 ? p.ncells - c0 : 32);
   if constexpr (RES) {
 #pragma unroll
     for (int c = 0; c < D; ++c)
@@ -241,6 +257,54 @@ __device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, 
         for (int s = 0; s < NS; ++s) v = fmaf(C[i * NS + s], u[s][c], v);
         row[c * NS + i] = v;
       }
+  }
+  if constexpr (BYROW) {
+    // one block row per pass, the loop kept rolled (unrolled, the compiler interleaved the passes
+    // and needed 255 registers): the component's u column selected without indexing by ci
+#pragma unroll 1
+    for (int ci = 0; ci < D; ++ci) {
+      float uc[NS];
+#pragma unroll
+      for (int r = 0; r < NS; ++r) uc[r] = ci == 0 ? u[r][0] : (D > 2 && ci == 2) ? u[r][D - 1] : u[r][1 % D];
+#pragma unroll
+      for (int o = 0; o < NB; ++o) {
+        float V[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float v = 0.f;
+#pragma unroll
+          for (int r = 0; r < NS; ++r) v = fmaf(uc[r], c_T[OFF + (r * D + a) * NB + o], v);
+          V[a] = v;
+        }
+        const int i = o / NS, j = o % NS;
+#pragma unroll
+        for (int cj = 0; cj < D; ++cj) {
+          float v = ci == cj ? C[o] : 0.f;
+#pragma unroll
+          for (int a = 0; a < D; ++a) v = fmaf(Pm[a][cj], V[a], v);
+          row[i * NDOF + cj * NS + j] = v;
+        }
+      }
+      // block row ci of the warp's cells: BR contiguous floats per cell, N apart
+      __syncwarp();
+      float* dst = p.out + c0 * N + ci * BR;
+      if (rows == 32 && (reinterpret_cast<uintptr_t>(p.out) & 15) == 0) {
+#pragma unroll 1
+        for (int v4 = lane; v4 < 8 * BR; v4 += 32) {
+          const int cell = v4 / (BR / 4), off = 4 * (v4 - cell * (BR / 4));
+          const float* sr = st + cell * SR + off;
+          __stcs(reinterpret_cast<float4*>(dst + (int64_t)cell * N + off), make_float4(sr[0], sr[1], sr[2], sr[3]));
+        }
+      } else {
+#pragma unroll 1
+        for (int x = lane; x < rows * BR; x += 32) {
+          const int cell = x / BR, off = x - cell * BR;
+          __stcs(dst + (int64_t)cell * N + off, st[cell * SR + off]);
+        }
+      }
+      __syncwarp();
+    }
+    return;
   }
 #pragma unroll
   for (int ci = 0; ci < (RES ? 0 : D); ++ci) {
@@ -265,7 +329,6 @@ __device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, 
     }
   }
   __syncwarp();
-  const int rows = (int)(p.ncells - c0 < 32 ? p.ncells - c0 : 32);
   float* dst = p.out + c0 * N;
   if (rows == 32 && (reinterpret_cast<uintptr_t>(p.out) & 15) == 0) {
 #pragma unroll 4
@@ -286,10 +349,9 @@ __device__ __forceinline__ void simt_tile_burgers(const TcParams& p, int64_t t, 
 
 template <int D, int DEG, bool RES>
 __global__ void __launch_bounds__(SIMT_BTHREADS) k_assemble_simt_burgers(const TcParams p) {
-  constexpr int NDOF = D * s_ns(D, DEG), N = RES ? NDOF : NDOF * NDOF;
   extern __shared__ float stage[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* st = stage + warp * 32 * (N | 1);
+  float* st = stage + warp * 32 * sb_stride<D, DEG, RES>(s_ns(D, DEG));
   const int64_t ntiles = (p.ncells + 31) / 32;
   for (int64_t t = (int64_t)blockIdx.x * (SIMT_BTHREADS / 32) + warp; t < ntiles;
        t += (int64_t)gridDim.x * (SIMT_BTHREADS / 32))
@@ -453,7 +515,11 @@ int launch_simt(int form, int degree, int cell, const TcParams& p, int num_sms, 
     return (int)e;
   }
   const int threads = burgers_like(form) ? SIMT_BTHREADS : SIMT_THREADS, warps = threads / 32;
-  const int smem = warps * 32 * (N | 1) * (int)sizeof(float);
+  // staging floats per cell: the element matrix (or vector), or one Burgers block row
+  const int sr = !burgers_like(form) ? (N | 1)
+                 : form == FORM_BURGERS_RES ? (nd | 1)
+                 : (ns * nd) % 4 == 0 ? ((ns * nd) | 1) : (N | 1);
+  const int smem = warps * 32 * sr * (int)sizeof(float);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return (int)e;
   int per_sm = 0;
