@@ -24,7 +24,8 @@
 namespace coffee {
 
 int nnodes(int cell, int k) {
-  return cell == 0 ? (k + 1) * (k + 2) / 2 : (k + 1) * (k + 2) * (k + 3) / 6;
+  return cell == 0 ? (k + 1) * (k + 2) / 2 : cell == 1 ? (k + 1) * (k + 2) * (k + 3) / 6
+                                                       : (k + 1) * (k + 2) / 2 * (k + 1);  // prism
 }
 
 int npairs(int d) { return d * (d + 1) / 2; }

@@ -79,3 +79,22 @@ def test_host_pipeline_with_pageable_memory_and_validation():
     with pytest.raises(coffee.CoffeeError) as ei:
         coffee.check_errors()
     assert ei.value.status == -4
+
+
+@pytest.mark.parametrize("form", [BURGERS_JAC, RES])
+def test_host_pipeline_prism_burgers(form):
+    """Vector Burgers on prisms (FP64) through the host pipeline: u per conforming P2 prism node,
+    288 cells in three chunks; bitwise the device launch, and the oracle's values."""
+    mesh = meshgen.prism_mesh(6, 4, perturb=0.15, seed=12)
+    u, c2d, _ = meshgen.burgers_coefficients(mesh, 2, seed=13)
+    pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dt).pin_memory()
+    x, c2v, cf, cd = (pin(mesh.coords, torch.float64), pin(mesh.cell2vert, torch.int32), pin(u, torch.float64),
+                      pin(c2d, torch.int32))
+    got = coffee.assemble_host(form, 2, coffee.PRISM, x, c2v, cf, cd, precision=coffee.FP64, chunks=3)
+    torch.cuda.synchronize()
+    ref_dev = coffee.assemble(form, 2, coffee.PRISM, x.to(DEV), c2v.to(DEV), cf.to(DEV), cd.to(DEV),
+                              precision=coffee.FP64)
+    coffee.check_errors()
+    assert torch.equal(got, ref_dev.cpu())
+    ref = oracle.prism_burgers(2, mesh.coords, mesh.cell2vert, u, c2d, residual=form == RES)
+    assert rel_err_per_cell(got.numpy(), ref) < 1e-12
