@@ -48,7 +48,7 @@ def test_prism_burgers_rule_integrates_monomials_exactly(k):
                 assert abs(val - ex) <= 4e-15 * ex + 1e-17, (a, b, c, val, ex)
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_affine_prism_burgers_residual_exact(k):
     """sum V.R(u) = int (u.grad u).v + nu grad u : grad v on a sheared right prism, for vector
     polynomials u, v of degree k (the prism space holds them exactly, the rule integrates the
