@@ -144,6 +144,10 @@ WORKLOADS["burgers-p2-prism"] = Workload("burgers-p2-prism", BURGERS_JAC, 2, PRI
                                          "unit cube, 24x24 two-triangle columns x 24 layers = 27,648 "
                                          "twisted prisms perturbed 0.15h (seed 6), vector P2 u~N(0,1) per "
                                          "conforming node, nu=0.01; FP64 only (--precision fp64)", _prism24)
+WORKLOADS["burgers-residual-p2-prism"] = Workload("burgers-residual-p2-prism", BURGERS_RESIDUAL, 2, PRISM,
+                                                  "unit cube, 24x24 two-triangle columns x 24 layers = 27,648 "
+                                                  "twisted prisms perturbed 0.15h (seed 6), vector P2 u~N(0,1) per "
+                                                  "conforming node, nu=0.01; element vectors; FP64 only", _prism24)
 WORKLOADS["helmholtz-p1-tri"] = Workload("helmholtz-p1-tri", HELMHOLTZ, 1, TRIANGLE,
                                          "unit square 64x64x2 triangles perturbed 0.2h (seed 1)", _tri64)
 # the same problem at a size where HBM, not the launch, sets the time (its roofline fraction)
